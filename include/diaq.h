@@ -1,0 +1,265 @@
+/*
+ * diaq.h - C ABI of libdiaq_gb300, a GB300 (sm_103a) implementation of the
+ * DiaQ gate-apply path of arXiv 2405.01250 ("DiaQ: Efficient State-Vector
+ * Quantum Simulation").
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * State vectors. An n-qubit state is N = 2^n complex amplitudes stored
+ * contiguously with interleaved (re, im) parts: complex64 (8 bytes per
+ * amplitude) or complex128 (16 bytes). Qubit q is bit q of the basis index
+ * (qubit 0 is the least significant bit). State buffers passed to the
+ * device entry points are DEVICE pointers, 16-byte aligned, owned by the
+ * caller; the library never frees them.
+ *
+ * Gates. A k-qubit gate on targets t[0..k-1] is a 2^k x 2^k complex matrix
+ * M in the local basis whose most significant bit is qubit t[0]; its
+ * full-system operator is the time-step unitary I_above (x) M (x) I_below of
+ * Section II-C, with the factors placed on the target bits.
+ *
+ * DiaQ. A matrix in DiaQ form (Section IV) is a map from diagonal index d to
+ * the N-|d| values of that diagonal, index d >= 0 holding A[t][t+d] and
+ * d < 0 holding A[t-d][t] for t = 0 .. N-|d|-1 (the orientation of
+ * Algorithm 2). Host-side value arrays are complex128, interleaved.
+ *
+ * Streams. diaq_stream_t is a cudaStream_t (NULL = the legacy default
+ * stream). Device work is enqueued on it; entry points that return a value
+ * to host memory synchronise that stream before returning.
+ *
+ * Errors. No entry point throws or aborts. Each returns a diaq_status; on
+ * failure diaq_last_error() gives a message for the calling thread. The
+ * paper's "not multiplyable" shape error (Algorithms 1 and 2) is
+ * DIAQ_ERR_SHAPE. Argument checks happen before any device work, so a
+ * rejected call leaves all buffers untouched.
+ *
+ * Ownership. diaq_op_t handles are created by diaq_build / diaq_build_diaq /
+ * diaq_fuse and released by diaq_op_destroy; an op owns its device memory
+ * (gate matrix, stored diagonals) on the device that was current when it was
+ * built, and must be used with that device current.
+ */
+#ifndef DIAQ_H
+#define DIAQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DIAQ_MAX_K 6        /* largest gate or fused operator, in qubits */
+#define DIAQ_MAX_QUBITS 34  /* largest state, in qubits */
+
+typedef enum {
+    DIAQ_OK = 0,
+    DIAQ_ERR_ARG = 1,         /* invalid argument (NULL, range, aliasing) */
+    DIAQ_ERR_SHAPE = 2,       /* operand shapes do not match ("not multiplyable") */
+    DIAQ_ERR_ALLOC = 3,       /* device or host allocation failed */
+    DIAQ_ERR_CUDA = 4,        /* a CUDA runtime call or launch failed */
+    DIAQ_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    DIAQ_ERR_BOUNDS = 6,      /* a device-side index check failed */
+    DIAQ_ERR_UNSUPPORTED = 7  /* valid request outside what this build handles */
+} diaq_status;
+
+typedef enum { DIAQ_C64 = 0, DIAQ_C128 = 1 } diaq_dtype;
+
+/* How an op multiplies: DIAQ_ONTHEFLY generates the full-system diagonals
+ * from the 2^k x 2^k gate while it streams the state (Algorithm 3,
+ * generalised to any target placement); DIAQ_STORED materialises them in
+ * device memory and runs the DiaQ SpMV of Algorithm 2 over them. */
+typedef enum { DIAQ_ONTHEFLY = 0, DIAQ_STORED = 1 } diaq_variant;
+
+typedef void* diaq_stream_t;
+typedef struct diaq_op_s* diaq_op_t;
+
+/* A gate. For a fixed gate, m points to the 2^k x 2^k row-major complex128
+ * matrix (host memory, read during the call only). A parametric gate sets
+ * param >= 0 and m = NULL; it is exp(-i a/2 P) = cos(a/2) I - i sin(a/2) P
+ * with a = scale * theta[param] and P the Pauli string gen (one letter from
+ * "IXYZ" per target, gen[0] acting on targets[0], NUL-terminated). */
+typedef struct {
+    int32_t k;
+    int32_t targets[DIAQ_MAX_K];
+    const double* m;
+    int32_t param;
+    double scale;
+    char gen[DIAQ_MAX_K + 2];
+} diaq_gate;
+
+/* Structural class of an op's local matrix, chosen by the builder. */
+typedef enum {
+    DIAQ_CLASS_GENERAL = 0,   /* dense or sparse complex */
+    DIAQ_CLASS_REAL = 1,      /* all entries real */
+    DIAQ_CLASS_DIAGONAL = 2,  /* only principal-diagonal entries (Section III-A) */
+    DIAQ_CLASS_PERMUTATION = 3, /* one entry 1 per row and column */
+    DIAQ_CLASS_MONOMIAL = 4,  /* one non-zero per row and column */
+    DIAQ_CLASS_RAW = 5        /* a DiaQ matrix with no gate structure */
+} diaq_class;
+
+typedef struct {
+    int32_t n_qubits;
+    int32_t dtype;           /* diaq_dtype */
+    int32_t variant;         /* diaq_variant */
+    int32_t op_class;        /* diaq_class */
+    int32_t k;               /* target count (0 for DIAQ_CLASS_RAW) */
+    int32_t targets[DIAQ_MAX_K];
+    int64_t n_diagonals;     /* full-system DiaQ diagonals of the op */
+    int64_t stored_bytes;    /* device bytes of materialised diagonals (0 if on-the-fly) */
+} diaq_op_info;
+
+/* ------------------------------------------------------------------------
+ * Library
+ * ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none). The string
+ * is owned by the library and valid until the next call on this thread. */
+const char* diaq_last_error(void);
+
+/* Version string, e.g. "diaq_gb300 0.1 (sm_103a)". */
+const char* diaq_version(void);
+
+/* ------------------------------------------------------------------------
+ * Builder (host part) - Section IV (DiaQ format), Section II-C (time-step
+ * unitary), Algorithm 3 (offset dIndex * dim_b of a gate diagonal).
+ * ------------------------------------------------------------------------ */
+
+/* Full-system diagonal indices of a gate on an n-qubit register, ascending:
+ * every index d = sum_a (c_a - r_a) 2^{t_a} over the (row r, column c) pairs
+ * of M with a non-zero entry (for a parametric gate, of I and P). Writes at
+ * most cap indices to offsets (host) and the total to *count; returns
+ * DIAQ_ERR_ARG if cap is too small (with *count set). No GPU needed. */
+diaq_status diaq_gate_offsets(const diaq_gate* g, int32_t n_qubits, int64_t* offsets,
+                              int64_t cap, int64_t* count);
+
+/* DiaQ matrix product C = A B on the host (Algorithm 1), complex128, for
+ * square matrices of order N. A and B are given as (count, indices,
+ * concatenated values in index order). Where several (a, b) pairs meet on
+ * one result index a+b their products are summed, and diagonals whose
+ * products have no overlap are dropped (the reading of "isValid"); exact
+ * zeros are kept. Two calls: with c_values == NULL it only reports
+ * *c_count and *c_values_len (elements); then call again with buffers of
+ * that size. No GPU needed. */
+diaq_status diaq_diaq_matmul_host(int64_t N,
+                                  int64_t a_count, const int64_t* a_idx, const double* a_values,
+                                  int64_t b_count, const int64_t* b_idx, const double* b_values,
+                                  int64_t* c_count, int64_t* c_idx, int64_t* c_values_len,
+                                  double* c_values);
+
+/* Gate fusion on the host (Section VI: spGEMM fuses consecutive gates):
+ * embeds each gate in the union of their targets (union order = first
+ * appearance, union[0] most significant) as a DiaQ matrix, multiplies them
+ * with the accumulating product of diaq_diaq_matmul_host, and returns the
+ * union targets and the dense 2^K x 2^K fused matrix (K <= DIAQ_MAX_K)
+ * = M_{count-1} ... M_0. theta is read for parametric gates (may be NULL if
+ * there are none). fused_m must hold 2 * 4^K doubles. No GPU needed. */
+diaq_status diaq_fuse_gates_host(const diaq_gate* gates, int32_t count, const double* theta,
+                                 int32_t* union_k, int32_t* union_targets, double* fused_m);
+
+/* ------------------------------------------------------------------------
+ * Ops
+ * ------------------------------------------------------------------------ */
+
+/* Build an op for gate g on an n-qubit register (1 <= n <= DIAQ_MAX_QUBITS,
+ * 1 <= k <= min(n, DIAQ_MAX_K), distinct targets in [0, n)). theta is read
+ * if g is parametric. DIAQ_STORED allocates sum_d (N - |d|) amplitudes of
+ * device memory and fills them with a kernel on `stream`. */
+diaq_status diaq_build(const diaq_gate* g, int32_t n_qubits, diaq_dtype dtype,
+                       diaq_variant variant, const double* theta, diaq_stream_t stream,
+                       diaq_op_t* out);
+
+/* Build a stored op from a DiaQ matrix given on the host (Section IV):
+ * count distinct indices |d| < 2^n, values concatenated in index order
+ * (complex128; converted to dtype). */
+diaq_status diaq_build_diaq(int32_t n_qubits, int64_t count, const int64_t* indices,
+                            const double* values, diaq_dtype dtype, diaq_stream_t stream,
+                            diaq_op_t* out);
+
+/* Release an op and its device memory (NULL is accepted). Synchronises the
+ * op's device before freeing. */
+diaq_status diaq_op_destroy(diaq_op_t op);
+
+diaq_status diaq_op_query(diaq_op_t op, diaq_op_info* info);
+
+/* Full-system diagonal indices of the op, as diaq_gate_offsets. */
+diaq_status diaq_op_offsets(diaq_op_t op, int64_t* offsets, int64_t cap, int64_t* count);
+
+/* Copy stored diagonal number `which` (in index order) to host memory as
+ * N-|d| amplitudes of the op's dtype; DIAQ_ERR_ARG for on-the-fly ops. */
+diaq_status diaq_op_read_diagonal(diaq_op_t op, int64_t which, void* host_out, diaq_stream_t stream);
+
+/* Fuse ops into one: out = ops[count-1] ... ops[0]. Gate-structured ops
+ * are fused on the host in their union target space (diaq_fuse_gates_host;
+ * the union must have at most DIAQ_MAX_K qubits, else DIAQ_ERR_UNSUPPORTED);
+ * if any op is DIAQ_CLASS_RAW, the full-system DiaQ product of Algorithm 1
+ * runs on the device instead and the result is stored. All ops must share
+ * n_qubits and dtype (DIAQ_ERR_SHAPE otherwise). `variant` selects the
+ * result's variant for gate-structured fusion. */
+diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
+                      diaq_stream_t stream, diaq_op_t* out);
+
+/* ------------------------------------------------------------------------
+ * Gate apply - the DiaQ SpMV (Algorithm 2 for stored ops; Algorithm 3,
+ * generalised, for on-the-fly ops): y[i] = sum_d A_d(i) x[i + d].
+ * ------------------------------------------------------------------------ */
+
+/* y = A x on `stream`. x, y: device state vectors of the op's n_qubits and
+ * dtype. y == x (in place) is allowed for on-the-fly ops only; otherwise x
+ * and y must not overlap (DIAQ_ERR_ARG). */
+diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t stream);
+
+/* Run ops[0..count-1] in order on a state: psi_in -> psi_out. psi_in and
+ * psi_out may each be host (pageable or pinned) or device pointers; host
+ * data are copied in and out on `stream` inside the call. work0 and work1
+ * are caller-owned device state buffers (work1 may be NULL when every op is
+ * on-the-fly). Synchronises `stream` before returning. */
+diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
+                          void* work0, void* work1, diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Reductions (FP64 accumulation for both dtypes; deterministic for a given
+ * n_qubits and dtype). The paper reads out expectation values and
+ * magnetisations (Section II-B); these compute them on the device.
+ * ------------------------------------------------------------------------ */
+
+/* ||psi||^2 into *out (host). */
+diaq_status diaq_norm(const void* psi, int32_t n_qubits, diaq_dtype dtype, double* out,
+                      diaq_stream_t stream);
+
+/* <psi| sum_t c_t P_t |psi> into out[0] (re), out[1] (im) (host). Term t is
+ * the Pauli string with X on the bits of xmask[t] only, Z on zmask[t] only
+ * and Y on both; coeff holds n_terms complex128 coefficients. n_terms may be
+ * 0 (result 0). Host arrays. */
+diaq_status diaq_expect(const void* psi, int32_t n_qubits, diaq_dtype dtype, int32_t n_terms,
+                        const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                        double* out, diaq_stream_t stream);
+
+/* lambda = (sum_t c_t P_t) psi on the device; lambda must not overlap psi. */
+diaq_status diaq_apply_pauli_sum(const void* psi, void* lambda, int32_t n_qubits,
+                                 diaq_dtype dtype, int32_t n_terms, const uint64_t* xmask,
+                                 const uint64_t* zmask, const double* coeff,
+                                 diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint gradient (not in the paper; the adjoint-state method for
+ * E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U_L ... U_1 psi0).
+ * ------------------------------------------------------------------------ */
+
+/* Energy and full gradient in one forward and one reverse sweep. For a
+ * parametric gate U = exp(-i a/2 P), a = scale * theta_p, the contribution
+ * to dE/dtheta_p is scale * Im <lambda_l| P |psi_l>, with psi_l the state
+ * after the gate and lambda_l = U_{l+1}^dag ... U_L^dag H psi_L.
+ * psi0: device initial state (read only). work_psi, work_lam: caller-owned
+ * device state buffers (overwritten). energy (host, may be NULL) and grad
+ * (host, n_params doubles, may be NULL). The observable is as in
+ * diaq_expect with real parts of coeff used (Hermitian H). */
+diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const double* theta,
+                              int32_t n_params, int32_t n_terms, const uint64_t* xmask,
+                              const uint64_t* zmask, const double* coeff, const void* psi0,
+                              void* work_psi, void* work_lam, int32_t n_qubits, diaq_dtype dtype,
+                              double* energy, double* grad, diaq_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIAQ_H */

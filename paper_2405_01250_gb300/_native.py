@@ -1,0 +1,119 @@
+"""ctypes declarations of the C ABI in include/diaq.h (libdiaq_gb300.so).
+
+The library is loaded from this package's _build/ directory. There is no
+fallback: if it is missing, every entry point raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdiaq_gb300.so")
+
+DIAQ_MAX_K = 6
+DIAQ_MAX_QUBITS = 34
+
+STATUS = {
+    0: "DIAQ_OK", 1: "DIAQ_ERR_ARG", 2: "DIAQ_ERR_SHAPE", 3: "DIAQ_ERR_ALLOC", 4: "DIAQ_ERR_CUDA",
+    5: "DIAQ_ERR_TIMEOUT", 6: "DIAQ_ERR_BOUNDS", 7: "DIAQ_ERR_UNSUPPORTED",
+}
+C64, C128 = 0, 1
+ONTHEFLY, STORED = 0, 1
+CLASSES = {0: "general", 1: "real", 2: "diagonal", 3: "permutation", 4: "monomial", 5: "raw"}
+
+
+class DiaqError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class diaq_gate(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32),
+        ("targets", ctypes.c_int32 * DIAQ_MAX_K),
+        ("m", ctypes.POINTER(ctypes.c_double)),
+        ("param", ctypes.c_int32),
+        ("scale", ctypes.c_double),
+        ("gen", ctypes.c_char * (DIAQ_MAX_K + 2)),
+    ]
+
+
+class diaq_op_info(ctypes.Structure):
+    _fields_ = [
+        ("n_qubits", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("variant", ctypes.c_int32),
+        ("op_class", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("targets", ctypes.c_int32 * DIAQ_MAX_K),
+        ("n_diagonals", ctypes.c_int64),
+        ("stored_bytes", ctypes.c_int64),
+    ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_vp = ctypes.c_void_p
+_op = ctypes.c_void_p
+_gp = ctypes.POINTER(diaq_gate)
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "diaq_last_error": (ctypes.c_char_p, []),
+    "diaq_version": (ctypes.c_char_p, []),
+    "diaq_gate_offsets": (ctypes.c_int, [_gp, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p]),
+    "diaq_diaq_matmul_host": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _i64p, _dp, ctypes.c_int64, _i64p, _dp,
+                                             _i64p, _i64p, _i64p, _dp]),
+    "diaq_fuse_gates_host": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, _i32p, _i32p, _dp]),
+    "diaq_build": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int, ctypes.c_int, _dp, _vp,
+                                  ctypes.POINTER(_op)]),
+    "diaq_build_diaq": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _i64p, _dp, ctypes.c_int, _vp,
+                                       ctypes.POINTER(_op)]),
+    "diaq_op_destroy": (ctypes.c_int, [_op]),
+    "diaq_op_query": (ctypes.c_int, [_op, ctypes.POINTER(diaq_op_info)]),
+    "diaq_op_offsets": (ctypes.c_int, [_op, _i64p, ctypes.c_int64, _i64p]),
+    "diaq_op_read_diagonal": (ctypes.c_int, [_op, ctypes.c_int64, _vp, _vp]),
+    "diaq_fuse": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, ctypes.c_int, _vp, ctypes.POINTER(_op)]),
+    "diaq_apply": (ctypes.c_int, [_op, _vp, _vp, _vp]),
+    "diaq_simulate": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "diaq_norm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
+    "diaq_expect": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _u64p, _u64p, _dp, _dp, _vp]),
+    "diaq_apply_pauli_sum": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _u64p, _u64p,
+                                            _dp, _vp]),
+    "diaq_adjoint_grad": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int32, _u64p, _u64p,
+                                         _dp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int, _dp, _dp, _vp]),
+}
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdiaq_gb300.so (after torch, so both share one CUDA runtime)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libdiaq_gb300.so is not built ({LIB_PATH} missing); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        try:
+            import torch  # noqa: F401  (loads libcudart first)
+        except ImportError:
+            pass
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def check(status: int) -> None:
+    if status != 0:
+        msg = lib().diaq_last_error().decode(errors="replace")
+        raise DiaqError(status, msg)

@@ -1,0 +1,340 @@
+"""Thin Python binding over libdiaq_gb300 (include/diaq.h).
+
+Argument marshalling only: tensors are passed by device pointer with the
+current CUDA stream; every step of the gate-apply path runs in the CUDA
+library. PyTorch supplies device memory and streams.
+
+Gates are any objects with ``targets``, ``matrix`` (2^k x 2^k complex, or
+None for a parametric gate), ``param`` (-1 for fixed), ``gen`` (Pauli letters)
+and ``scale`` attributes.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import DiaqError, check, lib  # noqa: F401
+
+__all__ = [
+    "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
+    "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
+    "DiaqError", "DiaqEnergy",
+]
+
+
+def version() -> str:
+    return lib().diaq_version().decode()
+
+
+def _dtype_code(dtype) -> int:
+    if dtype in (torch.complex128, np.complex128, "c128", "complex128"):
+        return N.C128
+    if dtype in (torch.complex64, np.complex64, "c64", "complex64"):
+        return N.C64
+    raise ValueError(f"unsupported dtype {dtype}")
+
+
+def _torch_dtype(code: int):
+    return torch.complex128 if code == N.C128 else torch.complex64
+
+
+def _variant_code(v) -> int:
+    if v in ("onthefly", "on_the_fly", N.ONTHEFLY):
+        return N.ONTHEFLY
+    if v in ("stored", N.STORED):
+        return N.STORED
+    raise ValueError(f"unknown variant {v}")
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def gate_struct(g, keep: list) -> N.diaq_gate:
+    """diaq_gate for a gate object; arrays it points to are appended to keep."""
+    s = N.diaq_gate()
+    t = tuple(int(q) for q in g.targets)
+    s.k = len(t)
+    if s.k > N.DIAQ_MAX_K:
+        raise ValueError(f"gate on {s.k} qubits exceeds {N.DIAQ_MAX_K}")
+    for a, q in enumerate(t):
+        s.targets[a] = q
+    param = int(getattr(g, "param", -1))
+    s.param = param
+    s.scale = float(getattr(g, "scale", 1.0))
+    if param >= 0:
+        gen = str(getattr(g, "gen", "")).encode()
+        s.gen = gen
+        s.m = None
+    else:
+        m = np.ascontiguousarray(np.asarray(g.matrix, dtype=np.complex128))
+        keep.append(m)
+        s.m = _dptr(m.view(np.float64))
+    return s
+
+
+def _gate_array(gates) -> tuple:
+    keep: list = []
+    arr = (N.diaq_gate * max(1, len(gates)))()
+    for i, g in enumerate(gates):
+        arr[i] = gate_struct(g, keep)
+    return arr, keep
+
+
+class Op:
+    """Owner of a diaq_op_t (destroyed with the object)."""
+
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().diaq_op_destroy(h)
+            except Exception:
+                pass
+            self.handle = ctypes.c_void_p(0)
+
+    def close(self):
+        self.__del__()
+
+    def info(self) -> dict:
+        inf = N.diaq_op_info()
+        check(lib().diaq_op_query(self.handle, ctypes.byref(inf)))
+        return {
+            "n_qubits": inf.n_qubits, "dtype": _torch_dtype(inf.dtype),
+            "variant": "stored" if inf.variant == N.STORED else "onthefly",
+            "class": N.CLASSES[inf.op_class], "k": inf.k,
+            "targets": tuple(inf.targets[a] for a in range(inf.k)),
+            "n_diagonals": inf.n_diagonals, "stored_bytes": inf.stored_bytes,
+        }
+
+    def offsets(self) -> np.ndarray:
+        cnt = ctypes.c_int64(0)
+        st = lib().diaq_op_offsets(self.handle, None, 0, ctypes.byref(cnt))
+        out = np.zeros(cnt.value, dtype=np.int64)
+        check(lib().diaq_op_offsets(self.handle, out.ctypes.data_as(N._i64p), cnt.value, ctypes.byref(cnt)))
+        del st
+        return out
+
+    def diagonal(self, which: int, stream=None) -> np.ndarray:
+        inf = self.info()
+        offs = self.offsets()
+        L = (1 << inf["n_qubits"]) - abs(int(offs[which]))
+        dt = np.complex128 if inf["dtype"] == torch.complex128 else np.complex64
+        out = np.zeros(L, dtype=dt)
+        check(lib().diaq_op_read_diagonal(self.handle, int(which), out.ctypes.data_as(ctypes.c_void_p),
+                                          _stream(stream)))
+        return out
+
+
+def build(gate, n_qubits: int, dtype=torch.complex128, variant="onthefly", theta=None, stream=None) -> Op:
+    keep: list = []
+    s = gate_struct(gate, keep)
+    th = None
+    if theta is not None:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        keep.append(th)
+    h = ctypes.c_void_p(0)
+    check(lib().diaq_build(ctypes.byref(s), int(n_qubits), _dtype_code(dtype), _variant_code(variant),
+                           _dptr(th) if th is not None else None, _stream(stream), ctypes.byref(h)))
+    return Op(h.value)
+
+
+def build_diaq(n_qubits: int, indices, values, dtype=torch.complex128, stream=None) -> Op:
+    idx = np.ascontiguousarray(np.asarray(indices, dtype=np.int64))
+    vals = [np.asarray(v, dtype=np.complex128) for v in values]
+    flat = np.ascontiguousarray(np.concatenate(vals)) if vals else np.zeros(1, np.complex128)
+    h = ctypes.c_void_p(0)
+    check(lib().diaq_build_diaq(int(n_qubits), len(idx), idx.ctypes.data_as(N._i64p), _dptr(flat.view(np.float64)),
+                                _dtype_code(dtype), _stream(stream), ctypes.byref(h)))
+    return Op(h.value)
+
+
+def fuse(ops, variant="onthefly", stream=None) -> Op:
+    arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
+    h = ctypes.c_void_p(0)
+    check(lib().diaq_fuse(arr, len(ops), _variant_code(variant), _stream(stream), ctypes.byref(h)))
+    return Op(h.value)
+
+
+def _check_state(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if t.dtype not in (torch.complex64, torch.complex128):
+        raise ValueError(f"{name} must be complex64 or complex128")
+
+
+def _nq(t: torch.Tensor) -> int:
+    n = int(t.numel()).bit_length() - 1
+    if (1 << n) != t.numel():
+        raise ValueError("state length must be a power of two")
+    return n
+
+
+def apply(op: Op, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = A x (y may be x for on-the-fly ops)."""
+    _check_state(x, "x")
+    _check_state(y, "y")
+    check(lib().diaq_apply(op.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), _stream(stream)))
+    return y
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if isinstance(t, torch.Tensor):
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def simulate(ops, psi_in, psi_out, work0: torch.Tensor, work1: torch.Tensor | None = None, stream=None):
+    """Run ops in order; psi_in / psi_out may be host (numpy / CPU tensor) or device."""
+    arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
+    check(lib().diaq_simulate(arr, len(ops), _ptr(psi_in), _ptr(psi_out), _ptr(work0),
+                              _ptr(work1) if work1 is not None else None, _stream(stream)))
+    return psi_out
+
+
+def norm(psi: torch.Tensor, stream=None) -> float:
+    _check_state(psi, "psi")
+    out = ctypes.c_double(0)
+    check(lib().diaq_norm(ctypes.c_void_p(psi.data_ptr()), _nq(psi), _dtype_code(psi.dtype), ctypes.byref(out),
+                          _stream(stream)))
+    return out.value
+
+
+def _terms(xmask, zmask, coeff):
+    xm = np.ascontiguousarray(np.asarray(xmask, dtype=np.uint64))
+    zm = np.ascontiguousarray(np.asarray(zmask, dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(coeff).astype(np.complex128))
+    if not (len(xm) == len(zm) == len(c)):
+        raise ValueError("xmask, zmask and coeff must have one entry per term")
+    return xm, zm, c
+
+
+def expect(psi: torch.Tensor, xmask, zmask, coeff, stream=None) -> complex:
+    _check_state(psi, "psi")
+    xm, zm, c = _terms(xmask, zmask, coeff)
+    out = (ctypes.c_double * 2)()
+    check(lib().diaq_expect(ctypes.c_void_p(psi.data_ptr()), _nq(psi), _dtype_code(psi.dtype), len(xm),
+                            xm.ctypes.data_as(N._u64p), zm.ctypes.data_as(N._u64p),
+                            _dptr(c.view(np.float64)) if len(c) else None, out, _stream(stream)))
+    return complex(out[0], out[1])
+
+
+def apply_pauli_sum(psi: torch.Tensor, lam: torch.Tensor, xmask, zmask, coeff, stream=None) -> torch.Tensor:
+    _check_state(psi, "psi")
+    _check_state(lam, "lam")
+    xm, zm, c = _terms(xmask, zmask, coeff)
+    check(lib().diaq_apply_pauli_sum(ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(lam.data_ptr()), _nq(psi),
+                                     _dtype_code(psi.dtype), len(xm), xm.ctypes.data_as(N._u64p),
+                                     zm.ctypes.data_as(N._u64p), _dptr(c.view(np.float64)) if len(c) else None,
+                                     _stream(stream)))
+    return lam
+
+
+def adjoint_grad(gates, theta, xmask, zmask, coeff, psi0: torch.Tensor, work_psi: torch.Tensor,
+                 work_lam: torch.Tensor, stream=None) -> tuple:
+    """(energy, gradient) of <psi(theta)|H|psi(theta)> by one adjoint sweep."""
+    for t, nm in ((psi0, "psi0"), (work_psi, "work_psi"), (work_lam, "work_lam")):
+        _check_state(t, nm)
+    arr, keep = _gate_array(gates)
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    xm, zm, c = _terms(xmask, zmask, coeff)
+    grad = np.zeros(len(th), dtype=np.float64)
+    e = ctypes.c_double(0)
+    check(lib().diaq_adjoint_grad(arr, len(gates), _dptr(th) if len(th) else None, len(th), len(xm),
+                                  xm.ctypes.data_as(N._u64p), zm.ctypes.data_as(N._u64p),
+                                  _dptr(c.view(np.float64)) if len(c) else None,
+                                  ctypes.c_void_p(psi0.data_ptr()), ctypes.c_void_p(work_psi.data_ptr()),
+                                  ctypes.c_void_p(work_lam.data_ptr()), _nq(psi0), _dtype_code(psi0.dtype),
+                                  ctypes.byref(e), _dptr(grad) if len(grad) else None, _stream(stream)))
+    del keep
+    return e.value, grad
+
+
+def gate_offsets(gate, n_qubits: int) -> np.ndarray:
+    keep: list = []
+    s = gate_struct(gate, keep)
+    cnt = ctypes.c_int64(0)
+    lib().diaq_gate_offsets(ctypes.byref(s), int(n_qubits), None, 0, ctypes.byref(cnt))
+    out = np.zeros(max(cnt.value, 1), dtype=np.int64)
+    check(lib().diaq_gate_offsets(ctypes.byref(s), int(n_qubits), out.ctypes.data_as(N._i64p), len(out),
+                                  ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def diaq_matmul_host(Nord: int, a_idx, a_vals, b_idx, b_vals) -> tuple:
+    """Host DiaQ product C = A B (Algorithm 1). Values are lists of arrays."""
+    def pack(idx, vals):
+        i = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        v = np.ascontiguousarray(np.concatenate([np.asarray(x, np.complex128) for x in vals])) if len(vals) \
+            else np.zeros(1, np.complex128)
+        return i, v
+    ai, av = pack(a_idx, a_vals)
+    bi, bv = pack(b_idx, b_vals)
+    cc = ctypes.c_int64(0)
+    cl = ctypes.c_int64(0)
+    L = lib()
+    check(L.diaq_diaq_matmul_host(Nord, len(ai), ai.ctypes.data_as(N._i64p), _dptr(av.view(np.float64)),
+                                  len(bi), bi.ctypes.data_as(N._i64p), _dptr(bv.view(np.float64)),
+                                  ctypes.byref(cc), None, ctypes.byref(cl), None))
+    ci = np.zeros(max(cc.value, 1), np.int64)
+    cv = np.zeros(max(cl.value, 1), np.complex128)
+    check(L.diaq_diaq_matmul_host(Nord, len(ai), ai.ctypes.data_as(N._i64p), _dptr(av.view(np.float64)),
+                                  len(bi), bi.ctypes.data_as(N._i64p), _dptr(bv.view(np.float64)),
+                                  ctypes.byref(cc), ci.ctypes.data_as(N._i64p), ctypes.byref(cl),
+                                  _dptr(cv.view(np.float64))))
+    out, pos = [], 0
+    for d in ci[:cc.value]:
+        n = Nord - abs(int(d))
+        out.append(cv[pos:pos + n].copy())
+        pos += n
+    return ci[:cc.value], out
+
+
+def fuse_gates_host(gates, theta=None) -> tuple:
+    """(union targets, fused 2^K x 2^K matrix) of gates[-1] ... gates[0]."""
+    arr, keep = _gate_array(gates)
+    th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    uk = ctypes.c_int32(0)
+    ut = (ctypes.c_int32 * N.DIAQ_MAX_K)()
+    fm = np.zeros(2 * (1 << (2 * N.DIAQ_MAX_K)), dtype=np.float64)
+    check(lib().diaq_fuse_gates_host(arr, len(gates), _dptr(th) if th is not None else None, ctypes.byref(uk), ut,
+                                     _dptr(fm)))
+    K = uk.value
+    m = fm[: 2 * (1 << (2 * K))].view(np.complex128).reshape(1 << K, 1 << K).copy()
+    del keep
+    return tuple(ut[a] for a in range(K)), m
+
+
+class DiaqEnergy(torch.autograd.Function):
+    """E(theta) = <psi(theta)|H|psi(theta)> with the gradient from the
+    adjoint sweep (diaq_adjoint_grad). Call as
+    DiaqEnergy.apply(theta, gates, (xmask, zmask, coeff), psi0)."""
+
+    @staticmethod
+    def forward(ctx, theta, gates, observable, psi0):
+        xm, zm, c = observable
+        work_psi = torch.empty_like(psi0)
+        work_lam = torch.empty_like(psi0)
+        e, g = adjoint_grad(gates, theta.detach().cpu().numpy(), xm, zm, c, psi0, work_psi, work_lam)
+        ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
+        return theta.new_tensor(e)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return grad_out * g, None, None, None

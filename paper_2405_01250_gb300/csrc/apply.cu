@@ -1,0 +1,608 @@
+// Gate-apply kernels of libdiaq_gb300: the DiaQ SpMV y[i] = sum_d A_d(i) x[i+d]
+// of arXiv 2405.01250, in its two variants.
+//
+//  * On the fly (Algorithm 3, generalised to any target placement): the
+//    full-system diagonals of I_above (x) M (x) I_below are never formed.
+//    Row i of the operator has its non-zeros at columns i + d(r, c), where
+//    r is i's local index on the targets, c runs over the 2^k local columns
+//    and d(r, c) = sum_a (c_a - r_a) 2^{t_a} is the diagonal M[r][c] lies
+//    on. The 2^k rows that share their non-target bits (a "group") read the
+//    same 2^k amplitudes, so each thread loads a group once into registers
+//    and produces all of its rows: every amplitude is read once and written
+//    once, with 16-byte coalesced accesses across the warp.
+//  * Stored (Algorithm 2): the diagonals live in device memory, one array of
+//    N - |d| values per index d; each output row sums over the diagonals,
+//    reading A_d(i) and, where it is non-zero, x[i + d]. Rows are visited
+//    in an order that keeps whole groups inside one block when the op has
+//    gate structure, so the shifted reads of x hit cache.
+//
+// Both write y exactly once per row (no atomics) and sum the terms of a row
+// in a fixed order.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace diaq {
+
+// ---------------------------------------------------------------------------
+// On-the-fly apply, k <= 3: matrix, entry types and offsets in kernel params.
+// ---------------------------------------------------------------------------
+template <typename R, int K>
+struct SmallGateArgs {
+    int64_t n_groups;
+    int st[K];                   // targets, ascending
+    int64_t off[1 << K];         // full-system offset of local index c
+    R re[1 << (2 * K)];
+    R im[1 << (2 * K)];
+    uint8_t type[1 << (2 * K)];
+};
+
+template <typename R, int K, int G>
+__global__ void __launch_bounds__(256)
+k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateArgs<R, K> a) {
+    constexpr int D = 1 << K;
+    using A = amp_t<R>;
+    const int64_t T = blockDim.x;
+    const int64_t g0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
+    A v[G][D];
+    int64_t b[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        const int64_t g = g0 + j * T;
+        b[j] = g < a.n_groups ? insert_zeros<K>(g, a.st) : int64_t(-1);
+        if (b[j] >= 0) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[j][c] = ld_stream(x + b[j] + a.off[c]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        if (b[j] < 0) continue;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            A acc;
+            acc.x = R(0);
+            acc.y = R(0);
+            bool first = true;
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                mac_typed<R>(acc, first, a.type[r * D + c], a.re[r * D + c], a.im[r * D + c], v[j][c]);
+            st_stream(y + b[j] + a.off[r], acc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// On-the-fly apply, 4 <= k <= 6: the local matrix is staged in shared memory
+// from the op's device copy; each block processes chunks of B groups whose
+// 2^k * B amplitudes it loads into shared memory (group index fastest, so
+// the loads coalesce), then writes the rows back.
+// ---------------------------------------------------------------------------
+struct LargeGateArgs {
+    int64_t n_groups;
+    int k;
+    int st[DIAQ_MAX_K];
+    int64_t off[1 << DIAQ_MAX_K];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_apply_large(const amp_t<R>* x, amp_t<R>* y, const void* dmat, const __grid_constant__ LargeGateArgs a,
+              int B) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int k = a.k;
+    const int D = 1 << k;
+    const int DD = D * D;
+    R* mre = reinterpret_cast<R*>(smem);
+    R* mim = mre + DD;
+    uint8_t* mty = reinterpret_cast<uint8_t*>(mim + DD);
+    A* xs = reinterpret_cast<A*>(smem + ((2 * DD * sizeof(R) + DD + 15) / 16) * 16);
+    // dmat layout: re[DD], im[DD] (R), type[DD] (uint8)
+    const R* gre = reinterpret_cast<const R*>(dmat);
+    const R* gim = gre + DD;
+    const uint8_t* gty = reinterpret_cast<const uint8_t*>(gim + DD);
+    for (int e = threadIdx.x; e < DD; e += blockDim.x) {
+        mre[e] = gre[e];
+        mim[e] = gim[e];
+        mty[e] = gty[e];
+    }
+    __syncthreads();
+    const int64_t n_chunks = (a.n_groups + B - 1) / B;
+    const int per = B * D;
+    for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        for (int e = threadIdx.x; e < per; e += blockDim.x) {
+            const int gi = e % B, c = e / B;
+            const int64_t g = ch * B + gi;
+            if (g < a.n_groups) xs[c * B + gi] = ld_stream(x + insert_zeros_rt(g, a.st, k) + a.off[c]);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < per; e += blockDim.x) {
+            const int gi = e % B, r = e / B;
+            const int64_t g = ch * B + gi;
+            if (g >= a.n_groups) continue;
+            A acc;
+            acc.x = R(0);
+            acc.y = R(0);
+            bool first = true;
+            for (int c = 0; c < D; ++c)
+                mac_typed<R>(acc, first, mty[r * D + c], mre[r * D + c], mim[r * D + c], xs[c * B + gi]);
+            st_stream(y + insert_zeros_rt(g, a.st, k) + a.off[r], acc);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launch helpers
+// ---------------------------------------------------------------------------
+static void sorted_targets(const GateDesc& g, int* st) {
+    for (int a = 0; a < g.k; ++a) st[a] = g.targets[a];
+    std::sort(st, st + g.k);
+}
+
+static void local_offsets(const GateDesc& g, int64_t* off) {
+    const int D = 1 << g.k;
+    for (int c = 0; c < D; ++c) {
+        int64_t o = 0;
+        for (int a = 0; a < g.k; ++a)
+            if ((c >> (g.k - 1 - a)) & 1) o += int64_t(1) << g.targets[a];
+        off[c] = o;
+    }
+}
+
+static int default_groups(diaq_dtype dt, int k) {
+    // enough independent 16-byte loads in flight per thread
+    if (k == 1) return dt == DIAQ_C128 ? 2 : 4;
+    if (k == 2) return dt == DIAQ_C128 ? 1 : 2;
+    return 1;
+}
+
+LaunchCfg& launch_cfg(diaq_dtype dt, int k) {
+    static LaunchCfg table[2][DIAQ_MAX_K + 1];
+    return table[dt == DIAQ_C128 ? 1 : 0][k < 0 ? 0 : (k > DIAQ_MAX_K ? DIAQ_MAX_K : k)];
+}
+
+template <typename R, int K, int G>
+static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void* y, int threads,
+                                  cudaStream_t s) {
+    SmallGateArgs<R, K> a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_groups = int64_t(1) << (n - K);
+    sorted_targets(g, a.st);
+    local_offsets(g, a.off);
+    constexpr int DD = 1 << (2 * K);
+    for (int e = 0; e < DD; ++e) {
+        a.re[e] = R(g.m[e].real());
+        a.im[e] = R(g.m[e].imag());
+        // classify after rounding to R so a c64 entry that rounds to 1 is exact
+        a.type[e] = entry_type(cplx(double(a.re[e]), double(a.im[e])));
+    }
+    const int64_t per_block = int64_t(threads) * G;
+    const int64_t blocks = (a.n_groups + per_block - 1) / per_block;
+    DIAQ_PRELAUNCH("k_apply_small");
+    k_apply_small<R, K, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
+        reinterpret_cast<const amp_t<R>*>(x), reinterpret_cast<amp_t<R>*>(y), a);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
+
+template <typename R, int K>
+static diaq_status launch_small(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y,
+                                cudaStream_t s) {
+    const LaunchCfg& cfg = launch_cfg(dt, K);
+    const int G = cfg.groups > 0 ? cfg.groups : default_groups(dt, K);
+    const int threads = cfg.threads;
+    switch (G) {
+        case 1: return launch_small_G<R, K, 1>(n, g, x, y, threads, s);
+        case 2: return launch_small_G<R, K, 2>(n, g, x, y, threads, s);
+        default: return launch_small_G<R, K, 4>(n, g, x, y, threads, s);
+    }
+}
+
+static size_t large_smem_bytes(diaq_dtype dt, int k, int B) {
+    const size_t DD = size_t(1) << (2 * k);
+    const size_t rs = dt == DIAQ_C128 ? 8 : 4;
+    const size_t head = ((2 * DD * rs + DD + 15) / 16) * 16;
+    return head + size_t(B) * (size_t(1) << k) * amp_bytes(dt);
+}
+
+template <typename R>
+static diaq_status launch_large(int n, diaq_dtype dt, const GateDesc& g, const void* dmat,
+                                const void* x, void* y, cudaStream_t s) {
+    LargeGateArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.k = g.k;
+    a.n_groups = int64_t(1) << (n - g.k);
+    sorted_targets(g, a.st);
+    local_offsets(g, a.off);
+    const int B = 32;
+    const size_t smem = large_smem_bytes(dt, g.k, B);
+    DIAQ_CUDA(cudaFuncSetAttribute(k_apply_large<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t n_chunks = (a.n_groups + B - 1) / B;
+    const int64_t blocks = std::min<int64_t>(n_chunks, int64_t(sms) * 8);
+    DIAQ_PRELAUNCH("k_apply_large");
+    k_apply_large<R><<<dim3((unsigned)blocks), 256, smem, s>>>(
+        reinterpret_cast<const amp_t<R>*>(x), reinterpret_cast<amp_t<R>*>(y), dmat, a, B);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
+
+// Device copy of a local matrix for the k >= 4 kernel: re[DD], im[DD], type[DD].
+diaq_status upload_matrix(diaq_op_s* op) {
+    const int k = op->gate.k;
+    const size_t DD = size_t(1) << (2 * k);
+    const size_t rs = op->dtype == DIAQ_C128 ? 8 : 4;
+    std::vector<unsigned char> buf(2 * DD * rs + DD);
+    for (size_t e = 0; e < DD; ++e) {
+        const cplx v = op->gate.m[e];
+        uint8_t t;
+        if (rs == 8) {
+            reinterpret_cast<double*>(buf.data())[e] = v.real();
+            reinterpret_cast<double*>(buf.data())[DD + e] = v.imag();
+            t = entry_type(v);
+        } else {
+            const float fr = float(v.real()), fi = float(v.imag());
+            reinterpret_cast<float*>(buf.data())[e] = fr;
+            reinterpret_cast<float*>(buf.data())[DD + e] = fi;
+            t = entry_type(cplx(fr, fi));
+        }
+        buf[2 * DD * rs + e] = t;
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, buf.size());
+    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMalloc of %zu bytes for the gate matrix failed: %s",
+                                      buf.size(), cudaGetErrorString(e));
+    e = cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(gate matrix)");
+    }
+    op->d_matrix = d;
+    return DIAQ_OK;
+}
+
+diaq_status launch_gate_local(int n, diaq_dtype dt, const GateDesc& g, const void* d_matrix,
+                              const void* x, void* y, cudaStream_t s) {
+    if (g.k <= 3) {
+        if (dt == DIAQ_C128) {
+            switch (g.k) {
+                case 1: return launch_small<double, 1>(n, dt, g, x, y, s);
+                case 2: return launch_small<double, 2>(n, dt, g, x, y, s);
+                default: return launch_small<double, 3>(n, dt, g, x, y, s);
+            }
+        }
+        switch (g.k) {
+            case 1: return launch_small<float, 1>(n, dt, g, x, y, s);
+            case 2: return launch_small<float, 2>(n, dt, g, x, y, s);
+            default: return launch_small<float, 3>(n, dt, g, x, y, s);
+        }
+    }
+    if (!d_matrix) return fail(DIAQ_ERR_ARG, "k = %d op has no device matrix", g.k);
+    return dt == DIAQ_C128 ? launch_large<double>(n, dt, g, d_matrix, x, y, s)
+                           : launch_large<float>(n, dt, g, d_matrix, x, y, s);
+}
+
+diaq_status launch_onthefly(const diaq_op_s* op, const void* x, void* y, cudaStream_t s) {
+    return launch_gate_local(op->n, op->dtype, op->gate, op->d_matrix, x, y, s);
+}
+
+// ---------------------------------------------------------------------------
+// Stored variant: materialise the diagonals, then the DiaQ SpMV.
+// ---------------------------------------------------------------------------
+struct RowMap {
+    // Row order that keeps whole groups inside a block: linear row j ->
+    // group g = (j_high << L) | j_low, local index c = (j >> L) & (2^k - 1),
+    // row = insert_zeros(g) + off[c]. k = 0 means identity.
+    int k;
+    int L;
+    int st[DIAQ_MAX_K];
+    int64_t off[1 << DIAQ_MAX_K];
+};
+
+__device__ __forceinline__ int64_t map_row(int64_t j, const RowMap& m) {
+    if (m.k == 0) return j;
+    const int64_t lowmask = (int64_t(1) << m.L) - 1;
+    const int64_t c = (j >> m.L) & ((int64_t(1) << m.k) - 1);
+    const int64_t g = ((j >> (m.L + m.k)) << m.L) | (j & lowmask);
+    return insert_zeros_rt(g, m.st, m.k) + m.off[c];
+}
+
+template <typename R, int G>
+__global__ void __launch_bounds__(256)
+k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* __restrict__ offs,
+              const int64_t* __restrict__ starts, const amp_t<R>* __restrict__ vals,
+              const __grid_constant__ RowMap map) {
+    using A = amp_t<R>;
+    const int64_t T = blockDim.x;
+    const int64_t j0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
+    int64_t row[G];
+    A acc[G];
+    bool first[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+        const int64_t j = j0 + u * T;
+        row[u] = j < N ? map_row(j, map) : int64_t(-1);
+        acc[u].x = R(0);
+        acc[u].y = R(0);
+        first[u] = true;
+    }
+    for (int q = 0; q < D; ++q) {
+        const int64_t d = offs[q];
+        const int64_t len = N - (d < 0 ? -d : d);
+        const int64_t shift = d < 0 ? -d : 0;
+        const A* v = vals + starts[q];
+        A a[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int64_t p = row[u] - shift;
+            if (row[u] >= 0 && p >= 0 && p < len) {
+                a[u] = ld_stream(v + p);
+            } else {
+                a[u].x = R(0);
+                a[u].y = R(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            if (a[u].x == R(0) && a[u].y == R(0)) continue;
+            const A xv = x[row[u] + d];
+            const uint8_t t = (a[u].y == R(0)) ? (a[u].x == R(1) ? 1 : 2) : 4;
+            mac_typed<R>(acc[u], first[u], t, a[u].x, a[u].y, xv);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+        if (row[u] >= 0) st_stream(y + row[u], acc[u]);
+}
+
+// v_q[t] = A[i][i+d], i = t + max(0, -d): M[local(i)][local(i+d)] when i
+// and i+d agree outside the targets, else 0.
+struct MatArgs {
+    int k;
+    int t[DIAQ_MAX_K];  // targets in gate order (t[0] = most significant local bit)
+    int64_t tmask;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_materialise(amp_t<R>* vals, int64_t N, const int64_t* __restrict__ offs,
+              const int64_t* __restrict__ starts, const R* __restrict__ mre, const R* __restrict__ mim,
+              const __grid_constant__ MatArgs ma) {
+    using A = amp_t<R>;
+    const int q = blockIdx.y;
+    const int64_t d = offs[q];
+    const int64_t len = N - (d < 0 ? -d : d);
+    const int64_t shift = d < 0 ? -d : 0;
+    const int k = ma.k;
+    const int D = 1 << k;
+    A* out = vals + starts[q];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t + shift, j = i + d;
+        A v;
+        v.x = R(0);
+        v.y = R(0);
+        if (((i ^ j) & ~ma.tmask) == 0) {
+            int r = 0, c = 0;
+            for (int a = 0; a < k; ++a) {
+                r |= int((i >> ma.t[a]) & 1) << (k - 1 - a);
+                c |= int((j >> ma.t[a]) & 1) << (k - 1 - a);
+            }
+            v.x = mre[r * D + c];
+            v.y = mim[r * D + c];
+        }
+        st_stream(out + t, v);
+    }
+}
+
+static RowMap make_rowmap(const GateDesc& g, int n, int threads, int G) {
+    RowMap m;
+    std::memset(&m, 0, sizeof(m));
+    m.k = g.k;
+    for (int a = 0; a < g.k; ++a) m.st[a] = g.targets[a];
+    std::sort(m.st, m.st + g.k);
+    local_offsets(g, m.off);
+    // low group bits per block: a block covers threads*G rows = 2^(L+k)
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= int64_t(threads) * G) ++lg;
+    m.L = std::max(0, std::min(lg - g.k, n - g.k));
+    return m;
+}
+
+diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStream_t s) {
+    const int64_t N = int64_t(1) << op->n;
+    const int threads = 256, G = 2;
+    RowMap map;
+    if (op->op_class == DIAQ_CLASS_RAW) {
+        std::memset(&map, 0, sizeof(map));
+    } else {
+        map = make_rowmap(op->gate, op->n, threads, G);
+    }
+    const int64_t blocks = (N + int64_t(threads) * G - 1) / (int64_t(threads) * G);
+    const int D = (int)op->offsets.size();
+    DIAQ_PRELAUNCH("k_stored_spmv");
+    if (op->dtype == DIAQ_C128)
+        k_stored_spmv<double, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
+            reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), N, D, op->d_offsets,
+            op->d_starts, reinterpret_cast<const double2*>(op->d_values), map);
+    else
+        k_stored_spmv<float, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
+            reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), N, D, op->d_offsets,
+            op->d_starts, reinterpret_cast<const float2*>(op->d_values), map);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
+
+diaq_status launch_materialise(diaq_op_s* op, cudaStream_t s) {
+    const int64_t N = int64_t(1) << op->n;
+    const int k = op->gate.k;
+    const int D = 1 << k;
+    // matrix (re, im) in the op's precision, temporary device copy
+    const size_t rs = op->dtype == DIAQ_C128 ? 8 : 4;
+    std::vector<unsigned char> buf(2 * size_t(D) * D * rs);
+    for (int e = 0; e < D * D; ++e) {
+        if (rs == 8) {
+            reinterpret_cast<double*>(buf.data())[e] = op->gate.m[e].real();
+            reinterpret_cast<double*>(buf.data())[D * D + e] = op->gate.m[e].imag();
+        } else {
+            reinterpret_cast<float*>(buf.data())[e] = float(op->gate.m[e].real());
+            reinterpret_cast<float*>(buf.data())[D * D + e] = float(op->gate.m[e].imag());
+        }
+    }
+    void* dm = nullptr;
+    cudaError_t e = cudaMallocAsync(&dm, buf.size(), s);
+    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(gate matrix): %s", cudaGetErrorString(e));
+    DIAQ_CUDA(cudaMemcpyAsync(dm, buf.data(), buf.size(), cudaMemcpyHostToDevice, s));
+    MatArgs ma;
+    std::memset(&ma, 0, sizeof(ma));
+    ma.k = k;
+    for (int a = 0; a < k; ++a) {
+        ma.t[a] = op->gate.targets[a];
+        ma.tmask |= int64_t(1) << op->gate.targets[a];
+    }
+    const int Dq = (int)op->offsets.size();
+    if (Dq == 0) {
+        // the zero operator: no diagonal to fill (its SpMV writes y = 0)
+        DIAQ_CUDA(cudaStreamSynchronize(s));
+        DIAQ_CUDA(cudaFreeAsync(dm, s));
+        return DIAQ_OK;
+    }
+    const int64_t bx = std::min<int64_t>((N + 255) / 256, 4096);
+    DIAQ_PRELAUNCH("k_materialise");
+    if (op->dtype == DIAQ_C128)
+        k_materialise<double><<<dim3((unsigned)bx, (unsigned)Dq), 256, 0, s>>>(
+            reinterpret_cast<double2*>(op->d_values), N, op->d_offsets, op->d_starts,
+            reinterpret_cast<const double*>(dm), reinterpret_cast<const double*>(dm) + D * D, ma);
+    else
+        k_materialise<float><<<dim3((unsigned)bx, (unsigned)Dq), 256, 0, s>>>(
+            reinterpret_cast<float2*>(op->d_values), N, op->d_offsets, op->d_starts,
+            reinterpret_cast<const float*>(dm), reinterpret_cast<const float*>(dm) + D * D, ma);
+    DIAQ_CUDA(cudaGetLastError());
+    // the host buffer must outlive the async copy
+    DIAQ_CUDA(cudaStreamSynchronize(s));
+    DIAQ_CUDA(cudaFreeAsync(dm, s));
+    return DIAQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device DiaQ product (Algorithm 1, accumulating): C_e(i) = sum over pairs
+// (a, b) with a + b = e of A(i, i+a) B(i+a, i+a+b), for the rows where both
+// factors exist. One thread per output element; pairs in fixed order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_spgemm(amp_t<R>* cvals, const int64_t* __restrict__ c_offs, const int64_t* __restrict__ c_starts,
+         const int32_t* __restrict__ pair_first, const int32_t* __restrict__ pair_a,
+         const int32_t* __restrict__ pair_b, const amp_t<R>* __restrict__ avals,
+         const int64_t* __restrict__ a_offs, const int64_t* __restrict__ a_starts,
+         const amp_t<R>* __restrict__ bvals, const int64_t* __restrict__ b_offs,
+         const int64_t* __restrict__ b_starts, int64_t N) {
+    using A = amp_t<R>;
+    const int q = blockIdx.y;
+    const int64_t e = c_offs[q];
+    const int64_t len = N - (e < 0 ? -e : e);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t + (e < 0 ? -e : 0);
+        A acc;
+        acc.x = R(0);
+        acc.y = R(0);
+        for (int p = pair_first[q]; p < pair_first[q + 1]; ++p) {
+            const int qa = pair_a[p], qb = pair_b[p];
+            const int64_t a = a_offs[qa], b = b_offs[qb];
+            const int64_t m = i + a;
+            if (m < 0 || m >= N || m + b < 0 || m + b >= N) continue;
+            const A av = avals[a_starts[qa] + (i - (a < 0 ? -a : 0))];
+            const A bv = bvals[b_starts[qb] + (m - (b < 0 ? -b : 0))];
+            acc.x = fma(av.x, bv.x, acc.x);
+            acc.x = fma(-av.y, bv.y, acc.x);
+            acc.y = fma(av.x, bv.y, acc.y);
+            acc.y = fma(av.y, bv.x, acc.y);
+        }
+        cvals[c_starts[q] + t] = acc;
+    }
+}
+
+diaq_status launch_spgemm(const diaq_op_s* A, const diaq_op_s* B, diaq_op_s* C, cudaStream_t s) {
+    // host: result indices and the (a, b) pairs meeting on each
+    const int64_t N = int64_t(1) << A->n;
+    std::vector<std::pair<int64_t, std::pair<int32_t, int32_t>>> pairs;
+    for (size_t qa = 0; qa < A->offsets.size(); ++qa)
+        for (size_t qb = 0; qb < B->offsets.size(); ++qb) {
+            const int64_t a = A->offsets[qa], b = B->offsets[qb], e = a + b;
+            const int64_t lo = std::max<int64_t>({0, -a, -e});
+            const int64_t hi = std::min<int64_t>({N, N - a, N - e});
+            if (lo >= hi) continue;  // no overlap: the product diagonal is not valid
+            pairs.push_back({e, {int32_t(qa), int32_t(qb)}});
+        }
+    std::stable_sort(pairs.begin(), pairs.end(),
+                     [](const auto& u, const auto& v) { return u.first < v.first; });
+    std::vector<int64_t> offs;
+    std::vector<int32_t> first, pa, pb;
+    for (size_t p = 0; p < pairs.size(); ++p) {
+        if (offs.empty() || offs.back() != pairs[p].first) {
+            offs.push_back(pairs[p].first);
+            first.push_back(int32_t(p));
+        }
+        pa.push_back(pairs[p].second.first);
+        pb.push_back(pairs[p].second.second);
+    }
+    first.push_back(int32_t(pairs.size()));
+    C->offsets = offs;
+    C->starts.resize(offs.size());
+    int64_t tot = 0;
+    for (size_t q = 0; q < offs.size(); ++q) {
+        C->starts[q] = tot;
+        tot += N - (offs[q] < 0 ? -offs[q] : offs[q]);
+    }
+    C->stored_elems = tot;
+    const size_t ab = amp_bytes(C->dtype);
+    cudaError_t e;
+    if ((e = cudaMalloc(&C->d_values, size_t(std::max<int64_t>(tot, 1)) * ab)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&C->d_offsets, std::max<size_t>(offs.size(), 1) * 8)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&C->d_starts, std::max<size_t>(offs.size(), 1) * 8)) != cudaSuccess)
+        return fail(DIAQ_ERR_ALLOC, "device allocation for the DiaQ product failed: %s", cudaGetErrorString(e));
+    int32_t* dp = nullptr;
+    const size_t pbytes = (first.size() + pa.size() + pb.size()) * 4;
+    if ((e = cudaMallocAsync((void**)&dp, pbytes, s)) != cudaSuccess)
+        return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(pairs): %s", cudaGetErrorString(e));
+    std::vector<int32_t> packed(first);
+    packed.insert(packed.end(), pa.begin(), pa.end());
+    packed.insert(packed.end(), pb.begin(), pb.end());
+    DIAQ_CUDA(cudaMemcpyAsync(dp, packed.data(), pbytes, cudaMemcpyHostToDevice, s));
+    DIAQ_CUDA(cudaMemcpyAsync(C->d_offsets, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, s));
+    DIAQ_CUDA(cudaMemcpyAsync(C->d_starts, C->starts.data(), offs.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!offs.empty()) {
+        DIAQ_PRELAUNCH("k_spgemm");
+        const int64_t bx = std::min<int64_t>((N + 255) / 256, 4096);
+        const int32_t* d_first = dp;
+        const int32_t* d_pa = dp + first.size();
+        const int32_t* d_pb = d_pa + pa.size();
+        if (C->dtype == DIAQ_C128)
+            k_spgemm<double><<<dim3((unsigned)bx, (unsigned)offs.size()), 256, 0, s>>>(
+                reinterpret_cast<double2*>(C->d_values), C->d_offsets, C->d_starts, d_first, d_pa, d_pb,
+                reinterpret_cast<const double2*>(A->d_values), A->d_offsets, A->d_starts,
+                reinterpret_cast<const double2*>(B->d_values), B->d_offsets, B->d_starts, N);
+        else
+            k_spgemm<float><<<dim3((unsigned)bx, (unsigned)offs.size()), 256, 0, s>>>(
+                reinterpret_cast<float2*>(C->d_values), C->d_offsets, C->d_starts, d_first, d_pa, d_pb,
+                reinterpret_cast<const float2*>(A->d_values), A->d_offsets, A->d_starts,
+                reinterpret_cast<const float2*>(B->d_values), B->d_offsets, B->d_starts, N);
+        DIAQ_CUDA(cudaGetLastError());
+    }
+    DIAQ_CUDA(cudaStreamSynchronize(s));  // host vectors feed async copies
+    DIAQ_CUDA(cudaFreeAsync(dp, s));
+    return DIAQ_OK;
+}
+
+}  // namespace diaq

@@ -1,0 +1,883 @@
+// Host side of libdiaq_gb300: argument checks, the DiaQ builder (offsets,
+// classes), the host DiaQ product of Algorithm 1 used for gate fusion, op
+// lifecycle and the C ABI entry points declared in include/diaq.h.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace diaq {
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_error;
+
+diaq_status fail(diaq_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_error = buf;
+    return s;
+}
+
+void clear_error() { g_error.clear(); }
+
+// Device entry points: also discard a non-sticky error that an earlier,
+// unchecked runtime call of the host application left pending, so the
+// launch checks below report only this call's own failures. (A sticky
+// error, such as a fault, persists and is reported by the next call.)
+static void clear_error_device() {
+    g_error.clear();
+    cudaGetLastError();
+}
+
+diaq_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(DIAQ_ERR_CUDA, "%s failed: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// Gate description
+// ---------------------------------------------------------------------------
+uint8_t entry_type(cplx v) {
+    if (v.real() == 0.0 && v.imag() == 0.0) return ET_ZERO;
+    if (v.imag() == 0.0) return v.real() == 1.0 ? ET_ONE : ET_REAL;
+    if (v.real() == 0.0) return ET_IMAG;
+    return ET_GENERAL;
+}
+
+std::vector<cplx> pauli_matrix(const char* gen, int k) {
+    std::vector<cplx> m(1, cplx(1.0, 0.0));
+    int dim = 1;
+    for (int a = 0; a < k; ++a) {
+        cplx p[4];
+        switch (gen[a]) {
+            case 'X': case 'x': p[0] = 0; p[1] = 1; p[2] = 1; p[3] = 0; break;
+            case 'Y': case 'y': p[0] = 0; p[1] = cplx(0, -1); p[2] = cplx(0, 1); p[3] = 0; break;
+            case 'Z': case 'z': p[0] = 1; p[1] = 0; p[2] = 0; p[3] = -1; break;
+            default: p[0] = 1; p[1] = 0; p[2] = 0; p[3] = 1; break;
+        }
+        // kron(m, p): earlier letters are more significant
+        std::vector<cplx> r(static_cast<size_t>(4) * dim * dim);
+        const int nd = 2 * dim;
+        for (int i = 0; i < dim; ++i)
+            for (int j = 0; j < dim; ++j)
+                for (int u = 0; u < 2; ++u)
+                    for (int v = 0; v < 2; ++v) r[(2 * i + u) * nd + (2 * j + v)] = m[i * dim + j] * p[2 * u + v];
+        m.swap(r);
+        dim = nd;
+    }
+    return m;
+}
+
+static diaq_status check_gate_shape(const diaq_gate* g, int n_qubits) {
+    if (!g) return fail(DIAQ_ERR_ARG, "gate is NULL");
+    if (n_qubits < 1 || n_qubits > DIAQ_MAX_QUBITS)
+        return fail(DIAQ_ERR_ARG, "n_qubits = %d outside [1, %d]", n_qubits, DIAQ_MAX_QUBITS);
+    if (g->k < 1 || g->k > DIAQ_MAX_K) return fail(DIAQ_ERR_ARG, "gate k = %d outside [1, %d]", g->k, DIAQ_MAX_K);
+    if (g->k > n_qubits) return fail(DIAQ_ERR_SHAPE, "gate on %d qubits does not fit %d qubits", g->k, n_qubits);
+    for (int a = 0; a < g->k; ++a) {
+        if (g->targets[a] < 0 || g->targets[a] >= n_qubits)
+            return fail(DIAQ_ERR_ARG, "target %d = %d outside [0, %d)", a, g->targets[a], n_qubits);
+        for (int b = 0; b < a; ++b)
+            if (g->targets[a] == g->targets[b]) return fail(DIAQ_ERR_ARG, "repeated target %d", g->targets[a]);
+    }
+    return DIAQ_OK;
+}
+
+static diaq_status check_gen(const diaq_gate* g) {
+    const size_t len = strnlen(g->gen, sizeof(g->gen));
+    if (len != size_t(g->k)) return fail(DIAQ_ERR_ARG, "generator \"%.*s\" must have one letter per target (k = %d)",
+                                         (int)len, g->gen, g->k);
+    for (int a = 0; a < g->k; ++a)
+        if (!strchr("IXYZixyz", g->gen[a])) return fail(DIAQ_ERR_ARG, "generator letter '%c' not in IXYZ", g->gen[a]);
+    return DIAQ_OK;
+}
+
+diaq_status gate_desc_from(const diaq_gate* g, int n_qubits, const double* theta, GateDesc* out) {
+    DIAQ_TRY(check_gate_shape(g, n_qubits));
+    out->k = g->k;
+    for (int a = 0; a < g->k; ++a) out->targets[a] = g->targets[a];
+    const size_t DD = size_t(1) << (2 * g->k);
+    out->m.assign(DD, cplx(0, 0));
+    if (g->param < 0) {
+        if (!g->m) return fail(DIAQ_ERR_ARG, "fixed gate has no matrix");
+        for (size_t e = 0; e < DD; ++e) {
+            out->m[e] = cplx(g->m[2 * e], g->m[2 * e + 1]);
+            if (!std::isfinite(g->m[2 * e]) || !std::isfinite(g->m[2 * e + 1]))
+                return fail(DIAQ_ERR_ARG, "gate matrix entry %zu is not finite", e);
+        }
+        return DIAQ_OK;
+    }
+    DIAQ_TRY(check_gen(g));
+    if (!theta) return fail(DIAQ_ERR_ARG, "parametric gate needs theta");
+    const double a = g->scale * theta[g->param];
+    if (!std::isfinite(a)) return fail(DIAQ_ERR_ARG, "parameter angle is not finite");
+    const std::vector<cplx> P = pauli_matrix(g->gen, g->k);
+    const double c = std::cos(0.5 * a), s = std::sin(0.5 * a);
+    const int D = 1 << g->k;
+    for (int r = 0; r < D; ++r)
+        for (int q = 0; q < D; ++q) out->m[r * D + q] = (r == q ? cplx(c, 0) : cplx(0, 0)) + cplx(0, -s) * P[r * D + q];
+    return DIAQ_OK;
+}
+
+int classify(const std::vector<cplx>& m, int k) {
+    const int D = 1 << k;
+    bool diag = true, real = true, mono = true, perm = true;
+    std::vector<int> colcount(D, 0);
+    for (int r = 0; r < D; ++r) {
+        int rowcount = 0;
+        for (int c = 0; c < D; ++c) {
+            const cplx v = m[r * D + c];
+            if (v.imag() != 0.0) real = false;
+            if (v != cplx(0, 0)) {
+                if (r != c) diag = false;
+                ++rowcount;
+                ++colcount[c];
+                if (v != cplx(1, 0)) perm = false;
+            }
+        }
+        if (rowcount != 1) mono = perm = false;
+    }
+    for (int c = 0; c < D; ++c)
+        if (colcount[c] != 1) mono = perm = false;
+    if (diag) return DIAQ_CLASS_DIAGONAL;
+    if (perm) return DIAQ_CLASS_PERMUTATION;
+    if (mono) return DIAQ_CLASS_MONOMIAL;
+    if (real) return DIAQ_CLASS_REAL;
+    return DIAQ_CLASS_GENERAL;
+}
+
+std::vector<int64_t> full_offsets(const GateDesc& g, const std::vector<uint8_t>* pattern) {
+    const int D = 1 << g.k;
+    std::vector<int64_t> out;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const bool nz = pattern ? (*pattern)[r * D + c] != 0 : g.m[r * D + c] != cplx(0, 0);
+            if (!nz) continue;
+            int64_t d = 0;
+            for (int a = 0; a < g.k; ++a) {
+                const int64_t rb = (r >> (g.k - 1 - a)) & 1, cb = (c >> (g.k - 1 - a)) & 1;
+                d += (cb - rb) * (int64_t(1) << g.targets[a]);
+            }
+            out.push_back(d);
+        }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
+}
+
+// Structural pattern: non-zeros of M for a fixed gate, of I and P for a
+// parametric one (so the offsets do not depend on the angle).
+static std::vector<uint8_t> gate_pattern(const diaq_gate* g, const GateDesc& d) {
+    const int D = 1 << d.k;
+    std::vector<uint8_t> p(static_cast<size_t>(D) * D, 0);
+    if (g->param < 0) {
+        for (int e = 0; e < D * D; ++e) p[e] = d.m[e] != cplx(0, 0);
+    } else {
+        const std::vector<cplx> P = pauli_matrix(g->gen, g->k);
+        for (int e = 0; e < D * D; ++e) p[e] = (P[e] != cplx(0, 0)) || (e / D == e % D);
+    }
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// Host DiaQ product (Algorithm 1, accumulating reading)
+// ---------------------------------------------------------------------------
+using DiaMap = std::map<int64_t, std::vector<cplx>>;
+
+static int64_t dlen(int64_t N, int64_t d) { return N - (d < 0 ? -d : d); }
+
+// C = A B. Row form: A(i, i+a) sits at position i - max(0, -a) of diagonal a.
+static DiaMap diaq_matmul(int64_t N, const DiaMap& A, const DiaMap& B) {
+    DiaMap C;
+    for (const auto& [a, va] : A)
+        for (const auto& [b, vb] : B) {
+            const int64_t e = a + b;
+            const int64_t lo = std::max<int64_t>({0, -a, -e});
+            const int64_t hi = std::min<int64_t>({N, N - a, N - e});
+            if (lo >= hi) continue;  // "isValid": the product diagonal has no element
+            auto it = C.find(e);
+            if (it == C.end()) it = C.emplace(e, std::vector<cplx>(size_t(dlen(N, e)), cplx(0, 0))).first;
+            std::vector<cplx>& vc = it->second;
+            const int64_t sa = a < 0 ? -a : 0, sb = b < 0 ? -b : 0, sc = e < 0 ? -e : 0;
+            for (int64_t i = lo; i < hi; ++i) vc[size_t(i - sc)] += va[size_t(i - sa)] * vb[size_t(i + a - sb)];
+        }
+    return C;
+}
+
+static DiaMap dense_to_map(const std::vector<cplx>& m, int64_t N) {
+    DiaMap out;
+    for (int64_t d = -(N - 1); d <= N - 1; ++d) {
+        const int64_t len = dlen(N, d), r0 = d < 0 ? -d : 0, c0 = d > 0 ? d : 0;
+        bool nz = false;
+        for (int64_t t = 0; t < len && !nz; ++t) nz = m[size_t((r0 + t) * N + c0 + t)] != cplx(0, 0);
+        if (!nz) continue;
+        std::vector<cplx> v(static_cast<size_t>(len));
+        for (int64_t t = 0; t < len; ++t) v[size_t(t)] = m[size_t((r0 + t) * N + c0 + t)];
+        out.emplace(d, std::move(v));
+    }
+    return out;
+}
+
+static std::vector<cplx> map_to_dense(const DiaMap& A, int64_t N) {
+    std::vector<cplx> m(static_cast<size_t>(N * N), cplx(0, 0));
+    for (const auto& [d, v] : A) {
+        const int64_t r0 = d < 0 ? -d : 0, c0 = d > 0 ? d : 0;
+        for (int64_t t = 0; t < int64_t(v.size()); ++t) m[size_t((r0 + t) * N + c0 + t)] = v[size_t(t)];
+    }
+    return m;
+}
+
+// Embedding of a gate in a union target space (union[0] most significant).
+static std::vector<cplx> embed(const GateDesc& g, const int* uni, int K) {
+    const int64_t DU = int64_t(1) << K;
+    int pos[DIAQ_MAX_K];
+    for (int a = 0; a < g.k; ++a)
+        for (int u = 0; u < K; ++u)
+            if (uni[u] == g.targets[a]) pos[a] = K - 1 - u;
+    int64_t gmask = 0;
+    for (int a = 0; a < g.k; ++a) gmask |= int64_t(1) << pos[a];
+    const int D = 1 << g.k;
+    std::vector<cplx> E(static_cast<size_t>(DU * DU), cplx(0, 0));
+    for (int64_t R = 0; R < DU; ++R)
+        for (int64_t C = 0; C < DU; ++C) {
+            if ((R & ~gmask) != (C & ~gmask)) continue;
+            int r = 0, c = 0;
+            for (int a = 0; a < g.k; ++a) {
+                r |= int((R >> pos[a]) & 1) << (g.k - 1 - a);
+                c |= int((C >> pos[a]) & 1) << (g.k - 1 - a);
+            }
+            E[size_t(R * DU + C)] = g.m[size_t(r * D + c)];
+        }
+    return E;
+}
+
+static diaq_status fuse_descs(const std::vector<GateDesc>& gs, GateDesc* out) {
+    int uni[DIAQ_MAX_K];
+    int K = 0;
+    for (const GateDesc& g : gs)
+        for (int a = 0; a < g.k; ++a) {
+            bool seen = false;
+            for (int u = 0; u < K; ++u) seen |= uni[u] == g.targets[a];
+            if (seen) continue;
+            if (K == DIAQ_MAX_K)
+                return fail(DIAQ_ERR_UNSUPPORTED, "fused gates span more than %d qubits", DIAQ_MAX_K);
+            uni[K++] = g.targets[a];
+        }
+    const int64_t DU = int64_t(1) << K;
+    DiaMap acc;
+    {
+        std::vector<cplx> I(static_cast<size_t>(DU * DU), cplx(0, 0));
+        for (int64_t i = 0; i < DU; ++i) I[size_t(i * DU + i)] = 1.0;
+        acc = dense_to_map(I, DU);
+    }
+    for (const GateDesc& g : gs) acc = diaq_matmul(DU, dense_to_map(embed(g, uni, K), DU), acc);
+    out->k = K;
+    for (int u = 0; u < K; ++u) out->targets[u] = uni[u];
+    out->m = map_to_dense(acc, DU);
+    return DIAQ_OK;
+}
+
+}  // namespace diaq
+
+using namespace diaq;
+
+// ---------------------------------------------------------------------------
+// Op helpers
+// ---------------------------------------------------------------------------
+static diaq_status check_op(diaq_op_t op) {
+    if (!op) return fail(DIAQ_ERR_ARG, "op is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != op->device)
+        return fail(DIAQ_ERR_ARG, "op was built on device %d but device %d is current", op->device, dev);
+    return DIAQ_OK;
+}
+
+static diaq_status free_op_memory(diaq_op_s* op) {
+    cudaError_t first = cudaSuccess;
+    for (void* p : {op->d_values, static_cast<void*>(op->d_offsets), static_cast<void*>(op->d_starts), op->d_matrix}) {
+        if (!p) continue;
+        const cudaError_t e = cudaFree(p);
+        if (e != cudaSuccess && first == cudaSuccess) first = e;
+    }
+    op->d_values = nullptr;
+    op->d_offsets = nullptr;
+    op->d_starts = nullptr;
+    op->d_matrix = nullptr;
+    return first == cudaSuccess ? DIAQ_OK : cuda_fail(first, "cudaFree(op memory)");
+}
+
+static diaq_status alloc_stored(diaq_op_s* op) {
+    const int64_t N = int64_t(1) << op->n;
+    op->starts.resize(op->offsets.size());
+    int64_t tot = 0;
+    for (size_t q = 0; q < op->offsets.size(); ++q) {
+        op->starts[q] = tot;
+        tot += dlen(N, op->offsets[q]);
+    }
+    op->stored_elems = tot;
+    const size_t bytes = size_t(std::max<int64_t>(tot, 1)) * amp_bytes(op->dtype);
+    cudaError_t e = cudaMalloc(&op->d_values, bytes);
+    if (e != cudaSuccess)
+        return fail(DIAQ_ERR_ALLOC, "cudaMalloc of %zu bytes for stored diagonals failed: %s", bytes,
+                    cudaGetErrorString(e));
+    const size_t ob = std::max<size_t>(op->offsets.size(), 1) * sizeof(int64_t);
+    if ((e = cudaMalloc((void**)&op->d_offsets, ob)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&op->d_starts, ob)) != cudaSuccess)
+        return fail(DIAQ_ERR_ALLOC, "cudaMalloc for diagonal indices failed: %s", cudaGetErrorString(e));
+    if (!op->offsets.empty()) {
+        DIAQ_CUDA(cudaMemcpy(op->d_offsets, op->offsets.data(), op->offsets.size() * 8, cudaMemcpyHostToDevice));
+        DIAQ_CUDA(cudaMemcpy(op->d_starts, op->starts.data(), op->starts.size() * 8, cudaMemcpyHostToDevice));
+    }
+    return DIAQ_OK;
+}
+
+// Finish a gate-structured op: class, offsets, device data.
+static diaq_status finish_gate_op(diaq_op_s* op, const std::vector<uint8_t>* pattern, cudaStream_t s) {
+    op->op_class = classify(op->gate.m, op->gate.k);
+    op->offsets = full_offsets(op->gate, pattern);
+    if (op->variant == DIAQ_ONTHEFLY) {
+        if (op->gate.k > 3) DIAQ_TRY(upload_matrix(op));
+        return DIAQ_OK;
+    }
+    DIAQ_TRY(alloc_stored(op));
+    return launch_materialise(op, s);
+}
+
+static bool overlaps(const void* a, const void* b, size_t bytes) {
+    const char* x = static_cast<const char*>(a);
+    const char* y = static_cast<const char*>(b);
+    return x < y + bytes && y < x + bytes;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* diaq_last_error(void) { return g_error.c_str(); }
+
+const char* diaq_version(void) { return "diaq_gb300 0.1 (sm_103a)"; }
+
+diaq_status diaq_gate_offsets(const diaq_gate* g, int32_t n_qubits, int64_t* offsets, int64_t cap,
+                              int64_t* count) {
+    clear_error();
+    if (!count) return fail(DIAQ_ERR_ARG, "count is NULL");
+    GateDesc d;
+    // structure only: a parametric gate's offsets do not depend on theta
+    if (g && g->param >= 0) {
+        DIAQ_TRY(check_gate_shape(g, n_qubits));
+        DIAQ_TRY(check_gen(g));
+        d.k = g->k;
+        for (int a = 0; a < g->k; ++a) d.targets[a] = g->targets[a];
+        d.m.assign(size_t(1) << (2 * g->k), cplx(0, 0));
+    } else {
+        DIAQ_TRY(gate_desc_from(g, n_qubits, nullptr, &d));
+    }
+    const std::vector<uint8_t> pat = gate_pattern(g, d);
+    const std::vector<int64_t> offs = full_offsets(d, &pat);
+    *count = int64_t(offs.size());
+    if (int64_t(offs.size()) > cap || (!offsets && !offs.empty()))
+        return fail(DIAQ_ERR_ARG, "offset buffer holds %lld, need %zu", (long long)cap, offs.size());
+    std::copy(offs.begin(), offs.end(), offsets);
+    return DIAQ_OK;
+}
+
+diaq_status diaq_diaq_matmul_host(int64_t N, int64_t a_count, const int64_t* a_idx, const double* a_values,
+                                  int64_t b_count, const int64_t* b_idx, const double* b_values,
+                                  int64_t* c_count, int64_t* c_idx, int64_t* c_values_len,
+                                  double* c_values) {
+    clear_error();
+    if (N < 1) return fail(DIAQ_ERR_ARG, "N = %lld < 1", (long long)N);
+    if (a_count < 0 || b_count < 0 || (a_count && (!a_idx || !a_values)) || (b_count && (!b_idx || !b_values)))
+        return fail(DIAQ_ERR_ARG, "bad operand arrays");
+    if (!c_count || !c_values_len) return fail(DIAQ_ERR_ARG, "c_count / c_values_len is NULL");
+    auto load = [&](int64_t cnt, const int64_t* idx, const double* vals, DiaMap* m, const char* nm) -> diaq_status {
+        const double* p = vals;
+        for (int64_t q = 0; q < cnt; ++q) {
+            const int64_t d = idx[q];
+            if (d <= -N || d >= N) return fail(DIAQ_ERR_SHAPE, "%s index %lld outside (-N, N)", nm, (long long)d);
+            if (m->count(d)) return fail(DIAQ_ERR_ARG, "%s index %lld repeated", nm, (long long)d);
+            std::vector<cplx> v(static_cast<size_t>(dlen(N, d)));
+            for (size_t t = 0; t < v.size(); ++t) v[t] = cplx(p[2 * t], p[2 * t + 1]);
+            p += 2 * v.size();
+            m->emplace(d, std::move(v));
+        }
+        return DIAQ_OK;
+    };
+    DiaMap A, B;
+    DIAQ_TRY(load(a_count, a_idx, a_values, &A, "A"));
+    DIAQ_TRY(load(b_count, b_idx, b_values, &B, "B"));
+    const DiaMap C = diaq_matmul(N, A, B);
+    int64_t len = 0;
+    for (const auto& kv : C) len += int64_t(kv.second.size());
+    *c_count = int64_t(C.size());
+    *c_values_len = len;
+    if (!c_values) return DIAQ_OK;
+    if (!c_idx) return fail(DIAQ_ERR_ARG, "c_idx is NULL");
+    double* p = c_values;
+    int64_t q = 0;
+    for (const auto& [d, v] : C) {
+        c_idx[q++] = d;
+        for (const cplx& z : v) {
+            *p++ = z.real();
+            *p++ = z.imag();
+        }
+    }
+    return DIAQ_OK;
+}
+
+diaq_status diaq_fuse_gates_host(const diaq_gate* gates, int32_t count, const double* theta,
+                                 int32_t* union_k, int32_t* union_targets, double* fused_m) {
+    clear_error();
+    if (!gates || count < 1) return fail(DIAQ_ERR_ARG, "need at least one gate");
+    if (!union_k || !union_targets || !fused_m) return fail(DIAQ_ERR_ARG, "NULL output");
+    int nq = 0;
+    for (int i = 0; i < count; ++i)
+        for (int a = 0; a < gates[i].k && a < DIAQ_MAX_K; ++a) nq = std::max(nq, gates[i].targets[a] + 1);
+    std::vector<GateDesc> ds(static_cast<size_t>(count));
+    for (int i = 0; i < count; ++i) DIAQ_TRY(gate_desc_from(&gates[i], std::max(nq, 1), theta, &ds[size_t(i)]));
+    GateDesc f;
+    DIAQ_TRY(fuse_descs(ds, &f));
+    *union_k = f.k;
+    for (int u = 0; u < f.k; ++u) union_targets[u] = f.targets[u];
+    for (size_t e = 0; e < f.m.size(); ++e) {
+        fused_m[2 * e] = f.m[e].real();
+        fused_m[2 * e + 1] = f.m[e].imag();
+    }
+    return DIAQ_OK;
+}
+
+diaq_status diaq_build(const diaq_gate* g, int32_t n_qubits, diaq_dtype dtype, diaq_variant variant,
+                       const double* theta, diaq_stream_t stream, diaq_op_t* out) {
+    clear_error_device();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (dtype != DIAQ_C64 && dtype != DIAQ_C128) return fail(DIAQ_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (variant != DIAQ_ONTHEFLY && variant != DIAQ_STORED) return fail(DIAQ_ERR_ARG, "bad variant %d", (int)variant);
+    GateDesc d;
+    DIAQ_TRY(gate_desc_from(g, n_qubits, theta, &d));
+    const std::vector<uint8_t> pat = gate_pattern(g, d);
+    diaq_op_s* op = new (std::nothrow) diaq_op_s();
+    if (!op) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+    op->n = n_qubits;
+    op->dtype = dtype;
+    op->variant = variant;
+    op->gate = d;
+    cudaError_t e = cudaGetDevice(&op->device);
+    if (e != cudaSuccess) {
+        delete op;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    diaq_status s = finish_gate_op(op, &pat, static_cast<cudaStream_t>(stream));
+    if (s != DIAQ_OK) {
+        free_op_memory(op);
+        delete op;
+        return s;
+    }
+    *out = op;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_build_diaq(int32_t n_qubits, int64_t count, const int64_t* indices, const double* values,
+                            diaq_dtype dtype, diaq_stream_t stream, diaq_op_t* out) {
+    clear_error_device();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > DIAQ_MAX_QUBITS) return fail(DIAQ_ERR_ARG, "n_qubits = %d out of range", n_qubits);
+    if (dtype != DIAQ_C64 && dtype != DIAQ_C128) return fail(DIAQ_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (count < 0 || (count && (!indices || !values))) return fail(DIAQ_ERR_ARG, "bad diagonal arrays");
+    const int64_t N = int64_t(1) << n_qubits;
+    std::vector<std::pair<int64_t, int64_t>> idx;  // (index, input position)
+    for (int64_t q = 0; q < count; ++q) {
+        if (indices[q] <= -N || indices[q] >= N)
+            return fail(DIAQ_ERR_SHAPE, "diagonal index %lld outside (-N, N)", (long long)indices[q]);
+        idx.push_back({indices[q], q});
+    }
+    std::sort(idx.begin(), idx.end());
+    for (size_t q = 1; q < idx.size(); ++q)
+        if (idx[q].first == idx[q - 1].first) return fail(DIAQ_ERR_ARG, "diagonal index %lld repeated", (long long)idx[q].first);
+    // input start of each diagonal
+    std::vector<int64_t> in_start(static_cast<size_t>(count));
+    int64_t pos = 0;
+    for (int64_t q = 0; q < count; ++q) {
+        in_start[size_t(q)] = pos;
+        pos += dlen(N, indices[q]);
+    }
+    diaq_op_s* op = new (std::nothrow) diaq_op_s();
+    if (!op) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+    op->n = n_qubits;
+    op->dtype = dtype;
+    op->variant = DIAQ_STORED;
+    op->op_class = DIAQ_CLASS_RAW;
+    cudaError_t e = cudaGetDevice(&op->device);
+    if (e != cudaSuccess) {
+        delete op;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    for (auto& p : idx) op->offsets.push_back(p.first);
+    diaq_status s = alloc_stored(op);
+    if (s == DIAQ_OK) {
+        // host staging in the op's precision, sorted order
+        const size_t ab = amp_bytes(dtype);
+        std::vector<unsigned char> buf(static_cast<size_t>(std::max<int64_t>(op->stored_elems, 1)) * ab);
+        for (size_t q = 0; q < idx.size(); ++q) {
+            const double* src = values + 2 * in_start[size_t(idx[q].second)];
+            const int64_t len = dlen(N, idx[q].first);
+            for (int64_t t = 0; t < len; ++t) {
+                const size_t at = size_t(op->starts[q] + t);
+                if (dtype == DIAQ_C128) {
+                    reinterpret_cast<double*>(buf.data())[2 * at] = src[2 * t];
+                    reinterpret_cast<double*>(buf.data())[2 * at + 1] = src[2 * t + 1];
+                } else {
+                    reinterpret_cast<float*>(buf.data())[2 * at] = float(src[2 * t]);
+                    reinterpret_cast<float*>(buf.data())[2 * at + 1] = float(src[2 * t + 1]);
+                }
+            }
+        }
+        e = cudaMemcpyAsync(op->d_values, buf.data(), size_t(op->stored_elems) * ab, cudaMemcpyHostToDevice,
+                            static_cast<cudaStream_t>(stream));
+        if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) s = cuda_fail(e, "upload of DiaQ diagonals");
+    }
+    if (s != DIAQ_OK) {
+        free_op_memory(op);
+        delete op;
+        return s;
+    }
+    *out = op;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_op_destroy(diaq_op_t op) {
+    clear_error();
+    if (!op) return DIAQ_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != op->device) cudaSetDevice(op->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    diaq_status s = free_op_memory(op);
+    if (cur >= 0 && cur != op->device) cudaSetDevice(cur);
+    delete op;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize (op destroy)");
+    return s;
+}
+
+diaq_status diaq_op_query(diaq_op_t op, diaq_op_info* info) {
+    clear_error();
+    if (!op || !info) return fail(DIAQ_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->n_qubits = op->n;
+    info->dtype = op->dtype;
+    info->variant = op->variant;
+    info->op_class = op->op_class;
+    info->k = op->op_class == DIAQ_CLASS_RAW ? 0 : op->gate.k;
+    for (int a = 0; a < info->k; ++a) info->targets[a] = op->gate.targets[a];
+    info->n_diagonals = int64_t(op->offsets.size());
+    info->stored_bytes = op->variant == DIAQ_STORED ? op->stored_elems * int64_t(amp_bytes(op->dtype)) : 0;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_op_offsets(diaq_op_t op, int64_t* offsets, int64_t cap, int64_t* count) {
+    clear_error();
+    if (!op || !count) return fail(DIAQ_ERR_ARG, "NULL argument");
+    *count = int64_t(op->offsets.size());
+    if (*count > cap || (!offsets && *count)) return fail(DIAQ_ERR_ARG, "offset buffer too small");
+    std::copy(op->offsets.begin(), op->offsets.end(), offsets);
+    return DIAQ_OK;
+}
+
+diaq_status diaq_op_read_diagonal(diaq_op_t op, int64_t which, void* host_out, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_op(op));
+    if (op->variant != DIAQ_STORED) return fail(DIAQ_ERR_ARG, "op is on-the-fly: no stored diagonals");
+    if (which < 0 || which >= int64_t(op->offsets.size())) return fail(DIAQ_ERR_ARG, "diagonal %lld out of range", (long long)which);
+    if (!host_out) return fail(DIAQ_ERR_ARG, "host_out is NULL");
+    const int64_t N = int64_t(1) << op->n;
+    const size_t ab = amp_bytes(op->dtype);
+    const char* src = static_cast<const char*>(op->d_values) + size_t(op->starts[size_t(which)]) * ab;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DIAQ_CUDA(cudaMemcpyAsync(host_out, src, size_t(dlen(N, op->offsets[size_t(which)])) * ab, cudaMemcpyDeviceToHost, s));
+    DIAQ_CUDA(cudaStreamSynchronize(s));
+    return DIAQ_OK;
+}
+
+diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant, diaq_stream_t stream,
+                      diaq_op_t* out) {
+    clear_error_device();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!ops || count < 1) return fail(DIAQ_ERR_ARG, "need at least one op");
+    if (variant != DIAQ_ONTHEFLY && variant != DIAQ_STORED) return fail(DIAQ_ERR_ARG, "bad variant %d", (int)variant);
+    bool raw = false;
+    for (int i = 0; i < count; ++i) {
+        DIAQ_TRY(check_op(ops[i]));
+        if (ops[i]->n != ops[0]->n || ops[i]->dtype != ops[0]->dtype)
+            return fail(DIAQ_ERR_SHAPE, "op %d is not multiplyable with op 0 (qubits or dtype differ)", i);
+        raw |= ops[i]->op_class == DIAQ_CLASS_RAW;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!raw) {
+        std::vector<GateDesc> ds;
+        for (int i = 0; i < count; ++i) ds.push_back(ops[i]->gate);
+        GateDesc f;
+        DIAQ_TRY(fuse_descs(ds, &f));
+        diaq_op_s* op = new (std::nothrow) diaq_op_s();
+        if (!op) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+        op->n = ops[0]->n;
+        op->dtype = ops[0]->dtype;
+        op->variant = variant;
+        op->device = ops[0]->device;
+        op->gate = f;
+        diaq_status st = finish_gate_op(op, nullptr, s);
+        if (st != DIAQ_OK) {
+            free_op_memory(op);
+            delete op;
+            return st;
+        }
+        *out = op;
+        return DIAQ_OK;
+    }
+    // device Algorithm 1 over full-system diagonals, left to right: C = ops[i] C
+    for (int i = 0; i < count; ++i)
+        if (ops[i]->variant != DIAQ_STORED)
+            return fail(DIAQ_ERR_UNSUPPORTED, "fusing a raw DiaQ op needs every op stored (op %d is on-the-fly)", i);
+    diaq_op_s* cur = nullptr;
+    for (int i = 1; i < count; ++i) {
+        diaq_op_s* c = new (std::nothrow) diaq_op_s();
+        if (!c) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+        c->n = ops[0]->n;
+        c->dtype = ops[0]->dtype;
+        c->variant = DIAQ_STORED;
+        c->op_class = DIAQ_CLASS_RAW;
+        c->device = ops[0]->device;
+        const diaq_op_s* right = cur ? cur : ops[0];
+        diaq_status st = launch_spgemm(ops[i], right, c, s);
+        if (cur) {
+            free_op_memory(cur);
+            delete cur;
+        }
+        if (st != DIAQ_OK) {
+            free_op_memory(c);
+            delete c;
+            return st;
+        }
+        cur = c;
+    }
+    if (!cur) {
+        // single op: copy it
+        diaq_op_s* c = new (std::nothrow) diaq_op_s();
+        if (!c) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+        *c = diaq_op_s();
+        c->n = ops[0]->n;
+        c->dtype = ops[0]->dtype;
+        c->variant = DIAQ_STORED;
+        c->op_class = DIAQ_CLASS_RAW;
+        c->device = ops[0]->device;
+        c->offsets = ops[0]->offsets;
+        diaq_status st = alloc_stored(c);
+        if (st == DIAQ_OK) {
+            cudaError_t e = cudaMemcpyAsync(c->d_values, ops[0]->d_values, size_t(c->stored_elems) * amp_bytes(c->dtype),
+                                            cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(copy op)");
+        }
+        if (st != DIAQ_OK) {
+            free_op_memory(c);
+            delete c;
+            return st;
+        }
+        cur = c;
+    }
+    *out = cur;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_op(op));
+    if (!x || !y) return fail(DIAQ_ERR_ARG, "x or y is NULL");
+    const size_t bytes = (size_t(1) << op->n) * amp_bytes(op->dtype);
+    if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+        return fail(DIAQ_ERR_ARG, "state buffers must be 16-byte aligned");
+    const bool inplace = x == y;
+    if (inplace && op->variant == DIAQ_STORED) return fail(DIAQ_ERR_ARG, "stored ops cannot run in place (x == y)");
+    if (!inplace && overlaps(x, y, bytes)) return fail(DIAQ_ERR_ARG, "x and y overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (op->variant == DIAQ_ONTHEFLY) return launch_onthefly(op, x, y, s);
+    return launch_stored(op, x, y, s);
+}
+
+static int mem_kind(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;  // unknown: treat as pageable host
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return 1;
+    return 0;
+}
+
+diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out, void* work0,
+                          void* work1, diaq_stream_t stream) {
+    clear_error_device();
+    if (count < 0 || (count && !ops)) return fail(DIAQ_ERR_ARG, "bad op list");
+    if (!psi_in || !psi_out || !work0) return fail(DIAQ_ERR_ARG, "NULL state or work buffer");
+    if (count == 0) return fail(DIAQ_ERR_ARG, "empty circuit: nothing to infer the state size from");
+    const int n = ops[0]->n;
+    const diaq_dtype dt = ops[0]->dtype;
+    bool any_stored = false;
+    for (int i = 0; i < count; ++i) {
+        DIAQ_TRY(check_op(ops[i]));
+        if (ops[i]->n != n || ops[i]->dtype != dt) return fail(DIAQ_ERR_SHAPE, "op %d has another size or dtype", i);
+        any_stored |= ops[i]->variant == DIAQ_STORED;
+    }
+    if (any_stored && !work1) return fail(DIAQ_ERR_ARG, "stored ops need a second work buffer");
+    if (mem_kind(work0) != 1 || (work1 && mem_kind(work1) != 1)) return fail(DIAQ_ERR_ARG, "work buffers must be device memory");
+    const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const cudaMemcpyKind kin = mem_kind(psi_in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DIAQ_CUDA(cudaMemcpyAsync(work0, psi_in, bytes, kin, s));
+    void* cur = work0;
+    void* other = work1;
+    for (int i = 0; i < count; ++i) {
+        if (ops[i]->variant == DIAQ_ONTHEFLY) {
+            DIAQ_TRY(launch_onthefly(ops[i], cur, cur, s));
+        } else {
+            DIAQ_TRY(launch_stored(ops[i], cur, other, s));
+            std::swap(cur, other);
+        }
+    }
+    const cudaMemcpyKind kout = mem_kind(psi_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    DIAQ_CUDA(cudaMemcpyAsync(psi_out, cur, bytes, kout, s));
+    DIAQ_CUDA(cudaStreamSynchronize(s));
+    return DIAQ_OK;
+}
+
+static diaq_status check_state(const void* psi, int n, diaq_dtype dt) {
+    if (!psi) return fail(DIAQ_ERR_ARG, "state is NULL");
+    if (n < 1 || n > DIAQ_MAX_QUBITS) return fail(DIAQ_ERR_ARG, "n_qubits = %d out of range", n);
+    if (dt != DIAQ_C64 && dt != DIAQ_C128) return fail(DIAQ_ERR_ARG, "bad dtype %d", (int)dt);
+    if (reinterpret_cast<uintptr_t>(psi) & 15) return fail(DIAQ_ERR_ARG, "state buffer must be 16-byte aligned");
+    return DIAQ_OK;
+}
+
+diaq_status diaq_norm(const void* psi, int32_t n_qubits, diaq_dtype dtype, double* out, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_state(psi, n_qubits, dtype));
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    return run_norm(psi, n_qubits, dtype, out, static_cast<cudaStream_t>(stream));
+}
+
+diaq_status diaq_expect(const void* psi, int32_t n_qubits, diaq_dtype dtype, int32_t n_terms, const uint64_t* xmask,
+                        const uint64_t* zmask, const double* coeff, double* out, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_state(psi, n_qubits, dtype));
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    if (n_terms < 0 || (n_terms && (!xmask || !zmask || !coeff))) return fail(DIAQ_ERR_ARG, "bad term arrays");
+    PauliGroups pg;
+    DIAQ_TRY(make_pauli_groups(n_qubits, n_terms, xmask, zmask, coeff, false, &pg));
+    return run_expect(psi, n_qubits, dtype, pg, out, static_cast<cudaStream_t>(stream));
+}
+
+diaq_status diaq_apply_pauli_sum(const void* psi, void* lambda, int32_t n_qubits, diaq_dtype dtype, int32_t n_terms,
+                                 const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                                 diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_state(psi, n_qubits, dtype));
+    DIAQ_TRY(check_state(lambda, n_qubits, dtype));
+    if (overlaps(psi, lambda, (size_t(1) << n_qubits) * amp_bytes(dtype))) return fail(DIAQ_ERR_ARG, "psi and lambda overlap");
+    if (n_terms < 0 || (n_terms && (!xmask || !zmask || !coeff))) return fail(DIAQ_ERR_ARG, "bad term arrays");
+    PauliGroups pg;
+    DIAQ_TRY(make_pauli_groups(n_qubits, n_terms, xmask, zmask, coeff, false, &pg));
+    return run_pauli_apply(psi, lambda, n_qubits, dtype, pg, static_cast<cudaStream_t>(stream));
+}
+
+diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_params,
+                              int32_t n_terms, const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                              const void* psi0, void* work_psi, void* work_lam, int32_t n_qubits, diaq_dtype dtype,
+                              double* energy, double* grad, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_state(psi0, n_qubits, dtype));
+    DIAQ_TRY(check_state(work_psi, n_qubits, dtype));
+    DIAQ_TRY(check_state(work_lam, n_qubits, dtype));
+    const size_t bytes = (size_t(1) << n_qubits) * amp_bytes(dtype);
+    if (overlaps(work_psi, work_lam, bytes) || overlaps(psi0, work_psi, bytes) || overlaps(psi0, work_lam, bytes))
+        return fail(DIAQ_ERR_ARG, "psi0, work_psi and work_lam must not overlap");
+    if (n_gates < 0 || (n_gates && !gates)) return fail(DIAQ_ERR_ARG, "bad gate list");
+    if (n_params < 0 || (n_params && !theta)) return fail(DIAQ_ERR_ARG, "bad parameter array");
+    if (n_terms < 0 || (n_terms && (!xmask || !zmask || !coeff))) return fail(DIAQ_ERR_ARG, "bad term arrays");
+    // host descriptions: forward matrices, their adjoints, generators
+    std::vector<GateDesc> fwd(static_cast<size_t>(n_gates)), bwd(static_cast<size_t>(n_gates)), gen(static_cast<size_t>(n_gates));
+    std::vector<int> slot(static_cast<size_t>(n_gates), -1);
+    int n_slots = 0;
+    for (int l = 0; l < n_gates; ++l) {
+        const diaq_gate* g = &gates[l];
+        if (g->param >= n_params) return fail(DIAQ_ERR_ARG, "gate %d uses parameter %d >= n_params", l, g->param);
+        DIAQ_TRY(gate_desc_from(g, n_qubits, theta, &fwd[size_t(l)]));
+        if (fwd[size_t(l)].k > 3) return fail(DIAQ_ERR_UNSUPPORTED, "adjoint sweep supports gates of at most 3 qubits");
+        GateDesc& b = bwd[size_t(l)];
+        b = fwd[size_t(l)];
+        const int D = 1 << b.k;
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) b.m[size_t(r * D + c)] = std::conj(fwd[size_t(l)].m[size_t(c * D + r)]);
+        if (g->param >= 0) {
+            gen[size_t(l)] = fwd[size_t(l)];
+            gen[size_t(l)].m = pauli_matrix(g->gen, g->k);
+            slot[size_t(l)] = n_slots++;
+        }
+    }
+    PauliGroups pg;
+    DIAQ_TRY(make_pauli_groups(n_qubits, n_terms, xmask, zmask, coeff, true, &pg));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // partial sums: energy row, then one row per parametric gate
+    int P = inner_partials(n_qubits);
+    for (int l = 0; l < n_gates; ++l)
+        if (slot[size_t(l)] >= 0) P = std::max(P, adjoint_partials(n_qubits, dtype, fwd[size_t(l)].k));
+    const int rows = 1 + n_slots;
+    double* d = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (size_t(rows) * P + rows), s);
+    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(adjoint partials): %s", cudaGetErrorString(e));
+    DIAQ_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t(rows) * P + rows), s));
+    DIAQ_CUDA(cudaMemcpyAsync(work_psi, psi0, bytes, cudaMemcpyDeviceToDevice, s));
+    for (int l = 0; l < n_gates; ++l)
+        DIAQ_TRY(launch_gate_local(n_qubits, dtype, fwd[size_t(l)], nullptr, work_psi, work_psi, s));
+    DIAQ_TRY(run_pauli_apply(work_psi, work_lam, n_qubits, dtype, pg, s));
+    const int Pe = inner_partials(n_qubits);
+    DIAQ_TRY(launch_inner_re(work_psi, work_lam, n_qubits, dtype, d, Pe, s));
+    for (int l = n_gates - 1; l >= 0; --l) {
+        const int sl = slot[size_t(l)];
+        const int Pl = adjoint_partials(n_qubits, dtype, fwd[size_t(l)].k);
+        DIAQ_TRY(launch_adjoint_step(n_qubits, dtype, bwd[size_t(l)], sl >= 0 ? &gen[size_t(l)] : nullptr, work_psi,
+                                     work_lam, sl >= 0 ? d + size_t(1 + sl) * P : nullptr, Pl, s));
+    }
+    // row sums (rows have at most P used columns; unused are zero)
+    DIAQ_TRY(launch_sum_rows(d, rows, P, d + size_t(rows) * P, s));
+    std::vector<double> res(static_cast<size_t>(rows));
+    DIAQ_CUDA(cudaMemcpyAsync(res.data(), d + size_t(rows) * P, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+    DIAQ_CUDA(cudaFreeAsync(d, s));
+    DIAQ_CUDA(cudaStreamSynchronize(s));
+    if (energy) *energy = res[0];
+    if (grad) {
+        for (int p = 0; p < n_params; ++p) grad[p] = 0.0;
+        for (int l = 0; l < n_gates; ++l)
+            if (slot[size_t(l)] >= 0) grad[gates[l].param] += gates[l].scale * res[size_t(1 + slot[size_t(l)])];
+    }
+    return DIAQ_OK;
+}
+
+}  // extern "C"

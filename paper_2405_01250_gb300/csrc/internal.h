@@ -1,0 +1,146 @@
+// Internal declarations shared by the host code and the CUDA kernels of
+// libdiaq_gb300. Not part of the public ABI (see include/diaq.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "diaq.h"
+
+namespace diaq {
+
+using cplx = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// Errors: thread-local message, status codes, CUDA checks.
+// ---------------------------------------------------------------------------
+diaq_status fail(diaq_status s, const char* fmt, ...);
+void clear_error();
+diaq_status cuda_fail(cudaError_t e, const char* what);
+
+#define DIAQ_CUDA(expr)                                                    \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return ::diaq::cuda_fail(e__, #expr);      \
+    } while (0)
+
+// Before a kernel launch: an error left by an earlier runtime call (ours or
+// the host application's) would otherwise be reported by the launch check.
+#define DIAQ_PRELAUNCH(name)                                               \
+    do {                                                                   \
+        cudaError_t e__ = cudaGetLastError();                              \
+        if (e__ != cudaSuccess) return ::diaq::cuda_fail(e__, "an earlier CUDA call (pending before launch of " name ")"); \
+    } while (0)
+
+#define DIAQ_TRY(expr)                                                     \
+    do {                                                                   \
+        diaq_status s__ = (expr);                                          \
+        if (s__ != DIAQ_OK) return s__;                                    \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Entry types of a local gate matrix. The kernels branch on them uniformly
+// (every thread of a launch sees the same matrix), so a diagonal, permutation
+// or real gate pays no FP64 work for its zero, unit or imaginary parts.
+// ---------------------------------------------------------------------------
+enum EntryType : uint8_t { ET_ZERO = 0, ET_ONE = 1, ET_REAL = 2, ET_IMAG = 3, ET_GENERAL = 4 };
+
+uint8_t entry_type(cplx v);
+
+// Host description of a gate-structured operator: k targets (targets[0] is
+// the most significant local bit) and its 2^k x 2^k local matrix.
+struct GateDesc {
+    int k = 0;
+    int targets[DIAQ_MAX_K] = {0};
+    std::vector<cplx> m;  // row-major, 4^k entries
+};
+
+// Local matrix of a public gate (fixed or parametric).
+diaq_status gate_desc_from(const diaq_gate* g, int n_qubits, const double* theta, GateDesc* out);
+// Pauli string matrix of a parametric gate's generator on its targets.
+std::vector<cplx> pauli_matrix(const char* gen, int k);
+// Structural class of a local matrix.
+int classify(const std::vector<cplx>& m, int k);
+// Full-system offsets of a local matrix on its targets (ascending).
+std::vector<int64_t> full_offsets(const GateDesc& g, const std::vector<uint8_t>* pattern);
+
+// ---------------------------------------------------------------------------
+// Ops
+// ---------------------------------------------------------------------------
+}  // namespace diaq
+
+struct diaq_op_s {
+    int n = 0;
+    diaq_dtype dtype = DIAQ_C128;
+    diaq_variant variant = DIAQ_ONTHEFLY;
+    int op_class = DIAQ_CLASS_GENERAL;
+    int device = 0;
+    diaq::GateDesc gate;                 // valid unless op_class == RAW
+    std::vector<int64_t> offsets;        // full-system diagonal indices, ascending
+    // stored variant
+    void* d_values = nullptr;            // concatenated diagonals (dtype)
+    int64_t* d_offsets = nullptr;        // device copy of offsets
+    int64_t* d_starts = nullptr;         // element start of each diagonal
+    std::vector<int64_t> starts;         // host copy of d_starts
+    int64_t stored_elems = 0;
+    // device copy of the local matrix for k > 3 (dtype complex, then types)
+    void* d_matrix = nullptr;
+};
+
+namespace diaq {
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (apply.cu, reduce.cu, adjoint.cu)
+// ---------------------------------------------------------------------------
+inline size_t amp_bytes(diaq_dtype dt) { return dt == DIAQ_C128 ? 16 : 8; }
+
+// Launch tuning knobs, filled by the autotuner (defaults otherwise).
+struct LaunchCfg {
+    int threads = 256;     // threads per block
+    int groups = 0;        // groups (target subspaces) per thread; 0 = default for k
+};
+LaunchCfg& launch_cfg(diaq_dtype dt, int k);
+
+diaq_status launch_onthefly(const diaq_op_s* op, const void* x, void* y, cudaStream_t s);
+diaq_status launch_gate_local(int n, diaq_dtype dt, const GateDesc& g, const void* d_matrix,
+                              const void* x, void* y, cudaStream_t s);
+diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStream_t s);
+diaq_status launch_materialise(diaq_op_s* op, cudaStream_t s);
+diaq_status launch_raw_upload(diaq_op_s* op, const double* host_values, cudaStream_t s);
+diaq_status launch_spgemm(const diaq_op_s* a, const diaq_op_s* b, diaq_op_s* c, cudaStream_t s);
+diaq_status upload_matrix(diaq_op_s* op);
+
+// Pauli-sum terms grouped by X mask, prepared on the host.
+struct PauliGroups {
+    std::vector<uint64_t> xmask;         // one per group
+    std::vector<int32_t> first;          // first term of each group (size groups+1)
+    std::vector<uint64_t> zmask;         // per term
+    std::vector<double> kappa;           // per term: c_t * i^{#Y}, interleaved complex
+};
+diaq_status make_pauli_groups(int n_qubits, int n_terms, const uint64_t* xm, const uint64_t* zm,
+                              const double* coeff, bool real_only, PauliGroups* out);
+
+// sum_i conj(psi[i ^ x_g]) psi[i] W_g(i) (complex, FP64) -> host out[2].
+diaq_status run_expect(const void* psi, int n, diaq_dtype dt, const PauliGroups& pg, double* out,
+                       cudaStream_t s);
+diaq_status run_pauli_apply(const void* psi, void* lam, int n, diaq_dtype dt, const PauliGroups& pg,
+                            cudaStream_t s);
+diaq_status run_norm(const void* psi, int n, diaq_dtype dt, double* out, cudaStream_t s);
+
+// Adjoint reverse step for one gate: optional gradient partial
+// Im <lam|P|psi> into partial[blockIdx] and, then, psi <- U^dag psi,
+// lam <- U^dag lam in place.
+diaq_status launch_adjoint_step(int n, diaq_dtype dt, const GateDesc& udag, const GateDesc* pauli,
+                                void* psi, void* lam, double* partials, int n_partials,
+                                cudaStream_t s);
+int adjoint_partials(int n, diaq_dtype dt, int k);
+diaq_status launch_sum_rows(const double* partials, int rows, int cols, double* out, cudaStream_t s);
+diaq_status launch_inner_re(const void* a, const void* b, int n, diaq_dtype dt, double* partials,
+                            int n_partials, cudaStream_t s);
+int inner_partials(int n);
+
+}  // namespace diaq

@@ -1,0 +1,153 @@
+"""C-ABI checks that need no GPU: the library loads and exports every symbol
+include/diaq.h declares, and the host parts of the path (builder offsets,
+Algorithm 1 product, gate fusion, argument validation) agree with the
+oracle."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+RNG = np.random.default_rng(77)
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2405_01250_gb300 import build as B
+    B.build()
+    from paper_2405_01250_gb300 import api as A
+    return A
+
+
+def _header_functions():
+    txt = open(os.path.join(ROOT, "include", "diaq.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(diaq_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(api):
+    from paper_2405_01250_gb300 import _native
+    names = _header_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(_native.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(_native.SIGNATURES), "binding and header disagree"
+    assert "sm_103a" in api.version()
+
+
+@pytest.mark.parametrize("n,k", [(3, 1), (6, 2), (8, 3), (5, 2)])
+def test_gate_offsets_match_oracle(api, n, k):
+    for kind in ("dense", "sparse", "perm", "diag", "monomial"):
+        t = [int(q) for q in RNG.choice(n, size=k, replace=False)]
+        m = synth.random_gate(k, RNG, kind)
+        got = api.gate_offsets(synth.Gate(tuple(t), m), n)
+        want, _ = oracle.gate_diaq(n, t, m)
+        assert list(got) == list(want), (kind, t)
+
+
+def test_gate_offsets_paper_patterns(api):
+    # Fig. 3: single H in a 4-qubit circuit; Section III-A: Z is the principal diagonal
+    for q, below in ((3, 8), (2, 4), (1, 2), (0, 1)):
+        assert list(api.gate_offsets(synth.Gate((q,), synth.H), 4)) == [-below, 0, below]
+        assert list(api.gate_offsets(synth.Gate((q,), np.diag([1, -1]).astype(complex)), 4)) == [0]
+    # CNOT chain of GHZ-12: offsets 0, +-2^(k+1)
+    for k in range(11):
+        assert list(api.gate_offsets(synth.Gate((k, k + 1), synth.CNOT), 12)) == [-(2 << k), 0, 2 << k]
+    # parametric gates: structure of I and the generator, independent of theta
+    g = synth.Gate((2, 5), None, param=0, gen="ZZ")
+    assert list(api.gate_offsets(g, 6)) == [0]
+    g = synth.Gate((3,), None, param=0, gen="Y")
+    assert list(api.gate_offsets(g, 6)) == [-8, 0, 8]
+
+
+def _dense_from(N, idx, vals):
+    A = np.zeros((N, N), dtype=np.complex128)
+    for d, v in zip(idx, vals):
+        r0, c0 = max(0, -int(d)), max(0, int(d))
+        t = np.arange(len(v))
+        A[r0 + t, c0 + t] = v
+    return A
+
+
+def test_algorithm1_product_matches_dense(api):
+    for N in (1, 5, 16, 33):
+        A = RNG.standard_normal((N, N)) + 1j * RNG.standard_normal((N, N))
+        B = RNG.standard_normal((N, N)) + 1j * RNG.standard_normal((N, N))
+        A *= RNG.random((N, N)) < 0.2
+        B *= RNG.random((N, N)) < 0.2
+        ai, av = oracle.dense_to_diaq(A)
+        bi, bv = oracle.dense_to_diaq(B)
+        ci, cv = api.diaq_matmul_host(N, ai, av, bi, bv)
+        assert list(ci) == sorted(ci)
+        np.testing.assert_allclose(_dense_from(N, ci, cv), A @ B, atol=1e-12)
+
+
+def test_algorithm1_accumulates_coinciding_diagonals(api):
+    """H * H: three (a, b) pairs meet on index 0. Overwriting (a literal
+    reading of the listing) would not give the identity."""
+    ai, av = oracle.dense_to_diaq(synth.H)
+    ci, cv = api.diaq_matmul_host(2, ai, av, ai, av)
+    np.testing.assert_allclose(_dense_from(2, ci, cv), np.eye(2), atol=1e-15)
+
+
+def test_fuse_gates_host_matches_oracle(api):
+    n = 8
+    for trial in range(6):
+        gates = []
+        for _ in range(int(RNG.integers(1, 5))):
+            k = int(RNG.integers(1, 3))
+            t = tuple(int(q) for q in RNG.choice(n, size=k, replace=False))
+            gates.append(synth.Gate(t, synth.random_gate(k, RNG, ["dense", "diag", "perm"][trial % 3])))
+        union = []
+        for g in gates:
+            for q in g.targets:
+                if q not in union:
+                    union.append(q)
+        if len(union) > 6:
+            continue
+        ut, F = api.fuse_gates_host(gates)
+        uo, Fo = oracle.fuse([(g.targets, g.matrix) for g in gates])
+        assert tuple(ut) == tuple(uo)
+        np.testing.assert_allclose(F, Fo, atol=1e-13)
+
+
+def test_fuse_gates_host_parametric(api):
+    th = np.array([0.7, -1.3])
+    gates = [synth.Gate((0,), None, param=0, gen="Y"), synth.Gate((0, 1), None, param=1, gen="ZZ", scale=2.0)]
+    ut, F = api.fuse_gates_host(gates, th)
+    _, Fo = oracle.fuse([(g.targets, oracle.gate_matrix(g, th)) for g in gates])
+    np.testing.assert_allclose(F, Fo, atol=1e-14)
+
+
+def test_argument_validation_without_gpu(api):
+    from paper_2405_01250_gb300._native import DiaqError
+    with pytest.raises(DiaqError, match="ERR_ARG"):
+        api.gate_offsets(synth.Gate((1, 1), synth.CNOT), 4)     # repeated target
+    with pytest.raises(DiaqError, match="ERR_ARG"):
+        api.gate_offsets(synth.Gate((4,), synth.H), 4)          # target outside register
+    with pytest.raises(DiaqError, match="ERR_SHAPE"):
+        api.gate_offsets(synth.Gate((0, 1, 2), synth.random_gate(3, RNG)), 2)  # k > n
+    with pytest.raises(DiaqError, match="ERR_ARG"):
+        api.gate_offsets(synth.Gate((0,), None, param=0, gen="Q"), 3)  # bad generator letter
+    with pytest.raises(DiaqError, match="ERR_SHAPE"):
+        api.diaq_matmul_host(4, [5], [np.zeros(1)], [0], [np.ones(4)])  # index outside the matrix
+    with pytest.raises(DiaqError, match="ERR_UNSUPPORTED"):
+        api.fuse_gates_host([synth.Gate((q,), synth.H) for q in range(7)])
+
+
+def test_device_entry_points_fail_loudly_without_gpu(api):
+    """On a machine with no GPU the device path reports an error; it never
+    falls back to a CPU computation."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2405_01250_gb300._native import DiaqError
+    with pytest.raises(DiaqError):
+        api.build(synth.Gate((0,), synth.H), 4, stream=0)

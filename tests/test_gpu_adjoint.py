@@ -1,0 +1,115 @@
+"""GPU parity of the adjoint gradient (energy and dE/dtheta for every
+parameter in one sweep) against the oracle's parameter-shift gradient and
+central finite differences; the autograd binding."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2405_01250_gb300 import build as B
+    B.build()
+    from paper_2405_01250_gb300 import api as A
+    return A
+
+
+def _run(api, circ, obs, n, dtype=torch.complex128, theta=None):
+    p0 = torch.zeros(1 << n, dtype=dtype, device="cuda")
+    p0[0] = 1
+    th = circ.theta if theta is None else theta
+    return api.adjoint_grad(circ.gates, th, obs.xmask, obs.zmask, obs.coeff, p0, torch.empty_like(p0),
+                            torch.empty_like(p0))
+
+
+@pytest.mark.parametrize("n,layers", [(2, 1), (5, 2), (8, 2)])
+def test_ansatz_gradient_c128(api, n, layers):
+    circ = synth.ansatz(n=n, layers=layers, seed=n)
+    obs = synth.ansatz_observable(n)
+    e, g = _run(api, circ, obs, n)
+    psi0 = synth.basis_state(n, 0)
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= 1e-12
+    g_ps = oracle.param_shift_grad(circ, obs, psi0)
+    assert np.max(np.abs(g - g_ps)) <= 1e-10
+    g_fd = oracle.fd_grad(circ, obs, psi0, h=1e-4)
+    assert np.max(np.abs(g - g_fd)) <= 1e-6
+
+
+def test_ansatz_gradient_c64(api):
+    n = 8
+    circ = synth.ansatz(n=n, layers=2, seed=3)
+    obs = synth.ansatz_observable(n)
+    e, g = _run(api, circ, obs, n, dtype=torch.complex64)
+    psi0 = synth.basis_state(n, 0)
+    g_ps = oracle.param_shift_grad(circ, obs, psi0)
+    # FP32 state, FP64 accumulation: error grows with depth; bound from the
+    # state error (~ gates * 2^-24 * sum|c|)
+    bound = len(circ.gates) * 2.0 ** -24 * float(np.sum(np.abs(obs.coeff))) * 8
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= bound
+    assert np.max(np.abs(g - g_ps)) <= bound
+
+
+def test_qaoa_shared_parameters(api):
+    circ, obs = synth.qaoa_instance(8, np.random.default_rng(4), p=2)
+    e, g = _run(api, circ, obs, 8)
+    psi0 = synth.basis_state(8, 0)
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= 1e-12
+    assert np.max(np.abs(g - oracle.param_shift_grad(circ, obs, psi0))) <= 1e-10
+
+
+def test_scaled_and_multi_qubit_generators(api):
+    n = 5
+    rng = np.random.default_rng(8)
+    gates = [synth.Gate((q,), synth.H) for q in range(n)]
+    gates += [synth.Gate((0, 3), None, param=0, gen="XY", scale=0.5),
+              synth.Gate((4, 1, 2), None, param=1, gen="ZXY", scale=-1.5),
+              synth.Gate((2,), synth.haar_u2(rng)),
+              synth.Gate((1, 4), None, param=0, gen="YY", scale=2.0)]
+    circ = synth.Circuit(n, gates, theta=rng.uniform(0, 2 * np.pi, 2))
+    obs = synth.Observable(np.array([0b10101, 0, 3], np.uint64), np.array([0b00110, 0b11000, 1], np.uint64),
+                           np.array([0.7, -1.1, 0.4]))
+    e, g = _run(api, circ, obs, n)
+    psi0 = synth.basis_state(n, 0)
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= 1e-12
+    assert np.max(np.abs(g - oracle.param_shift_grad(circ, obs, psi0))) <= 1e-10
+
+
+def test_ansatz20_sampled_parameters(api):
+    """Full-size ansatz (20 qubits, 8 layers, 320 parameters): the adjoint
+    gradient on sampled parameters against parameter shift."""
+    n = 20
+    circ = synth.ansatz(n=n, layers=8, seed=0)
+    obs = synth.ansatz_observable(n)
+    e, g = _run(api, circ, obs, n)
+    psi0 = synth.basis_state(n, 0)
+    sample = [0, 1, 157, 319]
+    g_ps = oracle.param_shift_grad(circ, obs, psi0, params=sample)
+    assert np.max(np.abs(g[sample] - g_ps[sample])) <= 1e-10
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= 1e-11
+
+
+def test_autograd_function(api):
+    n = 4
+    circ = synth.ansatz(n=n, layers=1, seed=9)
+    obs = synth.ansatz_observable(n)
+    theta = torch.tensor(circ.theta, dtype=torch.float64, requires_grad=True)
+    p0 = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    p0[0] = 1
+    E = api.DiaqEnergy.apply(theta, circ.gates, (obs.xmask, obs.zmask, obs.coeff), p0)
+    (2.0 * E).backward()
+    g_ps = oracle.param_shift_grad(circ, obs, synth.basis_state(n, 0))
+    assert np.max(np.abs(theta.grad.numpy() - 2 * g_ps)) <= 1e-10
+
+
+def test_empty_circuit_and_no_params(api):
+    n = 3
+    obs = synth.Observable(np.array([0], np.uint64), np.array([1], np.uint64), np.array([1.0]))
+    circ = synth.Circuit(n, [], theta=np.zeros(0))
+    e, g = _run(api, circ, obs, n)
+    assert e == 1.0 and len(g) == 0
