@@ -258,6 +258,38 @@ diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const dou
                               void* work_psi, void* work_lam, int32_t n_qubits, diaq_dtype dtype,
                               double* energy, double* grad, diaq_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free norm (the paper has no counterpart: this is a deployment
+ * variant of diaq_norm).
+ * ------------------------------------------------------------------------ */
+
+/* Size, in doubles, of the fixed scratch array behind diaq_norm_noalloc
+ * (32 KiB, resident on every device that loads the library until exit). */
+#define DIAQ_NOALLOC_SCRATCH_DOUBLES 4096
+
+/* ||psi||^2 into *out (host), the same value as diaq_norm, computed without
+ * allocating memory: no cudaMalloc, cudaMallocAsync or cudaFree. It is for
+ * callers that cannot allocate device memory - an application whose memory
+ * manager owns the whole device heap, or a latency-critical loop that must
+ * not pay for allocation - and keeps its partial sums in a fixed array
+ * compiled into the library instead.
+ *
+ * Limit: the reduction uses min(ceil(N / 1024), 8 x SM count) blocks and
+ * needs one double per block plus one; if that exceeds
+ * DIAQ_NOALLOC_SCRATCH_DOUBLES the call returns DIAQ_ERR_UNSUPPORTED
+ * (only on devices with more than 511 SMs).
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Sharing: all calls on a device use the same
+ * array, which keeps the last call's contents; every slot a call reads it
+ * has written itself, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (different streams, or host threads racing on one
+ * device) race on the array and must be serialised by the caller.
+ * Synchronises `stream` before returning. */
+diaq_status diaq_norm_noalloc(const void* psi, int32_t n_qubits, diaq_dtype dtype, double* out,
+                              diaq_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
