@@ -259,6 +259,119 @@ diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const dou
                               double* energy, double* grad, diaq_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuning and fusion planning (not in the paper; the paper fuses gates
+ * with spGEMM, Section VI, but gives no rule for which to fuse).
+ * ------------------------------------------------------------------------ */
+
+#define DIAQ_APPLY_TUNE_MAX 27
+#define DIAQ_FUSION_TUNE_MAX 8
+
+typedef struct {
+    int32_t n_rows;                     /* rows filled below */
+    int32_t k[DIAQ_APPLY_TUNE_MAX];
+    int32_t threads[DIAQ_APPLY_TUNE_MAX];
+    int32_t groups[DIAQ_APPLY_TUNE_MAX];
+    float ms[DIAQ_APPLY_TUNE_MAX];
+    int32_t best_threads[3];            /* per k = 1, 2, 3 */
+    int32_t best_groups[3];
+    float best_ms[3];
+} diaq_apply_tuning;
+
+typedef struct {
+    int32_t n_depths;
+    int32_t ops[DIAQ_FUSION_TUNE_MAX];  /* fused ops at depth d+1 */
+    float ms[DIAQ_FUSION_TUNE_MAX];     /* one pass of the circuit */
+    int32_t best_depth;
+} diaq_fusion_tuning;
+
+/* Time the on-the-fly kernel for k = 1, 2, 3 (a real butterfly, a
+ * controlled phase and a dense gate on the top qubits of an n_qubits state)
+ * over threads per block in {64, 128, 256} x groups per thread in
+ * {1, 2, 4}, using the caller's distinct device buffers x and y (contents
+ * overwritten), and keep the fastest shape per (dtype, k) for all later
+ * launches in this process. report may be NULL. */
+diaq_status diaq_autotune_apply(int32_t n_qubits, diaq_dtype dtype, void* x, void* y, int32_t reps,
+                                diaq_apply_tuning* report, diaq_stream_t stream);
+
+/* Set the launch shape of the on-the-fly kernel for (dtype, k), k in 1..3:
+ * threads a multiple of 32 in [32, 256], groups in {1, 2, 4}, or 0 for the
+ * built-in default of k. Process-wide. */
+diaq_status diaq_set_apply_launch(diaq_dtype dtype, int32_t k, int32_t threads, int32_t groups);
+
+/* Group consecutive gates for fusion: a group grows while the union of its
+ * targets has at most max_k qubits and it holds at most max_depth gates.
+ * Writes the group index of each gate (non-decreasing, from 0) and the group
+ * count. Host only. */
+diaq_status diaq_plan_fusion(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
+                             int32_t* group_of_gate, int32_t* n_groups);
+
+/* For each fusion depth 1..max_depth: plan, build and fuse the circuit's
+ * on-the-fly ops and time one in-place pass over the device state `work`
+ * (contents overwritten); report the times and the fastest depth. */
+diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
+                                 diaq_dtype dtype, void* work, int32_t max_k, int32_t max_depth,
+                                 diaq_fusion_tuning* report, diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched energies and gradients (not in the paper). Many circuits of
+ * uneven qubit counts run in one persistent launch replayed from a CUDA
+ * graph: every circuit starts from |0...0>, applies its gates (k <= 2),
+ * forms E = <psi|H|psi> and runs the adjoint sweep of diaq_adjoint_grad.
+ * ------------------------------------------------------------------------ */
+
+typedef struct diaq_batch_s* diaq_batch_t;
+
+#define DIAQ_BATCH_TUNE_MAX 12
+
+/* Launch shapes the autotuner timed and the one it kept. */
+typedef struct {
+    int32_t n_tried;
+    int32_t cluster[DIAQ_BATCH_TUNE_MAX];
+    int32_t threads[DIAQ_BATCH_TUNE_MAX];
+    float ms[DIAQ_BATCH_TUNE_MAX];
+    int32_t best_cluster;
+    int32_t best_threads;
+    float best_ms;
+} diaq_batch_tuning;
+
+/* Build a batch of n_inst circuits (host arrays, read during the call).
+ * Circuit i has n_qubits[i] in [2, 30] qubits, the gates
+ * gates[gate_first[i] .. gate_first[i+1]) (1 or 2 targets; parametric gates
+ * index the circuit's own parameters 0 .. param_first[i+1]-param_first[i]-1),
+ * and the observable terms [term_first[i] .. term_first[i+1]) of xmask,
+ * zmask, coeff (as diaq_expect; real parts used). The three *_first arrays
+ * have n_inst + 1 entries and are non-decreasing. Allocates the device arena
+ * (two states per circuit) and captures the launch in a CUDA graph with the
+ * default shape (1 block of 256 threads per circuit team). */
+diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int32_t* gate_first,
+                              const diaq_gate* gates, const int32_t* param_first, const int32_t* term_first,
+                              const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                              diaq_dtype dtype, diaq_batch_t* out);
+
+diaq_status diaq_batch_destroy(diaq_batch_t b);
+
+/* Choose the team shape: `cluster` blocks (1, 2, 4 or 8, one thread-block
+ * cluster) of `threads` threads per circuit; recaptures the graph. */
+diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threads);
+
+/* Energies (n_inst) and gradients (param_first[n_inst] doubles, circuit i's
+ * block at param_first[i]) for the concatenated parameters theta. Host
+ * arrays; energies or grads may be NULL. Replays the graph after the work
+ * already queued on `stream` and synchronises before returning. */
+diaq_status diaq_batch_run(diaq_batch_t b, const double* theta, double* energies, double* grads,
+                           diaq_stream_t stream);
+
+/* Time every team shape (cluster in {1,2,4,8} x threads in {256,512,1024})
+ * that fits, `reps` graph replays each with theta, keep the fastest. report
+ * may be NULL. */
+diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t reps, diaq_batch_tuning* report,
+                                diaq_stream_t stream);
+
+/* Current shape, number of teams resident at once, and arena size. */
+diaq_status diaq_batch_query(diaq_batch_t b, int32_t* cluster, int32_t* threads, int32_t* teams,
+                             int64_t* arena_bytes);
+
+/* ------------------------------------------------------------------------
  * Allocation-free norm (the paper has no counterpart: this is a deployment
  * variant of diaq_norm).
  * ------------------------------------------------------------------------ */

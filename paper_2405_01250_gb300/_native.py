@@ -90,6 +90,56 @@ SIGNATURES = {
     "diaq_norm_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
 }
 
+class diaq_batch_tuning(ctypes.Structure):
+    _fields_ = [
+        ("n_tried", ctypes.c_int32),
+        ("cluster", ctypes.c_int32 * 12),
+        ("threads", ctypes.c_int32 * 12),
+        ("ms", ctypes.c_float * 12),
+        ("best_cluster", ctypes.c_int32),
+        ("best_threads", ctypes.c_int32),
+        ("best_ms", ctypes.c_float),
+    ]
+
+
+class diaq_apply_tuning(ctypes.Structure):
+    _fields_ = [
+        ("n_rows", ctypes.c_int32),
+        ("k", ctypes.c_int32 * 27),
+        ("threads", ctypes.c_int32 * 27),
+        ("groups", ctypes.c_int32 * 27),
+        ("ms", ctypes.c_float * 27),
+        ("best_threads", ctypes.c_int32 * 3),
+        ("best_groups", ctypes.c_int32 * 3),
+        ("best_ms", ctypes.c_float * 3),
+    ]
+
+
+class diaq_fusion_tuning(ctypes.Structure):
+    _fields_ = [
+        ("n_depths", ctypes.c_int32),
+        ("ops", ctypes.c_int32 * 8),
+        ("ms", ctypes.c_float * 8),
+        ("best_depth", ctypes.c_int32),
+    ]
+
+
+SIGNATURES.update({
+    "diaq_autotune_apply": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int, _vp, _vp, ctypes.c_int32,
+                                           ctypes.POINTER(diaq_apply_tuning), _vp]),
+    "diaq_set_apply_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "diaq_plan_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
+    "diaq_autotune_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, _vp,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(diaq_fusion_tuning), _vp]),
+    "diaq_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _gp, _i32p, _i32p, _u64p, _u64p, _dp,
+                                         ctypes.c_int, ctypes.POINTER(_vp)]),
+    "diaq_batch_destroy": (ctypes.c_int, [_vp]),
+    "diaq_batch_set_launch": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "diaq_batch_run": (ctypes.c_int, [_vp, _dp, _dp, _dp, _vp]),
+    "diaq_batch_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.POINTER(diaq_batch_tuning), _vp]),
+    "diaq_batch_query": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i64p]),
+})
+
 _LIB = None
 
 

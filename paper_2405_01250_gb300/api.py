@@ -22,7 +22,8 @@ from ._native import DiaqError, check, lib  # noqa: F401
 __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
-    "DiaqError", "DiaqEnergy",
+    "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
+    "build_fused",
 ]
 
 
@@ -318,6 +319,141 @@ def fuse_gates_host(gates, theta=None) -> tuple:
     m = fm[: 2 * (1 << (2 * K))].view(np.complex128).reshape(1 << K, 1 << K).copy()
     del keep
     return tuple(ut[a] for a in range(K)), m
+
+
+def autotune_apply(n_qubits: int, x: torch.Tensor, y: torch.Tensor, reps: int = 3, stream=None) -> dict:
+    """Pick the on-the-fly launch shape per k (process-wide) by timing."""
+    _check_state(x, "x")
+    _check_state(y, "y")
+    rep = N.diaq_apply_tuning()
+    check(lib().diaq_autotune_apply(int(n_qubits), _dtype_code(x.dtype), ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(y.data_ptr()), int(reps), ctypes.byref(rep), _stream(stream)))
+    return {"rows": [(rep.k[i], rep.threads[i], rep.groups[i], rep.ms[i]) for i in range(rep.n_rows)],
+            "best": {k + 1: (rep.best_threads[k], rep.best_groups[k], rep.best_ms[k]) for k in range(3)}}
+
+
+def set_apply_launch(dtype, k: int, threads: int, groups: int) -> None:
+    check(lib().diaq_set_apply_launch(_dtype_code(dtype), int(k), int(threads), int(groups)))
+
+
+def plan_fusion(gates, max_k: int, max_depth: int) -> list:
+    """Group index of each gate for fusion (consecutive groups)."""
+    arr, keep = _gate_array(gates)
+    out = np.zeros(max(1, len(gates)), dtype=np.int32)
+    ng = ctypes.c_int32(0)
+    check(lib().diaq_plan_fusion(arr, len(gates), int(max_k), int(max_depth), out.ctypes.data_as(N._i32p),
+                                 ctypes.byref(ng)))
+    del keep
+    return out[:len(gates)].tolist()
+
+
+def build_fused(gates, n_qubits: int, max_k: int, max_depth: int, dtype=torch.complex128, variant="onthefly",
+                theta=None, stream=None) -> list:
+    """Ops for a circuit with consecutive gates fused per plan_fusion."""
+    grp = plan_fusion(gates, max_k, max_depth)
+    ops, i = [], 0
+    while i < len(gates):
+        j = i
+        while j < len(gates) and grp[j] == grp[i]:
+            j += 1
+        part = [build(g, n_qubits, dtype=dtype, variant="onthefly", theta=theta, stream=stream) for g in gates[i:j]]
+        if len(part) == 1 and variant == "onthefly":
+            ops.append(part[0])
+        else:
+            ops.append(fuse(part, variant=variant, stream=stream))
+        i = j
+    return ops
+
+
+def autotune_fusion(gates, n_qubits: int, work: torch.Tensor, max_k: int = 4, max_depth: int = 4, theta=None,
+                    stream=None) -> dict:
+    _check_state(work, "work")
+    arr, keep = _gate_array(gates)
+    th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    rep = N.diaq_fusion_tuning()
+    check(lib().diaq_autotune_fusion(arr, len(gates), _dptr(th) if th is not None else None, int(n_qubits),
+                                     _dtype_code(work.dtype), ctypes.c_void_p(work.data_ptr()), int(max_k),
+                                     int(max_depth), ctypes.byref(rep), _stream(stream)))
+    del keep
+    return {"ops": [rep.ops[d] for d in range(rep.n_depths)], "ms": [rep.ms[d] for d in range(rep.n_depths)],
+            "best_depth": rep.best_depth}
+
+
+class Batch:
+    """Energies and adjoint gradients of many circuits (uneven qubit counts)
+    in one persistent launch replayed from a CUDA graph (diaq_batch_*).
+
+    instances: list of (n_qubits, gates, n_params, (xmask, zmask, coeff));
+    every circuit starts from |0...0>."""
+
+    def __init__(self, instances, dtype=torch.complex128):
+        nq, gfirst, pfirst, tfirst = [], [0], [0], [0]
+        gates, xs, zs, cs = [], [], [], []
+        for n, gl, npar, (xm, zm, co) in instances:
+            nq.append(int(n))
+            gates.extend(gl)
+            gfirst.append(len(gates))
+            pfirst.append(pfirst[-1] + int(npar))
+            x, z, c = _terms(xm, zm, co)
+            xs.append(x)
+            zs.append(z)
+            cs.append(c)
+            tfirst.append(tfirst[-1] + len(x))
+        self.n_inst = len(nq)
+        self.param_first = list(pfirst)
+        arr, keep = _gate_array(gates)
+        i32 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.int32))  # noqa: E731
+        nq_a, gf_a, pf_a, tf_a = i32(nq), i32(gfirst), i32(pfirst), i32(tfirst)
+        xm = np.ascontiguousarray(np.concatenate(xs) if xs else np.zeros(0, np.uint64))
+        zm = np.ascontiguousarray(np.concatenate(zs) if zs else np.zeros(0, np.uint64))
+        co = np.ascontiguousarray(np.concatenate(cs) if cs else np.zeros(0, np.complex128))
+        h = ctypes.c_void_p(0)
+        p32 = N._i32p
+        check(lib().diaq_batch_create(self.n_inst, nq_a.ctypes.data_as(p32), gf_a.ctypes.data_as(p32), arr,
+                                      pf_a.ctypes.data_as(p32), tf_a.ctypes.data_as(p32),
+                                      xm.ctypes.data_as(N._u64p), zm.ctypes.data_as(N._u64p),
+                                      _dptr(co.view(np.float64)) if len(co) else None, _dtype_code(dtype),
+                                      ctypes.byref(h)))
+        del keep
+        self.handle = h
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().diaq_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = ctypes.c_void_p(0)
+
+    def close(self):
+        self.__del__()
+
+    def run(self, theta, stream=None) -> tuple:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        if len(th) != self.param_first[-1]:
+            raise ValueError(f"theta has {len(th)} values, the batch has {self.param_first[-1]} parameters")
+        e = np.zeros(self.n_inst)
+        g = np.zeros(max(1, len(th)))
+        check(lib().diaq_batch_run(self.handle, _dptr(th) if len(th) else None, _dptr(e), _dptr(g), _stream(stream)))
+        return e, [g[self.param_first[i]:self.param_first[i + 1]].copy() for i in range(self.n_inst)]
+
+    def set_launch(self, cluster: int, threads: int):
+        check(lib().diaq_batch_set_launch(self.handle, int(cluster), int(threads)))
+
+    def autotune(self, theta, reps: int = 2, stream=None) -> dict:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        rep = N.diaq_batch_tuning()
+        check(lib().diaq_batch_autotune(self.handle, _dptr(th) if len(th) else None, int(reps), ctypes.byref(rep),
+                                        _stream(stream)))
+        return {"tried": [(rep.cluster[i], rep.threads[i], rep.ms[i]) for i in range(rep.n_tried)],
+                "best_cluster": rep.best_cluster, "best_threads": rep.best_threads, "best_ms": rep.best_ms}
+
+    def query(self) -> dict:
+        c, t, tm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ab = ctypes.c_int64()
+        check(lib().diaq_batch_query(self.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(tm), ctypes.byref(ab)))
+        return {"cluster": c.value, "threads": t.value, "teams": tm.value, "arena_bytes": ab.value}
 
 
 class DiaqEnergy(torch.autograd.Function):

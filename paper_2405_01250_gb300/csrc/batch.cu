@@ -1,0 +1,793 @@
+// Batched energies and adjoint gradients: many circuits of uneven qubit
+// counts in one persistent launch, replayed from a CUDA graph.
+//
+// Each circuit ("instance") is processed by a team of C thread blocks that
+// form one thread-block cluster. A team runs the instance's whole adjoint
+// computation (forward sweep, lambda = H psi with the energy, reverse sweep
+// with the per-gate gradient partials) on the instance's own two state
+// buffers in the arena; between gates the team meets at the hardware
+// cluster barrier, so no block ever spins on a flag. Teams take instances
+// from a static schedule computed on the host (largest first, round robin
+// over teams), so the grid is sized to the teams that fit on the GPU at once
+// and every team works until its list is done. A second small kernel sums
+// the per-block partials of every instance in a fixed order.
+//
+// Gates have k <= 2 targets; a parametric gate is exp(-i a/2 P) with
+// a = scale * theta[param] and P a Pauli string, built on the device from
+// the instance's parameters so one captured graph serves every theta.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace diaq {
+
+// ---------------------------------------------------------------------------
+// Device records
+// ---------------------------------------------------------------------------
+struct BGate {
+    int32_t k;          // 1 or 2
+    int32_t t[2];       // targets, t[0] most significant local bit
+    int32_t param;      // -1 fixed
+    int32_t pauli[2];   // generator letters 0=I 1=X 2=Y 3=Z (parametric)
+    int32_t slot;       // partial-sum row of a parametric gate (instance relative), else -1
+    int32_t pad;
+    double scale;
+    double re[16], im[16];  // fixed gate matrix (row-major, 2^k x 2^k)
+};
+
+struct BInst {
+    int32_t n;
+    int32_t gate_begin, gate_end;
+    int32_t param_begin, n_params;
+    int32_t term_begin, term_end;
+    int32_t n_slots;         // 1 (energy) + parametric gates
+    int64_t psi_off, lam_off;  // amplitude offsets in the arena
+    int64_t part_off;        // first partial (doubles), rows of C columns
+};
+
+struct BTerm {
+    uint64_t x, z;
+    double kr, ki;  // coefficient times i^{#Y}
+};
+
+struct BatchArgs {
+    const BInst* inst;
+    const BGate* gates;
+    const BTerm* terms;
+    const int32_t* sched;      // instance ids, team-major: sched[team_first[c] .. team_first[c+1])
+    const int32_t* team_first;
+    const double* theta;
+    void* arena;
+    double* partials;
+    int C;                     // blocks per team (cluster size)
+};
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pauli2(int letter, int r, int c, double* re, double* im) {
+    // single-qubit Pauli element <r|sigma|c>
+    *re = 0.0;
+    *im = 0.0;
+    switch (letter) {
+        case 0: *re = (r == c) ? 1.0 : 0.0; break;
+        case 1: *re = (r != c) ? 1.0 : 0.0; break;
+        case 2: if (r != c) *im = (r == 0) ? -1.0 : 1.0; break;
+        default: if (r == c) *re = (r == 0) ? 1.0 : -1.0; break;
+    }
+}
+
+__device__ __forceinline__ uint8_t dev_entry_type(double re, double im) {
+    if (re == 0.0 && im == 0.0) return 0;
+    if (im == 0.0) return re == 1.0 ? 1 : 2;
+    if (re == 0.0) return 3;
+    return 4;
+}
+
+// Shared-memory gate matrices of the current step, written by thread 0.
+template <typename R>
+struct StepMats {
+    R ure[16], uim[16];
+    uint8_t uty[16];
+    R pre[16], pim[16];
+    uint8_t pty[16];
+    int has_p;
+};
+
+// U (or U^dag when dagger) and, for parametric gates, P into smem.
+template <typename R>
+__device__ void build_step(const BGate& g, const double* theta, bool dagger, StepMats<R>* s) {
+    const int D = 1 << g.k;
+    double ur[16], ui[16];
+    if (g.param < 0) {
+        for (int e = 0; e < D * D; ++e) {
+            ur[e] = g.re[e];
+            ui[e] = g.im[e];
+        }
+    } else {
+        const double a = g.scale * theta[g.param];
+        double sn, cs;
+        sincos(0.5 * a, &sn, &cs);
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) {
+                double pr = 1.0, pi = 0.0;
+                for (int q = 0; q < g.k; ++q) {
+                    double er, ei;
+                    pauli2(g.pauli[q], (r >> (g.k - 1 - q)) & 1, (c >> (g.k - 1 - q)) & 1, &er, &ei);
+                    const double nr = pr * er - pi * ei, ni = pr * ei + pi * er;
+                    pr = nr;
+                    pi = ni;
+                }
+                // U = cos I - i sin P
+                ur[r * D + c] = (r == c ? cs : 0.0) + sn * pi;
+                ui[r * D + c] = -sn * pr;
+                s->pre[r * D + c] = R(pr);
+                s->pim[r * D + c] = R(pi);
+                s->pty[r * D + c] = dev_entry_type(pr, pi);
+            }
+    }
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double vr = ur[r * D + c], vi = ui[r * D + c];
+            if (dagger) {
+                vr = ur[c * D + r];
+                vi = -ui[c * D + r];
+            }
+            s->ure[r * D + c] = R(vr);
+            s->uim[r * D + c] = R(vi);
+            s->uty[r * D + c] = dev_entry_type(double(R(vr)), double(R(vi)));
+        }
+    s->has_p = g.param >= 0;
+}
+
+__device__ __forceinline__ void team_sync(int C) {
+    if (C == 1) {
+        __syncthreads();
+    } else {
+        __threadfence();
+        cg::this_cluster().sync();
+    }
+}
+
+// One gate over the team's share of the groups; in place. With lam, the
+// gradient partial Im <lam|P|psi> is accumulated and U is applied to both.
+template <typename R, int K>
+__device__ double team_gate(amp_t<R>* psi, amp_t<R>* lam, int n, const BGate& g, const StepMats<R>& s,
+                            int64_t tid, int64_t nthreads) {
+    constexpr int D = 1 << K;
+    using A = amp_t<R>;
+    int st[K];
+    int64_t off[D];
+    {
+        int a = g.t[0], b = K == 2 ? g.t[1] : 0;
+        if (K == 1) {
+            st[0] = a;
+        } else {
+            st[0] = a < b ? a : b;
+            st[K - 1] = a < b ? b : a;
+        }
+        for (int c = 0; c < D; ++c) {
+            int64_t o = 0;
+            for (int q = 0; q < K; ++q)
+                if ((c >> (K - 1 - q)) & 1) o += int64_t(1) << g.t[q];
+            off[c] = o;
+        }
+    }
+    double acc = 0.0;
+    const int64_t G = int64_t(1) << (n - K);
+    for (int64_t gi = tid; gi < G; gi += nthreads) {
+        const int64_t b = insert_zeros<K>(gi, st);
+        A p[D], l[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) p[c] = psi[b + off[c]];
+        if (lam) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) l[c] = lam[b + off[c]];
+            if (s.has_p) {
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    A q;
+                    q.x = R(0);
+                    q.y = R(0);
+                    bool first = true;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) mac_typed<R>(q, first, s.pty[r * D + c], s.pre[r * D + c], s.pim[r * D + c], p[c]);
+                    acc = fma(double(l[r].x), double(q.y), acc);
+                    acc = fma(-double(l[r].y), double(q.x), acc);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            A u;
+            u.x = R(0);
+            u.y = R(0);
+            bool f = true;
+#pragma unroll
+            for (int c = 0; c < D; ++c) mac_typed<R>(u, f, s.uty[r * D + c], s.ure[r * D + c], s.uim[r * D + c], p[c]);
+            psi[b + off[r]] = u;
+        }
+        if (lam) {
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                A u;
+                u.x = R(0);
+                u.y = R(0);
+                bool f = true;
+#pragma unroll
+                for (int c = 0; c < D; ++c) mac_typed<R>(u, f, s.uty[r * D + c], s.ure[r * D + c], s.uim[r * D + c], l[c]);
+                lam[b + off[r]] = u;
+            }
+        }
+    }
+    return acc;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(1024) k_batch(const BatchArgs a) {
+    using A = amp_t<R>;
+    __shared__ StepMats<R> mats;
+    __shared__ double warps[32];
+    const int C = a.C;
+    const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
+    const int team = blockIdx.x / C;
+    const int64_t tid = int64_t(rank) * blockDim.x + threadIdx.x;
+    const int64_t nthreads = int64_t(C) * blockDim.x;
+    A* arena = reinterpret_cast<A*>(a.arena);
+    for (int s = a.team_first[team]; s < a.team_first[team + 1]; ++s) {
+        const BInst I = a.inst[a.sched[s]];
+        A* psi = arena + I.psi_off;
+        A* lam = arena + I.lam_off;
+        const int64_t N = int64_t(1) << I.n;
+        const double* th = a.theta + I.param_begin;
+        double* part = a.partials + I.part_off;
+        // |0...0>
+        for (int64_t i = tid; i < N; i += nthreads) {
+            A v;
+            v.x = R(i == 0 ? 1 : 0);
+            v.y = R(0);
+            psi[i] = v;
+        }
+        team_sync(C);
+        // forward sweep
+        for (int gi = I.gate_begin; gi < I.gate_end; ++gi) {
+            const BGate& g = a.gates[gi];
+            if (threadIdx.x == 0) build_step<R>(g, th, false, &mats);
+            __syncthreads();
+            if (g.k == 1) team_gate<R, 1>(psi, nullptr, I.n, g, mats, tid, nthreads);
+            else team_gate<R, 2>(psi, nullptr, I.n, g, mats, tid, nthreads);
+            team_sync(C);
+        }
+        // lambda = H psi and the energy Re <psi|lambda>
+        double e = 0.0;
+        for (int64_t i = tid; i < N; i += nthreads) {
+            double lr = 0.0, li = 0.0;
+            for (int t = I.term_begin; t < I.term_end; ++t) {
+                const BTerm T = a.terms[t];
+                const uint64_t j = uint64_t(i) ^ T.x;
+                const A pj = psi[j];
+                const double sgn = (__popcll(j & T.z) & 1) ? -1.0 : 1.0;
+                const double kr = sgn * T.kr, ki = sgn * T.ki;
+                lr = fma(kr, double(pj.x), lr);
+                lr = fma(-ki, double(pj.y), lr);
+                li = fma(kr, double(pj.y), li);
+                li = fma(ki, double(pj.x), li);
+            }
+            A o;
+            o.x = R(lr);
+            o.y = R(li);
+            lam[i] = o;
+            const A pi = psi[i];
+            e = fma(double(pi.x), lr, e);
+            e = fma(double(pi.y), li, e);
+        }
+        e = block_sum(e, warps);
+        if (threadIdx.x == 0) part[0 * C + rank] = e;
+        team_sync(C);
+        // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
+        for (int gi = I.gate_end - 1; gi >= I.gate_begin; --gi) {
+            const BGate& g = a.gates[gi];
+            if (threadIdx.x == 0) build_step<R>(g, th, true, &mats);
+            __syncthreads();
+            const double v = g.k == 1 ? team_gate<R, 1>(psi, lam, I.n, g, mats, tid, nthreads)
+                                      : team_gate<R, 2>(psi, lam, I.n, g, mats, tid, nthreads);
+            if (g.slot >= 0) {
+                const double sum = block_sum(v, warps);
+                if (threadIdx.x == 0) part[int64_t(g.slot) * C + rank] = sum;
+            }
+            team_sync(C);
+        }
+    }
+}
+
+// Per instance: energy and gradient from the partial rows, fixed order.
+__global__ void k_batch_finish(const BInst* inst, const BGate* gates, const double* partials, int C, int n_inst,
+                               double* energy, double* grad) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_inst) return;
+    const BInst I = inst[id];
+    const double* part = partials + I.part_off;
+    double e = 0.0;
+    for (int r = 0; r < C; ++r) e += part[r];
+    energy[id] = e;
+    double* g = grad + I.param_begin;
+    for (int p = 0; p < I.n_params; ++p) g[p] = 0.0;
+    for (int gi = I.gate_begin; gi < I.gate_end; ++gi) {
+        const BGate& G = gates[gi];
+        if (G.slot < 0) continue;
+        double v = 0.0;
+        for (int r = 0; r < C; ++r) v += part[int64_t(G.slot) * C + r];
+        g[G.param] += G.scale * v;
+    }
+}
+
+}  // namespace diaq
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+using namespace diaq;
+
+struct diaq_batch_s {
+    int device = 0;
+    diaq_dtype dtype = DIAQ_C128;
+    int n_inst = 0;
+    int n_params_total = 0;
+    std::vector<BInst> inst;
+    std::vector<BGate> gates;
+    std::vector<BTerm> terms;
+    std::vector<double> work;  // per-instance work estimate (amplitude-gates)
+    int64_t arena_elems = 0;
+    int64_t slots_total = 0;   // sum of n_slots
+    // device
+    BInst* d_inst = nullptr;
+    BGate* d_gates = nullptr;
+    BTerm* d_terms = nullptr;
+    void* d_arena = nullptr;
+    double* d_theta = nullptr;
+    double* d_partials = nullptr;
+    double* d_out = nullptr;   // energies then grads
+    int32_t* d_sched = nullptr;
+    int32_t* d_team_first = nullptr;
+    // pinned staging for graph replay
+    double* h_theta = nullptr;
+    double* h_out = nullptr;
+    // launch configuration and its graph
+    int C = 1, threads = 256, teams = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+static void batch_free(diaq_batch_s* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
+                    b->d_arena, static_cast<void*>(b->d_theta), static_cast<void*>(b->d_partials),
+                    static_cast<void*>(b->d_out), static_cast<void*>(b->d_sched), static_cast<void*>(b->d_team_first)})
+        if (p) cudaFree(p);
+    if (b->h_theta) cudaFreeHost(b->h_theta);
+    if (b->h_out) cudaFreeHost(b->h_out);
+}
+
+template <typename T>
+static diaq_status upload(T** d, const std::vector<T>& h) {
+    const size_t bytes = std::max<size_t>(h.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), bytes);
+    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMalloc(%zu) for batch tables: %s", bytes, cudaGetErrorString(e));
+    if (!h.empty()) DIAQ_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return DIAQ_OK;
+}
+
+template <typename R>
+static const void* batch_kernel() {
+    return reinterpret_cast<const void*>(&k_batch<R>);
+}
+
+// Teams that fit on the GPU at once for cluster size C and block size T.
+static diaq_status resident_teams(diaq_batch_s* b, int C, int T, int* teams) {
+    const void* fn = b->dtype == DIAQ_C128 ? batch_kernel<double>() : batch_kernel<float>();
+    if (C == 1) {
+        int per_sm = 0, sms = 0;
+        DIAQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0));
+        DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+        *teams = per_sm * sms;
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(T, 1, 1);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        DIAQ_CUDA(cudaOccupancyMaxActiveClusters(&n, fn, &cfg));
+        *teams = n;
+    }
+    if (*teams < 1) return fail(DIAQ_ERR_UNSUPPORTED, "no team of %d blocks x %d threads fits on the device", C, T);
+    return DIAQ_OK;
+}
+
+// Largest first, round robin over teams; balanced by a greedy least-loaded pick.
+static void make_schedule(const diaq_batch_s* b, int teams, std::vector<int32_t>* sched, std::vector<int32_t>* first) {
+    std::vector<int> order(static_cast<size_t>(b->n_inst));
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->work[size_t(x)] > b->work[size_t(y)]; });
+    std::vector<std::vector<int32_t>> lists(static_cast<size_t>(teams));
+    std::vector<double> load(size_t(teams), 0.0);
+    for (int id : order) {
+        size_t best = 0;
+        for (size_t t = 1; t < load.size(); ++t)
+            if (load[t] < load[best]) best = t;
+        lists[best].push_back(id);
+        load[best] += b->work[size_t(id)];
+    }
+    sched->clear();
+    first->clear();
+    for (auto& l : lists) {
+        first->push_back(int32_t(sched->size()));
+        sched->insert(sched->end(), l.begin(), l.end());
+    }
+    first->push_back(int32_t(sched->size()));
+}
+
+static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
+    BatchArgs a;
+    a.inst = b->d_inst;
+    a.gates = b->d_gates;
+    a.terms = b->d_terms;
+    a.sched = b->d_sched;
+    a.team_first = b->d_team_first;
+    a.theta = b->d_theta;
+    a.arena = b->d_arena;
+    a.partials = b->d_partials;
+    a.C = b->C;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(b->teams * b->C), 1, 1);
+    cfg.blockDim = dim3(unsigned(b->threads), 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(b->C);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = b->C > 1 ? 1 : 0;
+    if (b->dtype == DIAQ_C128)
+        DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<double>, a));
+    else
+        DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<float>, a));
+    const int fb = 128;
+    k_batch_finish<<<(b->n_inst + fb - 1) / fb, fb, 0, s>>>(b->d_inst, b->d_gates, b->d_partials, b->C, b->n_inst,
+                                                          b->d_out, b->d_out + b->n_inst);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
+
+// Schedule for (C, threads), then capture theta upload, both kernels and the
+// result download into a graph.
+static diaq_status configure(diaq_batch_s* b, int C, int T, cudaStream_t s) {
+    int teams = 0;
+    DIAQ_TRY(resident_teams(b, C, T, &teams));
+    teams = std::min(teams, b->n_inst);
+    std::vector<int32_t> sched, first;
+    make_schedule(b, teams, &sched, &first);
+    if (b->d_sched) cudaFree(b->d_sched);
+    if (b->d_team_first) cudaFree(b->d_team_first);
+    b->d_sched = nullptr;
+    b->d_team_first = nullptr;
+    DIAQ_TRY(upload(&b->d_sched, sched));
+    DIAQ_TRY(upload(&b->d_team_first, first));
+    // partial rows of C columns
+    if (b->d_partials) cudaFree(b->d_partials);
+    b->d_partials = nullptr;
+    std::vector<BInst> inst = b->inst;
+    int64_t pos = 0;
+    for (auto& I : inst) {
+        I.part_off = pos;
+        pos += int64_t(I.n_slots) * C;
+    }
+    cudaError_t e = cudaMalloc(&b->d_partials, size_t(std::max<int64_t>(pos, 1)) * sizeof(double));
+    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMalloc(batch partials): %s", cudaGetErrorString(e));
+    DIAQ_CUDA(cudaMemcpy(b->d_inst, inst.data(), inst.size() * sizeof(BInst), cudaMemcpyHostToDevice));
+    b->inst = inst;
+    b->C = C;
+    b->threads = T;
+    b->teams = teams;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    // capture on a private stream so the caller's stream may be the legacy default
+    if (!b->graph_stream) DIAQ_CUDA(cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    DIAQ_CUDA(cudaStreamBeginCapture(b->graph_stream, cudaStreamCaptureModeThreadLocal));
+    diaq_status st = DIAQ_OK;
+    const size_t nth = size_t(std::max(b->n_params_total, 1)) * sizeof(double);
+    const size_t nout = size_t(b->n_inst + b->n_params_total) * sizeof(double);
+    if (cudaMemcpyAsync(b->d_theta, b->h_theta, nth, cudaMemcpyHostToDevice, b->graph_stream) != cudaSuccess)
+        st = fail(DIAQ_ERR_CUDA, "capture of the parameter upload failed");
+    if (st == DIAQ_OK) st = launch_batch(b, b->graph_stream);
+    if (st == DIAQ_OK && cudaMemcpyAsync(b->h_out, b->d_out, nout, cudaMemcpyDeviceToHost, b->graph_stream) != cudaSuccess)
+        st = fail(DIAQ_ERR_CUDA, "capture of the result download failed");
+    e = cudaStreamEndCapture(b->graph_stream, &graph);
+    if (st != DIAQ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(batch)");
+    e = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
+    (void)s;
+    return DIAQ_OK;
+}
+
+static diaq_status run_graph(diaq_batch_s* b, cudaStream_t s) {
+    // order the replay after the caller's stream and the caller's stream after it
+    cudaEvent_t ev;
+    DIAQ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    DIAQ_CUDA(cudaEventRecord(ev, s));
+    DIAQ_CUDA(cudaStreamWaitEvent(b->graph_stream, ev, 0));
+    DIAQ_CUDA(cudaGraphLaunch(b->exec, b->graph_stream));
+    DIAQ_CUDA(cudaEventRecord(ev, b->graph_stream));
+    DIAQ_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    DIAQ_CUDA(cudaEventSynchronize(ev));
+    cudaEventDestroy(ev);
+    return DIAQ_OK;
+}
+
+extern "C" {
+
+diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int32_t* gate_first,
+                              const diaq_gate* gates, const int32_t* param_first, const int32_t* term_first,
+                              const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                              diaq_dtype dtype, diaq_batch_t* out) {
+    clear_error();
+    cudaGetLastError();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_inst < 1 || !n_qubits || !gate_first || !param_first || !term_first)
+        return fail(DIAQ_ERR_ARG, "need at least one instance and its index arrays");
+    if (dtype != DIAQ_C64 && dtype != DIAQ_C128) return fail(DIAQ_ERR_ARG, "bad dtype %d", (int)dtype);
+    diaq_batch_s* b = new (std::nothrow) diaq_batch_s();
+    if (!b) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+    b->dtype = dtype;
+    b->n_inst = n_inst;
+    diaq_status st = DIAQ_OK;
+    cudaError_t e = cudaSuccess;
+    int64_t arena = 0;
+    const int64_t align = 256 / int64_t(amp_bytes(dtype));
+    for (int i = 0; i < n_inst && st == DIAQ_OK; ++i) {
+        const int n = n_qubits[i];
+        if (n < 2 || n > 30) {
+            st = fail(DIAQ_ERR_ARG, "instance %d: n_qubits = %d outside [2, 30]", i, n);
+            break;
+        }
+        if (gate_first[i + 1] < gate_first[i] || param_first[i + 1] < param_first[i] || term_first[i + 1] < term_first[i]) {
+            st = fail(DIAQ_ERR_ARG, "instance %d: index arrays must be non-decreasing", i);
+            break;
+        }
+        BInst I = {};
+        I.n = n;
+        I.gate_begin = int32_t(b->gates.size());
+        I.param_begin = param_first[i];
+        I.n_params = param_first[i + 1] - param_first[i];
+        int slots = 1;
+        for (int gi = gate_first[i]; gi < gate_first[i + 1]; ++gi) {
+            const diaq_gate& g = gates[gi];
+            if (g.k < 1 || g.k > 2) {
+                st = fail(DIAQ_ERR_UNSUPPORTED, "instance %d gate %d: the batched path takes gates of 1 or 2 qubits", i, gi);
+                break;
+            }
+            GateDesc d;
+            std::vector<double> zero(size_t(std::max(I.n_params, 1)), 0.0);
+            st = gate_desc_from(&g, n, zero.data(), &d);  // validates targets and generator
+            if (st != DIAQ_OK) break;
+            if (g.param >= I.n_params) {
+                st = fail(DIAQ_ERR_ARG, "instance %d gate %d: parameter %d >= %d", i, gi, g.param, I.n_params);
+                break;
+            }
+            BGate B = {};
+            B.k = g.k;
+            B.t[0] = g.targets[0];
+            B.t[1] = g.k == 2 ? g.targets[1] : 0;
+            B.param = g.param;
+            B.scale = g.scale;
+            B.slot = -1;
+            if (g.param >= 0) {
+                for (int q = 0; q < g.k; ++q) {
+                    const char c = g.gen[q];
+                    B.pauli[q] = (c == 'X' || c == 'x') ? 1 : (c == 'Y' || c == 'y') ? 2 : (c == 'Z' || c == 'z') ? 3 : 0;
+                }
+                B.slot = slots++;
+            } else {
+                for (size_t x = 0; x < d.m.size(); ++x) {
+                    B.re[x] = d.m[x].real();
+                    B.im[x] = d.m[x].imag();
+                }
+            }
+            b->gates.push_back(B);
+        }
+        if (st != DIAQ_OK) break;
+        I.gate_end = int32_t(b->gates.size());
+        I.term_begin = int32_t(b->terms.size());
+        for (int t = term_first[i]; t < term_first[i + 1]; ++t) {
+            const uint64_t valid = (uint64_t(1) << n) - 1;
+            if ((xmask[t] & ~valid) || (zmask[t] & ~valid)) {
+                st = fail(DIAQ_ERR_ARG, "instance %d term %d acts on a qubit >= %d", i, t, n);
+                break;
+            }
+            BTerm T;
+            T.x = xmask[t];
+            T.z = zmask[t];
+            const int ny = __builtin_popcountll(xmask[t] & zmask[t]) & 3;
+            double kr = coeff[2 * t], ki = 0.0;  // Hermitian: real coefficient
+            for (int r = 0; r < ny; ++r) {
+                const double tr = -ki, ti = kr;
+                kr = tr;
+                ki = ti;
+            }
+            T.kr = kr;
+            T.ki = ki;
+            b->terms.push_back(T);
+        }
+        if (st != DIAQ_OK) break;
+        I.term_end = int32_t(b->terms.size());
+        I.n_slots = slots;
+        I.psi_off = arena;
+        arena += ((int64_t(1) << n) + align - 1) / align * align;
+        I.lam_off = arena;
+        arena += ((int64_t(1) << n) + align - 1) / align * align;
+        b->inst.push_back(I);
+        // forward + reverse touch psi once and psi, lam once per gate, plus the H psi pass
+        b->work.push_back(double(int64_t(1) << n) * (3.0 * (I.gate_end - I.gate_begin) + 2.0 + (I.term_end - I.term_begin)));
+        b->n_params_total = std::max(b->n_params_total, param_first[i + 1]);
+    }
+    b->arena_elems = arena;
+    // host tables validated; from here on the device is needed
+    if (st == DIAQ_OK && (e = cudaGetDevice(&b->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
+    if (st == DIAQ_OK) st = upload(&b->d_inst, b->inst);
+    if (st == DIAQ_OK) st = upload(&b->d_gates, b->gates);
+    if (st == DIAQ_OK) st = upload(&b->d_terms, b->terms);
+    if (st == DIAQ_OK) {
+        const size_t bytes = size_t(std::max<int64_t>(arena, 1)) * amp_bytes(dtype);
+        if ((e = cudaMalloc(&b->d_arena, bytes)) != cudaSuccess)
+            st = fail(DIAQ_ERR_ALLOC, "cudaMalloc of the %zu-byte state arena failed: %s", bytes, cudaGetErrorString(e));
+    }
+    const size_t nth = size_t(std::max(b->n_params_total, 1)) * sizeof(double);
+    const size_t nout = size_t(n_inst + b->n_params_total) * sizeof(double);
+    if (st == DIAQ_OK && ((e = cudaMalloc(reinterpret_cast<void**>(&b->d_theta), nth)) != cudaSuccess ||
+                          (e = cudaMalloc(reinterpret_cast<void**>(&b->d_out), nout)) != cudaSuccess ||
+                          (e = cudaMallocHost(reinterpret_cast<void**>(&b->h_theta), nth)) != cudaSuccess ||
+                          (e = cudaMallocHost(reinterpret_cast<void**>(&b->h_out), nout)) != cudaSuccess))
+        st = fail(DIAQ_ERR_ALLOC, "batch parameter/result buffers: %s", cudaGetErrorString(e));
+    if (st == DIAQ_OK) {
+        std::memset(b->h_theta, 0, nth);
+        st = configure(b, 1, 256, nullptr);
+    }
+    if (st != DIAQ_OK) {
+        batch_free(b);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_destroy(diaq_batch_t b) {
+    clear_error();
+    if (!b) return DIAQ_OK;
+    cudaDeviceSynchronize();
+    if (b->graph_stream) cudaStreamDestroy(b->graph_stream);
+    batch_free(b);
+    delete b;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threads) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
+        return fail(DIAQ_ERR_ARG, "cluster size %d not in {1, 2, 4, 8}", cluster);
+    if (threads < 64 || threads > 1024 || threads % 32)
+        return fail(DIAQ_ERR_ARG, "threads %d not a multiple of 32 in [64, 1024]", threads);
+    return configure(b, cluster, threads, nullptr);
+}
+
+diaq_status diaq_batch_run(diaq_batch_t b, const double* theta, double* energies, double* grads,
+                           diaq_stream_t stream) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (b->n_params_total > 0 && !theta) return fail(DIAQ_ERR_ARG, "theta is NULL");
+    for (int p = 0; p < b->n_params_total; ++p)
+        if (!std::isfinite(theta[p])) return fail(DIAQ_ERR_ARG, "theta[%d] is not finite", p);
+    if (b->n_params_total > 0) std::memcpy(b->h_theta, theta, sizeof(double) * size_t(b->n_params_total));
+    DIAQ_TRY(run_graph(b, static_cast<cudaStream_t>(stream)));
+    if (energies) std::memcpy(energies, b->h_out, sizeof(double) * size_t(b->n_inst));
+    if (grads) std::memcpy(grads, b->h_out + b->n_inst, sizeof(double) * size_t(b->n_params_total));
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t reps, diaq_batch_tuning* report,
+                                diaq_stream_t stream) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (b->n_params_total > 0 && !theta) return fail(DIAQ_ERR_ARG, "theta is NULL");
+    if (reps < 1) reps = 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cls[] = {1, 2, 4, 8};
+    const int ths[] = {256, 512, 1024};
+    float best = 1e30f;
+    int bc = 1, bt = 256, tried = 0;
+    cudaEvent_t e0, e1;
+    DIAQ_CUDA(cudaEventCreate(&e0));
+    DIAQ_CUDA(cudaEventCreate(&e1));
+    if (b->n_params_total > 0) std::memcpy(b->h_theta, theta, sizeof(double) * size_t(b->n_params_total));
+    for (int C : cls)
+        for (int T : ths) {
+            if (configure(b, C, T, s) != DIAQ_OK) {
+                clear_error();
+                cudaGetLastError();
+                continue;  // this shape does not fit: skip it
+            }
+            DIAQ_TRY(run_graph(b, s));  // warm
+            DIAQ_CUDA(cudaEventRecord(e0, b->graph_stream));
+            for (int r = 0; r < reps; ++r) DIAQ_CUDA(cudaGraphLaunch(b->exec, b->graph_stream));
+            DIAQ_CUDA(cudaEventRecord(e1, b->graph_stream));
+            DIAQ_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            DIAQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= float(reps);
+            if (report && tried < DIAQ_BATCH_TUNE_MAX) {
+                report->cluster[tried] = C;
+                report->threads[tried] = T;
+                report->ms[tried] = ms;
+            }
+            ++tried;
+            if (ms < best) {
+                best = ms;
+                bc = C;
+                bt = T;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no launch shape fits");
+    DIAQ_TRY(configure(b, bc, bt, s));
+    if (report) {
+        report->n_tried = std::min(tried, DIAQ_BATCH_TUNE_MAX);
+        report->best_cluster = bc;
+        report->best_threads = bt;
+        report->best_ms = best;
+    }
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_query(diaq_batch_t b, int32_t* cluster, int32_t* threads, int32_t* teams, int64_t* arena_bytes) {
+    clear_error();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (cluster) *cluster = b->C;
+    if (threads) *threads = b->threads;
+    if (teams) *teams = b->teams;
+    if (arena_bytes) *arena_bytes = b->arena_elems * int64_t(amp_bytes(b->dtype));
+    return DIAQ_OK;
+}
+
+}  // extern "C"

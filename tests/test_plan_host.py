@@ -1,0 +1,74 @@
+"""Host logic that needs no GPU: the fusion planner and the batch argument
+checks (which run before any device call)."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2405_01250_gb300 import build as B
+    B.build()
+    from paper_2405_01250_gb300 import api as A
+    return A
+
+
+def test_plan_fusion_respects_limits(api):
+    rng = np.random.default_rng(3)
+    n = 12
+    gates = []
+    for _ in range(200):
+        k = int(rng.integers(1, 3))
+        gates.append(synth.Gate(tuple(int(q) for q in rng.choice(n, size=k, replace=False)), synth.random_gate(k, rng)))
+    for max_k in (2, 3, 4, 6):
+        for depth in (1, 2, 4, 8):
+            grp = api.plan_fusion(gates, max_k, depth)
+            assert grp[0] == 0 and all(b - a in (0, 1) for a, b in zip(grp, grp[1:]))
+            for g in set(grp):
+                members = [gates[i] for i in range(len(gates)) if grp[i] == g]
+                assert 1 <= len(members) <= depth
+                assert len({q for m in members for q in m.targets}) <= max_k
+            if depth == 1:
+                assert grp == list(range(len(gates)))
+
+
+def test_plan_fusion_greedy_example(api):
+    H, CZ = synth.H, synth.CZ
+    gates = [synth.Gate((0,), H), synth.Gate((1,), H), synth.Gate((0, 1), CZ), synth.Gate((2,), H),
+             synth.Gate((2, 3), CZ), synth.Gate((0,), H)]
+    assert api.plan_fusion(gates, 2, 4) == [0, 0, 0, 1, 1, 2]
+    assert api.plan_fusion(gates, 3, 4) == [0, 0, 0, 0, 1, 1]
+    assert api.plan_fusion(gates, 4, 2) == [0, 0, 1, 1, 2, 2]
+
+
+def test_plan_fusion_rejects_bad_limits(api):
+    from paper_2405_01250_gb300._native import DiaqError
+    g = [synth.Gate((0, 1), synth.CZ)]
+    with pytest.raises(DiaqError, match="max_k"):
+        api.plan_fusion(g, 1, 2)
+    with pytest.raises(DiaqError):
+        api.plan_fusion(g, 7, 2)
+    with pytest.raises(DiaqError):
+        api.plan_fusion(g, 2, 0)
+
+
+def _batch_args(api, instances):
+    import torch  # noqa: F401
+    return instances
+
+
+def test_batch_validation_before_device(api):
+    from paper_2405_01250_gb300._native import DiaqError
+    obs = ([0], [3], [1.0])
+    with pytest.raises(DiaqError, match="1 or 2 qubits"):
+        api.Batch([(4, [synth.Gate((0, 1, 2), synth.random_gate(3, np.random.default_rng(0)))], 0, obs)])
+    with pytest.raises(DiaqError, match="n_qubits"):
+        api.Batch([(1, [synth.Gate((0,), synth.H)], 0, ([0], [1], [1.0]))])
+    with pytest.raises(DiaqError, match="parameter"):
+        api.Batch([(3, [synth.Gate((0,), None, param=2, gen="X")], 1, obs)])
+    with pytest.raises(DiaqError, match="qubit"):
+        api.Batch([(2, [synth.Gate((0,), synth.H)], 0, ([0], [1 << 5], [1.0]))])
