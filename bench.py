@@ -55,6 +55,25 @@ def _dist():
     return (dist.get_rank() if ws > 1 else 0), ws
 
 
+def reduce_max(value: float, world: int) -> float:
+    """Max over ranks of a host scalar (the slowest rank's time); gloo
+    reduces CPU tensors, NCCL device tensors."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(bytes_per_rank: float, ms_max: float, world: int) -> float:
+    """Whole-job GB/s: every rank runs the same replica, so the units
+    processed are world x one rank's, over the slowest rank's time."""
+    return world * bytes_per_rank / (ms_max / 1e3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -202,12 +221,9 @@ def run_ours(args, rank, world):
         for i, c in enumerate(classes):
             dur.setdefault(c, []).append(ev[s][i].elapsed_time(ev[s][i + 1]))
     apply_ms = sum(sum(v) for v in dur.values()) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * bytes_step * args.steps / (ms_total / 1e3) / 1e9
+    value = aggregate(bytes_step * args.steps, ms_total, world)
 
     # dominant kernel: controlled phase (diagonal class) launches
     dom = "diagonal"
@@ -283,8 +299,206 @@ def run_ours(args, rank, world):
         "e2e": e2e, "stored": stored, "clocks": clocks,
         "gpu_launches": args.steps * (len(ops) + 2),
     }
+    # free the QFT buffers before the secondary workloads
+    del a, b, x0, ops
+    torch.cuda.empty_cache()
+    extras = {}
+    if not args.no_adjoint:
+        extras["adjoint"] = bench_adjoint(api)
+    if not args.no_batch:
+        extras["batch"] = bench_batch(api, count=args.batch_count)
+    if args.random:
+        extras["random"] = bench_random(api, n=args.random_qubits)
+    if extras:
+        out["extras"] = extras
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n, circ, j, budget_s=args.cpu_seconds)
+    return out
+
+
+def bench_adjoint(api, n=20, layers=8, reps=3):
+    """Ansatz-20 energy + full gradient (320 parameters) by the adjoint sweep,
+    complex128 and complex64, against the plain FP64 path: the
+    parameter-shift gradient with one launch per gate (2 circuit
+    evaluations per parameter, each 472 on-the-fly applies + the FP64
+    expectation)."""
+    import torch
+    import synth
+    circ = synth.ansatz(n=n, layers=layers, seed=0)
+    obs = synth.ansatz_observable(n)
+    out = {"workload": f"ansatz-{n}, {layers} layers, {circ.n_params} parameters, {len(circ.gates)} gates"}
+    grads = {}
+    for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
+        p0 = torch.zeros(1 << n, dtype=dt, device="cuda")
+        p0[0] = 1
+        wp, wl = torch.empty_like(p0), torch.empty_like(p0)
+        for _ in range(2):
+            e, g = api.adjoint_grad(circ.gates, circ.theta, obs.xmask, obs.zmask, obs.coeff, p0, wp, wl)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e, g = api.adjoint_grad(circ.gates, circ.theta, obs.xmask, obs.zmask, obs.coeff, p0, wp, wl)
+        el = (time.perf_counter() - t0) / reps
+        grads[name] = g
+        out[f"adjoint_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3, "energy": e,
+                                  "launches_per_gradient": 2 * len(circ.gates) + 4 + circ.n_params}
+    # the same sweep recorded once as a CUDA graph and replayed per theta
+    for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
+        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dt)
+        for _ in range(2):
+            e, g = plan.run(circ.theta)
+        t0 = time.perf_counter()
+        r = 3 * reps
+        for _ in range(r):
+            e, g = plan.run(circ.theta)
+        el = (time.perf_counter() - t0) / r
+        out[f"adjoint_graph_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3,
+                                        "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(g - grads[name])))}
+        plan.close()
+    out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
+    # plain FP64 path: one circuit evaluation = 472 applies + expectation
+    ops = [api.build(g, n, theta=circ.theta) for g in circ.gates]
+    x = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+
+    def evaluate():
+        a, b = x, y
+        a.zero_()
+        a[0] = 1
+        for op in ops:
+            api.apply(op, a, b)
+            a, b = b, a
+        return api.expect(a, obs.xmask, obs.zmask, obs.coeff).real
+
+    evaluate()
+    t0 = time.perf_counter()
+    k = 6
+    for _ in range(k):
+        evaluate()
+    t_eval = (time.perf_counter() - t0) / k
+    n_eval = 2 * circ.n_params
+    out["plain_fp64_param_shift"] = {"ms_per_evaluation": t_eval * 1e3, "evaluations_per_gradient": n_eval,
+                                     "grads_per_s": 1.0 / (n_eval * t_eval),
+                                     "note": f"timed on {k} evaluations, a gradient needs {n_eval}"}
+    out["speedup_adjoint_c128_vs_plain"] = out["adjoint_c128"]["grads_per_s"] / out["plain_fp64_param_shift"]["grads_per_s"]
+    out["speedup_adjoint_c64_vs_plain"] = out["adjoint_c64"]["grads_per_s"] / out["plain_fp64_param_shift"]["grads_per_s"]
+    for name in ("c128", "c64"):
+        out[f"speedup_adjoint_graph_{name}_vs_plain"] = (out[f"adjoint_graph_{name}"]["grads_per_s"]
+                                                        / out["plain_fp64_param_shift"]["grads_per_s"])
+    return out
+
+
+def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "c128")):
+    """QAOA MaxCut batch: `count` circuits on random 3-regular graphs,
+    n in {14..22}, p = 4: energy + 8-parameter gradient per circuit in one
+    persistent launch replayed from a CUDA graph (launch shape chosen by the
+    autotuner on a 16-circuit proxy batch of the same size mix), complex64
+    and complex128, against the plain path: diaq_adjoint_grad per circuit in
+    FP64 (one launch per gate)."""
+    import torch
+    import synth
+    inst = synth.qaoa_batch(count, seed=0)
+    theta = np.concatenate([c.theta for c, _ in inst])
+    desc = [(c.n, c.gates, c.n_params, (o.xmask, o.zmask, o.coeff)) for c, o in inst]
+    sizes = sorted(set(c.n for c, _ in inst))
+    out = {"workload": f"qaoa batch: {count} circuits, n in {sizes}, p=4, energy + 8 grads each"}
+    energies = {}
+    for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        if name not in dtypes:
+            continue
+        if shape is None:
+            proxy = api.Batch(desc[:16], dtype=dt)
+            tune = proxy.autotune(np.concatenate([c.theta for c, _ in inst[:16]]), reps=1)
+            proxy.close()
+        else:
+            tune = {"best_cluster": shape[0], "best_threads": shape[1], "best_ms": None, "tried": []}
+        b = api.Batch(desc, dtype=dt)
+        b.set_launch(tune["best_cluster"], tune["best_threads"])
+        E, G = b.run(theta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            E, G = b.run(theta)
+        el = (time.perf_counter() - t0) / reps
+        energies[name] = E
+        q = b.query()
+        out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
+                                  "cluster": q["cluster"], "threads": q["threads"], "teams": q["teams"],
+                                  "arena_bytes": q["arena_bytes"], "launches_per_batch": 2,
+                                  "tuning": {"proxy_best_ms": tune["best_ms"], "shapes_tried": len(tune["tried"])}}
+        b.close()
+    if len(energies) == 2:
+        out["c64_vs_c128_max_abs_energy_diff"] = float(np.max(np.abs(energies["c64"] - energies["c128"])))
+    if plain and "c128" in energies:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_plain = []
+        for c, o in inst:
+            p0 = torch.zeros(1 << c.n, dtype=torch.complex128, device="cuda")
+            p0[0] = 1
+            e, g = api.adjoint_grad(c.gates, c.theta, o.xmask, o.zmask, o.coeff, p0, torch.empty_like(p0),
+                                    torch.empty_like(p0))
+            e_plain.append(e)
+        el = time.perf_counter() - t0
+        out["plain_fp64_per_circuit"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3}
+        out["batched_c128_vs_plain_max_abs_energy_diff"] = float(np.max(np.abs(np.array(e_plain) - energies["c128"])))
+        out["speedup_batched_c128_vs_plain"] = out["batched_c128"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]
+        out["speedup_batched_c64_vs_plain"] = out["batched_c64"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]
+    return out
+
+
+def bench_random(api, n=30, depth=40):
+    """Random layered circuit (Haar U(2) on every qubit + CZ on a random
+    matching per layer), complex64 vs complex128, one pass each; fusion depth
+    chosen by the autotuner for complex64; fidelity and max amplitude error of
+    complex64 against the complex128 result (the complex128 path matches the
+    FP64 oracle to 1e-12 at every size the oracle reaches)."""
+    import torch
+    import synth
+    circ = synth.random_layered(n, depth, seed=0)
+    N = 1 << n
+    out = {"workload": f"random-{n} depth {depth}: {len(circ.gates)} gates"}
+    res = {}
+    for name, dt, s in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
+        ops = [api.build(g, n, dtype=dt) for g in circ.gates]
+        x = torch.zeros(N, dtype=dt, device="cuda")
+        x[0] = 1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for op in ops:
+            api.apply(op, x, x)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        res[name] = x
+        out[name] = {"s_per_circuit": el, "gates_per_s": len(ops) / el, "gbs": len(ops) * 2 * N * s / el / 1e9,
+                     "norm": api.norm(x)}
+        del ops
+    a = res["c128"]
+    b = res["c64"].to(torch.complex128)
+    ov = torch.vdot(a, b)
+    out["c64_fidelity_vs_c128"] = float((ov.abs() ** 2 / (torch.vdot(a, a).real * torch.vdot(b, b).real)).item())
+    out["c64_max_abs_err_vs_c128"] = float((a - b).abs().max().item())
+    del b
+    res.pop("c64")
+    # fusion depth autotune (complex64), then the fused circuit
+    w = torch.zeros(N, dtype=torch.complex64, device="cuda")
+    w[0] = 1
+    tune = api.autotune_fusion(circ.gates[: 5 * (n + n // 2)], n, w, max_k=4, max_depth=4)
+    d = tune["best_depth"]
+    ops = api.build_fused(circ.gates, n, 4, d, dtype=torch.complex64)
+    w.zero_()
+    w[0] = 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for op in ops:
+        api.apply(op, w, w)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out["c64_fused"] = {"depth": d, "ops": len(ops), "s_per_circuit": el, "gates_per_s": len(circ.gates) / el,
+                        "tuning_ms_by_depth": tune["ms"]}
+    wf = w.to(torch.complex128)
+    out["c64_fused"]["fidelity_vs_c128"] = float(
+        (torch.vdot(a, wf).abs() ** 2 / (torch.vdot(a, a).real * torch.vdot(wf, wf).real)).item())
     return out
 
 
@@ -358,6 +572,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-stored", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-only", action="store_true", help="profiling entry: one batch run, fixed shape")
+    ap.add_argument("--batch-cluster", type=int, default=8)
+    ap.add_argument("--batch-threads", type=int, default=256)
+    ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--random", action="store_true", help="also run the random layered circuit (slow in c128)")
+    ap.add_argument("--random-qubits", type=int, default=30)
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -367,6 +590,16 @@ def main():
         if rank != 0:
             return
         print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if args.batch_only:
+        # profiling entry: one batch at a fixed team shape, no autotuning
+        import torch  # noqa: F401
+        from paper_2405_01250_gb300 import build as B
+        B.build()
+        from paper_2405_01250_gb300 import api
+        print(json.dumps(bench_batch(api, count=args.batch_count, reps=1, plain=False,
+                                     shape=(args.batch_cluster, args.batch_threads),
+                                     dtypes=(args.batch_dtype,))), flush=True)
         return
     rank, world = _dist()
     out = run_ours(args, rank, world)

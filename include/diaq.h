@@ -258,6 +258,27 @@ diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const dou
                               void* work_psi, void* work_lam, int32_t n_qubits, diaq_dtype dtype,
                               double* energy, double* grad, diaq_stream_t stream);
 
+/* Adjoint plan: the sweep of diaq_adjoint_grad for one circuit (gates of
+ * 1 or 2 qubits) recorded once as a CUDA graph and replayed per theta. The
+ * plan owns its two state buffers; gate matrices are derived on the device
+ * from the uploaded parameters, so no kernel argument changes between
+ * replays. */
+typedef struct diaq_adjoint_plan_s* diaq_adjoint_plan_t;
+
+diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, int32_t n_params, int32_t n_terms,
+                                     const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                                     int32_t n_qubits, diaq_dtype dtype, diaq_adjoint_plan_t* out);
+
+/* Energy and gradient for theta (host, n_params). psi0 is a device state of
+ * the plan's size and dtype, or NULL for |0...0>; a different psi0 pointer
+ * than the previous call re-records the graph. energy / grad are host
+ * outputs (may be NULL). Ordered after the work queued on `stream`;
+ * synchronises before returning. */
+diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, const void* psi0, double* energy,
+                                  double* grad, diaq_stream_t stream);
+
+diaq_status diaq_adjoint_plan_destroy(diaq_adjoint_plan_t p);
+
 /* ------------------------------------------------------------------------
  * Autotuning and fusion planning (not in the paper; the paper fuses gates
  * with spGEMM, Section VI, but gives no rule for which to fuse).
@@ -351,7 +372,8 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
 diaq_status diaq_batch_destroy(diaq_batch_t b);
 
 /* Choose the team shape: `cluster` blocks (1, 2, 4 or 8, one thread-block
- * cluster) of `threads` threads per circuit; recaptures the graph. */
+ * cluster) of `threads` threads (a multiple of 32 in [64, 512]) per
+ * circuit; recaptures the graph. */
 diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threads);
 
 /* Energies (n_inst) and gradients (param_first[n_inst] doubles, circuit i's
@@ -361,7 +383,7 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
 diaq_status diaq_batch_run(diaq_batch_t b, const double* theta, double* energies, double* grads,
                            diaq_stream_t stream);
 
-/* Time every team shape (cluster in {1,2,4,8} x threads in {256,512,1024})
+/* Time every team shape (cluster in {1,2,4,8} x threads in {128,256,512})
  * that fits, `reps` graph replays each with theta, keep the fastest. report
  * may be NULL. */
 diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t reps, diaq_batch_tuning* report,

@@ -23,7 +23,7 @@ __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
     "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
-    "build_fused",
+    "build_fused", "AdjointPlan",
 ]
 
 
@@ -379,6 +379,46 @@ def autotune_fusion(gates, n_qubits: int, work: torch.Tensor, max_k: int = 4, ma
             "best_depth": rep.best_depth}
 
 
+class AdjointPlan:
+    """The adjoint sweep of one circuit recorded as a CUDA graph
+    (diaq_adjoint_plan_*), replayed for each theta."""
+
+    def __init__(self, gates, n_params: int, observable, n_qubits: int, dtype=torch.complex128):
+        arr, keep = _gate_array(gates)
+        xm, zm, c = _terms(*observable)
+        h = ctypes.c_void_p(0)
+        check(lib().diaq_adjoint_plan_create(arr, len(gates), int(n_params), len(xm), xm.ctypes.data_as(N._u64p),
+                                             zm.ctypes.data_as(N._u64p),
+                                             _dptr(c.view(np.float64)) if len(c) else None, int(n_qubits),
+                                             _dtype_code(dtype), ctypes.byref(h)))
+        del keep
+        self.handle = h
+        self.n_params = int(n_params)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().diaq_adjoint_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = ctypes.c_void_p(0)
+
+    def close(self):
+        self.__del__()
+
+    def run(self, theta, psi0: torch.Tensor | None = None, stream=None) -> tuple:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        if len(th) != self.n_params:
+            raise ValueError("theta length does not match the plan")
+        g = np.zeros(max(1, self.n_params))
+        e = ctypes.c_double(0)
+        check(lib().diaq_adjoint_plan_run(self.handle, _dptr(th) if len(th) else None,
+                                          ctypes.c_void_p(psi0.data_ptr()) if psi0 is not None else None,
+                                          ctypes.byref(e), _dptr(g), _stream(stream)))
+        return e.value, g[:self.n_params].copy()
+
+
 class Batch:
     """Energies and adjoint gradients of many circuits (uneven qubit counts)
     in one persistent launch replayed from a CUDA graph (diaq_batch_*).
@@ -458,15 +498,21 @@ class Batch:
 
 class DiaqEnergy(torch.autograd.Function):
     """E(theta) = <psi(theta)|H|psi(theta)> with the gradient from the
-    adjoint sweep (diaq_adjoint_grad). Call as
-    DiaqEnergy.apply(theta, gates, (xmask, zmask, coeff), psi0)."""
+    adjoint sweep. Call as DiaqEnergy.apply(theta, gates, (xmask, zmask,
+    coeff), psi0) (diaq_adjoint_grad, one launch per gate), or as
+    DiaqEnergy.apply(theta, plan, None, psi0_or_None) with an AdjointPlan
+    (the graph-recorded sweep)."""
 
     @staticmethod
     def forward(ctx, theta, gates, observable, psi0):
-        xm, zm, c = observable
-        work_psi = torch.empty_like(psi0)
-        work_lam = torch.empty_like(psi0)
-        e, g = adjoint_grad(gates, theta.detach().cpu().numpy(), xm, zm, c, psi0, work_psi, work_lam)
+        th = theta.detach().cpu().numpy()
+        if isinstance(gates, AdjointPlan):
+            e, g = gates.run(th, psi0)
+        else:
+            xm, zm, c = observable
+            work_psi = torch.empty_like(psi0)
+            work_lam = torch.empty_like(psi0)
+            e, g = adjoint_grad(gates, th, xm, zm, c, psi0, work_psi, work_lam)
         ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype, device=theta.device))
         return theta.new_tensor(e)
 

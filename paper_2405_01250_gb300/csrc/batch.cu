@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "rot.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -42,8 +43,9 @@ struct BGate {
     int32_t param;      // -1 fixed
     int32_t pauli[2];   // generator letters 0=I 1=X 2=Y 3=Z (parametric)
     int32_t slot;       // partial-sum row of a parametric gate (instance relative), else -1
-    int32_t pad;
+    int32_t xl;         // local X mask of the generator (parametric)
     double scale;
+    RotShape rot;       // targets, offsets, Z mask and Y count (parametric)
     double re[16], im[16];  // fixed gate matrix (row-major, 2^k x 2^k)
 };
 
@@ -108,7 +110,7 @@ struct StepMats {
 
 // U (or U^dag when dagger) and, for parametric gates, P into smem.
 template <typename R>
-__device__ void build_step(const BGate& g, const double* theta, bool dagger, StepMats<R>* s) {
+__device__ __noinline__ void build_step(const BGate& g, const double* theta, bool dagger, StepMats<R>* s) {
     const int D = 1 << g.k;
     double ur[16], ui[16];
     if (g.param < 0) {
@@ -161,12 +163,16 @@ __device__ __forceinline__ void team_sync(int C) {
     }
 }
 
-// One gate over the team's share of the groups; in place. With lam, the
-// gradient partial Im <lam|P|psi> is accumulated and U is applied to both.
-template <typename R, int K>
-__device__ double team_gate(amp_t<R>* psi, amp_t<R>* lam, int n, const BGate& g, const StepMats<R>& s,
-                            int64_t tid, int64_t nthreads) {
+// A fixed gate over the team's share of the groups, in place on psi (and,
+// in the reverse sweep, lam). Each thread takes U groups per iteration (all
+// loads issued before any arithmetic); the 2^k x 2^k matrix is copied into
+// registers once, since the stores in the loop would otherwise force every
+// entry to be reloaded.
+template <typename R, int K, int U>
+__device__ __noinline__ void team_fixed_u(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
+                                          const BGate& g, const StepMats<R>& s, int64_t tid, int64_t nthreads) {
     constexpr int D = 1 << K;
+    constexpr int DD = D * D;
     using A = amp_t<R>;
     int st[K];
     int64_t off[D];
@@ -185,61 +191,89 @@ __device__ double team_gate(amp_t<R>* psi, amp_t<R>* lam, int n, const BGate& g,
             off[c] = o;
         }
     }
-    double acc = 0.0;
+    R ur[DD], ui[DD];
+    uint8_t ut[DD];
+#pragma unroll
+    for (int e = 0; e < DD; ++e) {
+        ur[e] = s.ure[e];
+        ui[e] = s.uim[e];
+        ut[e] = s.uty[e];
+    }
     const int64_t G = int64_t(1) << (n - K);
-    for (int64_t gi = tid; gi < G; gi += nthreads) {
-        const int64_t b = insert_zeros<K>(gi, st);
-        A p[D], l[D];
+    for (int64_t g0 = tid; g0 < G; g0 += int64_t(U) * nthreads) {
+        int64_t b[U];
+        A p[U][D], l[U][D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) p[c] = psi[b + off[c]];
-        if (lam) {
+        for (int u = 0; u < U; ++u) {
+            const int64_t gi = g0 + int64_t(u) * nthreads;
+            b[u] = gi < G ? insert_zeros<K>(gi, st) : int64_t(-1);
+            if (b[u] >= 0) {
 #pragma unroll
-            for (int c = 0; c < D; ++c) l[c] = lam[b + off[c]];
-            if (s.has_p) {
+                for (int c = 0; c < D; ++c) p[u][c] = psi[b[u] + off[c]];
+                if (lam) {
 #pragma unroll
-                for (int r = 0; r < D; ++r) {
-                    A q;
-                    q.x = R(0);
-                    q.y = R(0);
-                    bool first = true;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) mac_typed<R>(q, first, s.pty[r * D + c], s.pre[r * D + c], s.pim[r * D + c], p[c]);
-                    acc = fma(double(l[r].x), double(q.y), acc);
-                    acc = fma(-double(l[r].y), double(q.x), acc);
+                    for (int c = 0; c < D; ++c) l[u][c] = lam[b[u] + off[c]];
                 }
             }
         }
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
-            A u;
-            u.x = R(0);
-            u.y = R(0);
-            bool f = true;
-#pragma unroll
-            for (int c = 0; c < D; ++c) mac_typed<R>(u, f, s.uty[r * D + c], s.ure[r * D + c], s.uim[r * D + c], p[c]);
-            psi[b + off[r]] = u;
-        }
-        if (lam) {
+        for (int u = 0; u < U; ++u) {
+            if (b[u] < 0) continue;
 #pragma unroll
             for (int r = 0; r < D; ++r) {
-                A u;
-                u.x = R(0);
-                u.y = R(0);
+                A w;
+                w.x = R(0);
+                w.y = R(0);
                 bool f = true;
 #pragma unroll
-                for (int c = 0; c < D; ++c) mac_typed<R>(u, f, s.uty[r * D + c], s.ure[r * D + c], s.uim[r * D + c], l[c]);
-                lam[b + off[r]] = u;
+                for (int c = 0; c < D; ++c) mac_typed<R>(w, f, ut[r * D + c], ur[r * D + c], ui[r * D + c], p[u][c]);
+                psi[b[u] + off[r]] = w;
+            }
+            if (lam) {
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    A w;
+                    w.x = R(0);
+                    w.y = R(0);
+                    bool f = true;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) mac_typed<R>(w, f, ut[r * D + c], ur[r * D + c], ui[r * D + c], l[u][c]);
+                    lam[b[u] + off[r]] = w;
+                }
             }
         }
     }
-    return acc;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(1024) k_batch(const BatchArgs a) {
+__device__ __forceinline__ void team_fixed(amp_t<R>* psi, amp_t<R>* lam, int n, const BGate& g, const StepMats<R>& s,
+                                           int64_t tid, int64_t nthreads) {
+    if (g.k == 1) {
+        team_fixed_u<R, 1, 1>(psi, lam, n, g, s, tid, nthreads);
+    } else {
+        team_fixed_u<R, 2, 1>(psi, lam, n, g, s, tid, nthreads);
+    }
+}
+
+// kappa for U (dagger = false) or U^dag of a rotation, from its angle:
+// kappa = -i sin(a/2) i^ny, kappa' = +i sin(a/2) i^ny.
+__device__ __forceinline__ void rot_angle(const BGate& g, const double* theta, bool dagger, double* cs, double* kr,
+                                          double* ki) {
+    double sn, c;
+    sincos(0.5 * g.scale * theta[g.param], &sn, &c);
+    double2 z = make_double2(0.0, dagger ? sn : -sn);  // -+ i sin
+    z = mul_ipow(z, g.rot.ny);
+    *cs = c;
+    *kr = z.x;
+    *ki = z.y;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     using A = amp_t<R>;
     __shared__ StepMats<R> mats;
     __shared__ double warps[32];
+    __shared__ double ang[3];
     const int C = a.C;
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const int team = blockIdx.x / C;
@@ -264,10 +298,15 @@ __global__ void __launch_bounds__(1024) k_batch(const BatchArgs a) {
         // forward sweep
         for (int gi = I.gate_begin; gi < I.gate_end; ++gi) {
             const BGate& g = a.gates[gi];
-            if (threadIdx.x == 0) build_step<R>(g, th, false, &mats);
+            if (threadIdx.x == 0) {
+                if (g.param >= 0) rot_angle(g, th, false, &ang[0], &ang[1], &ang[2]);
+                else build_step<R>(g, th, false, &mats);
+            }
             __syncthreads();
-            if (g.k == 1) team_gate<R, 1>(psi, nullptr, I.n, g, mats, tid, nthreads);
-            else team_gate<R, 2>(psi, nullptr, I.n, g, mats, tid, nthreads);
+            if (g.param >= 0)
+                rot_dispatch<R>(g.k, g.xl, psi, nullptr, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid, nthreads);
+            else
+                team_fixed<R>(psi, nullptr, I.n, g, mats, tid, nthreads);
             team_sync(C);
         }
         // lambda = H psi and the energy Re <psi|lambda>
@@ -299,10 +338,16 @@ __global__ void __launch_bounds__(1024) k_batch(const BatchArgs a) {
         // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
         for (int gi = I.gate_end - 1; gi >= I.gate_begin; --gi) {
             const BGate& g = a.gates[gi];
-            if (threadIdx.x == 0) build_step<R>(g, th, true, &mats);
+            if (threadIdx.x == 0) {
+                if (g.param >= 0) rot_angle(g, th, true, &ang[0], &ang[1], &ang[2]);
+                else build_step<R>(g, th, true, &mats);
+            }
             __syncthreads();
-            const double v = g.k == 1 ? team_gate<R, 1>(psi, lam, I.n, g, mats, tid, nthreads)
-                                      : team_gate<R, 2>(psi, lam, I.n, g, mats, tid, nthreads);
+            double v = 0.0;
+            if (g.param >= 0)
+                v = rot_dispatch<R>(g.k, g.xl, psi, lam, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid, nthreads);
+            else
+                team_fixed<R>(psi, lam, I.n, g, mats, tid, nthreads);
             if (g.slot >= 0) {
                 const double sum = block_sum(v, warps);
                 if (threadIdx.x == 0) part[int64_t(g.slot) * C + rank] = sum;
@@ -370,6 +415,30 @@ struct diaq_batch_s {
     cudaStream_t graph_stream = nullptr;
 };
 
+// Rotation shape of a parametric gate from its generator letters.
+static void fill_rot(BGate* B) {
+    const int k = B->k;
+    B->xl = 0;
+    B->rot.zl = 0;
+    B->rot.ny = 0;
+    for (int a = 0; a < k; ++a) {
+        const int bit = 1 << (k - 1 - a);
+        const int L = B->pauli[a];  // 0 I, 1 X, 2 Y, 3 Z
+        if (L == 1 || L == 2) B->xl |= bit;
+        if (L == 2 || L == 3) B->rot.zl |= bit;
+        if (L == 2) B->rot.ny = (B->rot.ny + 1) & 3;
+    }
+    B->rot.st[0] = k == 2 ? std::min(B->t[0], B->t[1]) : B->t[0];
+    B->rot.st[1] = k == 2 ? std::max(B->t[0], B->t[1]) : 0;
+    for (int c = 0; c < 4; ++c) {
+        int64_t o = 0;
+        if (c < (1 << k))
+            for (int a = 0; a < k; ++a)
+                if ((c >> (k - 1 - a)) & 1) o += int64_t(1) << B->t[a];
+        B->rot.off[c] = o;
+    }
+}
+
 static void batch_free(diaq_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
@@ -397,15 +466,17 @@ static const void* batch_kernel() {
 // Teams that fit on the GPU at once for cluster size C and block size T.
 static diaq_status resident_teams(diaq_batch_s* b, int C, int T, int* teams) {
     const void* fn = b->dtype == DIAQ_C128 ? batch_kernel<double>() : batch_kernel<float>();
+    const size_t smem = 0;
     if (C == 1) {
         int per_sm = 0, sms = 0;
-        DIAQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, 0));
+        DIAQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem));
         DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
         *teams = per_sm * sms;
     } else {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C, 1, 1);
         cfg.blockDim = dim3(T, 1, 1);
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = C;
@@ -620,6 +691,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
                     B.im[x] = d.m[x].imag();
                 }
             }
+            fill_rot(&B);  // targets and offsets for every gate
             b->gates.push_back(B);
         }
         if (st != DIAQ_OK) break;
@@ -704,8 +776,8 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
     if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
     if (!(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
         return fail(DIAQ_ERR_ARG, "cluster size %d not in {1, 2, 4, 8}", cluster);
-    if (threads < 64 || threads > 1024 || threads % 32)
-        return fail(DIAQ_ERR_ARG, "threads %d not a multiple of 32 in [64, 1024]", threads);
+    if (threads < 32 || threads > 256 || threads % 32)
+        return fail(DIAQ_ERR_ARG, "threads %d not a multiple of 32 in [32, 256]", threads);
     return configure(b, cluster, threads, nullptr);
 }
 
@@ -733,7 +805,7 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
     if (reps < 1) reps = 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int cls[] = {1, 2, 4, 8};
-    const int ths[] = {256, 512, 1024};
+    const int ths[] = {64, 128, 256};  // k_batch is built for at most 256
     float best = 1e30f;
     int bc = 1, bt = 256, tried = 0;
     cudaEvent_t e0, e1;
@@ -787,6 +859,384 @@ diaq_status diaq_batch_query(diaq_batch_t b, int32_t* cluster, int32_t* threads,
     if (threads) *threads = b->threads;
     if (teams) *teams = b->teams;
     if (arena_bytes) *arena_bytes = b->arena_elems * int64_t(amp_bytes(b->dtype));
+    return DIAQ_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint plan: the adjoint sweep of one circuit as a CUDA graph. Fixed
+// gates are launched with their matrices in kernel parameters (they do not
+// change between replays); parametric gates are Pauli rotations whose
+// cos(a/2) and kappa a first kernel derives from the uploaded parameters.
+// The graph (parameter upload, sweeps, reductions, result download) is
+// captured once and replayed for every new theta.
+// ---------------------------------------------------------------------------
+namespace diaq {
+
+struct RotAngles {
+    double cs, kfr, kfi, kar, kai;  // cos(a/2), kappa of U, kappa of U^dag
+};
+
+__global__ void k_plan_angles(const BGate* gates, int n_gates, const double* theta, RotAngles* out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_gates || gates[g].param < 0) return;
+    RotAngles A;
+    rot_angle(gates[g], theta, false, &A.cs, &A.kfr, &A.kfi);
+    rot_angle(gates[g], theta, true, &A.cs, &A.kar, &A.kai);
+    out[g] = A;
+}
+
+template <typename R, int K, int XL>
+__global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, const BGate* gate,
+                                                  const RotAngles* ang, int n, double* part) {
+    __shared__ double warps[32];
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    const RotAngles a = *ang;
+    const bool adj = lam != nullptr;  // the reverse sweep applies U^dag
+    const double v = rot_groups<R, K, XL>(psi, lam, n, gate->rot, R(a.cs), R(adj ? a.kar : a.kfr),
+                                          R(adj ? a.kai : a.kfi), tid, nth);
+    if (part) {
+        const double s = block_sum(v, warps);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
+                                                     int n_terms, int64_t N, double* part) {
+    using A = amp_t<R>;
+    __shared__ double warps[32];
+    double e = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+        double lr = 0.0, li = 0.0;
+        for (int t = 0; t < n_terms; ++t) {
+            const BTerm T = terms[t];
+            const uint64_t j = uint64_t(i) ^ T.x;
+            const A pj = psi[j];
+            const double sgn = (__popcll(j & T.z) & 1) ? -1.0 : 1.0;
+            const double kr = sgn * T.kr, ki = sgn * T.ki;
+            lr = fma(kr, double(pj.x), lr);
+            lr = fma(-ki, double(pj.y), lr);
+            li = fma(kr, double(pj.y), li);
+            li = fma(ki, double(pj.x), li);
+        }
+        A o;
+        o.x = R(lr);
+        o.y = R(li);
+        lam[i] = o;
+        const A pi = psi[i];
+        e = fma(double(pi.x), lr, e);
+        e = fma(double(pi.y), li, e);
+    }
+    e = block_sum(e, warps);
+    if (threadIdx.x == 0) part[blockIdx.x] = e;
+}
+
+template <typename R>
+__global__ void k_plan_init(const amp_t<R>* psi0, amp_t<R>* psi, int64_t N) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+        amp_t<R> v;
+        if (psi0) {
+            v = psi0[i];
+        } else {
+            v.x = R(i == 0 ? 1 : 0);
+            v.y = R(0);
+        }
+        psi[i] = v;
+    }
+}
+
+// Row sums of the partials, one block per row (fixed shuffle tree).
+__global__ void __launch_bounds__(256) k_plan_rows(const double* __restrict__ part, int P, double* rows) {
+    __shared__ double warps[32];
+    const double* row = part + int64_t(blockIdx.x) * P;
+    double s = 0.0;
+    for (int c = threadIdx.x; c < P; c += blockDim.x) s += row[c];
+    s = block_sum(s, warps);
+    if (threadIdx.x == 0) rows[blockIdx.x] = s;
+}
+
+// out[0] = energy, out[1 + p] = dE/dtheta_p from the row sums, parameter
+// contributions accumulated in gate order.
+__global__ void k_plan_finish(const BGate* gates, int n_gates, const double* rows, int n_params, double* out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    out[0] = rows[0];
+    for (int p = 0; p < n_params; ++p) out[1 + p] = 0.0;
+    for (int g = 0; g < n_gates; ++g) {
+        const BGate& G = gates[g];
+        if (G.slot >= 0) out[1 + G.param] += G.scale * rows[G.slot];
+    }
+}
+
+template <typename R>
+static void launch_plan_rot(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
+                            int n, double* part, int P, cudaStream_t s) {
+    if (g.k == 1) {
+        if (g.xl == 0) k_plan_rot<R, 1, 0><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        else k_plan_rot<R, 1, 1><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        return;
+    }
+    switch (g.xl) {
+        case 0: k_plan_rot<R, 2, 0><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 1: k_plan_rot<R, 2, 1><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 2: k_plan_rot<R, 2, 2><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        default: k_plan_rot<R, 2, 3><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+    }
+}
+
+}  // namespace diaq
+
+struct diaq_adjoint_plan_s {
+    int device = 0;
+    int n = 0;
+    diaq_dtype dtype = DIAQ_C128;
+    int n_gates = 0, n_params = 0, n_terms = 0, n_slots = 1;
+    int P = 1;  // blocks of the rotation and reduction kernels (partial columns)
+    std::vector<BGate> gates;
+    std::vector<GateDesc> fwd, bwd;  // fixed gates: U and U^dag
+    BGate* d_gates = nullptr;
+    BTerm* d_terms = nullptr;
+    RotAngles* d_angles = nullptr;
+    void* d_psi = nullptr;
+    void* d_lam = nullptr;
+    double* d_theta = nullptr;
+    double* d_part = nullptr;
+    double* d_rows = nullptr;
+    double* d_out = nullptr;
+    double* h_theta = nullptr;
+    double* h_out = nullptr;
+    const void* psi0 = nullptr;  // captured initial-state pointer (NULL: |0...0>)
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void plan_free(diaq_adjoint_plan_s* p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    for (void* q : {static_cast<void*>(p->d_gates), static_cast<void*>(p->d_terms), static_cast<void*>(p->d_angles),
+                    p->d_psi, p->d_lam, static_cast<void*>(p->d_theta), static_cast<void*>(p->d_part),
+                    static_cast<void*>(p->d_rows), static_cast<void*>(p->d_out)})
+        if (q) cudaFree(q);
+    if (p->h_theta) cudaFreeHost(p->h_theta);
+    if (p->h_out) cudaFreeHost(p->h_out);
+    if (p->stream) cudaStreamDestroy(p->stream);
+}
+
+template <typename R>
+static diaq_status plan_record(diaq_adjoint_plan_s* p) {
+    using A = amp_t<R>;
+    cudaStream_t s = p->stream;
+    const int64_t N = int64_t(1) << p->n;
+    A* psi = static_cast<A*>(p->d_psi);
+    A* lam = static_cast<A*>(p->d_lam);
+    DIAQ_CUDA(cudaMemcpyAsync(p->d_theta, p->h_theta, sizeof(double) * size_t(std::max(p->n_params, 1)),
+                              cudaMemcpyHostToDevice, s));
+    if (p->n_gates) k_plan_angles<<<(p->n_gates + 127) / 128, 128, 0, s>>>(p->d_gates, p->n_gates, p->d_theta, p->d_angles);
+    k_plan_init<R><<<p->P, 256, 0, s>>>(static_cast<const A*>(p->psi0), psi, N);
+    DIAQ_CUDA(cudaGetLastError());
+    for (int g = 0; g < p->n_gates; ++g) {
+        const BGate& G = p->gates[size_t(g)];
+        if (G.param >= 0)
+            launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, s);
+        else
+            DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
+    }
+    k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
+    for (int g = p->n_gates - 1; g >= 0; --g) {
+        const BGate& G = p->gates[size_t(g)];
+        if (G.param >= 0) {
+            launch_plan_rot<R>(G, psi, lam, p->d_gates + g, p->d_angles + g, p->n, p->d_part + int64_t(G.slot) * p->P,
+                               p->P, s);
+        } else {
+            DIAQ_TRY(launch_adjoint_step(p->n, p->dtype, p->bwd[size_t(g)], nullptr, psi, lam, nullptr,
+                                         adjoint_partials(p->n, p->dtype, G.k), s));
+        }
+    }
+    k_plan_rows<<<p->n_slots, 256, 0, s>>>(p->d_part, p->P, p->d_rows);
+    k_plan_finish<<<1, 1, 0, s>>>(p->d_gates, p->n_gates, p->d_rows, p->n_params, p->d_out);
+    DIAQ_CUDA(cudaGetLastError());
+    DIAQ_CUDA(cudaMemcpyAsync(p->h_out, p->d_out, sizeof(double) * size_t(1 + p->n_params), cudaMemcpyDeviceToHost, s));
+    return DIAQ_OK;
+}
+
+static diaq_status plan_capture(diaq_adjoint_plan_s* p) {
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    DIAQ_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    diaq_status st = p->dtype == DIAQ_C128 ? plan_record<double>(p) : plan_record<float>(p);
+    cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+    if (st != DIAQ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(adjoint plan)");
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(adjoint plan)");
+    return DIAQ_OK;
+}
+
+extern "C" {
+
+diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, int32_t n_params, int32_t n_terms,
+                                     const uint64_t* xmask, const uint64_t* zmask, const double* coeff,
+                                     int32_t n_qubits, diaq_dtype dtype, diaq_adjoint_plan_t* out) {
+    clear_error();
+    cudaGetLastError();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_qubits < 2 || n_qubits > DIAQ_MAX_QUBITS) return fail(DIAQ_ERR_ARG, "n_qubits = %d out of range", n_qubits);
+    if (dtype != DIAQ_C64 && dtype != DIAQ_C128) return fail(DIAQ_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (n_gates < 0 || (n_gates && !gates) || n_params < 0 || n_terms < 0 ||
+        (n_terms && (!xmask || !zmask || !coeff)))
+        return fail(DIAQ_ERR_ARG, "bad gate, parameter or term arrays");
+    diaq_adjoint_plan_s* p = new (std::nothrow) diaq_adjoint_plan_s();
+    if (!p) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+    p->n = n_qubits;
+    p->dtype = dtype;
+    p->n_gates = n_gates;
+    p->n_params = n_params;
+    p->fwd.resize(static_cast<size_t>(n_gates));
+    p->bwd.resize(static_cast<size_t>(n_gates));
+    diaq_status st = DIAQ_OK;
+    std::vector<double> zero(static_cast<size_t>(std::max(n_params, 1)), 0.0);
+    for (int gi = 0; gi < n_gates && st == DIAQ_OK; ++gi) {
+        const diaq_gate& g = gates[gi];
+        if (g.k < 1 || g.k > 2) {
+            st = fail(DIAQ_ERR_UNSUPPORTED, "gate %d: the adjoint plan takes gates of 1 or 2 qubits", gi);
+            break;
+        }
+        if (g.param >= n_params) {
+            st = fail(DIAQ_ERR_ARG, "gate %d uses parameter %d >= n_params", gi, g.param);
+            break;
+        }
+        GateDesc d;
+        st = gate_desc_from(&g, n_qubits, zero.data(), &d);
+        if (st != DIAQ_OK) break;
+        BGate B = {};
+        B.k = g.k;
+        B.t[0] = g.targets[0];
+        B.t[1] = g.k == 2 ? g.targets[1] : 0;
+        B.param = g.param;
+        B.scale = g.scale;
+        B.slot = -1;
+        if (g.param >= 0) {
+            for (int q = 0; q < g.k; ++q) {
+                const char c = g.gen[q];
+                B.pauli[q] = (c == 'X' || c == 'x') ? 1 : (c == 'Y' || c == 'y') ? 2 : (c == 'Z' || c == 'z') ? 3 : 0;
+            }
+            fill_rot(&B);
+            B.slot = p->n_slots++;
+        } else {
+            p->fwd[size_t(gi)] = d;
+            GateDesc u = d;
+            const int D = 1 << d.k;
+            for (int r = 0; r < D; ++r)
+                for (int c = 0; c < D; ++c) u.m[size_t(r * D + c)] = std::conj(d.m[size_t(c * D + r)]);
+            p->bwd[size_t(gi)] = u;
+        }
+        p->gates.push_back(B);
+    }
+    std::vector<BTerm> terms;
+    const uint64_t valid = n_qubits >= 64 ? ~uint64_t(0) : ((uint64_t(1) << n_qubits) - 1);
+    for (int t = 0; t < n_terms && st == DIAQ_OK; ++t) {
+        if ((xmask[t] & ~valid) || (zmask[t] & ~valid)) {
+            st = fail(DIAQ_ERR_ARG, "Pauli term %d acts on a qubit >= n_qubits", t);
+            break;
+        }
+        BTerm T;
+        T.x = xmask[t];
+        T.z = zmask[t];
+        const int ny = __builtin_popcountll(xmask[t] & zmask[t]) & 3;
+        double kr = coeff[2 * t], ki = 0.0;
+        for (int r = 0; r < ny; ++r) {
+            const double tr = -ki, ti = kr;
+            kr = tr;
+            ki = ti;
+        }
+        T.kr = kr;
+        T.ki = ki;
+        terms.push_back(T);
+    }
+    p->n_terms = n_terms;
+    cudaError_t e = cudaSuccess;
+    if (st == DIAQ_OK && (e = cudaGetDevice(&p->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
+    if (st == DIAQ_OK) {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+        // one resident wave of the rotation kernels (about 2 blocks of 256
+        // per SM at their register counts); each thread loops over groups
+        const int64_t want = ((int64_t(1) << n_qubits) / 2 + 255) / 256;
+        p->P = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 2)));
+    }
+    const size_t ab = amp_bytes(dtype), N = size_t(1) << n_qubits;
+    if (st == DIAQ_OK) st = upload(&p->d_gates, p->gates);
+    if (st == DIAQ_OK) st = upload(&p->d_terms, terms);
+    if (st == DIAQ_OK &&
+        ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_angles), sizeof(RotAngles) * size_t(std::max(n_gates, 1)))) != cudaSuccess ||
+         (e = cudaMalloc(&p->d_psi, N * ab)) != cudaSuccess || (e = cudaMalloc(&p->d_lam, N * ab)) != cudaSuccess ||
+         (e = cudaMalloc(reinterpret_cast<void**>(&p->d_theta), sizeof(double) * size_t(std::max(n_params, 1)))) != cudaSuccess ||
+         (e = cudaMalloc(reinterpret_cast<void**>(&p->d_part), sizeof(double) * size_t(p->n_slots) * size_t(p->P))) != cudaSuccess ||
+         (e = cudaMalloc(reinterpret_cast<void**>(&p->d_rows), sizeof(double) * size_t(p->n_slots))) != cudaSuccess ||
+         (e = cudaMalloc(reinterpret_cast<void**>(&p->d_out), sizeof(double) * size_t(1 + n_params))) != cudaSuccess ||
+         (e = cudaMallocHost(reinterpret_cast<void**>(&p->h_theta), sizeof(double) * size_t(std::max(n_params, 1)))) != cudaSuccess ||
+         (e = cudaMallocHost(reinterpret_cast<void**>(&p->h_out), sizeof(double) * size_t(1 + n_params))) != cudaSuccess))
+        st = fail(DIAQ_ERR_ALLOC, "adjoint plan buffers: %s", cudaGetErrorString(e));
+    if (st == DIAQ_OK) {
+        std::memset(p->h_theta, 0, sizeof(double) * size_t(std::max(n_params, 1)));
+        if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            st = cuda_fail(e, "cudaStreamCreate(adjoint plan)");
+    }
+    if (st == DIAQ_OK) st = plan_capture(p);
+    if (st != DIAQ_OK) {
+        plan_free(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, const void* psi0, double* energy,
+                                  double* grad, diaq_stream_t stream) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (p->n_params > 0 && !theta) return fail(DIAQ_ERR_ARG, "theta is NULL");
+    for (int i = 0; i < p->n_params; ++i)
+        if (!std::isfinite(theta[i])) return fail(DIAQ_ERR_ARG, "theta[%d] is not finite", i);
+    if (psi0 && (reinterpret_cast<uintptr_t>(psi0) & 15)) return fail(DIAQ_ERR_ARG, "psi0 must be 16-byte aligned");
+    if (psi0 != p->psi0) {  // the initial-state pointer is part of the graph
+        p->psi0 = psi0;
+        DIAQ_TRY(plan_capture(p));
+    }
+    if (p->n_params) std::memcpy(p->h_theta, theta, sizeof(double) * size_t(p->n_params));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t ev;
+    DIAQ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    DIAQ_CUDA(cudaEventRecord(ev, s));
+    DIAQ_CUDA(cudaStreamWaitEvent(p->stream, ev, 0));
+    DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));
+    DIAQ_CUDA(cudaEventRecord(ev, p->stream));
+    DIAQ_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    DIAQ_CUDA(cudaEventSynchronize(ev));
+    cudaEventDestroy(ev);
+    if (energy) *energy = p->h_out[0];
+    if (grad)
+        for (int i = 0; i < p->n_params; ++i) grad[i] = p->h_out[1 + i];
+    return DIAQ_OK;
+}
+
+diaq_status diaq_adjoint_plan_destroy(diaq_adjoint_plan_t p) {
+    clear_error();
+    if (!p) return DIAQ_OK;
+    cudaDeviceSynchronize();
+    plan_free(p);
+    delete p;
     return DIAQ_OK;
 }
 

@@ -1,0 +1,158 @@
+// Pauli rotations exp(-i a/2 P) on k <= 2 targets, the parametric gates of
+// the adjoint sweep, with their structure resolved at compile time.
+//
+// For a Pauli string P on the targets with local X mask xl, local Z mask zl
+// and ny Y letters, P|c> = i^ny (-1)^{popc(c & zl)} |c ^ xl>, so
+//   (P x)_r = i^ny s_r x_{r ^ xl},  s_r = (-1)^{popc((r ^ xl) & zl)},
+// and U = cos(a/2) I - i sin(a/2) P gives
+//   (U x)_r = cos x_r + kappa s_r x_{r ^ xl},  kappa = -i sin(a/2) i^ny
+// (U^dag: kappa' = +i sin(a/2) i^ny). Every row has at most two terms and
+// xl is a template parameter, so the partner x_{r ^ xl} is a register, not
+// an indexed load; the angle enters as three numbers (cos, kappa).
+#pragma once
+
+#include "common.cuh"
+
+namespace diaq {
+
+struct RotShape {
+    int st[2];          // targets ascending
+    int64_t off[4];     // full-system offset of local index c
+    int zl;             // local Z mask
+    int ny;             // number of Y letters mod 4
+};
+
+// z * i^q
+template <typename A>
+__device__ __forceinline__ A mul_ipow(A z, int q) {
+    A w;
+    switch (q & 3) {
+        case 0: w = z; break;
+        case 1: w.x = -z.y; w.y = z.x; break;
+        case 2: w.x = -z.x; w.y = -z.y; break;
+        default: w.x = z.y; w.y = -z.x; break;
+    }
+    return w;
+}
+
+// One rotation over a grid-stride share of the groups, in place on psi
+// (and lam). cs = cos(a/2); (kr, ki) = kappa for the direction applied.
+// With lam (reverse step), returns this thread's share of
+// Im <lam|P|psi> taken before the update; otherwise 0. Each thread takes U
+// groups per iteration, all loads issued before any arithmetic.
+template <typename R, int K, int XL, int U>
+__device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
+                                            const RotShape& sh, R cs, R kr, R ki, int64_t tid, int64_t nthreads) {
+    constexpr int D = 1 << K;
+    using A = amp_t<R>;
+    int st[K];
+    int64_t off[D];
+#pragma unroll
+    for (int a = 0; a < K; ++a) st[a] = sh.st[a];
+#pragma unroll
+    for (int c = 0; c < D; ++c) off[c] = sh.off[c];
+    // per-row sign s_r folded into kappa once, so the loop spends no
+    // arithmetic on it; gradient terms are summed per row and signed at the end
+    R krr[D], kir[D];
+    bool sneg[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        sneg[r] = (__popc((r ^ XL) & sh.zl) & 1) != 0;
+        krr[r] = sneg[r] ? -kr : kr;
+        kir[r] = sneg[r] ? -ki : ki;
+    }
+    const bool kreal = ki == R(0), kimag = kr == R(0);
+    const int ny = sh.ny;
+    double accr[D];
+#pragma unroll
+    for (int r = 0; r < D; ++r) accr[r] = 0.0;
+    const int64_t G = int64_t(1) << (n - K);
+    for (int64_t g0 = tid; g0 < G; g0 += int64_t(U) * nthreads) {
+        int64_t b[U];
+        A p[U][D], l[U][D];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t gi = g0 + int64_t(u) * nthreads;
+            b[u] = gi < G ? insert_zeros<K>(gi, st) : int64_t(-1);
+            if (b[u] >= 0) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) p[u][c] = psi[b[u] + off[c]];
+                if (lam) {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) l[u][c] = lam[b[u] + off[c]];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b[u] < 0) continue;
+            if (lam) {
+                // Im conj(l_r) i^ny p_{r ^ XL}, per row (signed after the loop)
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    const A q = mul_ipow(p[u][r ^ XL], ny);
+                    accr[r] = fma(double(l[u][r].x), double(q.y), accr[r]);
+                    accr[r] = fma(-double(l[u][r].y), double(q.x), accr[r]);
+                }
+            }
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1 && !lam) break;
+                const A* v = pass == 0 ? p[u] : l[u];
+                A* dst = pass == 0 ? psi : lam;
+                A o[D];
+#pragma unroll
+                for (int r = 0; r < D; ++r) {
+                    const A x = v[r], y = v[r ^ XL];
+                    A w;
+                    if (kimag) {         // kappa_r = i ki_r: w = cs x + i ki_r y
+                        w.x = fma(cs, x.x, -kir[r] * y.y);
+                        w.y = fma(cs, x.y, kir[r] * y.x);
+                    } else if (kreal) {  // kappa_r = kr_r
+                        w.x = fma(cs, x.x, krr[r] * y.x);
+                        w.y = fma(cs, x.y, krr[r] * y.y);
+                    } else {
+                        w.x = fma(cs, x.x, fma(krr[r], y.x, -kir[r] * y.y));
+                        w.y = fma(cs, x.y, fma(krr[r], y.y, kir[r] * y.x));
+                    }
+                    o[r] = w;
+                }
+#pragma unroll
+                for (int r = 0; r < D; ++r) dst[b[u] + off[r]] = o[r];
+            }
+        }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) acc += sneg[r] ? -accr[r] : accr[r];
+    return acc;
+}
+
+// Groups per iteration: enough 16-byte loads in flight without spilling.
+template <typename R, int K, int XL>
+__device__ __forceinline__ double rot_groups(amp_t<R>* psi, amp_t<R>* lam, int n, const RotShape& sh, R cs, R kr,
+                                             R ki, int64_t tid, int64_t nthreads) {
+    constexpr int U = K == 1 ? 4 : (sizeof(R) == 4 ? 2 : 1);
+    if (lam) return rot_groups_u<R, K, XL, U>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
+    return rot_groups_u<R, K, XL, (K == 1 ? 4 : 2)>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
+}
+
+// Dispatch on (k, xl) for the persistent batch kernel: one group per
+// iteration, so its register budget (shared with every other gate path of
+// that kernel) is not exceeded.
+template <typename R>
+__device__ __forceinline__ double rot_dispatch(int k, int xl, amp_t<R>* psi, amp_t<R>* lam, int n,
+                                               const RotShape& sh, R cs, R kr, R ki, int64_t tid, int64_t nth) {
+    if (k == 1) {
+        if (xl == 0) return rot_groups_u<R, 1, 0, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        return rot_groups_u<R, 1, 1, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+    }
+    switch (xl) {
+        case 0: return rot_groups_u<R, 2, 0, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        case 1: return rot_groups_u<R, 2, 1, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        case 2: return rot_groups_u<R, 2, 2, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        default: return rot_groups_u<R, 2, 3, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+    }
+}
+
+}  // namespace diaq

@@ -51,7 +51,7 @@ def test_batch_matches_oracle_all_shapes(api):
     theta = np.concatenate([c.theta for c, _ in inst])
     b = _batch(api, inst, torch.complex128)
     for cluster in (1, 2, 4, 8):
-        for threads in (256, 1024):
+        for threads in (64, 256):
             b.set_launch(cluster, threads)
             E, G = b.run(theta)
             assert np.max(np.abs(E - E_ref)) <= 1e-12, (cluster, threads)
