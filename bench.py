@@ -480,12 +480,18 @@ def bench_random(api, n=30, depth=40):
     out["c64_max_abs_err_vs_c128"] = float((a - b).abs().max().item())
     del b
     res.pop("c64")
-    # fusion depth autotune (complex64), then the fused circuit
+    # fusion (commutation-aware grouping, the DIA x DIA product of Algorithm 1
+    # on each group): the autotuner times each depth for max_k 2 and 3 on
+    # the first five layers; the best plan then runs the whole circuit
     w = torch.zeros(N, dtype=torch.complex64, device="cuda")
     w[0] = 1
-    tune = api.autotune_fusion(circ.gates[: 5 * (n + n // 2)], n, w, max_k=4, max_depth=4)
-    d = tune["best_depth"]
-    ops = api.build_fused(circ.gates, n, 4, d, dtype=torch.complex64)
+    prefix = circ.gates[: 5 * (n + n // 2)]
+    tunes = {}
+    for mk in (2, 3):
+        tunes[mk] = api.autotune_fusion(prefix, n, w, max_k=mk, max_depth=8, commuting=True)
+    mk = min(tunes, key=lambda m: min(tunes[m]["ms"]))
+    d = tunes[mk]["best_depth"]
+    ops = api.build_fused(circ.gates, n, mk, d, dtype=torch.complex64, commuting=True)
     w.zero_()
     w[0] = 1
     torch.cuda.synchronize()
@@ -494,8 +500,9 @@ def bench_random(api, n=30, depth=40):
         api.apply(op, w, w)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    out["c64_fused"] = {"depth": d, "ops": len(ops), "s_per_circuit": el, "gates_per_s": len(circ.gates) / el,
-                        "tuning_ms_by_depth": tune["ms"]}
+    out["c64_fused"] = {"max_k": mk, "depth": d, "ops": len(ops), "s_per_circuit": el,
+                        "gates_per_s": len(circ.gates) / el,
+                        "tuning_ms_by_depth": {str(m): t["ms"] for m, t in tunes.items()}}
     wf = w.to(torch.complex128)
     out["c64_fused"]["fidelity_vs_c128"] = float(
         (torch.vdot(a, wf).abs() ** 2 / (torch.vdot(a, a).real * torch.vdot(wf, wf).real)).item())

@@ -326,11 +326,23 @@ diaq_status diaq_set_apply_launch(diaq_dtype dtype, int32_t k, int32_t threads, 
 diaq_status diaq_plan_fusion(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
                              int32_t* group_of_gate, int32_t* n_groups);
 
-/* For each fusion depth 1..max_depth: plan, build and fuse the circuit's
- * on-the-fly ops and time one in-place pass over the device state `work`
- * (contents overwritten); report the times and the fastest depth. */
+/* Group gates for fusion, moving a gate earlier past gates it commutes
+ * with (gates on disjoint qubits): each gate joins the latest group that
+ * touched any of its qubits when that group stays within max_k qubits and
+ * max_depth gates, else it opens a group. Writes the execution order of
+ * the gates (order[pos] = gate index), the group of each position
+ * (non-decreasing from 0) and the group count; the circuit's operator is
+ * unchanged. Host only. */
+diaq_status diaq_plan_fusion_commuting(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
+                                       int32_t* order, int32_t* group_of_pos, int32_t* n_groups);
+
+/* For each fusion depth 1..max_depth: plan (diaq_plan_fusion, or
+ * diaq_plan_fusion_commuting when `commuting` is non-zero), build and fuse
+ * the circuit's on-the-fly ops and time one in-place pass over the device
+ * state `work` (contents overwritten); report the times and the fastest
+ * depth. */
 diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
-                                 diaq_dtype dtype, void* work, int32_t max_k, int32_t max_depth,
+                                 diaq_dtype dtype, void* work, int32_t max_k, int32_t max_depth, int32_t commuting,
                                  diaq_fusion_tuning* report, diaq_stream_t stream);
 
 /* ------------------------------------------------------------------------

@@ -129,8 +129,11 @@ SIGNATURES.update({
                                            ctypes.POINTER(diaq_apply_tuning), _vp]),
     "diaq_set_apply_launch": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "diaq_plan_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
+    "diaq_plan_fusion_commuting": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                                                  _i32p]),
     "diaq_autotune_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, _vp,
-                                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(diaq_fusion_tuning), _vp]),
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(diaq_fusion_tuning), _vp]),
     "diaq_adjoint_plan_create": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _u64p, _u64p,
                                                 _dp, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(_vp)]),
     "diaq_adjoint_plan_run": (ctypes.c_int, [_vp, _dp, _vp, _dp, _dp, _vp]),

@@ -23,7 +23,7 @@ __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
     "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
-    "build_fused", "AdjointPlan",
+    "build_fused", "AdjointPlan", "plan_fusion_commuting",
 ]
 
 
@@ -347,10 +347,28 @@ def plan_fusion(gates, max_k: int, max_depth: int) -> list:
     return out[:len(gates)].tolist()
 
 
+def plan_fusion_commuting(gates, max_k: int, max_depth: int) -> tuple:
+    """(execution order, group of each position) with gates moved past
+    commuting gates (disjoint qubits) into earlier groups."""
+    arr, keep = _gate_array(gates)
+    order = np.zeros(max(1, len(gates)), dtype=np.int32)
+    grp = np.zeros(max(1, len(gates)), dtype=np.int32)
+    ng = ctypes.c_int32(0)
+    check(lib().diaq_plan_fusion_commuting(arr, len(gates), int(max_k), int(max_depth), order.ctypes.data_as(N._i32p),
+                                           grp.ctypes.data_as(N._i32p), ctypes.byref(ng)))
+    del keep
+    return order[:len(gates)].tolist(), grp[:len(gates)].tolist()
+
+
 def build_fused(gates, n_qubits: int, max_k: int, max_depth: int, dtype=torch.complex128, variant="onthefly",
-                theta=None, stream=None) -> list:
-    """Ops for a circuit with consecutive gates fused per plan_fusion."""
-    grp = plan_fusion(gates, max_k, max_depth)
+                theta=None, stream=None, commuting: bool = False) -> list:
+    """Ops for a circuit with gates fused per plan_fusion (consecutive
+    groups) or, with commuting=True, per plan_fusion_commuting."""
+    if commuting:
+        order, grp = plan_fusion_commuting(gates, max_k, max_depth)
+        gates = [gates[i] for i in order]
+    else:
+        grp = plan_fusion(gates, max_k, max_depth)
     ops, i = [], 0
     while i < len(gates):
         j = i
@@ -366,14 +384,14 @@ def build_fused(gates, n_qubits: int, max_k: int, max_depth: int, dtype=torch.co
 
 
 def autotune_fusion(gates, n_qubits: int, work: torch.Tensor, max_k: int = 4, max_depth: int = 4, theta=None,
-                    stream=None) -> dict:
+                    stream=None, commuting: bool = False) -> dict:
     _check_state(work, "work")
     arr, keep = _gate_array(gates)
     th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
     rep = N.diaq_fusion_tuning()
     check(lib().diaq_autotune_fusion(arr, len(gates), _dptr(th) if th is not None else None, int(n_qubits),
                                      _dtype_code(work.dtype), ctypes.c_void_p(work.data_ptr()), int(max_k),
-                                     int(max_depth), ctypes.byref(rep), _stream(stream)))
+                                     int(max_depth), int(bool(commuting)), ctypes.byref(rep), _stream(stream)))
     del keep
     return {"ops": [rep.ops[d] for d in range(rep.n_depths)], "ms": [rep.ms[d] for d in range(rep.n_depths)],
             "best_depth": rep.best_depth}

@@ -268,6 +268,35 @@ __device__ __forceinline__ void rot_angle(const BGate& g, const double* theta, b
     *ki = z.y;
 }
 
+// (H psi)_i for terms sorted by X mask: per group of equal masks the signed
+// weight W = sum_t kappa_t (-1)^{popc((i ^ x) & z_t)} is summed first, then
+// multiplied once by psi[i ^ x]. Arithmetic in the state's precision.
+template <typename R>
+__device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, int t0, int t1,
+                                                      int64_t i) {
+    using A = amp_t<R>;
+    R lr = R(0), li = R(0);
+    int t = t0;
+    while (t < t1) {
+        const uint64_t x = terms[t].x;
+        const uint64_t j = uint64_t(i) ^ x;
+        R wr = R(0), wi = R(0);
+        for (; t < t1 && terms[t].x == x; ++t) {
+            const bool neg = (__popcll(j & terms[t].z) & 1) != 0;
+            const R kr = R(terms[t].kr), ki = R(terms[t].ki);
+            wr += neg ? -kr : kr;
+            wi += neg ? -ki : ki;
+        }
+        const A pj = psi[j];
+        lr = fma(wr, pj.x, fma(-wi, pj.y, lr));
+        li = fma(wr, pj.y, fma(wi, pj.x, li));
+    }
+    A o;
+    o.x = lr;
+    o.y = li;
+    return o;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     using A = amp_t<R>;
@@ -310,30 +339,15 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
             team_sync(C);
         }
         // lambda = H psi and the energy Re <psi|lambda>
-        double e = 0.0;
+        Acc<R> e;
         for (int64_t i = tid; i < N; i += nthreads) {
-            double lr = 0.0, li = 0.0;
-            for (int t = I.term_begin; t < I.term_end; ++t) {
-                const BTerm T = a.terms[t];
-                const uint64_t j = uint64_t(i) ^ T.x;
-                const A pj = psi[j];
-                const double sgn = (__popcll(j & T.z) & 1) ? -1.0 : 1.0;
-                const double kr = sgn * T.kr, ki = sgn * T.ki;
-                lr = fma(kr, double(pj.x), lr);
-                lr = fma(-ki, double(pj.y), lr);
-                li = fma(kr, double(pj.y), li);
-                li = fma(ki, double(pj.x), li);
-            }
-            A o;
-            o.x = R(lr);
-            o.y = R(li);
+            const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
             lam[i] = o;
             const A pi = psi[i];
-            e = fma(double(pi.x), lr, e);
-            e = fma(double(pi.y), li, e);
+            e.add_dot(pi.x, o.x, pi.y, o.y);
         }
-        e = block_sum(e, warps);
-        if (threadIdx.x == 0) part[0 * C + rank] = e;
+        const double es = block_sum(e.value(), warps);
+        if (threadIdx.x == 0) part[0 * C + rank] = es;
         team_sync(C);
         // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
         for (int gi = I.gate_end - 1; gi >= I.gate_begin; --gi) {
@@ -718,6 +732,9 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
             b->terms.push_back(T);
         }
         if (st != DIAQ_OK) break;
+        // terms of equal X mask next to each other (the kernel sums their weights first)
+        std::stable_sort(b->terms.begin() + I.term_begin, b->terms.end(),
+                         [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
         I.term_end = int32_t(b->terms.size());
         I.n_slots = slots;
         I.psi_off = arena;
@@ -908,30 +925,15 @@ __global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<
                                                      int n_terms, int64_t N, double* part) {
     using A = amp_t<R>;
     __shared__ double warps[32];
-    double e = 0.0;
+    Acc<R> e;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-        double lr = 0.0, li = 0.0;
-        for (int t = 0; t < n_terms; ++t) {
-            const BTerm T = terms[t];
-            const uint64_t j = uint64_t(i) ^ T.x;
-            const A pj = psi[j];
-            const double sgn = (__popcll(j & T.z) & 1) ? -1.0 : 1.0;
-            const double kr = sgn * T.kr, ki = sgn * T.ki;
-            lr = fma(kr, double(pj.x), lr);
-            lr = fma(-ki, double(pj.y), lr);
-            li = fma(kr, double(pj.y), li);
-            li = fma(ki, double(pj.x), li);
-        }
-        A o;
-        o.x = R(lr);
-        o.y = R(li);
+        const A o = pauli_lambda_elem<R>(psi, terms, 0, n_terms, i);
         lam[i] = o;
         const A pi = psi[i];
-        e = fma(double(pi.x), lr, e);
-        e = fma(double(pi.y), li, e);
+        e.add_dot(pi.x, o.x, pi.y, o.y);
     }
-    e = block_sum(e, warps);
-    if (threadIdx.x == 0) part[blockIdx.x] = e;
+    const double es = block_sum(e.value(), warps);
+    if (threadIdx.x == 0) part[blockIdx.x] = es;
 }
 
 template <typename R>
@@ -1162,6 +1164,7 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
         T.ki = ki;
         terms.push_back(T);
     }
+    std::stable_sort(terms.begin(), terms.end(), [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
     p->n_terms = n_terms;
     cudaError_t e = cudaSuccess;
     if (st == DIAQ_OK && (e = cudaGetDevice(&p->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");

@@ -84,6 +84,44 @@ __device__ __forceinline__ void mac_typed(amp_t<R>& acc, bool& first, uint8_t ty
     }
 }
 
+// Per-thread running sum for the reductions. complex128 states accumulate
+// in FP64. complex64 states form their products in FP32 (the state's own
+// precision) and sum them with Kahan compensation in FP32, which carries
+// about twice the FP32 mantissa, so the FP64 pipe (1/64 of the FP32 rate on
+// this GPU) is not used per amplitude; the value joins the FP64 block sum.
+template <typename R>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    // s += a b - c d and s += a b + c d, two fused multiply-adds each
+    __device__ __forceinline__ void add_cross(double a, double b, double c, double d) {
+        s = fma(a, b, s);
+        s = fma(-c, d, s);
+    }
+    __device__ __forceinline__ void add_dot(double a, double b, double c, double d) {
+        s = fma(a, b, s);
+        s = fma(c, d, s);
+    }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <>
+struct Acc<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ void add_cross(float a, float b, float c_, float d) { add(fmaf(a, b, -c_ * d)); }
+    __device__ __forceinline__ void add_dot(float a, float b, float c_, float d) { add(fmaf(a, b, c_ * d)); }
+    __device__ __forceinline__ double value() const { return double(s) - double(c); }
+};
+
 // Deterministic block sum of one double per thread (fixed shuffle tree,
 // then warp 0 over the per-warp sums). Returns the total in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* smem_warps) {

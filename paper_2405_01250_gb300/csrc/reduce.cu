@@ -281,19 +281,24 @@ __global__ void __launch_bounds__(256)
 k_pauli_apply(const amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int64_t N, const DevGroups G) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        double lr = 0.0, li = 0.0;
+        R lr = R(0), li = R(0);
         for (int g = 0; g < G.n_groups; ++g) {
             const uint64_t j = (uint64_t)i ^ G.xmask[g];
-            const double2 p = to_d2<R>(psi[j]);
-            const double2 W = group_weight(G, g, j);
-            lr = fma(W.x, p.x, lr);
-            lr = fma(-W.y, p.y, lr);
-            li = fma(W.x, p.y, li);
-            li = fma(W.y, p.x, li);
+            const amp_t<R> p = psi[j];
+            // W_g(j) in the state's precision
+            R wr = R(0), wi = R(0);
+            for (int t = G.first[g]; t < G.first[g + 1]; ++t) {
+                const R kr = R(G.kappa[2 * t]), ki = R(G.kappa[2 * t + 1]);
+                const bool neg = (__popcll(j & G.zmask[t]) & 1) != 0;
+                wr += neg ? -kr : kr;
+                wi += neg ? -ki : ki;
+            }
+            lr = fma(wr, p.x, fma(-wi, p.y, lr));
+            li = fma(wr, p.y, fma(wi, p.x, li));
         }
         amp_t<R> o;
-        o.x = R(lr);
-        o.y = R(li);
+        o.x = lr;
+        o.y = li;
         lam[i] = o;
     }
 }
@@ -328,15 +333,14 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_inner_re(const amp_t<R>* __restrict__ a, const amp_t<R>* __restrict__ b, int64_t N, double* part) {
     __shared__ double warps[32];
-    double acc = 0.0;
+    Acc<R> acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-        const double2 u = to_d2<R>(a[i]), v = to_d2<R>(b[i]);
-        acc = fma(u.x, v.x, acc);
-        acc = fma(u.y, v.y, acc);
+        const amp_t<R> u = a[i], v = b[i];
+        acc.add_dot(u.x, v.x, u.y, v.y);
     }
-    acc = block_sum(acc, warps);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double t = block_sum(acc.value(), warps);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 int inner_partials(int n) { return reduce_blocks((int64_t(1) << n) / 4); }
@@ -378,7 +382,7 @@ k_adjoint_step(amp_t<R>* psi, amp_t<R>* lam, double* part, const __grid_constant
     constexpr int D = 1 << K;
     using A = amp_t<R>;
     __shared__ double warps[32];
-    double acc = 0.0;
+    Acc<R> acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.n_groups; g += stride) {
         const int64_t b = insert_zeros<K>(g, a.st);
@@ -398,8 +402,7 @@ k_adjoint_step(amp_t<R>* psi, amp_t<R>* lam, double* part, const __grid_constant
 #pragma unroll
                 for (int c = 0; c < D; ++c) mac_typed<R>(q, first, a.ptype[r * D + c], a.pre[r * D + c], a.pim[r * D + c], p[c]);
                 // Im(conj(l) q) = l.x q.y - l.y q.x
-                acc = fma(double(l[r].x), double(q.y), acc);
-                acc = fma(-double(l[r].y), double(q.x), acc);
+                acc.add_cross(l[r].x, q.y, l[r].y, q.x);
             }
         }
 #pragma unroll
@@ -420,8 +423,8 @@ k_adjoint_step(amp_t<R>* psi, amp_t<R>* lam, double* part, const __grid_constant
         }
     }
     if (part) {
-        acc = block_sum(acc, warps);
-        if (threadIdx.x == 0) part[blockIdx.x] = acc;
+        const double t = block_sum(acc.value(), warps);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
 }
 

@@ -63,9 +63,7 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
     }
     const bool kreal = ki == R(0), kimag = kr == R(0);
     const int ny = sh.ny;
-    double accr[D];
-#pragma unroll
-    for (int r = 0; r < D; ++r) accr[r] = 0.0;
+    Acc<R> accr[D];
     const int64_t G = int64_t(1) << (n - K);
     for (int64_t g0 = tid; g0 < G; g0 += int64_t(U) * nthreads) {
         int64_t b[U];
@@ -91,8 +89,7 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
 #pragma unroll
                 for (int r = 0; r < D; ++r) {
                     const A q = mul_ipow(p[u][r ^ XL], ny);
-                    accr[r] = fma(double(l[u][r].x), double(q.y), accr[r]);
-                    accr[r] = fma(-double(l[u][r].y), double(q.x), accr[r]);
+                    accr[r].add_cross(l[u][r].x, q.y, l[u][r].y, q.x);
                 }
             }
 #pragma unroll
@@ -124,7 +121,7 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
     }
     double acc = 0.0;
 #pragma unroll
-    for (int r = 0; r < D; ++r) acc += sneg[r] ? -accr[r] : accr[r];
+    for (int r = 0; r < D; ++r) acc += sneg[r] ? -accr[r].value() : accr[r].value();
     return acc;
 }
 

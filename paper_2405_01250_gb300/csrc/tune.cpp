@@ -158,8 +158,109 @@ diaq_status diaq_plan_fusion(const diaq_gate* gates, int32_t n_gates, int32_t ma
     return DIAQ_OK;
 }
 
+diaq_status diaq_plan_fusion_commuting(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
+                                       int32_t* order, int32_t* group_of_pos, int32_t* n_groups) {
+    clear_error();
+    if (n_gates < 0 || (n_gates && (!gates || !order || !group_of_pos)) || !n_groups)
+        return fail(DIAQ_ERR_ARG, "bad arrays");
+    if (max_k < 1 || max_k > DIAQ_MAX_K) return fail(DIAQ_ERR_ARG, "max_k = %d outside [1, %d]", max_k, DIAQ_MAX_K);
+    if (max_depth < 1) return fail(DIAQ_ERR_ARG, "max_depth = %d < 1", max_depth);
+    // A gate depends on the last block that touched any of its qubits; it may
+    // join that block (the latest of them) if the block stays within max_k
+    // qubits and max_depth gates: every block created after it touches none
+    // of the gate's qubits, so the gate commutes past them unchanged.
+    struct Block {
+        std::vector<int> gates;
+        std::vector<int> qubits;
+    };
+    std::vector<Block> blocks;
+    std::vector<int> last;  // per qubit: last block touching it, -1 if none
+    for (int i = 0; i < n_gates; ++i) {
+        const diaq_gate& g = gates[i];
+        if (g.k < 1 || g.k > DIAQ_MAX_K) return fail(DIAQ_ERR_ARG, "gate %d has k = %d", i, g.k);
+        if (g.k > max_k) return fail(DIAQ_ERR_ARG, "gate %d (k = %d) exceeds max_k = %d", i, g.k, max_k);
+        int dep = -1;
+        for (int a = 0; a < g.k; ++a) {
+            const int q = g.targets[a];
+            if (q < 0) return fail(DIAQ_ERR_ARG, "gate %d has a negative target", i);
+            if (q >= int(last.size())) last.resize(size_t(q) + 1, -1);
+            dep = std::max(dep, last[size_t(q)]);
+        }
+        bool joined = false;
+        // Blocks this gate depends on besides the latest one: one that no
+        // later block has touched commutes forward past everything after
+        // it, so it can merge into the latest block (their qubit sets are
+        // disjoint, so the order between them does not matter).
+        if (dep >= 0) {
+            std::vector<int> others;
+            for (int a = 0; a < g.k; ++a) {
+                const int d = last[size_t(g.targets[a])];
+                if (d >= 0 && d != dep && std::find(others.begin(), others.end(), d) == others.end()) others.push_back(d);
+            }
+            std::vector<int> u = blocks[size_t(dep)].qubits;
+            size_t depth = blocks[size_t(dep)].gates.size() + 1;
+            bool ok = true;
+            for (int d : others) {
+                const Block& A = blocks[size_t(d)];
+                for (int q : A.qubits) ok &= last[size_t(q)] == d;
+                for (int q : A.qubits)
+                    if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
+                depth += A.gates.size();
+            }
+            for (int a = 0; a < g.k; ++a)
+                if (std::find(u.begin(), u.end(), g.targets[a]) == u.end()) u.push_back(g.targets[a]);
+            if (ok && !others.empty() && int(u.size()) <= max_k && int(depth) <= max_depth) {
+                Block& B = blocks[size_t(dep)];
+                std::vector<int> merged;
+                for (int d : others) {
+                    merged.insert(merged.end(), blocks[size_t(d)].gates.begin(), blocks[size_t(d)].gates.end());
+                    for (int q : blocks[size_t(d)].qubits) last[size_t(q)] = dep;
+                    blocks[size_t(d)].gates.clear();
+                    blocks[size_t(d)].qubits.clear();
+                }
+                merged.insert(merged.end(), B.gates.begin(), B.gates.end());
+                merged.push_back(i);
+                B.gates = merged;
+                B.qubits = u;
+                joined = true;
+            }
+        }
+        if (!joined && dep >= 0) {
+            Block& B = blocks[size_t(dep)];
+            std::vector<int> u = B.qubits;
+            for (int a = 0; a < g.k; ++a)
+                if (std::find(u.begin(), u.end(), g.targets[a]) == u.end()) u.push_back(g.targets[a]);
+            if (int(u.size()) <= max_k && int(B.gates.size()) < max_depth) {
+                B.gates.push_back(i);
+                B.qubits = u;
+                joined = true;
+            }
+        }
+        if (!joined) {
+            Block B;
+            B.gates.push_back(i);
+            B.qubits.assign(g.targets, g.targets + g.k);
+            blocks.push_back(B);
+            dep = int(blocks.size()) - 1;
+        }
+        for (int a = 0; a < g.k; ++a) last[size_t(g.targets[a])] = dep;
+    }
+    int pos = 0, grp = 0;
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        if (blocks[b].gates.empty()) continue;  // merged into a later block
+        for (int gi : blocks[b].gates) {
+            order[pos] = gi;
+            group_of_pos[pos] = grp;
+            ++pos;
+        }
+        ++grp;
+    }
+    *n_groups = grp;
+    return DIAQ_OK;
+}
+
 diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
-                                 diaq_dtype dtype, void* work, int32_t max_k, int32_t max_depth,
+                                 diaq_dtype dtype, void* work, int32_t max_k, int32_t max_depth, int32_t commuting,
                                  diaq_fusion_tuning* report, diaq_stream_t stream) {
     clear_error();
     cudaGetLastError();
@@ -167,12 +268,17 @@ diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const 
     if (max_depth < 1 || max_depth > DIAQ_FUSION_TUNE_MAX) return fail(DIAQ_ERR_ARG, "max_depth outside [1, %d]", DIAQ_FUSION_TUNE_MAX);
     if (n_gates < 1 || !gates) return fail(DIAQ_ERR_ARG, "need at least one gate");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    std::vector<int32_t> grp(static_cast<size_t>(n_gates));
+    std::vector<int32_t> grp(static_cast<size_t>(n_gates)), order(static_cast<size_t>(n_gates));
     float best = 1e30f;
     int bestd = 1;
     for (int d = 1; d <= max_depth; ++d) {
         int32_t ng = 0;
-        DIAQ_TRY(diaq_plan_fusion(gates, n_gates, max_k, d, grp.data(), &ng));
+        if (commuting) {
+            DIAQ_TRY(diaq_plan_fusion_commuting(gates, n_gates, max_k, d, order.data(), grp.data(), &ng));
+        } else {
+            DIAQ_TRY(diaq_plan_fusion(gates, n_gates, max_k, d, grp.data(), &ng));
+            for (int i = 0; i < n_gates; ++i) order[size_t(i)] = i;
+        }
         std::vector<diaq_op_t> ops;
         diaq_status st = DIAQ_OK;
         for (int i = 0; i < n_gates && st == DIAQ_OK;) {
@@ -180,7 +286,7 @@ diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const 
             std::vector<diaq_op_t> part;
             while (j < n_gates && grp[size_t(j)] == grp[size_t(i)] && st == DIAQ_OK) {
                 diaq_op_t o = nullptr;
-                st = diaq_build(&gates[j], n_qubits, dtype, DIAQ_ONTHEFLY, theta, stream, &o);
+                st = diaq_build(&gates[order[size_t(j)]], n_qubits, dtype, DIAQ_ONTHEFLY, theta, stream, &o);
                 if (st == DIAQ_OK) part.push_back(o);
                 ++j;
             }

@@ -134,3 +134,21 @@ def test_fused_circuit_and_fusion_autotune(api):
     w = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
     rep = api.autotune_fusion(circ.gates, n, w, max_k=4, max_depth=4)
     assert 1 <= rep["best_depth"] <= 4 and rep["ops"][0] == len(circ.gates)
+
+
+def test_commuting_fused_circuit(api):
+    n = 12
+    circ = synth.random_layered(n, 4, seed=8)
+    psi0 = synth.basis_state(n, 0)
+    want = oracle.run_circuit(circ, psi0)
+    for max_k, depth in ((2, 4), (3, 8)):
+        for dtype, tol in ((torch.complex128, TOL_C128), (torch.complex64, 2e-5)):
+            ops = api.build_fused(circ.gates, n, max_k, depth, dtype=dtype, commuting=True)
+            assert len(ops) < len(circ.gates) // 2
+            x = dev(psi0, dtype)
+            for op in ops:
+                api.apply(op, x, x)
+            assert maxerr(host(x), want) <= tol
+    w = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    rep = api.autotune_fusion(circ.gates, n, w, max_k=2, max_depth=4, commuting=True)
+    assert rep["ops"][0] == len(circ.gates) and rep["ops"][3] < rep["ops"][0]

@@ -72,3 +72,36 @@ def test_batch_validation_before_device(api):
         api.Batch([(3, [synth.Gate((0,), None, param=2, gen="X")], 1, obs)])
     with pytest.raises(DiaqError, match="qubit"):
         api.Batch([(2, [synth.Gate((0,), synth.H)], 0, ([0], [1 << 5], [1.0]))])
+
+
+def test_plan_fusion_commuting_valid_and_exact(api):
+    """Commutation-aware grouping: the order is a permutation that moves a
+    gate only past gates on disjoint qubits, groups respect the limits, and
+    the reordered circuit is the same operator (checked with the oracle)."""
+    import oracle
+    for seed in range(3):
+        circ = synth.random_layered(8, 4, seed=seed)
+        for max_k, depth in ((2, 4), (3, 8), (4, 6)):
+            order, grp = api.plan_fusion_commuting(circ.gates, max_k, depth)
+            assert sorted(order) == list(range(len(circ.gates)))
+            assert grp[0] == 0 and all(b - a in (0, 1) for a, b in zip(grp, grp[1:]))
+            for g in set(grp):
+                members = [circ.gates[order[p]] for p in range(len(order)) if grp[p] == g]
+                assert len(members) <= depth
+                assert len({q for m in members for q in m.targets}) <= max_k
+            # any two gates that swapped relative order act on disjoint qubits
+            pos = {gi: p for p, gi in enumerate(order)}
+            for a in range(len(circ.gates)):
+                for b in range(a + 1, len(circ.gates)):
+                    if pos[a] > pos[b]:
+                        assert not set(circ.gates[a].targets) & set(circ.gates[b].targets)
+            psi = synth.random_state(8, np.random.default_rng(seed))
+            ref = oracle.run_circuit(circ, psi)
+            got = psi
+            for gi in order:
+                got = oracle.apply_gate(got, circ.gates[gi].targets, circ.gates[gi].matrix)
+            assert np.max(np.abs(got - ref)) < 1e-13
+    # the random-layer structure fuses to one group per CZ pair and layer at max_k = 2
+    circ = synth.random_layered(30, 4, seed=0)
+    _, grp = api.plan_fusion_commuting(circ.gates, 2, 4)
+    assert max(grp) + 1 == 60
