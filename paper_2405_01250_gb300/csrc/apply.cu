@@ -341,23 +341,27 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
         const int64_t len = N - (d < 0 ? -d : d);
         const int64_t shift = d < 0 ? -d : 0;
         const A* v = vals + starts[q];
-        A a[G];
+        // value and x loads issued together (no dependent round trip); x is
+        // read for every row in the diagonal's range, used where A_d(i) != 0
+        A a[G], xv[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             const int64_t p = row[u] - shift;
             if (row[u] >= 0 && p >= 0 && p < len) {
                 a[u] = ld_stream(v + p);
+                xv[u] = x[row[u] + d];
             } else {
                 a[u].x = R(0);
                 a[u].y = R(0);
+                xv[u].x = R(0);
+                xv[u].y = R(0);
             }
         }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             if (a[u].x == R(0) && a[u].y == R(0)) continue;
-            const A xv = x[row[u] + d];
             const uint8_t t = (a[u].y == R(0)) ? (a[u].x == R(1) ? 1 : 2) : 4;
-            mac_typed<R>(acc[u], first[u], t, a[u].x, a[u].y, xv);
+            mac_typed<R>(acc[u], first[u], t, a[u].x, a[u].y, xv[u]);
         }
     }
 #pragma unroll
