@@ -24,6 +24,8 @@ from .circuits import (  # noqa: F401
     random_layered,
     ansatz,
     ansatz_observable,
+    tfim,
+    magnetisation_observable,
     qaoa_instance,
     qaoa_batch,
     random_state,

@@ -15,8 +15,9 @@ Conventions, shared as *data layout* by both sides of every parity check:
   coeff)`` triples: bit ``q`` of ``xmask``/``zmask`` set means an X/Z factor
   on qubit ``q``; both set means Y.
 
-The circuits stand in for the paper's SupermarQ GHZ and QASMBench QFT
-workloads (Section VII), which are not available here; the random-layer,
+The circuits stand in for the paper's SupermarQ GHZ and Hamiltonian-simulation
+(TFIM) and QASMBench QFT workloads (Section VII), which are not available
+here; the random-layer,
 ansatz and QAOA circuits exercise the precision, adjoint and batching paths.
 """
 
@@ -220,6 +221,30 @@ def ansatz_observable(n: int = 20) -> Observable:
     terms = [({i: "Z", i + 1: "Z"}, 1.0) for i in range(n - 1)]
     terms += [({i: "X"}, 0.5) for i in range(n)]
     return _observable(terms)
+
+
+def tfim(n: int, steps: int, dt: float, J: float = 1.0, h: float = 1.0) -> Circuit:
+    """First-order Trotter circuit of the 1D transverse-field Ising model
+    H = -J sum_{i<n-1} Z_i Z_{i+1} - h sum_i X_i (open chain), the paper's
+    Hamiltonian-simulation (HAM) workload, from |0...0>. Each of `steps`
+    steps applies exp(+i J dt Z_i Z_{i+1}) on every bond (i = 0..n-2), then
+    exp(+i h dt X_i) on every qubit. As parametric gates exp(-i a/2 P):
+    every bond gate uses theta[0] = -2 J dt (generator ZZ), every field gate
+    theta[1] = -2 h dt (generator X)."""
+    gates = []
+    for _ in range(steps):
+        for i in range(n - 1):
+            gates.append(Gate((i, i + 1), None, param=0, gen="ZZ", name="rzz"))
+        for q in range(n):
+            gates.append(Gate((q,), None, param=1, gen="X", name="rx"))
+    theta = np.array([-2.0 * J * dt, -2.0 * h * dt], dtype=np.float64)
+    return Circuit(n, gates, theta=theta,
+                   meta={"workload": f"tfim-{n}-s{steps}", "J": J, "h": h, "dt": dt, "steps": steps})
+
+
+def magnetisation_observable(n: int) -> Observable:
+    """Average magnetisation M_z = (1/n) sum_i Z_i."""
+    return _observable([({i: "Z"}, 1.0 / n) for i in range(n)])
 
 
 def _random_3_regular(n: int, rng: np.random.Generator) -> list:
