@@ -233,7 +233,35 @@ def run_ours(args, rank, world):
     per_class = {c: {"launches_per_step": len(v) // args.steps, "mean_ms": statistics.mean(v),
                      "gbs": bytes_op / (statistics.mean(v) / 1e3) / 1e9} for c, v in dur.items()}
 
-    # end to end through diaq_simulate: pinned host |j> in, pinned host result out
+    # in place: the same 420 ops with the identity-row skip (a controlled
+    # phase reads and writes a quarter of the rows, a SWAP half, H all);
+    # bytes counted per op as the path moves them
+    inplace_bytes = sum(op.apply_bytes(in_place=True) for op in ops)
+    inplace = None
+    if not args.no_inplace:
+        c = a.clone()
+        for _ in range(2):
+            for op in ops:
+                api.apply(op, c, c)
+        i0 = torch.cuda.Event(enable_timing=True)
+        i1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        i0.record(stream)
+        for _ in range(args.steps):
+            for op in ops:
+                api.apply(op, c, c)
+        i1.record(stream)
+        torch.cuda.synchronize()
+        ims = i0.elapsed_time(i1) / args.steps
+        inplace = {"workload": f"qft-{n} complex128, {len(ops)} ops in place (identity rows skipped)",
+                   "ms_per_step": ims, "gates_per_s": len(ops) / (ims / 1e3),
+                   "bytes_per_step": inplace_bytes, "gbs": inplace_bytes / (ims / 1e3) / 1e9,
+                   "speedup_vs_out_of_place_step": apply_ms / ims, "norm": api.norm(c)}
+        del c
+
+    # end to end through diaq_simulate: pinned host |j> in, pinned host result
+    # out; its ops run in place with the identity-row skip, so the bytes are
+    # the in-place bytes of each op
     e2e = None
     if not args.no_e2e:
         hin = torch.zeros(N, dtype=torch.complex128, pin_memory=True)
@@ -248,9 +276,11 @@ def run_ours(args, rank, world):
             api.simulate(ops, hin, hout, w0)
         e_s = (time.perf_counter() - te) / e_steps
         amp_ok = abs(complex(hout[0]) - 1 / math.sqrt(N)) < 1e-12
-        e2e = {"value": world * len(ops) * bytes_op / e_s / 1e9, "unit": UNIT,
+        e2e = {"value": world * inplace_bytes / e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16, "ms_per_step": e_s * 1e3,
-               "api": "diaq_simulate (in-place on-the-fly ops, pinned host buffers)", "checked": bool(amp_ok)}
+               "gates_per_s": world * len(ops) / e_s,
+               "api": "diaq_simulate (on-the-fly ops in place with the identity-row skip, pinned host buffers); "
+                      "GB/s over the bytes the in-place ops move", "checked": bool(amp_ok)}
         del hin, hout, w0
 
     # stored-diagonal variant: a sample of ops materialised and applied
@@ -296,7 +326,7 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "hbm", "kernel": "k_apply_small<double,2,1> (controlled phase, diagonal class)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": _traffic("cp_c128")},
-        "e2e": e2e, "stored": stored, "clocks": clocks,
+        "e2e": e2e, "inplace": inplace, "stored": stored, "clocks": clocks,
         "gpu_launches": args.steps * (len(ops) + 2),
     }
     # free the QFT buffers before the secondary workloads
@@ -307,6 +337,10 @@ def run_ours(args, rank, world):
         extras["adjoint"] = bench_adjoint(api)
     if not args.no_batch:
         extras["batch"] = bench_batch(api, count=args.batch_count)
+    if not args.no_tfim:
+        extras["tfim"] = bench_tfim(api, n=args.tfim_qubits)
+    if not args.no_unitary:
+        extras["unitary"] = bench_unitary(api)
     if args.random:
         extras["random"] = bench_random(api, n=args.random_qubits)
     if extras:
@@ -354,6 +388,23 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
         el = (time.perf_counter() - t0) / r
         out[f"adjoint_graph_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3,
                                         "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(g - grads[name])))}
+        # window-fused sweeps: blocks of <= w qubits, one launch per block
+        best = None
+        for w in (3, 4, 5):
+            plan.set_window(w)
+            for _ in range(2):
+                e, gw = plan.run(circ.theta)
+            t0 = time.perf_counter()
+            for _ in range(r):
+                e, gw = plan.run(circ.theta)
+            elw = (time.perf_counter() - t0) / r
+            rec = {"window": w, "launches_per_sweep": plan.window()[1], "grads_per_s": 1.0 / elw,
+                   "ms_per_gradient": elw * 1e3,
+                   "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(gw - grads[name])))}
+            out[f"adjoint_window{w}_{name}"] = rec
+            if best is None or rec["grads_per_s"] > best["grads_per_s"]:
+                best = rec
+        out[f"adjoint_best_{name}"] = best
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
     # plain FP64 path: one circuit evaluation = 472 applies + expectation
@@ -385,6 +436,8 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
     for name in ("c128", "c64"):
         out[f"speedup_adjoint_graph_{name}_vs_plain"] = (out[f"adjoint_graph_{name}"]["grads_per_s"]
                                                         / out["plain_fp64_param_shift"]["grads_per_s"])
+        out[f"speedup_adjoint_best_{name}_vs_plain"] = (out[f"adjoint_best_{name}"]["grads_per_s"]
+                                                       / out["plain_fp64_param_shift"]["grads_per_s"])
     return out
 
 
@@ -411,8 +464,10 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
             tune = proxy.autotune(np.concatenate([c.theta for c, _ in inst[:16]]), reps=1)
             proxy.close()
         else:
-            tune = {"best_cluster": shape[0], "best_threads": shape[1], "best_ms": None, "tried": []}
+            tune = {"best_cluster": shape[0], "best_threads": shape[1], "best_window": shape[2] if len(shape) > 2 else 0,
+                    "best_ms": None, "tried": []}
         b = api.Batch(desc, dtype=dt)
+        b.set_window(tune.get("best_window", 0))
         b.set_launch(tune["best_cluster"], tune["best_threads"])
         E, G = b.run(theta)
         torch.cuda.synchronize()
@@ -423,7 +478,8 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
         energies[name] = E
         q = b.query()
         out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
-                                  "cluster": q["cluster"], "threads": q["threads"], "teams": q["teams"],
+                                  "cluster": q["cluster"], "threads": q["threads"], "window": b.window(),
+                                  "teams": q["teams"],
                                   "arena_bytes": q["arena_bytes"], "launches_per_batch": 2,
                                   "tuning": {"proxy_best_ms": tune["best_ms"], "shapes_tried": len(tune["tried"])}}
         b.close()
@@ -444,6 +500,70 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
         out["batched_c128_vs_plain_max_abs_energy_diff"] = float(np.max(np.abs(np.array(e_plain) - energies["c128"])))
         out["speedup_batched_c128_vs_plain"] = out["batched_c128"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]
         out["speedup_batched_c64_vs_plain"] = out["batched_c64"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]
+    return out
+
+
+def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7):
+    """Trotterised 1D transverse-field Ising model (the paper's
+    Hamiltonian-simulation workload): `steps` first-order Trotter steps of
+    ZZ bond rotations and X field rotations, in place, complex128 and
+    complex64, read out as the average magnetisation (FP64 reduction)."""
+    import torch
+    import synth
+    circ = synth.tfim(n, steps, dt, J=J, h=h)
+    obs = synth.magnetisation_observable(n)
+    N = 1 << n
+    out = {"workload": f"tfim-{n}, {steps} Trotter steps (dt {dt}, J {J}, h {h}): {len(circ.gates)} gates, "
+                       "in place + magnetisation"}
+    stream = torch.cuda.current_stream()
+    mags = {}
+    for name, dt_ in (("c128", torch.complex128), ("c64", torch.complex64)):
+        ops = [api.build(g, n, dtype=dt_, theta=circ.theta) for g in circ.gates]
+        nbytes = sum(op.apply_bytes(in_place=True) for op in ops)
+        x = torch.zeros(N, dtype=dt_, device="cuda")
+        for rep in range(2):  # the first pass warms up, the second is timed
+            x.zero_()
+            x[0] = 1
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for op in ops:
+                api.apply(op, x, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        mags[name] = api.expect(x, obs.xmask, obs.zmask, obs.coeff).real
+        out[name] = {"ms_per_circuit": ms, "gates_per_s": len(ops) / (ms / 1e3), "gbs": nbytes / (ms / 1e3) / 1e9,
+                     "magnetisation": mags[name], "norm": api.norm(x)}
+        del ops, x
+    out["c64_vs_c128_magnetisation_diff"] = abs(mags["c64"] - mags["c128"])
+    return out
+
+
+def bench_unitary(api):
+    """Unitary simulation by chained device DiaQ products (Algorithm 1), with
+    all-zero diagonals pruned after each product: GHZ-12 (stays sparse) and
+    TFIM-10 with 2 Trotter steps (fills in), complex128. Reports the time per
+    chain, the diagonals and non-zeros at the end, and the peak."""
+    import torch
+    import synth
+    out = {}
+    for name, n, circ in (("ghz", 12, synth.ghz(12)), ("tfim", 10, synth.tfim(10, 2, 0.1, J=1.0, h=0.7))):
+        N = 1 << n
+        op, nd, nz = api.unitary_chain(circ.gates, n, theta=circ.theta if circ.n_params else None)
+        del op
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op, nd, nz = api.unitary_chain(circ.gates, n, theta=circ.theta if circ.n_params else None)
+        el = time.perf_counter() - t0
+        out[f"{name}-{n}"] = {"gates": len(circ.gates), "ms_per_chain": el * 1e3,
+                               "products_per_s": (len(circ.gates) - 1) / el,
+                               "final_diagonals": int(nd[-1]), "final_nnz": int(nz[-1]),
+                               "final_sparsity": 1.0 - float(nz[-1]) / (N * N),
+                               "min_sparsity": 1.0 - float(np.max(nz)) / (N * N),
+                               "max_diagonals": int(np.max(nd))}
+        del op
     return out
 
 
@@ -581,11 +701,16 @@ def main():
     ap.add_argument("--no-stored", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-inplace", action="store_true")
+    ap.add_argument("--no-tfim", action="store_true")
+    ap.add_argument("--no-unitary", action="store_true")
+    ap.add_argument("--tfim-qubits", type=int, default=28)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-only", action="store_true", help="profiling entry: one batch run, fixed shape")
     ap.add_argument("--batch-cluster", type=int, default=8)
     ap.add_argument("--batch-threads", type=int, default=256)
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--batch-window", type=int, default=0)
     ap.add_argument("--random", action="store_true", help="also run the random layered circuit (slow in c128)")
     ap.add_argument("--random-qubits", type=int, default=30)
     args = ap.parse_args()
@@ -605,7 +730,7 @@ def main():
         B.build()
         from paper_2405_01250_gb300 import api
         print(json.dumps(bench_batch(api, count=args.batch_count, reps=1, plain=False,
-                                     shape=(args.batch_cluster, args.batch_threads),
+                                     shape=(args.batch_cluster, args.batch_threads, args.batch_window),
                                      dtypes=(args.batch_dtype,))), flush=True)
         return
     rank, world = _dist()

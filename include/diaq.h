@@ -204,16 +204,63 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
 
 /* y = A x on `stream`. x, y: device state vectors of the op's n_qubits and
  * dtype. y == x (in place) is allowed for on-the-fly ops only; otherwise x
- * and y must not overlap (DIAQ_ERR_ARG). */
+ * and y must not overlap (DIAQ_ERR_ARG).
+ *
+ * In place, an op of k <= 3 qubits whose local matrix has identity rows
+ * (row r equal to e_r exactly, e.g. a controlled phase, CZ, CNOT or SWAP;
+ * Section III-A) reads only the local columns its other rows use and writes
+ * only those rows: a controlled phase or CZ moves a quarter of the bytes of
+ * a full pass, a CNOT or SWAP half. The result is bit-identical to the full
+ * pass. diaq_op_apply_bytes reports the bytes either way. */
 diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t stream);
+
+/* Algorithmic HBM bytes of one diaq_apply of op into *bytes: out of place
+ * (in_place = 0) 2 N s for on-the-fly ops and 2 N s + s sum_d (N - |d|) for
+ * stored ops (s = bytes per amplitude); in place (on-the-fly ops only,
+ * DIAQ_ERR_ARG for stored) N / 2^k x (columns read + rows written) x s when
+ * the op has identity rows, else 2 N s. Host only. */
+diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
 
 /* Run ops[0..count-1] in order on a state: psi_in -> psi_out. psi_in and
  * psi_out may each be host (pageable or pinned) or device pointers; host
  * data are copied in and out on `stream` inside the call. work0 and work1
  * are caller-owned device state buffers (work1 may be NULL when every op is
- * on-the-fly). Synchronises `stream` before returning. */
+ * on-the-fly). On-the-fly ops run in place in work0 (with the identity-row
+ * skip of diaq_apply). Synchronises `stream` before returning. */
 diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
                           void* work0, void* work1, diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Unitary simulation - Section II-A (a circuit's unitary as the product of
+ * its gate unitaries) and Section III-A (the number of diagonals and the
+ * sparsity of that product after each time step, e.g. GHZ(10) stays at
+ * least 99.8 % sparse). The products run on the device by Algorithm 1.
+ * ------------------------------------------------------------------------ */
+
+/* Per stored diagonal of op (in index order), the number of values that are
+ * not exactly zero, into nnz (host, n_diagonals entries). DIAQ_ERR_ARG for
+ * on-the-fly ops. Synchronises `stream`. */
+diaq_status diaq_op_diagonal_nnz(diaq_op_t op, int64_t* nnz, diaq_stream_t stream);
+
+/* A new stored DIAQ_CLASS_RAW op equal to op without the diagonals whose
+ * values are all exactly zero. No value changes, and values that are
+ * non-zero only by rounding are kept (no tolerance is applied). DIAQ_ERR_ARG
+ * for on-the-fly ops. Synchronises `stream`. */
+diaq_status diaq_op_prune(diaq_op_t op, diaq_stream_t stream, diaq_op_t* out);
+
+/* The unitary U = G_{n_gates-1} ... G_0 of a circuit: each gate is built as
+ * a stored op (diaq_build) and multiplied onto U on the device with the
+ * accumulating DiaQ product of Algorithm 1, one time step at a time. With
+ * prune != 0, diagonals that come out exactly zero are dropped after each
+ * product (diaq_op_prune). After time step t, n_diagonals[t] and nnz[t]
+ * (host arrays of n_gates entries, each may be NULL) receive the diagonal
+ * count and the number of non-zero values of U. The result is a stored
+ * DIAQ_CLASS_RAW op owned by the caller. Memory grows with the diagonals of
+ * U (up to 2N - 1 of them, N^2 values for a dense unitary); the product
+ * launches one grid row per result diagonal, so n_qubits <= 15. */
+diaq_status diaq_unitary_chain(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
+                               diaq_dtype dtype, int32_t prune, int64_t* n_diagonals, int64_t* nnz,
+                               diaq_stream_t stream, diaq_op_t* out);
 
 /* ------------------------------------------------------------------------
  * Reductions (FP64 accumulation for both dtypes; deterministic for a given
@@ -276,6 +323,21 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
  * synchronises before returning. */
 diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, const void* psi0, double* energy,
                                   double* grad, diaq_stream_t stream);
+
+/* Choose how the plan sweeps. window = 0: one launch per gate (the
+ * default). window = 2..5: gates are grouped into blocks acting on at most
+ * `window` qubits and at most 32 gates, moving a gate only past gates on
+ * disjoint qubits (so the operator and every gradient term are unchanged),
+ * and one launch runs a whole block: each thread stages the 2^w amplitudes
+ * of psi (and lambda) that share their other bits in shared memory and runs
+ * the block's gates there, reading and writing each state once per block
+ * instead of once per gate. Re-records the graph; on failure the plan falls
+ * back to window 0 and the status says why. */
+diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window);
+
+/* Current window and the number of launches per sweep (blocks, or gates
+ * when window = 0); either pointer may be NULL. */
+diaq_status diaq_adjoint_plan_get_window(diaq_adjoint_plan_t p, int32_t* window, int32_t* n_blocks);
 
 diaq_status diaq_adjoint_plan_destroy(diaq_adjoint_plan_t p);
 
@@ -354,16 +416,19 @@ diaq_status diaq_autotune_fusion(const diaq_gate* gates, int32_t n_gates, const 
 
 typedef struct diaq_batch_s* diaq_batch_t;
 
-#define DIAQ_BATCH_TUNE_MAX 12
+#define DIAQ_BATCH_TUNE_MAX 24
 
-/* Launch shapes the autotuner timed and the one it kept. */
+/* Launch shapes the autotuner timed and the one it kept (window 0: one pass
+ * per gate; w > 0: the window-fused kernel of diaq_batch_set_window). */
 typedef struct {
     int32_t n_tried;
     int32_t cluster[DIAQ_BATCH_TUNE_MAX];
     int32_t threads[DIAQ_BATCH_TUNE_MAX];
+    int32_t window[DIAQ_BATCH_TUNE_MAX];
     float ms[DIAQ_BATCH_TUNE_MAX];
     int32_t best_cluster;
     int32_t best_threads;
+    int32_t best_window;
     float best_ms;
 } diaq_batch_tuning;
 
@@ -395,9 +460,22 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
 diaq_status diaq_batch_run(diaq_batch_t b, const double* theta, double* energies, double* grads,
                            diaq_stream_t stream);
 
-/* Time every team shape (cluster in {1,2,4,8} x threads in {128,256,512})
- * that fits, `reps` graph replays each with theta, keep the fastest. report
- * may be NULL. */
+/* Choose how teams sweep. window = 0: one pass over the instance's states
+ * per gate (the default). window = 2..5: gates are grouped into blocks of at
+ * most `window` qubits and 32 gates, moving a gate only past gates on
+ * disjoint qubits (operator and gradients unchanged); a team stages every
+ * group of a block's window in shared memory, runs the block there, and
+ * meets at the cluster barrier once per block. This kernel runs 128 threads
+ * per block; the cluster size is kept. Recaptures the graph; on failure the
+ * batch falls back to window 0 with 1 x 256 and the status says why. */
+diaq_status diaq_batch_set_window(diaq_batch_t b, int32_t window);
+
+diaq_status diaq_batch_get_window(diaq_batch_t b, int32_t* window);
+
+/* Time every team shape that fits - window 0 with cluster in {1,2,4,8} x
+ * threads in {64,128,256}, and windows 3, 4, 5 with cluster in {1,2,4,8}
+ * x 128 threads - `reps` graph replays each with theta, keep the fastest.
+ * report may be NULL. */
 diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t reps, diaq_batch_tuning* report,
                                 diaq_stream_t stream);
 

@@ -80,6 +80,11 @@ SIGNATURES = {
     "diaq_op_read_diagonal": (ctypes.c_int, [_op, ctypes.c_int64, _vp, _vp]),
     "diaq_fuse": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, ctypes.c_int, _vp, ctypes.POINTER(_op)]),
     "diaq_apply": (ctypes.c_int, [_op, _vp, _vp, _vp]),
+    "diaq_op_apply_bytes": (ctypes.c_int, [_op, ctypes.c_int32, _i64p]),
+    "diaq_op_diagonal_nnz": (ctypes.c_int, [_op, _i64p, _vp]),
+    "diaq_op_prune": (ctypes.c_int, [_op, _vp, ctypes.POINTER(_op)]),
+    "diaq_unitary_chain": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
+                                          _i64p, _i64p, _vp, ctypes.POINTER(_op)]),
     "diaq_simulate": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
     "diaq_norm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
     "diaq_expect": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _u64p, _u64p, _dp, _dp, _vp]),
@@ -93,11 +98,13 @@ SIGNATURES = {
 class diaq_batch_tuning(ctypes.Structure):
     _fields_ = [
         ("n_tried", ctypes.c_int32),
-        ("cluster", ctypes.c_int32 * 12),
-        ("threads", ctypes.c_int32 * 12),
-        ("ms", ctypes.c_float * 12),
+        ("cluster", ctypes.c_int32 * 24),
+        ("threads", ctypes.c_int32 * 24),
+        ("window", ctypes.c_int32 * 24),
+        ("ms", ctypes.c_float * 24),
         ("best_cluster", ctypes.c_int32),
         ("best_threads", ctypes.c_int32),
+        ("best_window", ctypes.c_int32),
         ("best_ms", ctypes.c_float),
     ]
 
@@ -138,6 +145,10 @@ SIGNATURES.update({
                                                 _dp, ctypes.c_int32, ctypes.c_int, ctypes.POINTER(_vp)]),
     "diaq_adjoint_plan_run": (ctypes.c_int, [_vp, _dp, _vp, _dp, _dp, _vp]),
     "diaq_adjoint_plan_destroy": (ctypes.c_int, [_vp]),
+    "diaq_adjoint_plan_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_batch_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_batch_get_window": (ctypes.c_int, [_vp, _i32p]),
+    "diaq_adjoint_plan_get_window": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _gp, _i32p, _i32p, _u64p, _u64p, _dp,
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
     "diaq_batch_destroy": (ctypes.c_int, [_vp]),

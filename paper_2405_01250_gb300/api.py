@@ -121,6 +121,25 @@ class Op:
             "n_diagonals": inf.n_diagonals, "stored_bytes": inf.stored_bytes,
         }
 
+    def apply_bytes(self, in_place: bool = False) -> int:
+        """Algorithmic HBM bytes of one apply of this op (diaq_op_apply_bytes)."""
+        b = ctypes.c_int64(0)
+        check(lib().diaq_op_apply_bytes(self.handle, int(bool(in_place)), ctypes.byref(b)))
+        return int(b.value)
+
+    def diagonal_nnz(self, stream=None) -> np.ndarray:
+        """Values that are not exactly zero, per stored diagonal (index order)."""
+        d = int(self.info()["n_diagonals"])
+        out = np.zeros(max(d, 1), dtype=np.int64)
+        check(lib().diaq_op_diagonal_nnz(self.handle, out.ctypes.data_as(N._i64p), _stream(stream)))
+        return out[:d]
+
+    def prune(self, stream=None) -> "Op":
+        """A stored copy without its all-zero diagonals (diaq_op_prune)."""
+        h = ctypes.c_void_p(0)
+        check(lib().diaq_op_prune(self.handle, _stream(stream), ctypes.byref(h)))
+        return Op(h.value)
+
     def offsets(self) -> np.ndarray:
         cnt = ctypes.c_int64(0)
         st = lib().diaq_op_offsets(self.handle, None, 0, ctypes.byref(cnt))
@@ -198,6 +217,21 @@ def _ptr(t) -> ctypes.c_void_p:
     if isinstance(t, np.ndarray):
         return ctypes.c_void_p(t.ctypes.data)
     raise TypeError(type(t))
+
+
+def unitary_chain(gates, n_qubits: int, dtype=torch.complex128, theta=None, prune: bool = True, stream=None):
+    """Unitary of a circuit by chained device DiaQ products (diaq_unitary_chain).
+    Returns (op, diagonals per time step, non-zeros per time step)."""
+    arr, keep = _gate_array(gates)
+    th = np.ascontiguousarray(np.asarray(theta if theta is not None else [0.0], dtype=np.float64))
+    nd = np.zeros(len(gates), dtype=np.int64)
+    nz = np.zeros(len(gates), dtype=np.int64)
+    h = ctypes.c_void_p(0)
+    check(lib().diaq_unitary_chain(arr, len(gates), _dptr(th), int(n_qubits), _dtype_code(dtype), int(bool(prune)),
+                                   nd.ctypes.data_as(N._i64p), nz.ctypes.data_as(N._i64p), _stream(stream),
+                                   ctypes.byref(h)))
+    del keep
+    return Op(h.value), nd, nz
 
 
 def simulate(ops, psi_in, psi_out, work0: torch.Tensor, work1: torch.Tensor | None = None, stream=None):
@@ -436,6 +470,17 @@ class AdjointPlan:
                                           ctypes.byref(e), _dptr(g), _stream(stream)))
         return e.value, g[:self.n_params].copy()
 
+    def set_window(self, window: int) -> None:
+        """0: one launch per gate; 2..5: window-fused blocks (diaq_adjoint_plan_set_window)."""
+        check(lib().diaq_adjoint_plan_set_window(self.handle, int(window)))
+
+    def window(self) -> tuple:
+        """(window, launches per sweep)."""
+        w = ctypes.c_int32(0)
+        nb = ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_window(self.handle, ctypes.byref(w), ctypes.byref(nb)))
+        return w.value, nb.value
+
 
 class Batch:
     """Energies and adjoint gradients of many circuits (uneven qubit counts)
@@ -504,8 +549,18 @@ class Batch:
         rep = N.diaq_batch_tuning()
         check(lib().diaq_batch_autotune(self.handle, _dptr(th) if len(th) else None, int(reps), ctypes.byref(rep),
                                         _stream(stream)))
-        return {"tried": [(rep.cluster[i], rep.threads[i], rep.ms[i]) for i in range(rep.n_tried)],
-                "best_cluster": rep.best_cluster, "best_threads": rep.best_threads, "best_ms": rep.best_ms}
+        return {"tried": [(rep.cluster[i], rep.threads[i], rep.window[i], rep.ms[i]) for i in range(rep.n_tried)],
+                "best_cluster": rep.best_cluster, "best_threads": rep.best_threads, "best_window": rep.best_window,
+                "best_ms": rep.best_ms}
+
+    def set_window(self, window: int):
+        """0: one pass per gate; 2..5: window-fused blocks (diaq_batch_set_window)."""
+        check(lib().diaq_batch_set_window(self.handle, int(window)))
+
+    def window(self) -> int:
+        w = ctypes.c_int32(0)
+        check(lib().diaq_batch_get_window(self.handle, ctypes.byref(w)))
+        return w.value
 
     def query(self) -> dict:
         c, t, tm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

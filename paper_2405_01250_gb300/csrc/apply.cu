@@ -41,6 +41,12 @@ struct SmallGateArgs {
     R re[1 << (2 * K)];
     R im[1 << (2 * K)];
     uint8_t type[1 << (2 * K)];
+    // k = 1 only: both rows start with the same non-zero entry in column 0
+    // (a Hadamard, any [[a, b], [a, d]]), so the product m00 x0 that opens
+    // both rows' sums is formed once. Same roundings, fewer FP64 instructions.
+    // 1: every entry real and non-zero (the butterfly, written out with no
+    // entry-type dispatch); 2: any other such matrix.
+    int share_col0;
 };
 
 template <typename R, int K, int G>
@@ -60,6 +66,41 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
 #pragma unroll
             for (int c = 0; c < D; ++c) v[j][c] = ld_stream(x + b[j] + a.off[c]);
         }
+    }
+    if (K == 1 && a.share_col0 == 1) {
+        // real butterfly: p = a x0 (two products), y_r = fma(m_r1, x1, p)
+        const R m00 = a.re[0], m01 = a.re[1], m11 = a.re[3];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+            const A x0 = v[j][0], x1 = v[j][1];
+            const R px = m00 * x0.x, py = m00 * x0.y;
+            A y0, y1;
+            y0.x = fma(m01, x1.x, px);
+            y0.y = fma(m01, x1.y, py);
+            y1.x = fma(m11, x1.x, px);
+            y1.y = fma(m11, x1.y, py);
+            st_stream(y + b[j] + a.off[0], y0);
+            st_stream(y + b[j] + a.off[1], y1);
+        }
+        return;
+    }
+    if (K == 1 && a.share_col0) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+            A p;
+            bool first = true;
+            mac_typed<R>(p, first, a.type[0], a.re[0], a.im[0], v[j][0]);
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                A acc = p;
+                bool f = false;
+                mac_typed<R>(acc, f, a.type[r * D + 1], a.re[r * D + 1], a.im[r * D + 1], v[j][1]);
+                st_stream(y + b[j] + a.off[r], acc);
+            }
+        }
+        return;
     }
 #pragma unroll
     for (int j = 0; j < G; ++j) {
@@ -183,6 +224,11 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
         a.im[e] = R(g.m[e].imag());
         // classify after rounding to R so a c64 entry that rounds to 1 is exact
         a.type[e] = entry_type(cplx(double(a.re[e]), double(a.im[e])));
+    }
+    if (K == 1) {
+        const bool shared = a.type[0] != ET_ZERO && a.type[2] == a.type[0] && a.re[2] == a.re[0] && a.im[2] == a.im[0];
+        const bool butterfly = shared && a.type[0] == ET_REAL && a.type[1] == ET_REAL && a.type[3] == ET_REAL;
+        a.share_col0 = butterfly ? 1 : (shared ? 2 : 0);
     }
     const int64_t per_block = int64_t(threads) * G;
     const int64_t blocks = (a.n_groups + per_block - 1) / per_block;

@@ -29,6 +29,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "rot.cuh"
+#include "win.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -52,6 +53,7 @@ struct BGate {
 struct BInst {
     int32_t n;
     int32_t gate_begin, gate_end;
+    int32_t block_begin, block_end;  // window blocks of the instance (window-fused kernel)
     int32_t param_begin, n_params;
     int32_t term_begin, term_end;
     int32_t n_slots;         // 1 (energy) + parametric gates
@@ -371,6 +373,151 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     }
 }
 
+// Window-fused batch: the same team schedule and reductions as k_batch, but
+// each team runs an instance's gates block by block (blocks of at most w
+// qubits from the commutation-aware planner), staging every group of the
+// window in shared memory, and meets at the cluster barrier once per block
+// instead of once per gate. Block size WIN_THREADS.
+template <typename R>
+__device__ __forceinline__ void batch_stage(const WinBlock* __restrict__ blocks, int b, WinBlock* w,
+                                            const WinGate* __restrict__ wg, const BGate* __restrict__ gates,
+                                            const double* th, bool rev, WinOp<R>* ops, Acc<R>* sa) {
+    const int T = blockDim.x, t = threadIdx.x;
+    __syncthreads();  // the previous block's records are no longer in use
+    {
+        const int* src = reinterpret_cast<const int*>(blocks + b);
+        int* dst = reinterpret_cast<int*>(w);
+        for (int i = t; i < int(sizeof(WinBlock) / sizeof(int)); i += T) dst[i] = src[i];
+    }
+    __syncthreads();
+    for (int i = t; i < w->count; i += T) {
+        const WinGate x = wg[w->first + i];
+        const BGate& G = gates[x.g];
+        WinOp<R>& o = ops[i];
+        o.k = G.k;
+        o.b0 = x.b0;
+        o.b1 = x.b1;
+        o.j = G.param >= 0 ? x.j : -1;
+        o.xl = G.xl;
+        o.zl = G.rot.zl;
+        o.ny = G.rot.ny;
+        o.cs = R(0);
+        o.kr = R(0);
+        o.ki = R(0);
+        const int Dk = 1 << G.k;
+        if (G.param >= 0) {
+            double cs, kr, ki;
+            rot_angle(G, th, rev, &cs, &kr, &ki);
+            o.cs = R(cs);
+            o.kr = R(kr);
+            o.ki = R(ki);
+        } else {
+            for (int r = 0; r < Dk; ++r)
+                for (int c = 0; c < Dk; ++c) {
+                    const double vr = rev ? G.re[c * Dk + r] : G.re[r * Dk + c];
+                    const double vi = rev ? -G.im[c * Dk + r] : G.im[r * Dk + c];
+                    o.mre[r * Dk + c] = R(vr);
+                    o.mim[r * Dk + c] = R(vi);
+                    o.ty[r * Dk + c] = dev_entry_type(double(R(vr)), double(R(vi)));
+                }
+        }
+    }
+    if (rev)
+        for (int j = 0; j < w->np; ++j) sa[j * T + t] = Acc<R>();
+    __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(WIN_THREADS) k_batch_win(const BatchArgs a, const WinBlock* __restrict__ blocks,
+                                                           const WinGate* __restrict__ wg, int window) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double warps[32];
+    __shared__ __align__(16) WinBlock w;
+    const int T = WIN_THREADS, t = threadIdx.x;
+    const int C = a.C;
+    const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
+    const int team = blockIdx.x / C;
+    const int64_t tid = int64_t(rank) * T + t;
+    const int64_t nthreads = int64_t(C) * T;
+    const int Dmax = 1 << window;
+    WinOp<R>* ops = reinterpret_cast<WinOp<R>*>(sm);
+    A* sp = reinterpret_cast<A*>(sm + ((sizeof(WinOp<R>) * WIN_MAXG + 15) / 16) * 16);
+    A* sl = sp + Dmax * T;
+    Acc<R>* sa = reinterpret_cast<Acc<R>*>(sl + Dmax * T);
+    A* cp = sp + t;
+    A* cl = sl + t;
+    A* arena = reinterpret_cast<A*>(a.arena);
+    for (int s = a.team_first[team]; s < a.team_first[team + 1]; ++s) {
+        const BInst I = a.inst[a.sched[s]];
+        A* psi = arena + I.psi_off;
+        A* lam = arena + I.lam_off;
+        const int64_t N = int64_t(1) << I.n;
+        const double* th = a.theta + I.param_begin;
+        double* part = a.partials + I.part_off;
+        for (int64_t i = tid; i < N; i += nthreads) {
+            A v;
+            v.x = R(i == 0 ? 1 : 0);
+            v.y = R(0);
+            psi[i] = v;
+        }
+        team_sync(C);
+        // forward sweep, block by block
+        for (int b = I.block_begin; b < I.block_end; ++b) {
+            batch_stage<R>(blocks, b, &w, wg, a.gates, th, false, ops, sa);
+            const int D = 1 << w.nq;
+            const int64_t G = int64_t(1) << (I.n - w.nq);
+            for (int64_t g = tid; g < G; g += nthreads) {
+                const int64_t base = insert_zeros_rt(g, w.q, w.nq);
+                for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
+                for (int i = 0; i < w.count; ++i) win_apply<R>(ops[i], cp, nullptr, D, T, nullptr);
+                for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
+            }
+            team_sync(C);
+        }
+        // lambda = H psi and the energy Re <psi|lambda>
+        Acc<R> e;
+        for (int64_t i = tid; i < N; i += nthreads) {
+            const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
+            lam[i] = o;
+            const A pi = psi[i];
+            e.add_dot(pi.x, o.x, pi.y, o.y);
+        }
+        const double es = block_sum(e.value(), warps);
+        if (t == 0) part[0 * C + rank] = es;
+        team_sync(C);
+        // reverse sweep: blocks in reverse, gates in reverse within a block
+        for (int b = I.block_end - 1; b >= I.block_begin; --b) {
+            batch_stage<R>(blocks, b, &w, wg, a.gates, th, true, ops, sa);
+            const int D = 1 << w.nq;
+            const int64_t G = int64_t(1) << (I.n - w.nq);
+            for (int64_t g = tid; g < G; g += nthreads) {
+                const int64_t base = insert_zeros_rt(g, w.q, w.nq);
+                for (int e2 = 0; e2 < D; ++e2) cp[e2 * T] = psi[base + w.off[e2]];
+                for (int e2 = 0; e2 < D; ++e2) cl[e2 * T] = lam[base + w.off[e2]];
+                for (int i = w.count - 1; i >= 0; --i) {
+                    const WinOp<R>& o = ops[i];
+                    win_apply<R>(o, cp, cl, D, T, o.j >= 0 ? sa + o.j * T + t : nullptr);
+                }
+                for (int e2 = 0; e2 < D; ++e2) psi[base + w.off[e2]] = cp[e2 * T];
+                for (int e2 = 0; e2 < D; ++e2) lam[base + w.off[e2]] = cl[e2 * T];
+            }
+            for (int j = 0; j < w.np; ++j) {
+                const double v = block_sum(sa[j * T + t].value(), warps);
+                if (t == 0) part[int64_t(w.slot[j]) * C + rank] = v;
+            }
+            team_sync(C);
+        }
+    }
+}
+
+// Dynamic shared memory of k_batch_win for a window of w qubits.
+static size_t batch_win_smem(diaq_dtype dt, int w) {
+    const size_t opb = dt == DIAQ_C128 ? sizeof(WinOp<double>) : sizeof(WinOp<float>);
+    return ((opb * WIN_MAXG + 15) / 16) * 16 + 2 * (size_t(1) << w) * WIN_THREADS * amp_bytes(dt) +
+           size_t(WIN_MAXG) * WIN_THREADS * sizeof(double);
+}
+
 // Per instance: energy and gradient from the partial rows, fixed order.
 __global__ void k_batch_finish(const BInst* inst, const BGate* gates, const double* partials, int C, int n_inst,
                                double* energy, double* grad) {
@@ -427,6 +574,10 @@ struct diaq_batch_s {
     int C = 1, threads = 256, teams = 0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t graph_stream = nullptr;
+    // window-fused kernel (window > 0): blocks of every instance
+    int window = 0;
+    WinBlock* d_blocks = nullptr;
+    WinGate* d_wg = nullptr;
 };
 
 // Rotation shape of a parametric gate from its generator letters.
@@ -453,8 +604,73 @@ static void fill_rot(BGate* B) {
     }
 }
 
+// Window blocks of at most `window` qubits and WIN_MAXG gates for the gates
+// [0, n_gates) of one circuit, from the commutation-aware planner (a gate
+// moves only past gates on disjoint qubits). Appends the blocks and their
+// gate entries; WinGate::g is gate_base + the gate's index, first is
+// relative to the whole entry list.
+static diaq_status make_windows(const BGate* gates, int n_gates, int gate_base, int window,
+                                std::vector<WinBlock>* blocks, std::vector<WinGate>* wg) {
+    if (n_gates == 0) return DIAQ_OK;
+    std::vector<diaq_gate> g(static_cast<size_t>(n_gates));
+    for (int i = 0; i < n_gates; ++i) {
+        std::memset(&g[size_t(i)], 0, sizeof(diaq_gate));
+        g[size_t(i)].k = gates[i].k;
+        g[size_t(i)].targets[0] = gates[i].t[0];
+        g[size_t(i)].targets[1] = gates[i].t[1];
+        g[size_t(i)].param = -1;
+    }
+    std::vector<int32_t> order(static_cast<size_t>(n_gates)), grp(static_cast<size_t>(n_gates));
+    int32_t ng = 0;
+    DIAQ_TRY(diaq_plan_fusion_commuting(g.data(), n_gates, window, WIN_MAXG, order.data(), grp.data(), &ng));
+    for (int pos = 0; pos < n_gates;) {
+        int end = pos;
+        while (end < n_gates && grp[size_t(end)] == grp[size_t(pos)]) ++end;
+        WinBlock w;
+        std::memset(&w, 0, sizeof(w));
+        std::vector<int> qs;
+        for (int i = pos; i < end; ++i) {
+            const BGate& G = gates[order[size_t(i)]];
+            for (int a = 0; a < G.k; ++a)
+                if (std::find(qs.begin(), qs.end(), G.t[a]) == qs.end()) qs.push_back(G.t[a]);
+        }
+        std::sort(qs.begin(), qs.end());
+        if (int(qs.size()) > WIN_MAX || end - pos > WIN_MAXG)
+            return fail(DIAQ_ERR_UNSUPPORTED, "a fused block exceeds %d qubits or %d gates", WIN_MAX, WIN_MAXG);
+        w.nq = int(qs.size());
+        for (int a = 0; a < w.nq; ++a) w.q[a] = qs[size_t(a)];
+        for (int e = 0; e < (1 << w.nq); ++e) {
+            int64_t o = 0;
+            for (int a = 0; a < w.nq; ++a)
+                if ((e >> a) & 1) o += int64_t(1) << w.q[a];
+            w.off[e] = o;
+        }
+        w.first = int(wg->size());
+        w.count = end - pos;
+        for (int i = pos; i < end; ++i) {
+            const int gi = order[size_t(i)];
+            const BGate& G = gates[gi];
+            WinGate x;
+            x.g = gate_base + gi;
+            x.b0 = int(std::find(qs.begin(), qs.end(), G.t[0]) - qs.begin());
+            x.b1 = G.k == 2 ? int(std::find(qs.begin(), qs.end(), G.t[1]) - qs.begin()) : 0;
+            x.j = -1;
+            if (G.param >= 0) {
+                x.j = w.np;
+                w.slot[w.np++] = G.slot;
+            }
+            wg->push_back(x);
+        }
+        blocks->push_back(w);
+        pos = end;
+    }
+    return DIAQ_OK;
+}
+
 static void batch_free(diaq_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_blocks) cudaFree(b->d_blocks);
+    if (b->d_wg) cudaFree(b->d_wg);
     for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
                     b->d_arena, static_cast<void*>(b->d_theta), static_cast<void*>(b->d_partials),
                     static_cast<void*>(b->d_out), static_cast<void*>(b->d_sched), static_cast<void*>(b->d_team_first)})
@@ -477,10 +693,18 @@ static const void* batch_kernel() {
     return reinterpret_cast<const void*>(&k_batch<R>);
 }
 
+template <typename R>
+static const void* batch_win_kernel() {
+    return reinterpret_cast<const void*>(&k_batch_win<R>);
+}
+
 // Teams that fit on the GPU at once for cluster size C and block size T.
 static diaq_status resident_teams(diaq_batch_s* b, int C, int T, int* teams) {
-    const void* fn = b->dtype == DIAQ_C128 ? batch_kernel<double>() : batch_kernel<float>();
-    const size_t smem = 0;
+    const bool win = b->window > 0;
+    const void* fn = win ? (b->dtype == DIAQ_C128 ? batch_win_kernel<double>() : batch_win_kernel<float>())
+                         : (b->dtype == DIAQ_C128 ? batch_kernel<double>() : batch_kernel<float>());
+    const size_t smem = win ? batch_win_smem(b->dtype, b->window) : 0;
+    if (win) DIAQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     if (C == 1) {
         int per_sm = 0, sms = 0;
         DIAQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, T, smem));
@@ -551,10 +775,19 @@ static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = b->C > 1 ? 1 : 0;
-    if (b->dtype == DIAQ_C128)
+    if (b->window > 0) {
+        cfg.dynamicSmemBytes = batch_win_smem(b->dtype, b->window);
+        const WinBlock* blk = b->d_blocks;
+        const WinGate* wg = b->d_wg;
+        if (b->dtype == DIAQ_C128)
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win<double>, a, blk, wg, b->window));
+        else
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win<float>, a, blk, wg, b->window));
+    } else if (b->dtype == DIAQ_C128) {
         DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<double>, a));
-    else
+    } else {
         DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<float>, a));
+    }
     const int fb = 128;
     k_batch_finish<<<(b->n_inst + fb - 1) / fb, fb, 0, s>>>(b->d_inst, b->d_gates, b->d_partials, b->C, b->n_inst,
                                                           b->d_out, b->d_out + b->n_inst);
@@ -618,6 +851,30 @@ static diaq_status configure(diaq_batch_s* b, int C, int T, cudaStream_t s) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate(batch)");
     (void)s;
+    return DIAQ_OK;
+}
+
+// Window tables for every instance (window 0 clears them); the caller
+// reconfigures, which uploads the instances' block ranges.
+static diaq_status batch_windows(diaq_batch_s* b, int window) {
+    if (b->d_blocks) cudaFree(b->d_blocks);
+    if (b->d_wg) cudaFree(b->d_wg);
+    b->d_blocks = nullptr;
+    b->d_wg = nullptr;
+    b->window = 0;
+    for (auto& I : b->inst) I.block_begin = I.block_end = 0;
+    if (window == 0) return DIAQ_OK;
+    std::vector<WinBlock> blocks;
+    std::vector<WinGate> wg;
+    for (auto& I : b->inst) {
+        I.block_begin = int32_t(blocks.size());
+        DIAQ_TRY(make_windows(b->gates.data() + I.gate_begin, I.gate_end - I.gate_begin, I.gate_begin, window,
+                              &blocks, &wg));
+        I.block_end = int32_t(blocks.size());
+    }
+    DIAQ_TRY(upload(&b->d_blocks, blocks));
+    DIAQ_TRY(upload(&b->d_wg, wg));
+    b->window = window;
     return DIAQ_OK;
 }
 
@@ -795,7 +1052,35 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
         return fail(DIAQ_ERR_ARG, "cluster size %d not in {1, 2, 4, 8}", cluster);
     if (threads < 32 || threads > 256 || threads % 32)
         return fail(DIAQ_ERR_ARG, "threads %d not a multiple of 32 in [32, 256]", threads);
+    if (b->window > 0 && threads != WIN_THREADS)
+        return fail(DIAQ_ERR_ARG, "the window-fused kernel runs %d threads per block (got %d)", WIN_THREADS, threads);
     return configure(b, cluster, threads, nullptr);
+}
+
+diaq_status diaq_batch_set_window(diaq_batch_t b, int32_t window) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (window != 0 && (window < 2 || window > WIN_MAX))
+        return fail(DIAQ_ERR_ARG, "window = %d: use 0 (one pass per gate) or 2..%d qubits", window, WIN_MAX);
+    const int C = b->C;
+    const int T = window > 0 ? WIN_THREADS : (b->window > 0 ? 256 : b->threads);
+    diaq_status st = batch_windows(b, window);
+    if (st == DIAQ_OK) st = configure(b, C, T, nullptr);
+    if (st != DIAQ_OK) {
+        const diaq_status first = st;
+        batch_windows(b, 0);
+        configure(b, 1, 256, nullptr);
+        return first;
+    }
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_get_window(diaq_batch_t b, int32_t* window) {
+    clear_error();
+    if (!b || !window) return fail(DIAQ_ERR_ARG, "NULL argument");
+    *window = b->window;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_batch_run(diaq_batch_t b, const double* theta, double* energies, double* grads,
@@ -823,14 +1108,22 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int cls[] = {1, 2, 4, 8};
     const int ths[] = {64, 128, 256};  // k_batch is built for at most 256
+    const int wins[] = {0, 3, 4, 5};   // 0: one pass per gate; else the window-fused kernel
     float best = 1e30f;
-    int bc = 1, bt = 256, tried = 0;
+    int bc = 1, bt = 256, bw = 0, tried = 0;
     cudaEvent_t e0, e1;
     DIAQ_CUDA(cudaEventCreate(&e0));
     DIAQ_CUDA(cudaEventCreate(&e1));
     if (b->n_params_total > 0) std::memcpy(b->h_theta, theta, sizeof(double) * size_t(b->n_params_total));
-    for (int C : cls)
+    for (int W : wins) {
+      if (batch_windows(b, W) != DIAQ_OK) {
+          clear_error();
+          cudaGetLastError();
+          continue;  // this window does not fit the circuits: skip it
+      }
+      for (int C : cls)
         for (int T : ths) {
+            if (W > 0 && T != WIN_THREADS) continue;
             if (configure(b, C, T, s) != DIAQ_OK) {
                 clear_error();
                 cudaGetLastError();
@@ -847,6 +1140,7 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
             if (report && tried < DIAQ_BATCH_TUNE_MAX) {
                 report->cluster[tried] = C;
                 report->threads[tried] = T;
+                report->window[tried] = W;
                 report->ms[tried] = ms;
             }
             ++tried;
@@ -854,16 +1148,20 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
                 best = ms;
                 bc = C;
                 bt = T;
+                bw = W;
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no launch shape fits");
+    DIAQ_TRY(batch_windows(b, bw));
     DIAQ_TRY(configure(b, bc, bt, s));
     if (report) {
         report->n_tried = std::min(tried, DIAQ_BATCH_TUNE_MAX);
         report->best_cluster = bc;
         report->best_threads = bt;
+        report->best_window = bw;
         report->best_ms = best;
     }
     return DIAQ_OK;
@@ -988,6 +1286,102 @@ static void launch_plan_rot(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Window-fused sweep. The gates are grouped into blocks that act on at most
+// WIN_MAX qubits (the window), moving gates only past gates on disjoint
+// qubits, so the circuit's operator and every gradient term are unchanged.
+// One launch runs one block over the whole state: each thread takes a group
+// (the 2^w amplitudes that share their bits outside the window), stages it
+// in shared memory, runs the block's gates on it in order (forward) or in
+// reverse order with each parametric gate's partial Im <lam|P|psi> taken
+// before U^dag (reverse), and writes it back. The state is read and written
+// once per block instead of once per gate.
+// ---------------------------------------------------------------------------
+static size_t win_smem(diaq_dtype dt, int nq, int count, int np) {
+    const size_t opb = dt == DIAQ_C128 ? sizeof(WinOp<double>) : sizeof(WinOp<float>);
+    const size_t ab = amp_bytes(dt);
+    const size_t head = ((opb * size_t(count) + 15) / 16) * 16;
+    return head + 2 * (size_t(1) << nq) * WIN_THREADS * ab + size_t(np) * WIN_THREADS * sizeof(double);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(WIN_THREADS) k_plan_win(amp_t<R>* psi, amp_t<R>* lam, const BGate* __restrict__ gates,
+                                                          const RotAngles* __restrict__ ang,
+                                                          const WinGate* __restrict__ wg,
+                                                          const __grid_constant__ WinBlock w, int n, double* part,
+                                                          int P) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double warps[32];
+    const int T = WIN_THREADS, t = threadIdx.x;
+    const int D = 1 << w.nq;
+    const bool rev = lam != nullptr;
+    WinOp<R>* ops = reinterpret_cast<WinOp<R>*>(sm);
+    A* sp = reinterpret_cast<A*>(sm + ((sizeof(WinOp<R>) * size_t(w.count) + 15) / 16) * 16);
+    A* sl = sp + D * T;
+    Acc<R>* sa = reinterpret_cast<Acc<R>*>(sl + D * T);
+    // stage the block's gates in the direction of this sweep
+    for (int i = t; i < w.count; i += T) {
+        const WinGate x = wg[w.first + i];
+        const BGate& G = gates[x.g];
+        WinOp<R>& o = ops[i];
+        o.k = G.k;
+        o.b0 = x.b0;
+        o.b1 = x.b1;
+        o.j = G.param >= 0 ? x.j : -1;
+        o.xl = G.xl;
+        o.zl = G.rot.zl;
+        o.ny = G.rot.ny;
+        o.cs = R(0);
+        o.kr = R(0);
+        o.ki = R(0);
+        const int Dk = 1 << G.k;
+        if (G.param >= 0) {
+            const RotAngles a = ang[x.g];
+            o.cs = R(a.cs);
+            o.kr = R(rev ? a.kar : a.kfr);
+            o.ki = R(rev ? a.kai : a.kfi);
+        } else {
+            for (int r = 0; r < Dk; ++r)
+                for (int c = 0; c < Dk; ++c) {
+                    const double vr = rev ? G.re[c * Dk + r] : G.re[r * Dk + c];
+                    const double vi = rev ? -G.im[c * Dk + r] : G.im[r * Dk + c];
+                    o.mre[r * Dk + c] = R(vr);
+                    o.mim[r * Dk + c] = R(vi);
+                    o.ty[r * Dk + c] = dev_entry_type(double(R(vr)), double(R(vi)));
+                }
+        }
+    }
+    for (int j = 0; j < w.np; ++j) sa[j * T + t] = Acc<R>();
+    __syncthreads();
+    const int64_t G = int64_t(1) << (n - w.nq);
+    A* cp = sp + t;
+    A* cl = sl + t;
+    for (int64_t g = int64_t(blockIdx.x) * T + t; g < G; g += int64_t(gridDim.x) * T) {
+        const int64_t base = insert_zeros_rt(g, w.q, w.nq);
+        for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
+        if (rev)
+            for (int e = 0; e < D; ++e) cl[e * T] = lam[base + w.off[e]];
+        if (!rev) {
+            for (int i = 0; i < w.count; ++i) win_apply<R>(ops[i], cp, nullptr, D, T, nullptr);
+        } else {
+            for (int i = w.count - 1; i >= 0; --i) {
+                const WinOp<R>& o = ops[i];
+                win_apply<R>(o, cp, cl, D, T, o.j >= 0 ? sa + o.j * T + t : nullptr);
+            }
+        }
+        for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
+        if (rev)
+            for (int e = 0; e < D; ++e) lam[base + w.off[e]] = cl[e * T];
+    }
+    if (rev) {
+        for (int j = 0; j < w.np; ++j) {
+            const double v = block_sum(sa[j * T + t].value(), warps);
+            if (t == 0) part[int64_t(w.slot[j]) * P + blockIdx.x] = v;
+        }
+    }
+}
+
 }  // namespace diaq
 
 struct diaq_adjoint_plan_s {
@@ -1012,10 +1406,15 @@ struct diaq_adjoint_plan_s {
     const void* psi0 = nullptr;  // captured initial-state pointer (NULL: |0...0>)
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int window = 0;                  // 0: one launch per gate; else window-fused blocks of <= window qubits
+    std::vector<WinBlock> blocks;
+    WinGate* d_wg = nullptr;
 };
 
 static void plan_free(diaq_adjoint_plan_s* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->d_wg) cudaFree(p->d_wg);
+    p->d_wg = nullptr;
     for (void* q : {static_cast<void*>(p->d_gates), static_cast<void*>(p->d_terms), static_cast<void*>(p->d_angles),
                     p->d_psi, p->d_lam, static_cast<void*>(p->d_theta), static_cast<void*>(p->d_part),
                     static_cast<void*>(p->d_rows), static_cast<void*>(p->d_out)})
@@ -1037,28 +1436,63 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
     if (p->n_gates) k_plan_angles<<<(p->n_gates + 127) / 128, 128, 0, s>>>(p->d_gates, p->n_gates, p->d_theta, p->d_angles);
     k_plan_init<R><<<p->P, 256, 0, s>>>(static_cast<const A*>(p->psi0), psi, N);
     DIAQ_CUDA(cudaGetLastError());
-    for (int g = 0; g < p->n_gates; ++g) {
-        const BGate& G = p->gates[size_t(g)];
-        if (G.param >= 0)
-            launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, s);
-        else
-            DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
-    }
-    k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
-    for (int g = p->n_gates - 1; g >= 0; --g) {
-        const BGate& G = p->gates[size_t(g)];
-        if (G.param >= 0) {
-            launch_plan_rot<R>(G, psi, lam, p->d_gates + g, p->d_angles + g, p->n, p->d_part + int64_t(G.slot) * p->P,
-                               p->P, s);
-        } else {
-            DIAQ_TRY(launch_adjoint_step(p->n, p->dtype, p->bwd[size_t(g)], nullptr, psi, lam, nullptr,
-                                         adjoint_partials(p->n, p->dtype, G.k), s));
+    if (p->window > 0) {
+        for (const WinBlock& w : p->blocks)
+            k_plan_win<R><<<p->P, WIN_THREADS, win_smem(p->dtype, w.nq, w.count, w.np), s>>>(
+                psi, nullptr, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
+        for (size_t b = p->blocks.size(); b-- > 0;) {
+            const WinBlock& w = p->blocks[b];
+            k_plan_win<R><<<p->P, WIN_THREADS, win_smem(p->dtype, w.nq, w.count, w.np), s>>>(
+                psi, lam, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
+        }
+        DIAQ_CUDA(cudaGetLastError());
+    } else {
+        for (int g = 0; g < p->n_gates; ++g) {
+            const BGate& G = p->gates[size_t(g)];
+            if (G.param >= 0)
+                launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, s);
+            else
+                DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
+        }
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
+        for (int g = p->n_gates - 1; g >= 0; --g) {
+            const BGate& G = p->gates[size_t(g)];
+            if (G.param >= 0) {
+                launch_plan_rot<R>(G, psi, lam, p->d_gates + g, p->d_angles + g, p->n,
+                                   p->d_part + int64_t(G.slot) * p->P, p->P, s);
+            } else {
+                DIAQ_TRY(launch_adjoint_step(p->n, p->dtype, p->bwd[size_t(g)], nullptr, psi, lam, nullptr,
+                                             adjoint_partials(p->n, p->dtype, G.k), s));
+            }
         }
     }
     k_plan_rows<<<p->n_slots, 256, 0, s>>>(p->d_part, p->P, p->d_rows);
     k_plan_finish<<<1, 1, 0, s>>>(p->d_gates, p->n_gates, p->d_rows, p->n_params, p->d_out);
     DIAQ_CUDA(cudaGetLastError());
     DIAQ_CUDA(cudaMemcpyAsync(p->h_out, p->d_out, sizeof(double) * size_t(1 + p->n_params), cudaMemcpyDeviceToHost, s));
+    return DIAQ_OK;
+}
+
+// Blocks of at most `window` qubits and WIN_MAXG gates from the
+// commutation-aware planner; window 0 clears them.
+static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window) {
+    p->blocks.clear();
+    if (p->d_wg) {
+        cudaFree(p->d_wg);
+        p->d_wg = nullptr;
+    }
+    p->window = window;
+    if (window == 0 || p->n_gates == 0) return DIAQ_OK;
+    std::vector<WinGate> wg;
+    DIAQ_TRY(make_windows(p->gates.data(), p->n_gates, 0, window, &p->blocks, &wg));
+    DIAQ_TRY(upload(&p->d_wg, wg));
+    size_t most = 0;
+    for (const WinBlock& w : p->blocks) most = std::max(most, win_smem(p->dtype, w.nq, w.count, w.np));
+    if (p->dtype == DIAQ_C128)
+        DIAQ_CUDA(cudaFuncSetAttribute(k_plan_win<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most)));
+    else
+        DIAQ_CUDA(cudaFuncSetAttribute(k_plan_win<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most)));
     return DIAQ_OK;
 }
 
@@ -1135,6 +1569,11 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
             B.slot = p->n_slots++;
         } else {
             p->fwd[size_t(gi)] = d;
+            // the device record carries the matrix for the window-fused sweep
+            for (size_t e = 0; e < d.m.size() && e < 16; ++e) {
+                B.re[e] = d.m[e].real();
+                B.im[e] = d.m[e].imag();
+            }
             GateDesc u = d;
             const int D = 1 << d.k;
             for (int r = 0; r < D; ++r)
@@ -1231,6 +1670,33 @@ diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, co
     if (energy) *energy = p->h_out[0];
     if (grad)
         for (int i = 0; i < p->n_params; ++i) grad[i] = p->h_out[1 + i];
+    return DIAQ_OK;
+}
+
+diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (window != 0 && (window < 2 || window > WIN_MAX))
+        return fail(DIAQ_ERR_ARG, "window = %d: use 0 (one launch per gate) or 2..%d qubits", window, WIN_MAX);
+    int dev = -1;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
+    DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    diaq_status st = plan_windows(p, window);
+    if (st != DIAQ_OK) {
+        plan_windows(p, 0);
+        plan_capture(p);
+        return st;
+    }
+    return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_window(diaq_adjoint_plan_t p, int32_t* window, int32_t* n_blocks) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (window) *window = p->window;
+    if (n_blocks) *n_blocks = p->window > 0 ? int32_t(p->blocks.size()) : p->n_gates;
     return DIAQ_OK;
 }
 

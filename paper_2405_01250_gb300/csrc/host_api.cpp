@@ -718,8 +718,158 @@ diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t strea
     if (inplace && op->variant == DIAQ_STORED) return fail(DIAQ_ERR_ARG, "stored ops cannot run in place (x == y)");
     if (!inplace && overlaps(x, y, bytes)) return fail(DIAQ_ERR_ARG, "x and y overlap");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (inplace) {
+        bool done = false;
+        DIAQ_TRY(launch_inplace_skip(op, y, s, &done));
+        if (done) return DIAQ_OK;
+    }
     if (op->variant == DIAQ_ONTHEFLY) return launch_onthefly(op, x, y, s);
     return launch_stored(op, x, y, s);
+}
+
+diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes) {
+    clear_error();
+    if (!op || !bytes) return fail(DIAQ_ERR_ARG, "NULL argument");
+    const int64_t N = int64_t(1) << op->n;
+    const int64_t s = int64_t(amp_bytes(op->dtype));
+    if (op->variant == DIAQ_STORED) {
+        if (in_place) return fail(DIAQ_ERR_ARG, "stored ops cannot run in place");
+        *bytes = 2 * N * s + op->stored_elems * s;
+    } else if (in_place) {
+        *bytes = inplace_bytes(op->n, op->dtype, op->gate);
+    } else {
+        *bytes = 2 * N * s;
+    }
+    return DIAQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Unitary simulation (Section II-A; per-time-step sparsity of Section III-A)
+// ---------------------------------------------------------------------------
+diaq_status diaq_op_diagonal_nnz(diaq_op_t op, int64_t* nnz, diaq_stream_t stream) {
+    clear_error_device();
+    DIAQ_TRY(check_op(op));
+    if (!nnz) return fail(DIAQ_ERR_ARG, "nnz is NULL");
+    if (op->variant != DIAQ_STORED) return fail(DIAQ_ERR_ARG, "op is on-the-fly: no stored diagonals");
+    std::vector<int64_t> c;
+    DIAQ_TRY(count_diagonal_nnz(op, &c, static_cast<cudaStream_t>(stream)));
+    std::copy(c.begin(), c.end(), nnz);
+    return DIAQ_OK;
+}
+
+// A stored raw op holding the diagonals of src whose count is non-zero.
+static diaq_status prune_with_counts(const diaq_op_s* src, const std::vector<int64_t>& counts, cudaStream_t s,
+                                     diaq_op_s** out) {
+    *out = nullptr;
+    diaq_op_s* c = new (std::nothrow) diaq_op_s();
+    if (!c) return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+    c->n = src->n;
+    c->dtype = src->dtype;
+    c->variant = DIAQ_STORED;
+    c->op_class = DIAQ_CLASS_RAW;
+    c->device = src->device;
+    std::vector<int32_t> keep;
+    for (size_t q = 0; q < src->offsets.size(); ++q)
+        if (counts[q] > 0) {
+            keep.push_back(int32_t(q));
+            c->offsets.push_back(src->offsets[q]);
+        }
+    diaq_status st = alloc_stored(c);
+    if (st == DIAQ_OK) st = launch_gather_diagonals(src, keep, c, s);
+    if (st != DIAQ_OK) {
+        free_op_memory(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_op_prune(diaq_op_t op, diaq_stream_t stream, diaq_op_t* out) {
+    clear_error_device();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    DIAQ_TRY(check_op(op));
+    if (op->variant != DIAQ_STORED) return fail(DIAQ_ERR_ARG, "op is on-the-fly: no stored diagonals");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int64_t> counts;
+    DIAQ_TRY(count_diagonal_nnz(op, &counts, s));
+    return prune_with_counts(op, counts, s, out);
+}
+
+diaq_status diaq_unitary_chain(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
+                               diaq_dtype dtype, int32_t prune, int64_t* n_diagonals, int64_t* nnz,
+                               diaq_stream_t stream, diaq_op_t* out) {
+    clear_error_device();
+    if (!out) return fail(DIAQ_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!gates || n_gates < 1) return fail(DIAQ_ERR_ARG, "need at least one gate");
+    if (n_qubits < 1 || n_qubits > 15) return fail(DIAQ_ERR_ARG, "unitary chain needs 1 <= n_qubits <= 15 (got %d)", n_qubits);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    diaq_op_s* U = nullptr;
+    auto drop = [](diaq_op_s* p) {
+        if (p) {
+            free_op_memory(p);
+            delete p;
+        }
+    };
+    for (int t = 0; t < n_gates; ++t) {
+        diaq_op_t g = nullptr;
+        diaq_status st = diaq_build(&gates[t], n_qubits, dtype, DIAQ_STORED, theta, stream, &g);
+        if (st != DIAQ_OK) {
+            drop(U);
+            return st;
+        }
+        diaq_op_s* C = nullptr;
+        if (!U) {
+            C = g;  // the first time step is the unitary so far
+            C->op_class = DIAQ_CLASS_RAW;
+        } else {
+            C = new (std::nothrow) diaq_op_s();
+            if (!C) {
+                drop(U);
+                drop(g);
+                return fail(DIAQ_ERR_ALLOC, "host allocation failed");
+            }
+            C->n = n_qubits;
+            C->dtype = dtype;
+            C->variant = DIAQ_STORED;
+            C->op_class = DIAQ_CLASS_RAW;
+            C->device = g->device;
+            st = launch_spgemm(g, U, C, s);  // C = G_t U (Algorithm 1)
+            drop(U);
+            drop(g);
+            U = nullptr;
+            if (st != DIAQ_OK) {
+                drop(C);
+                return st;
+            }
+        }
+        std::vector<int64_t> counts;
+        if (prune || nnz) {
+            st = count_diagonal_nnz(C, &counts, s);
+            if (st != DIAQ_OK) {
+                drop(C);
+                return st;
+            }
+        }
+        if (prune) {
+            diaq_op_s* P = nullptr;
+            st = prune_with_counts(C, counts, s, &P);
+            drop(C);
+            if (st != DIAQ_OK) return st;
+            C = P;
+        }
+        U = C;
+        if (n_diagonals) n_diagonals[t] = int64_t(U->offsets.size());
+        if (nnz) {
+            int64_t z = 0;
+            for (int64_t v : counts) z += v;
+            nnz[t] = z;
+        }
+    }
+    *out = U;
+    return DIAQ_OK;
 }
 
 static int mem_kind(const void* p) {
@@ -756,7 +906,9 @@ diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_i
     void* other = work1;
     for (int i = 0; i < count; ++i) {
         if (ops[i]->variant == DIAQ_ONTHEFLY) {
-            DIAQ_TRY(launch_onthefly(ops[i], cur, cur, s));
+            bool done = false;
+            DIAQ_TRY(launch_inplace_skip(ops[i], cur, s, &done));
+            if (!done) DIAQ_TRY(launch_onthefly(ops[i], cur, cur, s));
         } else {
             DIAQ_TRY(launch_stored(ops[i], cur, other, s));
             std::swap(cur, other);

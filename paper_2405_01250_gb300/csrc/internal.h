@@ -114,6 +114,23 @@ diaq_status launch_raw_upload(diaq_op_s* op, const double* host_values, cudaStre
 diaq_status launch_spgemm(const diaq_op_s* a, const diaq_op_s* b, diaq_op_s* c, cudaStream_t s);
 diaq_status upload_matrix(diaq_op_s* op);
 
+// Unitary simulation helpers (unitary.cu): per-diagonal count of values
+// that are not exactly zero (synchronises s), and a gather of the stored
+// diagonals keep[] of src into dst (dst offsets/starts already set).
+diaq_status count_diagonal_nnz(const diaq_op_s* op, std::vector<int64_t>* nnz, cudaStream_t s);
+diaq_status launch_gather_diagonals(const diaq_op_s* src, const std::vector<int32_t>& keep, diaq_op_s* dst,
+                                    cudaStream_t s);
+
+// In-place apply that reads and writes only the rows an op changes
+// (inplace.cu). Sets *launched = false, and does nothing, when the op has
+// no identity row or is not a k <= 3 on-the-fly gate op; the caller then
+// runs the full kernel.
+diaq_status launch_inplace_skip(const diaq_op_s* op, void* x, cudaStream_t s, bool* launched);
+// Local columns read and local rows written by that kernel.
+void inplace_masks(const GateDesc& g, diaq_dtype dt, uint32_t* ld_mask, uint32_t* st_mask);
+// Algorithmic bytes of one in-place on-the-fly apply of g.
+int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
+
 // Pauli-sum terms grouped by X mask, prepared on the host.
 struct PauliGroups {
     std::vector<uint64_t> xmask;         // one per group
