@@ -405,6 +405,9 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
             if best is None or rec["grads_per_s"] > best["grads_per_s"]:
                 best = rec
         out[f"adjoint_best_{name}"] = best
+        tune = plan.autotune(circ.theta, reps=5)
+        out[f"adjoint_autotune_{name}"] = {"best_window": tune["best_window"], "best_ms_device": tune["best_ms"],
+                                          "ms_by_window": {str(w): m for w, m in tune["tried"]}}
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
     # plain FP64 path: one circuit evaluation = 472 applies + expectation

@@ -335,6 +335,23 @@ diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, co
  * back to window 0 and the status says why. */
 diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window);
 
+#define DIAQ_PLAN_TUNE_MAX 8
+
+typedef struct {
+    int32_t n_tried;
+    int32_t window[DIAQ_PLAN_TUNE_MAX];
+    float ms[DIAQ_PLAN_TUNE_MAX];  /* one graph replay (energy + gradient) */
+    int32_t best_window;
+    float best_ms;
+} diaq_plan_tuning;
+
+/* Time the sweep for windows 0, 3, 4 and 5 (`reps` graph replays each, with
+ * theta, host array of n_params) and keep the fastest; complex64 circuits
+ * usually gain from a window, complex128 ones (FP64-bound) rarely. report
+ * may be NULL. Synchronises. */
+diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
+                                       diaq_plan_tuning* report);
+
 /* Current window and the number of launches per sweep (blocks, or gates
  * when window = 0); either pointer may be NULL. */
 diaq_status diaq_adjoint_plan_get_window(diaq_adjoint_plan_t p, int32_t* window, int32_t* n_blocks);

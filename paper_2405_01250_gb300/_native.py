@@ -122,6 +122,16 @@ class diaq_apply_tuning(ctypes.Structure):
     ]
 
 
+class diaq_plan_tuning(ctypes.Structure):
+    _fields_ = [
+        ("n_tried", ctypes.c_int32),
+        ("window", ctypes.c_int32 * 8),
+        ("ms", ctypes.c_float * 8),
+        ("best_window", ctypes.c_int32),
+        ("best_ms", ctypes.c_float),
+    ]
+
+
 class diaq_fusion_tuning(ctypes.Structure):
     _fields_ = [
         ("n_depths", ctypes.c_int32),
@@ -146,6 +156,7 @@ SIGNATURES.update({
     "diaq_adjoint_plan_run": (ctypes.c_int, [_vp, _dp, _vp, _dp, _dp, _vp]),
     "diaq_adjoint_plan_destroy": (ctypes.c_int, [_vp]),
     "diaq_adjoint_plan_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.POINTER(diaq_plan_tuning)]),
     "diaq_batch_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_batch_get_window": (ctypes.c_int, [_vp, _i32p]),
     "diaq_adjoint_plan_get_window": (ctypes.c_int, [_vp, _i32p, _i32p]),

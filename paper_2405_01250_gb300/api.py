@@ -474,6 +474,15 @@ class AdjointPlan:
         """0: one launch per gate; 2..5: window-fused blocks (diaq_adjoint_plan_set_window)."""
         check(lib().diaq_adjoint_plan_set_window(self.handle, int(window)))
 
+    def autotune(self, theta, reps: int = 3) -> dict:
+        """Time windows 0, 3, 4, 5 and keep the fastest (diaq_adjoint_plan_autotune)."""
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        rep = N.diaq_plan_tuning()
+        check(lib().diaq_adjoint_plan_autotune(self.handle, _dptr(th) if len(th) else None, int(reps),
+                                               ctypes.byref(rep)))
+        return {"tried": [(rep.window[i], rep.ms[i]) for i in range(rep.n_tried)],
+                "best_window": rep.best_window, "best_ms": rep.best_ms}
+
     def window(self) -> tuple:
         """(window, launches per sweep)."""
         w = ctypes.c_int32(0)

@@ -1390,6 +1390,7 @@ struct diaq_adjoint_plan_s {
     diaq_dtype dtype = DIAQ_C128;
     int n_gates = 0, n_params = 0, n_terms = 0, n_slots = 1;
     int P = 1;  // blocks of the rotation and reduction kernels (partial columns)
+    int P_gate = 1;  // P of the one-launch-per-gate sweep (window-fused sweeps size their own)
     std::vector<BGate> gates;
     std::vector<GateDesc> fwd, bwd;  // fixed gates: U and U^dag
     BGate* d_gates = nullptr;
@@ -1483,10 +1484,27 @@ static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window) {
         p->d_wg = nullptr;
     }
     p->window = window;
-    if (window == 0 || p->n_gates == 0) return DIAQ_OK;
+    int P = p->P_gate;
     std::vector<WinGate> wg;
-    DIAQ_TRY(make_windows(p->gates.data(), p->n_gates, 0, window, &p->blocks, &wg));
-    DIAQ_TRY(upload(&p->d_wg, wg));
+    if (window > 0 && p->n_gates > 0) {
+        DIAQ_TRY(make_windows(p->gates.data(), p->n_gates, 0, window, &p->blocks, &wg));
+        DIAQ_TRY(upload(&p->d_wg, wg));
+        // one group per thread for the widest block, at most 4 blocks per SM
+        int wmax = 1, sms = 1;
+        for (const WinBlock& w : p->blocks) wmax = std::max(wmax, w.nq);
+        DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+        const int64_t want = (int64_t(1) << (p->n - wmax)) / WIN_THREADS;
+        P = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 4)));
+    }
+    if (P != p->P) {  // the partial rows have P columns
+        double* part = nullptr;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&part), sizeof(double) * size_t(p->n_slots) * size_t(P));
+        if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "adjoint plan partials: %s", cudaGetErrorString(e));
+        cudaFree(p->d_part);
+        p->d_part = part;
+        p->P = P;
+    }
+    if (window == 0 || p->n_gates == 0) return DIAQ_OK;
     size_t most = 0;
     for (const WinBlock& w : p->blocks) most = std::max(most, win_smem(p->dtype, w.nq, w.count, w.np));
     if (p->dtype == DIAQ_C128)
@@ -1614,6 +1632,7 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
         // per SM at their register counts); each thread loops over groups
         const int64_t want = ((int64_t(1) << n_qubits) / 2 + 255) / 256;
         p->P = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 2)));
+        p->P_gate = p->P;
     }
     const size_t ab = amp_bytes(dtype), N = size_t(1) << n_qubits;
     if (st == DIAQ_OK) st = upload(&p->d_gates, p->gates);
@@ -1690,6 +1709,56 @@ diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window) 
         return st;
     }
     return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
+                                       diaq_plan_tuning* report) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (p->n_params > 0 && !theta) return fail(DIAQ_ERR_ARG, "theta is NULL");
+    if (reps < 1) reps = 1;
+    const int wins[] = {0, 3, 4, 5};
+    int best_w = 0, tried = 0;
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    DIAQ_CUDA(cudaEventCreate(&e0));
+    DIAQ_CUDA(cudaEventCreate(&e1));
+    if (p->n_params) std::memcpy(p->h_theta, theta, sizeof(double) * size_t(p->n_params));
+    for (int w : wins) {
+        if (diaq_adjoint_plan_set_window(p, w) != DIAQ_OK) {
+            clear_error();
+            cudaGetLastError();
+            continue;  // this window does not fit the circuit
+        }
+        DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));  // warm
+        DIAQ_CUDA(cudaEventRecord(e0, p->stream));
+        for (int r = 0; r < reps; ++r) DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));
+        DIAQ_CUDA(cudaEventRecord(e1, p->stream));
+        DIAQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        DIAQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= float(reps);
+        if (report && tried < DIAQ_PLAN_TUNE_MAX) {
+            report->window[tried] = w;
+            report->ms[tried] = ms;
+        }
+        ++tried;
+        if (ms < best) {
+            best = ms;
+            best_w = w;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no sweep fits");
+    DIAQ_TRY(diaq_adjoint_plan_set_window(p, best_w));
+    if (report) {
+        report->n_tried = std::min(tried, DIAQ_PLAN_TUNE_MAX);
+        report->best_window = best_w;
+        report->best_ms = best;
+    }
+    return DIAQ_OK;
 }
 
 diaq_status diaq_adjoint_plan_get_window(diaq_adjoint_plan_t p, int32_t* window, int32_t* n_blocks) {

@@ -52,118 +52,178 @@ __device__ __forceinline__ int win_row(int base, int c, int k, int b0, int b1) {
     return base | (((c >> 1) & 1) << b0) | ((c & 1) << b1);
 }
 
-// Rotation rows of one gate subspace: partial (reverse) and update, with
-// the generator's X mask XL fixed at compile time so every partner
-// amplitude is a register.
-template <typename R, int XL>
-__device__ __forceinline__ void win_rot(const WinOp<R>& op, int Dk, amp_t<R>* v, amp_t<R>* w, bool rev,
-                                        Acc<R>* acc) {
+// One rotation exp(-i a/2 P) over every subspace of the window, with the
+// gate's shape fixed at compile time: K targets, the generator's local X
+// mask XL, NYP = parity of its Y count (kappa = -i sin(a/2) i^ny is then
+// imaginary for even ny and real for odd ny, and i^ny turns the partial's
+// Im into a Re), and REV (reverse sweep: partial Im <l|P|p> before U^dag,
+// and the same update of l). The per-row signs s_r are folded into kappa
+// once. Rows of a subspace are registers; subspaces of one column are
+// disjoint, so iterations do not depend on each other.
+template <typename R, int K, int XL, int NYP, bool REV>
+__device__ __noinline__ void win_rot_loop(amp_t<R>* __restrict__ p, amp_t<R>* __restrict__ l, int D, int T,
+                                          int b0, int b1, int zl, bool negp, R cs, R kr, R ki, Acc<R>* acc) {
     using A = amp_t<R>;
-    if (rev) {
-        // Im conj(l_r) i^ny s_r p_{r ^ xl}
-        R sr = R(0);
+    constexpr int Dk = 1 << K;
+    const int lo = K == 1 ? b0 : min(b0, b1), hi = K == 1 ? 0 : max(b0, b1);
+    int ro[Dk];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            if (r < Dk) {
-                const A q = mul_ipow(v[r ^ XL], op.ny);
-                const R t = w[r].x * q.y - w[r].y * q.x;
-                sr += (__popc((r ^ XL) & op.zl) & 1) ? -t : t;
-            }
-        }
-        acc->add(sr);
+    for (int c = 0; c < Dk; ++c)
+        ro[c] = (K == 1 ? ((c & 1) << b0) : ((((c >> 1) & 1) << b0) | ((c & 1) << b1))) * T;
+    bool sneg[Dk];
+    R kk[Dk];
+#pragma unroll
+    for (int r = 0; r < Dk; ++r) {
+        sneg[r] = (__popc((r ^ XL) & zl) & 1) != 0;
+        const R kv = NYP ? kr : ki;  // the non-zero part of kappa
+        kk[r] = sneg[r] ? -kv : kv;
     }
-    const bool kimag = op.kr == R(0), kreal = op.ki == R(0);
+    Acc<R> loc;
+    const int H = D >> K;
+#pragma unroll 2
+    for (int h = 0; h < H; ++h) {
+        const int base = (K == 1 ? ins0(h, lo) : ins0(ins0(h, lo), hi)) * T;
+        A v[Dk], w[Dk];
 #pragma unroll
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1 && !rev) break;
-        A* x = pass == 0 ? v : w;
-        A o[4];
+        for (int c = 0; c < Dk; ++c) {
+            v[c] = p[base + ro[c]];
+            if (REV) w[c] = l[base + ro[c]];
+        }
+        if (REV) {
+            // Im conj(w_r) i^ny s_r v_{r^XL}: a cross product for even ny,
+            // a dot product for odd ny; the sign of i^ny (ny & 2) is applied
+            // to the sum at the end
+            R sr = R(0);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            if (r < Dk) {
-                const bool neg = (__popc((r ^ XL) & op.zl) & 1) != 0;
-                const R krr = neg ? -op.kr : op.kr, kir = neg ? -op.ki : op.ki;
+            for (int r = 0; r < Dk; ++r) {
+                const A q = v[r ^ XL];
+                const R t = NYP ? fma(w[r].x, q.x, w[r].y * q.y) : fma(w[r].x, q.y, -w[r].y * q.x);
+                sr += sneg[r] ? -t : t;
+            }
+            loc.add(sr);
+        }
+#pragma unroll
+        for (int pass = 0; pass < (REV ? 2 : 1); ++pass) {
+            A* x = pass == 0 ? v : w;
+            A o[Dk];
+#pragma unroll
+            for (int r = 0; r < Dk; ++r) {
                 const A a = x[r], b = x[r ^ XL];
-                if (kimag) {
-                    o[r].x = fma(op.cs, a.x, -kir * b.y);
-                    o[r].y = fma(op.cs, a.y, kir * b.x);
-                } else if (kreal) {
-                    o[r].x = fma(op.cs, a.x, krr * b.x);
-                    o[r].y = fma(op.cs, a.y, krr * b.y);
-                } else {
-                    o[r].x = fma(op.cs, a.x, fma(krr, b.x, -kir * b.y));
-                    o[r].y = fma(op.cs, a.y, fma(krr, b.y, kir * b.x));
+                if (NYP) {  // kappa real
+                    o[r].x = fma(cs, a.x, kk[r] * b.x);
+                    o[r].y = fma(cs, a.y, kk[r] * b.y);
+                } else {    // kappa = i kk
+                    o[r].x = fma(cs, a.x, -kk[r] * b.y);
+                    o[r].y = fma(cs, a.y, kk[r] * b.x);
                 }
             }
+#pragma unroll
+            for (int r = 0; r < Dk; ++r) x[r] = o[r];
         }
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (r < Dk) x[r] = o[r];
+        for (int c = 0; c < Dk; ++c) {
+            p[base + ro[c]] = v[c];
+            if (REV) l[base + ro[c]] = w[c];
+        }
+    }
+    if (REV) {
+        const double v = loc.value();
+        acc->add(R(negp ? -v : v));
     }
 }
 
-// One gate on the staged column of psi (and, in the reverse sweep, lambda),
-// stride T in shared memory; a rotation in the reverse sweep also adds its
-// partial into acc before the update.
+// One fixed gate (its matrix, or M^dag in the reverse sweep, staged in op)
+// over every subspace of the window; REV also updates l.
+template <typename R, int K, bool REV>
+__device__ __noinline__ void win_fixed_loop(const WinOp<R>& op, amp_t<R>* __restrict__ p, amp_t<R>* __restrict__ l,
+                                            int D, int T) {
+    using A = amp_t<R>;
+    constexpr int Dk = 1 << K;
+    const int b0 = op.b0, b1 = op.b1;
+    const int lo = K == 1 ? b0 : min(b0, b1), hi = K == 1 ? 0 : max(b0, b1);
+    int ro[Dk];
+#pragma unroll
+    for (int c = 0; c < Dk; ++c)
+        ro[c] = (K == 1 ? ((c & 1) << b0) : ((((c >> 1) & 1) << b0) | ((c & 1) << b1))) * T;
+    R mr[Dk * Dk], mi[Dk * Dk];
+    uint8_t ty[Dk * Dk];
+#pragma unroll
+    for (int e = 0; e < Dk * Dk; ++e) {
+        mr[e] = op.mre[e];
+        mi[e] = op.mim[e];
+        ty[e] = op.ty[e];
+    }
+    const int H = D >> K;
+#pragma unroll 2
+    for (int h = 0; h < H; ++h) {
+        const int base = (K == 1 ? ins0(h, lo) : ins0(ins0(h, lo), hi)) * T;
+#pragma unroll
+        for (int pass = 0; pass < (REV ? 2 : 1); ++pass) {
+            A* col = pass == 0 ? p : l;
+            A x[Dk], o[Dk];
+#pragma unroll
+            for (int c = 0; c < Dk; ++c) x[c] = col[base + ro[c]];
+#pragma unroll
+            for (int r = 0; r < Dk; ++r) {
+                A s;
+                s.x = R(0);
+                s.y = R(0);
+                bool first = true;
+#pragma unroll
+                for (int c = 0; c < Dk; ++c) mac_typed<R>(s, first, ty[r * Dk + c], mr[r * Dk + c], mi[r * Dk + c], x[c]);
+                o[r] = s;
+            }
+#pragma unroll
+            for (int c = 0; c < Dk; ++c) col[base + ro[c]] = o[c];
+        }
+    }
+}
+
+template <typename R, int K, bool REV>
+__device__ __forceinline__ void win_rot_dispatch(const WinOp<R>& op, amp_t<R>* p, amp_t<R>* l, int D, int T,
+                                                 Acc<R>* acc) {
+    const int nyp = op.ny & 1;
+    const bool negp = (op.ny & 2) != 0;
+    const R cs = op.cs, kr = op.kr, ki = op.ki;
+    const int b0 = op.b0, b1 = op.b1, zl = op.zl;
+#define DIAQ_WROT(XL, NYP) win_rot_loop<R, K, XL, NYP, REV>(p, l, D, T, b0, b1, zl, negp, cs, kr, ki, acc)
+    if (K == 1) {
+        if (op.xl == 0) {
+            if (nyp) DIAQ_WROT(0, 1); else DIAQ_WROT(0, 0);
+        } else {
+            if (nyp) DIAQ_WROT(1, 1); else DIAQ_WROT(1, 0);
+        }
+    } else {
+        switch (op.xl) {
+            case 0: if (nyp) DIAQ_WROT(0, 1); else DIAQ_WROT(0, 0); break;
+            case 1: if (nyp) DIAQ_WROT(1, 1); else DIAQ_WROT(1, 0); break;
+            case 2: if (nyp) DIAQ_WROT(2, 1); else DIAQ_WROT(2, 0); break;
+            default: if (nyp) DIAQ_WROT(3, 1); else DIAQ_WROT(3, 0); break;
+        }
+    }
+#undef DIAQ_WROT
+}
+
+// One gate of a block on the staged columns p (and, in the reverse sweep,
+// l); a rotation in the reverse sweep also adds its partial into acc. The
+// gate's kind is resolved here, once, ahead of the loop over subspaces.
 template <typename R>
 __device__ __forceinline__ void win_apply(const WinOp<R>& op, amp_t<R>* p, amp_t<R>* l, int D, int T,
                                           Acc<R>* acc) {
-    using A = amp_t<R>;
-    const int k = op.k, Dk = 1 << k;
-    const int lo = k == 1 ? op.b0 : min(op.b0, op.b1), hi = k == 1 ? 0 : max(op.b0, op.b1);
-    const int H = D >> k;
-    const bool rev = l != nullptr;
-    for (int h = 0; h < H; ++h) {
-        const int base = k == 1 ? ins0(h, lo) : ins0(ins0(h, lo), hi);
-        int row[4];
-        A v[4], w[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            row[c] = 0;
-            if (c < Dk) {
-                row[c] = win_row(base, c, k, op.b0, op.b1) * T;
-                v[c] = p[row[c]];
-                if (rev) w[c] = l[row[c]];
-            }
-        }
-        if (op.j >= 0) {
-            switch (op.xl) {
-                case 0: win_rot<R, 0>(op, Dk, v, w, rev, acc); break;
-                case 1: win_rot<R, 1>(op, Dk, v, w, rev, acc); break;
-                case 2: win_rot<R, 2>(op, Dk, v, w, rev, acc); break;
-                default: win_rot<R, 3>(op, Dk, v, w, rev, acc); break;
-            }
+    if (op.j >= 0) {
+        if (l) {
+            if (op.k == 1) win_rot_dispatch<R, 1, true>(op, p, l, D, T, acc);
+            else win_rot_dispatch<R, 2, true>(op, p, l, D, T, acc);
         } else {
-#pragma unroll
-            for (int pass = 0; pass < 2; ++pass) {
-                if (pass == 1 && !rev) break;
-                A* x = pass == 0 ? v : w;
-                A o[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    if (r < Dk) {
-                        A s;
-                        s.x = R(0);
-                        s.y = R(0);
-                        bool first = true;
-#pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (c < Dk) mac_typed<R>(s, first, op.ty[r * Dk + c], op.mre[r * Dk + c], op.mim[r * Dk + c], x[c]);
-                        o[r] = s;
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (r < Dk) x[r] = o[r];
-            }
+            if (op.k == 1) win_rot_dispatch<R, 1, false>(op, p, l, D, T, acc);
+            else win_rot_dispatch<R, 2, false>(op, p, l, D, T, acc);
         }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (c < Dk) {
-                p[row[c]] = v[c];
-                if (rev) l[row[c]] = w[c];
-            }
-        }
+    } else if (l) {
+        if (op.k == 1) win_fixed_loop<R, 1, true>(op, p, l, D, T);
+        else win_fixed_loop<R, 2, true>(op, p, l, D, T);
+    } else {
+        if (op.k == 1) win_fixed_loop<R, 1, false>(op, p, l, D, T);
+        else win_fixed_loop<R, 2, false>(op, p, l, D, T);
     }
 }
 

@@ -72,7 +72,7 @@ def test_batch_window_fused_matches_oracle(api, dtype):
     barrier per block) gives the oracle's energies and gradients for every
     window and cluster size, and the per-gate kernel's to rounding."""
     rng = np.random.default_rng(24)
-    inst = _instances(rng, [4, 6, 8, 10, 7, 5])
+    inst = _instances(rng, [4, 6, 8, 10, 12, 6])
     E_ref, G_ref = _ref(inst)
     theta = np.concatenate([c.theta for c, _ in inst])
     b = _batch(api, inst, dtype)

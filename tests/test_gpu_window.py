@@ -129,6 +129,21 @@ def test_window_plan_full_size_ansatz20(api):
     assert np.max(np.abs(g[sample] - g_ps[sample])) <= 1e-10
 
 
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_plan_autotune_keeps_parity(api, dtype):
+    name, circ, obs = CASES[1]
+    n = circ.n
+    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+    rep = plan.autotune(circ.theta, reps=2)
+    assert {w for w, _ in rep["tried"]} == {0, 3, 4, 5}
+    assert plan.window()[0] == rep["best_window"]
+    e, g = plan.run(circ.theta)
+    psi0 = synth.basis_state(n, 0)
+    tol_e, tol_g = _tols(dtype, circ, obs)
+    assert abs(e - oracle.energy(circ, obs, psi0)) <= tol_e
+    assert np.max(np.abs(g - oracle.param_shift_grad(circ, obs, psi0))) <= tol_g
+
+
 def test_window_argument_errors(api):
     circ = synth.ansatz(n=3, layers=1, seed=1)
     obs = synth.ansatz_observable(3)
