@@ -335,20 +335,30 @@ diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, co
  * back to window 0 and the status says why. */
 diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window);
 
+/* As diaq_adjoint_plan_set_window, choosing also how many threads share a
+ * group of the window: lanes = 1 (a thread runs the block's gates on its
+ * own group) or 4 (four threads of a warp split each gate's subspaces,
+ * which quadruples the threads at work and suits FP64-bound complex128
+ * sweeps). lanes is ignored for window 0. */
+diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, int32_t lanes);
+
+diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, int32_t* lanes, int32_t* n_blocks);
+
 #define DIAQ_PLAN_TUNE_MAX 8
 
 typedef struct {
     int32_t n_tried;
     int32_t window[DIAQ_PLAN_TUNE_MAX];
+    int32_t lanes[DIAQ_PLAN_TUNE_MAX];
     float ms[DIAQ_PLAN_TUNE_MAX];  /* one graph replay (energy + gradient) */
     int32_t best_window;
+    int32_t best_lanes;
     float best_ms;
 } diaq_plan_tuning;
 
-/* Time the sweep for windows 0, 3, 4 and 5 (`reps` graph replays each, with
- * theta, host array of n_params) and keep the fastest; complex64 circuits
- * usually gain from a window, complex128 ones (FP64-bound) rarely. report
- * may be NULL. Synchronises. */
+/* Time the sweep per gate and window-fused with windows 3, 4 and 5 at 1 and
+ * 4 lanes (`reps` graph replays each, with theta, host array of n_params)
+ * and keep the fastest. report may be NULL. Synchronises. */
 diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
                                        diaq_plan_tuning* report);
 

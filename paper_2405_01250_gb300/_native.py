@@ -126,8 +126,10 @@ class diaq_plan_tuning(ctypes.Structure):
     _fields_ = [
         ("n_tried", ctypes.c_int32),
         ("window", ctypes.c_int32 * 8),
+        ("lanes", ctypes.c_int32 * 8),
         ("ms", ctypes.c_float * 8),
         ("best_window", ctypes.c_int32),
+        ("best_lanes", ctypes.c_int32),
         ("best_ms", ctypes.c_float),
     ]
 
@@ -156,6 +158,8 @@ SIGNATURES.update({
     "diaq_adjoint_plan_run": (ctypes.c_int, [_vp, _dp, _vp, _dp, _dp, _vp]),
     "diaq_adjoint_plan_destroy": (ctypes.c_int, [_vp]),
     "diaq_adjoint_plan_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_set_sweep": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "diaq_adjoint_plan_get_sweep": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "diaq_adjoint_plan_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.POINTER(diaq_plan_tuning)]),
     "diaq_batch_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_batch_get_window": (ctypes.c_int, [_vp, _i32p]),

@@ -480,8 +480,18 @@ class AdjointPlan:
         rep = N.diaq_plan_tuning()
         check(lib().diaq_adjoint_plan_autotune(self.handle, _dptr(th) if len(th) else None, int(reps),
                                                ctypes.byref(rep)))
-        return {"tried": [(rep.window[i], rep.ms[i]) for i in range(rep.n_tried)],
-                "best_window": rep.best_window, "best_ms": rep.best_ms}
+        return {"tried": [(rep.window[i], rep.lanes[i], rep.ms[i]) for i in range(rep.n_tried)],
+                "best_window": rep.best_window, "best_lanes": rep.best_lanes, "best_ms": rep.best_ms}
+
+    def set_sweep(self, window: int, lanes: int) -> None:
+        """window 0 (per gate) or 2..5, with 1 or 4 threads per group (diaq_adjoint_plan_set_sweep)."""
+        check(lib().diaq_adjoint_plan_set_sweep(self.handle, int(window), int(lanes)))
+
+    def sweep(self) -> tuple:
+        """(window, lanes, launches per sweep)."""
+        w, ln, nb = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_sweep(self.handle, ctypes.byref(w), ctypes.byref(ln), ctypes.byref(nb)))
+        return w.value, ln.value, nb.value
 
     def window(self) -> tuple:
         """(window, launches per sweep)."""

@@ -1304,6 +1304,124 @@ static size_t win_smem(diaq_dtype dt, int nq, int count, int np) {
     return head + 2 * (size_t(1) << nq) * WIN_THREADS * ab + size_t(np) * WIN_THREADS * sizeof(double);
 }
 
+// Stage the block's gates for the sweep's direction (thread i < count
+// writes op i) and clear the partial accumulators.
+template <typename R>
+__device__ __forceinline__ void plan_stage(const BGate* __restrict__ gates, const RotAngles* __restrict__ ang,
+                                           const WinGate* __restrict__ wg, const WinBlock& w, bool rev,
+                                           WinOp<R>* ops, Acc<R>* sa) {
+    const int T = blockDim.x, t = threadIdx.x;
+    for (int i = t; i < w.count; i += T) {
+        const WinGate x = wg[w.first + i];
+        const BGate& G = gates[x.g];
+        WinOp<R>& o = ops[i];
+        o.k = G.k;
+        o.b0 = x.b0;
+        o.b1 = x.b1;
+        o.j = G.param >= 0 ? x.j : -1;
+        o.xl = G.xl;
+        o.zl = G.rot.zl;
+        o.ny = G.rot.ny;
+        o.cs = R(0);
+        o.kr = R(0);
+        o.ki = R(0);
+        const int Dk = 1 << G.k;
+        if (G.param >= 0) {
+            const RotAngles a = ang[x.g];
+            o.cs = R(a.cs);
+            o.kr = R(rev ? a.kar : a.kfr);
+            o.ki = R(rev ? a.kai : a.kfi);
+        } else {
+            for (int r = 0; r < Dk; ++r)
+                for (int c = 0; c < Dk; ++c) {
+                    const double vr = rev ? G.re[c * Dk + r] : G.re[r * Dk + c];
+                    const double vi = rev ? -G.im[c * Dk + r] : G.im[r * Dk + c];
+                    o.mre[r * Dk + c] = R(vr);
+                    o.mim[r * Dk + c] = R(vi);
+                    o.ty[r * Dk + c] = dev_entry_type(double(R(vr)), double(R(vi)));
+                }
+        }
+    }
+    for (int j = 0; j < w.np; ++j) sa[j * T + t] = Acc<R>();
+    __syncthreads();
+}
+
+// Lanes per group of the window-fused plan kernel: a group's 2^w amplitudes
+// are shared by WIN_LANES threads of one warp, which split its subspaces
+// gate by gate (a __syncwarp between gates), so a block of 128 threads
+// works on 32 groups at once and a thread's chain of dependent steps per
+// gate is WIN_LANES times shorter.
+constexpr int WIN_LANES = 4;
+
+static size_t win_smem_lanes(diaq_dtype dt, int nq, int count, int np) {
+    const size_t opb = dt == DIAQ_C128 ? sizeof(WinOp<double>) : sizeof(WinOp<float>);
+    const size_t head = ((opb * size_t(count) + 15) / 16) * 16;
+    const size_t gpc = WIN_THREADS / WIN_LANES;
+    return head + 2 * gpc * ((size_t(1) << nq) + 1) * amp_bytes(dt) + size_t(np) * WIN_THREADS * sizeof(double);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(WIN_THREADS, 4) k_plan_win_l(amp_t<R>* psi, amp_t<R>* lam,
+                                                               const BGate* __restrict__ gates,
+                                                               const RotAngles* __restrict__ ang,
+                                                               const WinGate* __restrict__ wg,
+                                                               const __grid_constant__ WinBlock w, int n,
+                                                               double* part, int P) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double warps[32];
+    constexpr int L = WIN_LANES;
+    const int T = WIN_THREADS, t = threadIdx.x;
+    const int GPC = T / L, gs = t / L, li = t % L;
+    const int D = 1 << w.nq, SD = D + 1;  // one padding amplitude per group against bank conflicts
+    const bool rev = lam != nullptr;
+    WinOp<R>* ops = reinterpret_cast<WinOp<R>*>(sm);
+    A* sp = reinterpret_cast<A*>(sm + ((sizeof(WinOp<R>) * size_t(w.count) + 15) / 16) * 16);
+    A* sl = sp + GPC * SD;
+    Acc<R>* sa = reinterpret_cast<Acc<R>*>(sl + GPC * SD);
+    plan_stage<R>(gates, ang, wg, w, rev, ops, sa);
+    const int64_t G = int64_t(1) << (n - w.nq);
+    A* gp = sp + gs * SD;
+    A* gl = sl + gs * SD;
+    // every thread of the block makes the same number of trips, so every
+    // lane of a warp reaches each __syncwarp
+    for (int64_t g0 = int64_t(blockIdx.x) * GPC; g0 < G; g0 += int64_t(gridDim.x) * GPC) {
+        const int64_t g = g0 + gs;
+        const bool valid = g < G;
+        const int64_t base = valid ? insert_zeros_rt(g, w.q, w.nq) : 0;
+        if (valid) {
+            for (int e = li; e < D; e += L) gp[e] = psi[base + w.off[e]];
+            if (rev)
+                for (int e = li; e < D; e += L) gl[e] = lam[base + w.off[e]];
+        }
+        __syncwarp();
+        if (!rev) {
+            for (int i = 0; i < w.count; ++i) {
+                win_apply<R, 1>(ops[i], gp, nullptr, D, 1, nullptr, li, L);
+                __syncwarp();
+            }
+        } else {
+            for (int i = w.count - 1; i >= 0; --i) {
+                const WinOp<R>& o = ops[i];
+                win_apply<R, 1>(o, gp, gl, D, 1, (valid && o.j >= 0) ? sa + o.j * T + t : nullptr, li, L);
+                __syncwarp();
+            }
+        }
+        if (valid) {
+            for (int e = li; e < D; e += L) psi[base + w.off[e]] = gp[e];
+            if (rev)
+                for (int e = li; e < D; e += L) lam[base + w.off[e]] = gl[e];
+        }
+        __syncwarp();
+    }
+    if (rev) {
+        for (int j = 0; j < w.np; ++j) {
+            const double v = block_sum(sa[j * T + t].value(), warps);
+            if (t == 0) part[int64_t(w.slot[j]) * P + blockIdx.x] = v;
+        }
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(WIN_THREADS) k_plan_win(amp_t<R>* psi, amp_t<R>* lam, const BGate* __restrict__ gates,
                                                           const RotAngles* __restrict__ ang,
@@ -1408,6 +1526,7 @@ struct diaq_adjoint_plan_s {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     int window = 0;                  // 0: one launch per gate; else window-fused blocks of <= window qubits
+    int lanes = 1;                   // threads per group of the window-fused kernel (1 or WIN_LANES)
     std::vector<WinBlock> blocks;
     WinGate* d_wg = nullptr;
 };
@@ -1438,15 +1557,17 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
     k_plan_init<R><<<p->P, 256, 0, s>>>(static_cast<const A*>(p->psi0), psi, N);
     DIAQ_CUDA(cudaGetLastError());
     if (p->window > 0) {
-        for (const WinBlock& w : p->blocks)
-            k_plan_win<R><<<p->P, WIN_THREADS, win_smem(p->dtype, w.nq, w.count, w.np), s>>>(
-                psi, nullptr, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
+        auto block = [&](const WinBlock& w, A* l) {
+            if (p->lanes > 1)
+                k_plan_win_l<R><<<p->P, WIN_THREADS, win_smem_lanes(p->dtype, w.nq, w.count, w.np), s>>>(
+                    psi, l, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
+            else
+                k_plan_win<R><<<p->P, WIN_THREADS, win_smem(p->dtype, w.nq, w.count, w.np), s>>>(
+                    psi, l, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
+        };
+        for (const WinBlock& w : p->blocks) block(w, nullptr);
         k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
-        for (size_t b = p->blocks.size(); b-- > 0;) {
-            const WinBlock& w = p->blocks[b];
-            k_plan_win<R><<<p->P, WIN_THREADS, win_smem(p->dtype, w.nq, w.count, w.np), s>>>(
-                psi, lam, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
-        }
+        for (size_t b = p->blocks.size(); b-- > 0;) block(p->blocks[b], lam);
         DIAQ_CUDA(cudaGetLastError());
     } else {
         for (int g = 0; g < p->n_gates; ++g) {
@@ -1477,13 +1598,14 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
 
 // Blocks of at most `window` qubits and WIN_MAXG gates from the
 // commutation-aware planner; window 0 clears them.
-static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window) {
+static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window, int lanes) {
     p->blocks.clear();
     if (p->d_wg) {
         cudaFree(p->d_wg);
         p->d_wg = nullptr;
     }
     p->window = window;
+    p->lanes = window > 0 ? lanes : 1;
     int P = p->P_gate;
     std::vector<WinGate> wg;
     if (window > 0 && p->n_gates > 0) {
@@ -1493,7 +1615,7 @@ static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window) {
         int wmax = 1, sms = 1;
         for (const WinBlock& w : p->blocks) wmax = std::max(wmax, w.nq);
         DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-        const int64_t want = (int64_t(1) << (p->n - wmax)) / WIN_THREADS;
+        const int64_t want = (int64_t(1) << (p->n - wmax)) / (WIN_THREADS / p->lanes);
         P = int(std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sms) * 4)));
     }
     if (P != p->P) {  // the partial rows have P columns
@@ -1506,11 +1628,15 @@ static diaq_status plan_windows(diaq_adjoint_plan_s* p, int window) {
     }
     if (window == 0 || p->n_gates == 0) return DIAQ_OK;
     size_t most = 0;
-    for (const WinBlock& w : p->blocks) most = std::max(most, win_smem(p->dtype, w.nq, w.count, w.np));
-    if (p->dtype == DIAQ_C128)
-        DIAQ_CUDA(cudaFuncSetAttribute(k_plan_win<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most)));
-    else
-        DIAQ_CUDA(cudaFuncSetAttribute(k_plan_win<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most)));
+    for (const WinBlock& w : p->blocks)
+        most = std::max(most, p->lanes > 1 ? win_smem_lanes(p->dtype, w.nq, w.count, w.np)
+                                           : win_smem(p->dtype, w.nq, w.count, w.np));
+    const void* fn = p->lanes > 1
+        ? (p->dtype == DIAQ_C128 ? reinterpret_cast<const void*>(&k_plan_win_l<double>)
+                                 : reinterpret_cast<const void*>(&k_plan_win_l<float>))
+        : (p->dtype == DIAQ_C128 ? reinterpret_cast<const void*>(&k_plan_win<double>)
+                                 : reinterpret_cast<const void*>(&k_plan_win<float>));
+    DIAQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(most)));
     return DIAQ_OK;
 }
 
@@ -1693,22 +1819,37 @@ diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, co
 }
 
 diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window) {
+    return diaq_adjoint_plan_set_sweep(p, window, 1);
+}
+
+diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, int32_t lanes) {
     clear_error();
     cudaGetLastError();
     if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
     if (window != 0 && (window < 2 || window > WIN_MAX))
         return fail(DIAQ_ERR_ARG, "window = %d: use 0 (one launch per gate) or 2..%d qubits", window, WIN_MAX);
+    if (lanes != 1 && lanes != WIN_LANES)
+        return fail(DIAQ_ERR_ARG, "lanes = %d: use 1 or %d threads per group", lanes, WIN_LANES);
     int dev = -1;
     DIAQ_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
     DIAQ_CUDA(cudaStreamSynchronize(p->stream));
-    diaq_status st = plan_windows(p, window);
+    diaq_status st = plan_windows(p, window, lanes);
     if (st != DIAQ_OK) {
-        plan_windows(p, 0);
+        plan_windows(p, 0, 1);
         plan_capture(p);
         return st;
     }
     return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, int32_t* lanes, int32_t* n_blocks) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (window) *window = p->window;
+    if (lanes) *lanes = p->lanes;
+    if (n_blocks) *n_blocks = p->window > 0 ? int32_t(p->blocks.size()) : p->n_gates;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
@@ -1718,15 +1859,17 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
     if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
     if (p->n_params > 0 && !theta) return fail(DIAQ_ERR_ARG, "theta is NULL");
     if (reps < 1) reps = 1;
-    const int wins[] = {0, 3, 4, 5};
-    int best_w = 0, tried = 0;
+    const int wins[] = {0, 3, 4, 5, 3, 4, 5};
+    const int lns[] = {1, 1, 1, 1, WIN_LANES, WIN_LANES, WIN_LANES};
+    int best_w = 0, best_l = 1, tried = 0;
     float best = 1e30f;
     cudaEvent_t e0, e1;
     DIAQ_CUDA(cudaEventCreate(&e0));
     DIAQ_CUDA(cudaEventCreate(&e1));
     if (p->n_params) std::memcpy(p->h_theta, theta, sizeof(double) * size_t(p->n_params));
-    for (int w : wins) {
-        if (diaq_adjoint_plan_set_window(p, w) != DIAQ_OK) {
+    for (int c = 0; c < 7; ++c) {
+        const int w = wins[c], ln = lns[c];
+        if (diaq_adjoint_plan_set_sweep(p, w, ln) != DIAQ_OK) {
             clear_error();
             cudaGetLastError();
             continue;  // this window does not fit the circuit
@@ -1741,21 +1884,24 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
         ms /= float(reps);
         if (report && tried < DIAQ_PLAN_TUNE_MAX) {
             report->window[tried] = w;
+            report->lanes[tried] = ln;
             report->ms[tried] = ms;
         }
         ++tried;
         if (ms < best) {
             best = ms;
             best_w = w;
+            best_l = ln;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no sweep fits");
-    DIAQ_TRY(diaq_adjoint_plan_set_window(p, best_w));
+    DIAQ_TRY(diaq_adjoint_plan_set_sweep(p, best_w, best_l));
     if (report) {
         report->n_tried = std::min(tried, DIAQ_PLAN_TUNE_MAX);
         report->best_window = best_w;
+        report->best_lanes = best_l;
         report->best_ms = best;
     }
     return DIAQ_OK;

@@ -60,9 +60,10 @@ __device__ __forceinline__ int win_row(int base, int c, int k, int b0, int b1) {
 // and the same update of l). The per-row signs s_r are folded into kappa
 // once. Rows of a subspace are registers; subspaces of one column are
 // disjoint, so iterations do not depend on each other.
-template <typename R, int K, int XL, int NYP, bool REV>
+template <typename R, int K, int XL, int NYP, bool REV, int UNR>
 __device__ __noinline__ void win_rot_loop(amp_t<R>* __restrict__ p, amp_t<R>* __restrict__ l, int D, int T,
-                                          int b0, int b1, int zl, bool negp, R cs, R kr, R ki, Acc<R>* acc) {
+                                          int h0, int hs, int b0, int b1, int zl, bool negp, R cs, R kr, R ki,
+                                          Acc<R>* acc) {
     using A = amp_t<R>;
     constexpr int Dk = 1 << K;
     const int lo = K == 1 ? b0 : min(b0, b1), hi = K == 1 ? 0 : max(b0, b1);
@@ -80,8 +81,8 @@ __device__ __noinline__ void win_rot_loop(amp_t<R>* __restrict__ p, amp_t<R>* __
     }
     Acc<R> loc;
     const int H = D >> K;
-#pragma unroll 2
-    for (int h = 0; h < H; ++h) {
+#pragma unroll UNR
+    for (int h = h0; h < H; h += hs) {
         const int base = (K == 1 ? ins0(h, lo) : ins0(ins0(h, lo), hi)) * T;
         A v[Dk], w[Dk];
 #pragma unroll
@@ -126,7 +127,7 @@ __device__ __noinline__ void win_rot_loop(amp_t<R>* __restrict__ p, amp_t<R>* __
             if (REV) l[base + ro[c]] = w[c];
         }
     }
-    if (REV) {
+    if (REV && acc) {
         const double v = loc.value();
         acc->add(R(negp ? -v : v));
     }
@@ -134,9 +135,9 @@ __device__ __noinline__ void win_rot_loop(amp_t<R>* __restrict__ p, amp_t<R>* __
 
 // One fixed gate (its matrix, or M^dag in the reverse sweep, staged in op)
 // over every subspace of the window; REV also updates l.
-template <typename R, int K, bool REV>
+template <typename R, int K, bool REV, int UNR>
 __device__ __noinline__ void win_fixed_loop(const WinOp<R>& op, amp_t<R>* __restrict__ p, amp_t<R>* __restrict__ l,
-                                            int D, int T) {
+                                            int D, int T, int h0, int hs) {
     using A = amp_t<R>;
     constexpr int Dk = 1 << K;
     const int b0 = op.b0, b1 = op.b1;
@@ -154,8 +155,8 @@ __device__ __noinline__ void win_fixed_loop(const WinOp<R>& op, amp_t<R>* __rest
         ty[e] = op.ty[e];
     }
     const int H = D >> K;
-#pragma unroll 2
-    for (int h = 0; h < H; ++h) {
+#pragma unroll UNR
+    for (int h = h0; h < H; h += hs) {
         const int base = (K == 1 ? ins0(h, lo) : ins0(ins0(h, lo), hi)) * T;
 #pragma unroll
         for (int pass = 0; pass < (REV ? 2 : 1); ++pass) {
@@ -179,14 +180,14 @@ __device__ __noinline__ void win_fixed_loop(const WinOp<R>& op, amp_t<R>* __rest
     }
 }
 
-template <typename R, int K, bool REV>
+template <typename R, int K, bool REV, int UNR>
 __device__ __forceinline__ void win_rot_dispatch(const WinOp<R>& op, amp_t<R>* p, amp_t<R>* l, int D, int T,
-                                                 Acc<R>* acc) {
+                                                 int h0, int hs, Acc<R>* acc) {
     const int nyp = op.ny & 1;
     const bool negp = (op.ny & 2) != 0;
     const R cs = op.cs, kr = op.kr, ki = op.ki;
     const int b0 = op.b0, b1 = op.b1, zl = op.zl;
-#define DIAQ_WROT(XL, NYP) win_rot_loop<R, K, XL, NYP, REV>(p, l, D, T, b0, b1, zl, negp, cs, kr, ki, acc)
+#define DIAQ_WROT(XL, NYP) win_rot_loop<R, K, XL, NYP, REV, UNR>(p, l, D, T, h0, hs, b0, b1, zl, negp, cs, kr, ki, acc)
     if (K == 1) {
         if (op.xl == 0) {
             if (nyp) DIAQ_WROT(0, 1); else DIAQ_WROT(0, 0);
@@ -204,26 +205,29 @@ __device__ __forceinline__ void win_rot_dispatch(const WinOp<R>& op, amp_t<R>* p
 #undef DIAQ_WROT
 }
 
-// One gate of a block on the staged columns p (and, in the reverse sweep,
-// l); a rotation in the reverse sweep also adds its partial into acc. The
-// gate's kind is resolved here, once, ahead of the loop over subspaces.
-template <typename R>
+// One gate of a block on the staged amplitudes p (and, in the reverse
+// sweep, l): window row r of the group is p[r * T]; this thread takes the
+// gate's subspaces h0, h0 + hs, ... (a group may be shared by hs threads),
+// UNR of them per loop trip. A rotation in the reverse sweep also adds its
+// partial into acc (if acc is not NULL). The gate's kind is resolved here,
+// once, ahead of the loop.
+template <typename R, int UNR = 2>
 __device__ __forceinline__ void win_apply(const WinOp<R>& op, amp_t<R>* p, amp_t<R>* l, int D, int T,
-                                          Acc<R>* acc) {
+                                          Acc<R>* acc, int h0 = 0, int hs = 1) {
     if (op.j >= 0) {
         if (l) {
-            if (op.k == 1) win_rot_dispatch<R, 1, true>(op, p, l, D, T, acc);
-            else win_rot_dispatch<R, 2, true>(op, p, l, D, T, acc);
+            if (op.k == 1) win_rot_dispatch<R, 1, true, UNR>(op, p, l, D, T, h0, hs, acc);
+            else win_rot_dispatch<R, 2, true, UNR>(op, p, l, D, T, h0, hs, acc);
         } else {
-            if (op.k == 1) win_rot_dispatch<R, 1, false>(op, p, l, D, T, acc);
-            else win_rot_dispatch<R, 2, false>(op, p, l, D, T, acc);
+            if (op.k == 1) win_rot_dispatch<R, 1, false, UNR>(op, p, l, D, T, h0, hs, acc);
+            else win_rot_dispatch<R, 2, false, UNR>(op, p, l, D, T, h0, hs, acc);
         }
     } else if (l) {
-        if (op.k == 1) win_fixed_loop<R, 1, true>(op, p, l, D, T);
-        else win_fixed_loop<R, 2, true>(op, p, l, D, T);
+        if (op.k == 1) win_fixed_loop<R, 1, true, UNR>(op, p, l, D, T, h0, hs);
+        else win_fixed_loop<R, 2, true, UNR>(op, p, l, D, T, h0, hs);
     } else {
-        if (op.k == 1) win_fixed_loop<R, 1, false>(op, p, l, D, T);
-        else win_fixed_loop<R, 2, false>(op, p, l, D, T);
+        if (op.k == 1) win_fixed_loop<R, 1, false, UNR>(op, p, l, D, T, h0, hs);
+        else win_fixed_loop<R, 2, false, UNR>(op, p, l, D, T, h0, hs);
     }
 }
 

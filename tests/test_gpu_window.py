@@ -75,14 +75,15 @@ def test_window_fused_plan_matches_oracle(api, dtype, case):
     plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
     e0, g0 = plan.run(circ.theta)
     for w in (2, 3, 4, 5):
-        plan.set_window(w)
-        win, launches = plan.window()
-        assert win == w and 0 < launches <= len(circ.gates)
-        e, g = plan.run(circ.theta)
-        assert abs(e - e_ref) <= tol_e, (name, w)
-        assert np.max(np.abs(g - g_ref)) <= tol_g, (name, w)
-        if dtype == torch.complex128:
-            assert abs(e - e0) <= 1e-12 and np.max(np.abs(g - g0)) <= 1e-12
+        for lanes in (1, 4):
+            plan.set_sweep(w, lanes)
+            win, ln, launches = plan.sweep()
+            assert win == w and ln == lanes and 0 < launches <= len(circ.gates)
+            e, g = plan.run(circ.theta)
+            assert abs(e - e_ref) <= tol_e, (name, w, lanes)
+            assert np.max(np.abs(g - g_ref)) <= tol_g, (name, w, lanes)
+            if dtype == torch.complex128:
+                assert abs(e - e0) <= 1e-12 and np.max(np.abs(g - g0)) <= 1e-12
     # back to one launch per gate
     plan.set_window(0)
     assert plan.window() == (0, len(circ.gates))
@@ -121,9 +122,10 @@ def test_window_plan_full_size_ansatz20(api):
     plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n)
     e0, g0 = plan.run(circ.theta)
     for w in (3, 4, 5):
-        plan.set_window(w)
-        e, g = plan.run(circ.theta)
-        assert abs(e - e0) <= 1e-11 and np.max(np.abs(g - g0)) <= 1e-11, w
+        for lanes in (1, 4):
+            plan.set_sweep(w, lanes)
+            e, g = plan.run(circ.theta)
+            assert abs(e - e0) <= 1e-11 and np.max(np.abs(g - g0)) <= 1e-11, (w, lanes)
     sample = [0, 1, 200, 319]
     g_ps = oracle.param_shift_grad(circ, obs, synth.basis_state(n, 0), params=sample)
     assert np.max(np.abs(g[sample] - g_ps[sample])) <= 1e-10
@@ -135,8 +137,8 @@ def test_plan_autotune_keeps_parity(api, dtype):
     n = circ.n
     plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
     rep = plan.autotune(circ.theta, reps=2)
-    assert {w for w, _ in rep["tried"]} == {0, 3, 4, 5}
-    assert plan.window()[0] == rep["best_window"]
+    assert {(w, ln) for w, ln, _ in rep["tried"]} == {(0, 1), (3, 1), (4, 1), (5, 1), (3, 4), (4, 4), (5, 4)}
+    assert plan.sweep()[:2] == (rep["best_window"], rep["best_lanes"])
     e, g = plan.run(circ.theta)
     psi0 = synth.basis_state(n, 0)
     tol_e, tol_g = _tols(dtype, circ, obs)
@@ -151,6 +153,9 @@ def test_window_argument_errors(api):
     for bad in (1, 6, -1):
         with pytest.raises(Exception):
             plan.set_window(bad)
+    for bad_lanes in (0, 2, 8):
+        with pytest.raises(Exception):
+            plan.set_sweep(4, bad_lanes)
     e, g = plan.run(circ.theta)
     assert abs(e - oracle.energy(circ, obs, synth.basis_state(3, 0))) <= 1e-12
     empty = api.AdjointPlan([], 0, (obs.xmask, obs.zmask, obs.coeff), 3)
