@@ -466,9 +466,9 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
             proxy.close()
         else:
             tune = {"best_cluster": shape[0], "best_threads": shape[1], "best_window": shape[2] if len(shape) > 2 else 0,
-                    "best_ms": None, "tried": []}
+                    "best_lanes": shape[3] if len(shape) > 3 else 1, "best_ms": None, "tried": []}
         b = api.Batch(desc, dtype=dt)
-        b.set_window(tune.get("best_window", 0))
+        b.set_sweep(tune.get("best_window", 0), tune.get("best_lanes", 1))
         b.set_launch(tune["best_cluster"], tune["best_threads"])
         E, G = b.run(theta)
         torch.cuda.synchronize()
@@ -479,7 +479,8 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
         energies[name] = E
         q = b.query()
         out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
-                                  "cluster": q["cluster"], "threads": q["threads"], "window": b.window(),
+                                  "cluster": q["cluster"], "threads": q["threads"], "window": b.sweep()[0],
+                                  "lanes": b.sweep()[1],
                                   "teams": q["teams"],
                                   "arena_bytes": q["arena_bytes"], "launches_per_batch": 2,
                                   "tuning": {"proxy_best_ms": tune["best_ms"], "shapes_tried": len(tune["tried"])}}
@@ -712,6 +713,7 @@ def main():
     ap.add_argument("--batch-threads", type=int, default=256)
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--batch-window", type=int, default=0)
+    ap.add_argument("--batch-lanes", type=int, default=1)
     ap.add_argument("--random", action="store_true", help="also run the random layered circuit (slow in c128)")
     ap.add_argument("--random-qubits", type=int, default=30)
     args = ap.parse_args()
@@ -731,7 +733,8 @@ def main():
         B.build()
         from paper_2405_01250_gb300 import api
         print(json.dumps(bench_batch(api, count=args.batch_count, reps=1, plain=False,
-                                     shape=(args.batch_cluster, args.batch_threads, args.batch_window),
+                                     shape=(args.batch_cluster, args.batch_threads, args.batch_window,
+                                            args.batch_lanes),
                                      dtypes=(args.batch_dtype,))), flush=True)
         return
     rank, world = _dist()

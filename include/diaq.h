@@ -452,10 +452,12 @@ typedef struct {
     int32_t cluster[DIAQ_BATCH_TUNE_MAX];
     int32_t threads[DIAQ_BATCH_TUNE_MAX];
     int32_t window[DIAQ_BATCH_TUNE_MAX];
+    int32_t lanes[DIAQ_BATCH_TUNE_MAX];
     float ms[DIAQ_BATCH_TUNE_MAX];
     int32_t best_cluster;
     int32_t best_threads;
     int32_t best_window;
+    int32_t best_lanes;
     float best_ms;
 } diaq_batch_tuning;
 
@@ -499,10 +501,17 @@ diaq_status diaq_batch_set_window(diaq_batch_t b, int32_t window);
 
 diaq_status diaq_batch_get_window(diaq_batch_t b, int32_t* window);
 
+/* As diaq_batch_set_window, choosing also how many threads share a group of
+ * the window: 1, or 4 (four threads of a warp split each gate's subspaces).
+ * lanes is ignored for window 0. */
+diaq_status diaq_batch_set_sweep(diaq_batch_t b, int32_t window, int32_t lanes);
+
+diaq_status diaq_batch_get_sweep(diaq_batch_t b, int32_t* window, int32_t* lanes);
+
 /* Time every team shape that fits - window 0 with cluster in {1,2,4,8} x
- * threads in {64,128,256}, and windows 3, 4, 5 with cluster in {1,2,4,8}
- * x 128 threads - `reps` graph replays each with theta, keep the fastest.
- * report may be NULL. */
+ * threads in {64,128,256}, and windows 3, 4, 5 at 1 and 4 lanes with
+ * cluster in {2,8} x 128 threads - `reps` graph replays each with theta,
+ * keep the fastest. report may be NULL. */
 diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t reps, diaq_batch_tuning* report,
                                 diaq_stream_t stream);
 

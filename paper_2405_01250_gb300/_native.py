@@ -101,10 +101,12 @@ class diaq_batch_tuning(ctypes.Structure):
         ("cluster", ctypes.c_int32 * 24),
         ("threads", ctypes.c_int32 * 24),
         ("window", ctypes.c_int32 * 24),
+        ("lanes", ctypes.c_int32 * 24),
         ("ms", ctypes.c_float * 24),
         ("best_cluster", ctypes.c_int32),
         ("best_threads", ctypes.c_int32),
         ("best_window", ctypes.c_int32),
+        ("best_lanes", ctypes.c_int32),
         ("best_ms", ctypes.c_float),
     ]
 
@@ -163,6 +165,8 @@ SIGNATURES.update({
     "diaq_adjoint_plan_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.POINTER(diaq_plan_tuning)]),
     "diaq_batch_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_batch_get_window": (ctypes.c_int, [_vp, _i32p]),
+    "diaq_batch_set_sweep": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "diaq_batch_get_sweep": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_adjoint_plan_get_window": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _gp, _i32p, _i32p, _u64p, _u64p, _dp,
                                          ctypes.c_int, ctypes.POINTER(_vp)]),

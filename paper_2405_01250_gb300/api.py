@@ -568,9 +568,19 @@ class Batch:
         rep = N.diaq_batch_tuning()
         check(lib().diaq_batch_autotune(self.handle, _dptr(th) if len(th) else None, int(reps), ctypes.byref(rep),
                                         _stream(stream)))
-        return {"tried": [(rep.cluster[i], rep.threads[i], rep.window[i], rep.ms[i]) for i in range(rep.n_tried)],
+        return {"tried": [(rep.cluster[i], rep.threads[i], rep.window[i], rep.lanes[i], rep.ms[i])
+                          for i in range(rep.n_tried)],
                 "best_cluster": rep.best_cluster, "best_threads": rep.best_threads, "best_window": rep.best_window,
-                "best_ms": rep.best_ms}
+                "best_lanes": rep.best_lanes, "best_ms": rep.best_ms}
+
+    def set_sweep(self, window: int, lanes: int):
+        """window 0 or 2..5, with 1 or 4 threads per group (diaq_batch_set_sweep)."""
+        check(lib().diaq_batch_set_sweep(self.handle, int(window), int(lanes)))
+
+    def sweep(self) -> tuple:
+        w, ln = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_batch_get_sweep(self.handle, ctypes.byref(w), ctypes.byref(ln)))
+        return w.value, ln.value
 
     def set_window(self, window: int):
         """0: one pass per gate; 2..5: window-fused blocks (diaq_batch_set_window)."""

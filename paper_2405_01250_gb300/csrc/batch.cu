@@ -518,6 +518,117 @@ static size_t batch_win_smem(diaq_dtype dt, int w) {
            size_t(WIN_MAXG) * WIN_THREADS * sizeof(double);
 }
 
+// Four-lane form of k_batch_win: WIN_LANES threads of a warp share each
+// group (subspaces split gate by gate, __syncwarp between gates), groups
+// stored contiguously with one padding amplitude. Every thread of a block
+// makes the same number of trips over the groups, so every lane reaches
+// each __syncwarp.
+template <typename R>
+__global__ void __launch_bounds__(WIN_THREADS, 4) k_batch_win_l(const BatchArgs a, const WinBlock* __restrict__ blocks,
+                                                                const WinGate* __restrict__ wg, int window) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double warps[32];
+    __shared__ __align__(16) WinBlock w;
+    constexpr int L = WIN_LANES;
+    const int T = WIN_THREADS, t = threadIdx.x;
+    const int GPC = T / L, gs = t / L, li = t % L;
+    const int C = a.C;
+    const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
+    const int team = blockIdx.x / C;
+    const int64_t tid = int64_t(rank) * T + t;
+    const int64_t nthreads = int64_t(C) * T;
+    const int SDmax = (1 << window) + 1;
+    WinOp<R>* ops = reinterpret_cast<WinOp<R>*>(sm);
+    A* sp = reinterpret_cast<A*>(sm + ((sizeof(WinOp<R>) * WIN_MAXG + 15) / 16) * 16);
+    A* sl = sp + GPC * SDmax;
+    Acc<R>* sa = reinterpret_cast<Acc<R>*>(sl + GPC * SDmax);
+    A* arena = reinterpret_cast<A*>(a.arena);
+    for (int s = a.team_first[team]; s < a.team_first[team + 1]; ++s) {
+        const BInst I = a.inst[a.sched[s]];
+        A* psi = arena + I.psi_off;
+        A* lam = arena + I.lam_off;
+        const int64_t N = int64_t(1) << I.n;
+        const double* th = a.theta + I.param_begin;
+        double* part = a.partials + I.part_off;
+        for (int64_t i = tid; i < N; i += nthreads) {
+            A v;
+            v.x = R(i == 0 ? 1 : 0);
+            v.y = R(0);
+            psi[i] = v;
+        }
+        team_sync(C);
+        for (int dir = 0; dir < 2; ++dir) {
+            const bool rev = dir == 1;
+            if (rev) {
+                // lambda = H psi and the energy Re <psi|lambda>
+                Acc<R> e;
+                for (int64_t i = tid; i < N; i += nthreads) {
+                    const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
+                    lam[i] = o;
+                    const A pi = psi[i];
+                    e.add_dot(pi.x, o.x, pi.y, o.y);
+                }
+                const double es = block_sum(e.value(), warps);
+                if (t == 0) part[0 * C + rank] = es;
+                team_sync(C);
+            }
+            const int nb = I.block_end - I.block_begin;
+            for (int bi = 0; bi < nb; ++bi) {
+                const int b = rev ? I.block_end - 1 - bi : I.block_begin + bi;
+                batch_stage<R>(blocks, b, &w, wg, a.gates, th, rev, ops, sa);
+                const int D = 1 << w.nq, SD = D + 1;
+                const int64_t G = int64_t(1) << (I.n - w.nq);
+                A* gp = sp + gs * SD;
+                A* gl = sl + gs * SD;
+                for (int64_t g0 = int64_t(rank) * GPC; g0 < G; g0 += int64_t(C) * GPC) {
+                    const int64_t g = g0 + gs;
+                    const bool valid = g < G;
+                    const int64_t base = valid ? insert_zeros_rt(g, w.q, w.nq) : 0;
+                    if (valid) {
+                        for (int e2 = li; e2 < D; e2 += L) gp[e2] = psi[base + w.off[e2]];
+                        if (rev)
+                            for (int e2 = li; e2 < D; e2 += L) gl[e2] = lam[base + w.off[e2]];
+                    }
+                    __syncwarp();
+                    if (!rev) {
+                        for (int i = 0; i < w.count; ++i) {
+                            win_apply<R, 1>(ops[i], gp, nullptr, D, 1, nullptr, li, L);
+                            __syncwarp();
+                        }
+                    } else {
+                        for (int i = w.count - 1; i >= 0; --i) {
+                            const WinOp<R>& o = ops[i];
+                            win_apply<R, 1>(o, gp, gl, D, 1, (valid && o.j >= 0) ? sa + o.j * T + t : nullptr, li, L);
+                            __syncwarp();
+                        }
+                    }
+                    if (valid) {
+                        for (int e2 = li; e2 < D; e2 += L) psi[base + w.off[e2]] = gp[e2];
+                        if (rev)
+                            for (int e2 = li; e2 < D; e2 += L) lam[base + w.off[e2]] = gl[e2];
+                    }
+                    __syncwarp();
+                }
+                if (rev) {
+                    for (int j = 0; j < w.np; ++j) {
+                        const double v = block_sum(sa[j * T + t].value(), warps);
+                        if (t == 0) part[int64_t(w.slot[j]) * C + rank] = v;
+                    }
+                }
+                team_sync(C);
+            }
+        }
+    }
+}
+
+static size_t batch_win_smem_lanes(diaq_dtype dt, int w) {
+    const size_t opb = dt == DIAQ_C128 ? sizeof(WinOp<double>) : sizeof(WinOp<float>);
+    const size_t gpc = WIN_THREADS / WIN_LANES;
+    return ((opb * WIN_MAXG + 15) / 16) * 16 + 2 * gpc * ((size_t(1) << w) + 1) * amp_bytes(dt) +
+           size_t(WIN_MAXG) * WIN_THREADS * sizeof(double);
+}
+
 // Per instance: energy and gradient from the partial rows, fixed order.
 __global__ void k_batch_finish(const BInst* inst, const BGate* gates, const double* partials, int C, int n_inst,
                                double* energy, double* grad) {
@@ -576,6 +687,7 @@ struct diaq_batch_s {
     cudaStream_t graph_stream = nullptr;
     // window-fused kernel (window > 0): blocks of every instance
     int window = 0;
+    int lanes = 1;  // threads per group of the window-fused kernel (1 or WIN_LANES)
     WinBlock* d_blocks = nullptr;
     WinGate* d_wg = nullptr;
 };
@@ -694,16 +806,17 @@ static const void* batch_kernel() {
 }
 
 template <typename R>
-static const void* batch_win_kernel() {
-    return reinterpret_cast<const void*>(&k_batch_win<R>);
+static const void* batch_win_kernel(int lanes) {
+    return lanes > 1 ? reinterpret_cast<const void*>(&k_batch_win_l<R>) : reinterpret_cast<const void*>(&k_batch_win<R>);
 }
 
 // Teams that fit on the GPU at once for cluster size C and block size T.
 static diaq_status resident_teams(diaq_batch_s* b, int C, int T, int* teams) {
     const bool win = b->window > 0;
-    const void* fn = win ? (b->dtype == DIAQ_C128 ? batch_win_kernel<double>() : batch_win_kernel<float>())
+    const void* fn = win ? (b->dtype == DIAQ_C128 ? batch_win_kernel<double>(b->lanes) : batch_win_kernel<float>(b->lanes))
                          : (b->dtype == DIAQ_C128 ? batch_kernel<double>() : batch_kernel<float>());
-    const size_t smem = win ? batch_win_smem(b->dtype, b->window) : 0;
+    const size_t smem = !win ? 0 : (b->lanes > 1 ? batch_win_smem_lanes(b->dtype, b->window)
+                                                 : batch_win_smem(b->dtype, b->window));
     if (win) DIAQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     if (C == 1) {
         int per_sm = 0, sms = 0;
@@ -775,7 +888,15 @@ static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = b->C > 1 ? 1 : 0;
-    if (b->window > 0) {
+    if (b->window > 0 && b->lanes > 1) {
+        cfg.dynamicSmemBytes = batch_win_smem_lanes(b->dtype, b->window);
+        const WinBlock* blk = b->d_blocks;
+        const WinGate* wg = b->d_wg;
+        if (b->dtype == DIAQ_C128)
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win_l<double>, a, blk, wg, b->window));
+        else
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win_l<float>, a, blk, wg, b->window));
+    } else if (b->window > 0) {
         cfg.dynamicSmemBytes = batch_win_smem(b->dtype, b->window);
         const WinBlock* blk = b->d_blocks;
         const WinGate* wg = b->d_wg;
@@ -1058,17 +1179,25 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
 }
 
 diaq_status diaq_batch_set_window(diaq_batch_t b, int32_t window) {
+    return diaq_batch_set_sweep(b, window, 1);
+}
+
+diaq_status diaq_batch_set_sweep(diaq_batch_t b, int32_t window, int32_t lanes) {
     clear_error();
     cudaGetLastError();
     if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
     if (window != 0 && (window < 2 || window > WIN_MAX))
         return fail(DIAQ_ERR_ARG, "window = %d: use 0 (one pass per gate) or 2..%d qubits", window, WIN_MAX);
+    if (lanes != 1 && lanes != WIN_LANES)
+        return fail(DIAQ_ERR_ARG, "lanes = %d: use 1 or %d threads per group", lanes, WIN_LANES);
     const int C = b->C;
     const int T = window > 0 ? WIN_THREADS : (b->window > 0 ? 256 : b->threads);
+    b->lanes = window > 0 ? lanes : 1;
     diaq_status st = batch_windows(b, window);
     if (st == DIAQ_OK) st = configure(b, C, T, nullptr);
     if (st != DIAQ_OK) {
         const diaq_status first = st;
+        b->lanes = 1;
         batch_windows(b, 0);
         configure(b, 1, 256, nullptr);
         return first;
@@ -1080,6 +1209,14 @@ diaq_status diaq_batch_get_window(diaq_batch_t b, int32_t* window) {
     clear_error();
     if (!b || !window) return fail(DIAQ_ERR_ARG, "NULL argument");
     *window = b->window;
+    return DIAQ_OK;
+}
+
+diaq_status diaq_batch_get_sweep(diaq_batch_t b, int32_t* window, int32_t* lanes) {
+    clear_error();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (window) *window = b->window;
+    if (lanes) *lanes = b->lanes;
     return DIAQ_OK;
 }
 
@@ -1108,14 +1245,18 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int cls[] = {1, 2, 4, 8};
     const int ths[] = {64, 128, 256};  // k_batch is built for at most 256
-    const int wins[] = {0, 3, 4, 5};   // 0: one pass per gate; else the window-fused kernel
+    // window 0: one pass per gate; else the window-fused kernel, 1 or 4 lanes
+    const int wins[] = {0, 3, 4, 5, 3, 4, 5};
+    const int lns[] = {1, 1, 1, 1, WIN_LANES, WIN_LANES, WIN_LANES};
     float best = 1e30f;
-    int bc = 1, bt = 256, bw = 0, tried = 0;
+    int bc = 1, bt = 256, bw = 0, bl = 1, tried = 0;
     cudaEvent_t e0, e1;
     DIAQ_CUDA(cudaEventCreate(&e0));
     DIAQ_CUDA(cudaEventCreate(&e1));
     if (b->n_params_total > 0) std::memcpy(b->h_theta, theta, sizeof(double) * size_t(b->n_params_total));
-    for (int W : wins) {
+    for (int wi = 0; wi < 7; ++wi) {
+      const int W = wins[wi], Ln = lns[wi];
+      b->lanes = Ln;
       if (batch_windows(b, W) != DIAQ_OK) {
           clear_error();
           cudaGetLastError();
@@ -1123,7 +1264,7 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
       }
       for (int C : cls)
         for (int T : ths) {
-            if (W > 0 && T != WIN_THREADS) continue;
+            if (W > 0 && (T != WIN_THREADS || C == 1 || C == 4)) continue;  // fused shapes: clusters of 2 and 8
             if (configure(b, C, T, s) != DIAQ_OK) {
                 clear_error();
                 cudaGetLastError();
@@ -1141,6 +1282,7 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
                 report->cluster[tried] = C;
                 report->threads[tried] = T;
                 report->window[tried] = W;
+                report->lanes[tried] = Ln;
                 report->ms[tried] = ms;
             }
             ++tried;
@@ -1149,12 +1291,14 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
                 bc = C;
                 bt = T;
                 bw = W;
+                bl = Ln;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no launch shape fits");
+    b->lanes = bl;
     DIAQ_TRY(batch_windows(b, bw));
     DIAQ_TRY(configure(b, bc, bt, s));
     if (report) {
@@ -1162,6 +1306,7 @@ diaq_status diaq_batch_autotune(diaq_batch_t b, const double* theta, int32_t rep
         report->best_cluster = bc;
         report->best_threads = bt;
         report->best_window = bw;
+        report->best_lanes = bl;
         report->best_ms = best;
     }
     return DIAQ_OK;
@@ -1346,12 +1491,6 @@ __device__ __forceinline__ void plan_stage(const BGate* __restrict__ gates, cons
     __syncthreads();
 }
 
-// Lanes per group of the window-fused plan kernel: a group's 2^w amplitudes
-// are shared by WIN_LANES threads of one warp, which split its subspaces
-// gate by gate (a __syncwarp between gates), so a block of 128 threads
-// works on 32 groups at once and a thread's chain of dependent steps per
-// gate is WIN_LANES times shorter.
-constexpr int WIN_LANES = 4;
 
 static size_t win_smem_lanes(diaq_dtype dt, int nq, int count, int np) {
     const size_t opb = dt == DIAQ_C128 ? sizeof(WinOp<double>) : sizeof(WinOp<float>);

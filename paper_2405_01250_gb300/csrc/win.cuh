@@ -18,6 +18,12 @@ namespace diaq {
 constexpr int WIN_MAX = 5;     // window qubits
 constexpr int WIN_MAXG = 32;   // gates per block
 constexpr int WIN_THREADS = 128;
+// Lanes per group of the four-lane kernels: a group's 2^w amplitudes are
+// shared by WIN_LANES threads of one warp, which split its subspaces gate by
+// gate (a __syncwarp between gates), so a block of 128 threads works on 32
+// groups at once and a thread's chain of dependent steps per gate is
+// WIN_LANES times shorter.
+constexpr int WIN_LANES = 4;
 
 struct WinBlock {
     int nq;                     // window qubits

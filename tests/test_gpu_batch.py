@@ -77,19 +77,19 @@ def test_batch_window_fused_matches_oracle(api, dtype):
     theta = np.concatenate([c.theta for c, _ in inst])
     b = _batch(api, inst, dtype)
     E0, G0 = b.run(theta)
-    for w in (2, 3, 4, 5):
-        b.set_window(w)
-        assert b.window() == w
+    for w, lanes in ((2, 1), (3, 1), (4, 1), (5, 1), (3, 4), (4, 4), (5, 4)):
+        b.set_sweep(w, lanes)
+        assert b.window() == w and b.sweep() == (w, lanes)
         for cluster in (1, 2, 8):
             b.set_launch(cluster, 128)
             E, G = b.run(theta)
             for (c, o), e, er, g, gr, e0, g0 in zip(inst, E, E_ref, G, G_ref, E0, G0):
                 if dtype == torch.complex128:
-                    assert abs(e - er) <= 1e-12 and np.max(np.abs(g - gr)) <= 1e-10, (w, cluster)
-                    assert abs(e - e0) <= 1e-12 and np.max(np.abs(g - g0)) <= 1e-12, (w, cluster)
+                    assert abs(e - er) <= 1e-12 and np.max(np.abs(g - gr)) <= 1e-10, (w, lanes, cluster)
+                    assert abs(e - e0) <= 1e-12 and np.max(np.abs(g - g0)) <= 1e-12, (w, lanes, cluster)
                 else:
                     bound = len(c.gates) * 2.0 ** -24 * float(np.sum(np.abs(o.coeff))) * 8
-                    assert abs(e - er) <= bound and np.max(np.abs(g - gr)) <= bound, (w, cluster)
+                    assert abs(e - er) <= bound and np.max(np.abs(g - gr)) <= bound, (w, lanes, cluster)
     with pytest.raises(Exception):
         b.set_launch(2, 256)  # the window-fused kernel runs 128 threads per block
     b.set_window(0)
@@ -98,6 +98,8 @@ def test_batch_window_fused_matches_oracle(api, dtype):
     assert np.array_equal(E, E0)
     with pytest.raises(Exception):
         b.set_window(6)
+    with pytest.raises(Exception):
+        b.set_sweep(4, 3)
 
 
 def test_batch_c64(api):
@@ -120,10 +122,10 @@ def test_batch_deterministic_and_autotune(api):
     b = _batch(api, inst, torch.complex128)
     rep = b.autotune(theta, reps=1)
     assert rep["tried"] and rep["best_cluster"] in (1, 2, 4, 8)
-    assert {w for _, _, w, _ in rep["tried"]} >= {0, 3, 4}
+    assert {(w, ln) for _, _, w, ln, _ in rep["tried"]} >= {(0, 1), (3, 1), (4, 1), (3, 4), (4, 4)}
     q = b.query()
     assert q["cluster"] == rep["best_cluster"] and q["threads"] == rep["best_threads"]
-    assert b.window() == rep["best_window"]
+    assert b.sweep() == (rep["best_window"], rep["best_lanes"])
     E1, G1 = b.run(theta)
     E2, G2 = b.run(theta)
     assert np.array_equal(E1, E2) and all(np.array_equal(a, c) for a, c in zip(G1, G2))
