@@ -583,6 +583,8 @@ def bench_random(api, n=30, depth=40):
     res = {}
     for name, dt, s in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
         ops = [api.build(g, n, dtype=dt) for g in circ.gates]
+        # in place: CZ gates take the identity-row skip, so count the bytes moved
+        moved = sum(op.apply_bytes(in_place=True) for op in ops)
         x = torch.zeros(N, dtype=dt, device="cuda")
         x[0] = 1
         torch.cuda.synchronize()
@@ -592,8 +594,8 @@ def bench_random(api, n=30, depth=40):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         res[name] = x
-        out[name] = {"s_per_circuit": el, "gates_per_s": len(ops) / el, "gbs": len(ops) * 2 * N * s / el / 1e9,
-                     "norm": api.norm(x)}
+        out[name] = {"s_per_circuit": el, "gates_per_s": len(ops) / el, "gbs": moved / el / 1e9,
+                     "bytes_moved": moved, "norm": api.norm(x)}
         del ops
     a = res["c128"]
     b = res["c64"].to(torch.complex128)

@@ -520,6 +520,18 @@ diaq_status diaq_batch_query(diaq_batch_t b, int32_t* cluster, int32_t* threads,
                              int64_t* arena_bytes);
 
 /* ------------------------------------------------------------------------
+ * Testing hook (not in the paper)
+ * ------------------------------------------------------------------------ */
+
+/* Make the library's after-th next device or pinned-host allocation (0: the
+ * next one) fail as if memory were exhausted, once; -1 turns it off. The
+ * failing call returns DIAQ_ERR_ALLOC (or the status of the step that
+ * needed the memory) after releasing what it had allocated, and the library
+ * stays usable. It happens on the host: no GPU work is affected.
+ * Process-wide. */
+diaq_status diaq_debug_inject_alloc_failure(int32_t after);
+
+/* ------------------------------------------------------------------------
  * Allocation-free norm (the paper has no counterpart: this is a deployment
  * variant of diaq_norm).
  * ------------------------------------------------------------------------ */

@@ -219,6 +219,11 @@ def _ptr(t) -> ctypes.c_void_p:
     raise TypeError(type(t))
 
 
+def inject_alloc_failure(after: int) -> None:
+    """Testing hook: the after-th next library allocation fails (-1: off)."""
+    check(lib().diaq_debug_inject_alloc_failure(int(after)))
+
+
 def unitary_chain(gates, n_qubits: int, dtype=torch.complex128, theta=None, prune: bool = True, stream=None):
     """Unitary of a circuit by chained device DiaQ products (diaq_unitary_chain).
     Returns (op, diagonals per time step, non-zeros per time step)."""

@@ -924,6 +924,13 @@ static diaq_status configure(diaq_batch_s* b, int C, int T, cudaStream_t s) {
     teams = std::min(teams, b->n_inst);
     std::vector<int32_t> sched, first;
     make_schedule(b, teams, &sched, &first);
+    // the old graph uses the buffers replaced below: drop it first, so a
+    // failure from here on leaves no graph (diaq_batch_run then refuses)
+    // rather than one that points at freed memory
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
     if (b->d_sched) cudaFree(b->d_sched);
     if (b->d_team_first) cudaFree(b->d_team_first);
     b->d_sched = nullptr;
@@ -978,6 +985,10 @@ static diaq_status configure(diaq_batch_s* b, int C, int T, cudaStream_t s) {
 // Window tables for every instance (window 0 clears them); the caller
 // reconfigures, which uploads the instances' block ranges.
 static diaq_status batch_windows(diaq_batch_s* b, int window) {
+    if (b->exec) {  // it may use the tables freed below
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
     if (b->d_blocks) cudaFree(b->d_blocks);
     if (b->d_wg) cudaFree(b->d_wg);
     b->d_blocks = nullptr;
@@ -1000,6 +1011,9 @@ static diaq_status batch_windows(diaq_batch_s* b, int window) {
 }
 
 static diaq_status run_graph(diaq_batch_s* b, cudaStream_t s) {
+    if (!b->exec)
+        return fail(DIAQ_ERR_ARG, "the batch has no launch configuration (an earlier reconfiguration failed): "
+                                  "call diaq_batch_set_launch again");
     // order the replay after the caller's stream and the caller's stream after it
     cudaEvent_t ev;
     DIAQ_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1936,7 +1950,7 @@ diaq_status diaq_adjoint_plan_run(diaq_adjoint_plan_t p, const double* theta, co
     for (int i = 0; i < p->n_params; ++i)
         if (!std::isfinite(theta[i])) return fail(DIAQ_ERR_ARG, "theta[%d] is not finite", i);
     if (psi0 && (reinterpret_cast<uintptr_t>(psi0) & 15)) return fail(DIAQ_ERR_ARG, "psi0 must be 16-byte aligned");
-    if (psi0 != p->psi0) {  // the initial-state pointer is part of the graph
+    if (psi0 != p->psi0 || !p->exec) {  // the initial-state pointer is part of the graph
         p->psi0 = psi0;
         DIAQ_TRY(plan_capture(p));
     }
@@ -1973,6 +1987,10 @@ diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, i
     DIAQ_CUDA(cudaGetDevice(&dev));
     if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
     DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->exec) {  // it uses the tables and partials replaced below
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
     diaq_status st = plan_windows(p, window, lanes);
     if (st != DIAQ_OK) {
         plan_windows(p, 0, 1);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -294,6 +295,42 @@ static diaq_status fuse_descs(const std::vector<GateDesc>& gs, GateDesc* out) {
 }  // namespace diaq
 
 using namespace diaq;
+
+// ---------------------------------------------------------------------------
+// Allocation-failure injection (testing hook)
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_fail_in{-1};
+
+// true if this allocation is the one chosen to fail
+static bool inject_now() {
+    int v = g_fail_in.load();
+    while (v >= 0) {
+        if (g_fail_in.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+namespace diaq {
+cudaError_t inj_malloc(void** p, size_t n) {
+    if (inject_now()) return cudaErrorMemoryAllocation;
+    return (cudaMalloc)(p, n);
+}
+cudaError_t inj_malloc_async(void** p, size_t n, cudaStream_t s) {
+    if (inject_now()) return cudaErrorMemoryAllocation;
+    return (cudaMallocAsync)(p, n, s);
+}
+cudaError_t inj_malloc_host(void** p, size_t n) {
+    if (inject_now()) return cudaErrorMemoryAllocation;
+    return (cudaMallocHost)(p, n);
+}
+}  // namespace diaq
+
+extern "C" diaq_status diaq_debug_inject_alloc_failure(int32_t after) {
+    clear_error();
+    if (after < -1) return fail(DIAQ_ERR_ARG, "after = %d: use -1 (off) or >= 0", after);
+    g_fail_in.store(after);
+    return DIAQ_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Op helpers
@@ -1004,25 +1041,33 @@ diaq_status diaq_adjoint_grad(const diaq_gate* gates, int32_t n_gates, const dou
     double* d = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (size_t(rows) * P + rows), s);
     if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(adjoint partials): %s", cudaGetErrorString(e));
-    DIAQ_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t(rows) * P + rows), s));
-    DIAQ_CUDA(cudaMemcpyAsync(work_psi, psi0, bytes, cudaMemcpyDeviceToDevice, s));
-    for (int l = 0; l < n_gates; ++l)
-        DIAQ_TRY(launch_gate_local(n_qubits, dtype, fwd[size_t(l)], nullptr, work_psi, work_psi, s));
-    DIAQ_TRY(run_pauli_apply(work_psi, work_lam, n_qubits, dtype, pg, s));
-    const int Pe = inner_partials(n_qubits);
-    DIAQ_TRY(launch_inner_re(work_psi, work_lam, n_qubits, dtype, d, Pe, s));
-    for (int l = n_gates - 1; l >= 0; --l) {
-        const int sl = slot[size_t(l)];
-        const int Pl = adjoint_partials(n_qubits, dtype, fwd[size_t(l)].k);
-        DIAQ_TRY(launch_adjoint_step(n_qubits, dtype, bwd[size_t(l)], sl >= 0 ? &gen[size_t(l)] : nullptr, work_psi,
-                                     work_lam, sl >= 0 ? d + size_t(1 + sl) * P : nullptr, Pl, s));
-    }
-    // row sums (rows have at most P used columns; unused are zero)
-    DIAQ_TRY(launch_sum_rows(d, rows, P, d + size_t(rows) * P, s));
     std::vector<double> res(static_cast<size_t>(rows));
-    DIAQ_CUDA(cudaMemcpyAsync(res.data(), d + size_t(rows) * P, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
-    DIAQ_CUDA(cudaFreeAsync(d, s));
-    DIAQ_CUDA(cudaStreamSynchronize(s));
+    // the sweep; every exit below frees the partials buffer
+    auto sweep = [&]() -> diaq_status {
+        DIAQ_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * (size_t(rows) * P + rows), s));
+        DIAQ_CUDA(cudaMemcpyAsync(work_psi, psi0, bytes, cudaMemcpyDeviceToDevice, s));
+        for (int l = 0; l < n_gates; ++l)
+            DIAQ_TRY(launch_gate_local(n_qubits, dtype, fwd[size_t(l)], nullptr, work_psi, work_psi, s));
+        DIAQ_TRY(run_pauli_apply(work_psi, work_lam, n_qubits, dtype, pg, s));
+        const int Pe = inner_partials(n_qubits);
+        DIAQ_TRY(launch_inner_re(work_psi, work_lam, n_qubits, dtype, d, Pe, s));
+        for (int l = n_gates - 1; l >= 0; --l) {
+            const int sl = slot[size_t(l)];
+            const int Pl = adjoint_partials(n_qubits, dtype, fwd[size_t(l)].k);
+            DIAQ_TRY(launch_adjoint_step(n_qubits, dtype, bwd[size_t(l)], sl >= 0 ? &gen[size_t(l)] : nullptr,
+                                         work_psi, work_lam, sl >= 0 ? d + size_t(1 + sl) * P : nullptr, Pl, s));
+        }
+        // row sums (rows have at most P used columns; unused are zero)
+        DIAQ_TRY(launch_sum_rows(d, rows, P, d + size_t(rows) * P, s));
+        DIAQ_CUDA(cudaMemcpyAsync(res.data(), d + size_t(rows) * P, sizeof(double) * rows, cudaMemcpyDeviceToHost, s));
+        return DIAQ_OK;
+    };
+    const diaq_status st = sweep();
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    const cudaError_t es = cudaStreamSynchronize(s);
+    if (st != DIAQ_OK) return st;
+    DIAQ_CUDA(ef);
+    DIAQ_CUDA(es);
     if (energy) *energy = res[0];
     if (grad) {
         for (int p = 0; p < n_params; ++p) grad[p] = 0.0;

@@ -11,6 +11,19 @@
 
 #include "diaq.h"
 
+// Every device and pinned allocation of the library goes through these, so
+// a test can make the n-th one fail (diaq_debug_inject_alloc_failure) and
+// drive each error path on the host, with no GPU fault. The real runtime
+// functions are called as (cudaMalloc)(...), which the macros do not touch.
+namespace diaq {
+cudaError_t inj_malloc(void** p, size_t n);
+cudaError_t inj_malloc_async(void** p, size_t n, cudaStream_t s);
+cudaError_t inj_malloc_host(void** p, size_t n);
+}  // namespace diaq
+#define cudaMalloc(P, N) ::diaq::inj_malloc(reinterpret_cast<void**>(P), (N))
+#define cudaMallocAsync(P, N, S) ::diaq::inj_malloc_async(reinterpret_cast<void**>(P), (N), (S))
+#define cudaMallocHost(P, N) ::diaq::inj_malloc_host(reinterpret_cast<void**>(P), (N))
+
 namespace diaq {
 
 using cplx = std::complex<double>;

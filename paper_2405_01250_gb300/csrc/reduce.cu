@@ -181,11 +181,17 @@ static diaq_status upload_groups(const PauliGroups& pg, cudaStream_t s, void** m
     cudaError_t e = cudaMallocAsync((void**)&d, bytes, s);
     if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(Pauli terms): %s", cudaGetErrorString(e));
     e = cudaMemcpyAsync(d, buf.data(), bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(Pauli terms)");
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, s);
+        return cuda_fail(e, "cudaMemcpyAsync(Pauli terms)");
+    }
     // pageable source: the copy has completed when cudaMemcpyAsync returns
     // for pageable memory only after staging; synchronise to be safe.
     e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (e != cudaSuccess) {
+        cudaFreeAsync(d, s);
+        return cuda_fail(e, "cudaStreamSynchronize");
+    }
     dg->xmask = reinterpret_cast<const uint64_t*>(d + o_x);
     dg->zmask = reinterpret_cast<const uint64_t*>(d + o_z);
     dg->kappa = reinterpret_cast<const double*>(d + o_k);
@@ -255,7 +261,10 @@ diaq_status run_expect(const void* psi, int n, diaq_dtype dt, const PauliGroups&
     const int P = reduce_blocks(N / 4);
     double* d = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (2 * P + 2), s);
-    if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(expect partials): %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaFreeAsync(gm, s);
+        return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(expect partials): %s", cudaGetErrorString(e));
+    }
     DIAQ_PRELAUNCH("k_expect");
     if (dt == DIAQ_C128)
         k_expect<double><<<P, 256, 0, s>>>(reinterpret_cast<const double2*>(psi), N, G, d);
