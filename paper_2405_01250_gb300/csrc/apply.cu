@@ -47,6 +47,10 @@ struct SmallGateArgs {
     // 1: every entry real and non-zero (the butterfly, written out with no
     // entry-type dispatch); 2: any other such matrix.
     int share_col0;
+    // k = 1 only: every entry general complex (a Haar U(2)): the rows are
+    // written out as fused multiply-adds in the order of the typed path,
+    // with no entry-type dispatch.
+    int dense1;
 };
 
 template <typename R, int K, int G>
@@ -66,6 +70,30 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
 #pragma unroll
             for (int c = 0; c < D; ++c) v[j][c] = ld_stream(x + b[j] + a.off[c]);
         }
+    }
+    if (K == 1 && a.dense1) {
+        // y_r = m_r0 x0 + m_r1 x1, each complex product as in mac_typed:
+        // first term re = mr x.re - mi x.im (a product, then an FMA), then two FMAs per part
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+            const A x0 = v[j][0], x1 = v[j][1];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const R ar = a.re[2 * r], ai = a.im[2 * r], br = a.re[2 * r + 1], bi = a.im[2 * r + 1];
+                A acc;
+                acc.x = ar * x0.x;
+                acc.x = fma(-ai, x0.y, acc.x);
+                acc.y = ar * x0.y;
+                acc.y = fma(ai, x0.x, acc.y);
+                acc.x = fma(br, x1.x, acc.x);
+                acc.x = fma(-bi, x1.y, acc.x);
+                acc.y = fma(br, x1.y, acc.y);
+                acc.y = fma(bi, x1.x, acc.y);
+                st_stream(y + b[j] + a.off[r], acc);
+            }
+        }
+        return;
     }
     if (K == 1 && a.share_col0 == 1) {
         // real butterfly: p = a x0 (two products), y_r = fma(m_r1, x1, p)
@@ -229,6 +257,8 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
         const bool shared = a.type[0] != ET_ZERO && a.type[2] == a.type[0] && a.re[2] == a.re[0] && a.im[2] == a.im[0];
         const bool butterfly = shared && a.type[0] == ET_REAL && a.type[1] == ET_REAL && a.type[3] == ET_REAL;
         a.share_col0 = butterfly ? 1 : (shared ? 2 : 0);
+        a.dense1 = a.type[0] == ET_GENERAL && a.type[1] == ET_GENERAL && a.type[2] == ET_GENERAL &&
+                   a.type[3] == ET_GENERAL;
     }
     const int64_t per_block = int64_t(threads) * G;
     const int64_t blocks = (a.n_groups + per_block - 1) / per_block;
