@@ -51,6 +51,11 @@ struct SmallGateArgs {
     // written out as fused multiply-adds in the order of the typed path,
     // with no entry-type dispatch.
     int dense1;
+    // Other patterns written out the same way (same operations, same order
+    // as the typed path): 1 every entry real and non-zero (RY), 2 real
+    // non-zero diagonal with imaginary non-zero off-diagonal (RX),
+    // 3 diagonal, every diagonal entry general complex (RZ; RZZ for k = 2).
+    int pattern;
 };
 
 template <typename R, int K, int G>
@@ -90,6 +95,67 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
                 acc.x = fma(-bi, x1.y, acc.x);
                 acc.y = fma(br, x1.y, acc.y);
                 acc.y = fma(bi, x1.x, acc.y);
+                st_stream(y + b[j] + a.off[r], acc);
+            }
+        }
+        return;
+    }
+    if (a.pattern == 3) {
+        // diagonal phases: y_r = m_rr x_r, first-general product then FMA
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const R mr = a.re[r * D + r], mi = a.im[r * D + r];
+                const A x = v[j][r];
+                A acc;
+                acc.x = mr * x.x;
+                acc.x = fma(-mi, x.y, acc.x);
+                acc.y = mr * x.y;
+                acc.y = fma(mi, x.x, acc.y);
+                st_stream(y + b[j] + a.off[r], acc);
+            }
+        }
+        return;
+    }
+    if (K == 1 && (a.pattern == 1 || a.pattern == 2)) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+            const A x0 = v[j][0], x1 = v[j][1];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const R d = a.re[3 * r];  // real diagonal entry m_rr
+                const A xd = r == 0 ? x0 : x1, xo = r == 0 ? x1 : x0;
+                A acc;
+                if (r == 0) {  // column 0 first: the diagonal entry opens the sum
+                    acc.x = d * xd.x;
+                    acc.y = d * xd.y;
+                } 
+                if (a.pattern == 1) {  // real off-diagonal m_r,1-r
+                    const R o = a.re[r == 0 ? 1 : 2];
+                    if (r == 0) {
+                        acc.x = fma(o, xo.x, acc.x);
+                        acc.y = fma(o, xo.y, acc.y);
+                    } else {  // row 1: column 0 (off-diagonal) opens the sum
+                        acc.x = o * xo.x;
+                        acc.y = o * xo.y;
+                        acc.x = fma(d, xd.x, acc.x);
+                        acc.y = fma(d, xd.y, acc.y);
+                    }
+                } else {  // imaginary off-diagonal i*o
+                    const R o = a.im[r == 0 ? 1 : 2];
+                    if (r == 0) {
+                        acc.x = fma(-o, xo.y, acc.x);
+                        acc.y = fma(o, xo.x, acc.y);
+                    } else {
+                        acc.x = -o * xo.y;
+                        acc.y = o * xo.x;
+                        acc.x = fma(d, xd.x, acc.x);
+                        acc.y = fma(d, xd.y, acc.y);
+                    }
+                }
                 st_stream(y + b[j] + a.off[r], acc);
             }
         }
@@ -259,6 +325,18 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
         a.share_col0 = butterfly ? 1 : (shared ? 2 : 0);
         a.dense1 = a.type[0] == ET_GENERAL && a.type[1] == ET_GENERAL && a.type[2] == ET_GENERAL &&
                    a.type[3] == ET_GENERAL;
+        if (!a.dense1 && a.share_col0 != 1) {
+            const bool rd = a.type[0] == ET_REAL && a.type[3] == ET_REAL;  // real diagonal, not 0 or 1
+            if (rd && a.type[1] == ET_REAL && a.type[2] == ET_REAL) a.pattern = 1;
+            else if (rd && a.type[1] == ET_IMAG && a.type[2] == ET_IMAG) a.pattern = 2;
+        }
+    }
+    {
+        bool diag = true;
+        for (int r = 0; r < (1 << K); ++r)
+            for (int c = 0; c < (1 << K); ++c)
+                if (r == c ? a.type[r * (1 << K) + c] != ET_GENERAL : a.type[r * (1 << K) + c] != ET_ZERO) diag = false;
+        if (diag) a.pattern = 3;
     }
     const int64_t per_block = int64_t(threads) * G;
     const int64_t blocks = (a.n_groups + per_block - 1) / per_block;

@@ -1361,7 +1361,7 @@ __global__ void k_plan_angles(const BGate* gates, int n_gates, const double* the
     out[g] = A;
 }
 
-template <typename R, int K, int XL>
+template <typename R, int K, int XL, int KT>
 __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, const BGate* gate,
                                                   const RotAngles* ang, int n, double* part) {
     __shared__ double warps[32];
@@ -1369,7 +1369,7 @@ __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, 
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
     const RotAngles a = *ang;
     const bool adj = lam != nullptr;  // the reverse sweep applies U^dag
-    const double v = rot_groups<R, K, XL>(psi, lam, n, gate->rot, R(a.cs), R(adj ? a.kar : a.kfr),
+    const double v = rot_groups<R, K, XL, KT>(psi, lam, n, gate->rot, R(a.cs), R(adj ? a.kar : a.kfr),
                                           R(adj ? a.kai : a.kfi), tid, nth);
     if (part) {
         const double s = block_sum(v, warps);
@@ -1429,20 +1429,29 @@ __global__ void k_plan_finish(const BGate* gates, int n_gates, const double* row
     }
 }
 
-template <typename R>
-static void launch_plan_rot(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
-                            int n, double* part, int P, cudaStream_t s) {
+// kappa's form follows from the generator: imaginary for an even Y count
+// (KT = 1), real for an odd one (KT = 2)
+template <typename R, int KT>
+static void launch_plan_rot_kt(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
+                               int n, double* part, int P, cudaStream_t s) {
     if (g.k == 1) {
-        if (g.xl == 0) k_plan_rot<R, 1, 0><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
-        else k_plan_rot<R, 1, 1><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        if (g.xl == 0) k_plan_rot<R, 1, 0, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        else k_plan_rot<R, 1, 1, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
         return;
     }
     switch (g.xl) {
-        case 0: k_plan_rot<R, 2, 0><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        case 1: k_plan_rot<R, 2, 1><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        case 2: k_plan_rot<R, 2, 2><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        default: k_plan_rot<R, 2, 3><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 0: k_plan_rot<R, 2, 0, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 1: k_plan_rot<R, 2, 1, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 2: k_plan_rot<R, 2, 2, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        default: k_plan_rot<R, 2, 3, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
     }
+}
+
+template <typename R>
+static void launch_plan_rot(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
+                            int n, double* part, int P, cudaStream_t s) {
+    if (g.rot.ny & 1) launch_plan_rot_kt<R, 2>(g, psi, lam, dg, da, n, part, P, s);
+    else launch_plan_rot_kt<R, 1>(g, psi, lam, dg, da, n, part, P, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,11 @@ __device__ __forceinline__ A mul_ipow(A z, int q) {
 // With lam (reverse step), returns this thread's share of
 // Im <lam|P|psi> taken before the update; otherwise 0. Each thread takes U
 // groups per iteration, all loads issued before any arithmetic.
-template <typename R, int K, int XL, int U>
+// KT fixes kappa's form when the caller knows the parity of the Y count
+// (kappa = -i sin(a/2) i^ny): 1 imaginary (even ny), 2 real (odd ny), 0 read
+// from the values. With KT != 0 the partial's i^ny is a cross (even) or a
+// dot (odd) product, its sign applied once to the sum: the same values.
+template <typename R, int K, int XL, int U, int KT = 0>
 __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
                                             const RotShape& sh, R cs, R kr, R ki, int64_t tid, int64_t nthreads) {
     constexpr int D = 1 << K;
@@ -88,8 +92,16 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
                 // Im conj(l_r) i^ny p_{r ^ XL}, per row (signed after the loop)
 #pragma unroll
                 for (int r = 0; r < D; ++r) {
-                    const A q = mul_ipow(p[u][r ^ XL], ny);
-                    accr[r].add_cross(l[u][r].x, q.y, l[u][r].y, q.x);
+                    if (KT == 1) {
+                        const A q = p[u][r ^ XL];
+                        accr[r].add_cross(l[u][r].x, q.y, l[u][r].y, q.x);
+                    } else if (KT == 2) {
+                        const A q = p[u][r ^ XL];
+                        accr[r].add_dot(l[u][r].x, q.x, l[u][r].y, q.y);
+                    } else {
+                        const A q = mul_ipow(p[u][r ^ XL], ny);
+                        accr[r].add_cross(l[u][r].x, q.y, l[u][r].y, q.x);
+                    }
                 }
             }
 #pragma unroll
@@ -102,10 +114,10 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
                 for (int r = 0; r < D; ++r) {
                     const A x = v[r], y = v[r ^ XL];
                     A w;
-                    if (kimag) {         // kappa_r = i ki_r: w = cs x + i ki_r y
+                    if (KT == 1 || (KT == 0 && kimag)) {  // kappa_r = i ki_r: w = cs x + i ki_r y
                         w.x = fma(cs, x.x, -kir[r] * y.y);
                         w.y = fma(cs, x.y, kir[r] * y.x);
-                    } else if (kreal) {  // kappa_r = kr_r
+                    } else if (KT == 2 || (KT == 0 && kreal)) {  // kappa_r = kr_r
                         w.x = fma(cs, x.x, krr[r] * y.x);
                         w.y = fma(cs, x.y, krr[r] * y.y);
                     } else {
@@ -122,16 +134,17 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
     double acc = 0.0;
 #pragma unroll
     for (int r = 0; r < D; ++r) acc += sneg[r] ? -accr[r].value() : accr[r].value();
+    if (KT != 0 && (ny & 2)) acc = -acc;  // i^ny = -1 or -i
     return acc;
 }
 
 // Groups per iteration: enough 16-byte loads in flight without spilling.
-template <typename R, int K, int XL>
+template <typename R, int K, int XL, int KT = 0>
 __device__ __forceinline__ double rot_groups(amp_t<R>* psi, amp_t<R>* lam, int n, const RotShape& sh, R cs, R kr,
                                              R ki, int64_t tid, int64_t nthreads) {
     constexpr int U = K == 1 ? 4 : (sizeof(R) == 4 ? 2 : 1);
-    if (lam) return rot_groups_u<R, K, XL, U>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
-    return rot_groups_u<R, K, XL, (K == 1 ? 4 : 2)>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
+    if (lam) return rot_groups_u<R, K, XL, U, KT>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
+    return rot_groups_u<R, K, XL, (K == 1 ? 4 : 2), KT>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
 }
 
 // Dispatch on (k, xl) for the persistent batch kernel: one group per
