@@ -3,8 +3,6 @@ phase or CZ changes a quarter of the rows, a CNOT or SWAP half; Section
 III-A): bit-identical to the full out-of-place pass, within 1e-12 of the FP64
 oracle, and its byte accounting."""
 
-import math
-
 import numpy as np
 import pytest
 import torch

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import TOL_C128, dev, host, maxerr
+from gpu_util import TOL_C128, host, maxerr
 
 pytestmark = pytest.mark.gpu
 

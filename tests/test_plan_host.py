@@ -1,8 +1,6 @@
 """Host logic that needs no GPU: the fusion planner and the batch argument
 checks (which run before any device call)."""
 
-import ctypes
-
 import numpy as np
 import pytest
 
