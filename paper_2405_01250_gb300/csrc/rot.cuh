@@ -147,22 +147,29 @@ __device__ __forceinline__ double rot_groups(amp_t<R>* psi, amp_t<R>* lam, int n
     return rot_groups_u<R, K, XL, (K == 1 ? 4 : 2), KT>(psi, lam, n, sh, cs, kr, ki, tid, nthreads);
 }
 
-// Dispatch on (k, xl) for the persistent batch kernel: one group per
-// iteration, so its register budget (shared with every other gate path of
-// that kernel) is not exceeded.
+// Dispatch on (k, xl, parity of the Y count) for the persistent batch
+// kernel: one group per iteration, so its register budget (shared with
+// every other gate path of that kernel) is not exceeded.
+template <typename R, int KT>
+__device__ __forceinline__ double rot_dispatch_kt(int k, int xl, amp_t<R>* psi, amp_t<R>* lam, int n,
+                                                  const RotShape& sh, R cs, R kr, R ki, int64_t tid, int64_t nth) {
+    if (k == 1) {
+        if (xl == 0) return rot_groups_u<R, 1, 0, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        return rot_groups_u<R, 1, 1, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+    }
+    switch (xl) {
+        case 0: return rot_groups_u<R, 2, 0, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        case 1: return rot_groups_u<R, 2, 1, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        case 2: return rot_groups_u<R, 2, 2, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+        default: return rot_groups_u<R, 2, 3, 1, KT>(psi, lam, n, sh, cs, kr, ki, tid, nth);
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ double rot_dispatch(int k, int xl, amp_t<R>* psi, amp_t<R>* lam, int n,
                                                const RotShape& sh, R cs, R kr, R ki, int64_t tid, int64_t nth) {
-    if (k == 1) {
-        if (xl == 0) return rot_groups_u<R, 1, 0, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-        return rot_groups_u<R, 1, 1, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-    }
-    switch (xl) {
-        case 0: return rot_groups_u<R, 2, 0, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-        case 1: return rot_groups_u<R, 2, 1, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-        case 2: return rot_groups_u<R, 2, 2, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-        default: return rot_groups_u<R, 2, 3, 1>(psi, lam, n, sh, cs, kr, ki, tid, nth);
-    }
+    if (sh.ny & 1) return rot_dispatch_kt<R, 2>(k, xl, psi, lam, n, sh, cs, kr, ki, tid, nth);
+    return rot_dispatch_kt<R, 1>(k, xl, psi, lam, n, sh, cs, kr, ki, tid, nth);
 }
 
 }  // namespace diaq
