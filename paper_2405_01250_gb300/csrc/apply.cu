@@ -471,6 +471,25 @@ __device__ __forceinline__ int64_t map_row(int64_t j, const RowMap& m) {
     return insert_zeros_rt(g, m.st, m.k) + m.off[c];
 }
 
+// Entry type of a stored value (0 zero, 1 one, 2 real, 4 otherwise),
+// decided on the 32-bit halves of its bit pattern with integer operations:
+// the FP64 compares this replaces ran on the FP64 pipe, three per value,
+// and saturated it. Same decisions: -0 counts as zero, NaN as non-zero.
+__device__ __forceinline__ uint8_t stored_type(double re, double im) {
+    const int rh = __double2hiint(re), rl = __double2loint(re);
+    const int ih = __double2hiint(im), il = __double2loint(im);
+    const bool iz = ((ih & 0x7fffffff) | il) == 0;
+    if (!iz) return 4;
+    if (((rh & 0x7fffffff) | rl) == 0) return 0;
+    return (rh == 0x3ff00000 && rl == 0) ? 1 : 2;
+}
+__device__ __forceinline__ uint8_t stored_type(float re, float im) {
+    const int r = __float_as_int(re), i = __float_as_int(im);
+    if ((i & 0x7fffffff) != 0) return 4;
+    if ((r & 0x7fffffff) == 0) return 0;
+    return r == 0x3f800000 ? 1 : 2;
+}
+
 template <typename R, int G>
 __global__ void __launch_bounds__(256)
 k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* __restrict__ offs,
@@ -513,8 +532,8 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
         }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            if (a[u].x == R(0) && a[u].y == R(0)) continue;
-            const uint8_t t = (a[u].y == R(0)) ? (a[u].x == R(1) ? 1 : 2) : 4;
+            const uint8_t t = stored_type(a[u].x, a[u].y);
+            if (t == 0) continue;
             mac_typed<R>(acc[u], first[u], t, a[u].x, a[u].y, xv[u]);
         }
     }
