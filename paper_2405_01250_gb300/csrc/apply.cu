@@ -471,57 +471,79 @@ __device__ __forceinline__ int64_t map_row(int64_t j, const RowMap& m) {
     return insert_zeros_rt(g, m.st, m.k) + m.off[c];
 }
 
-// Entry type of a stored value (0 zero, 1 one, 2 real, 4 otherwise),
-// decided on the 32-bit halves of its bit pattern with integer operations:
-// the FP64 compares this replaces ran on the FP64 pipe, three per value,
-// and saturated it. Same decisions: -0 counts as zero, NaN as non-zero.
-__device__ __forceinline__ uint8_t stored_type(double re, double im) {
-    const int rh = __double2hiint(re), rl = __double2loint(re);
-    const int ih = __double2hiint(im), il = __double2loint(im);
-    const bool iz = ((ih & 0x7fffffff) | il) == 0;
-    if (!iz) return 4;
-    if (((rh & 0x7fffffff) | rl) == 0) return 0;
-    return (rh == 0x3ff00000 && rl == 0) ? 1 : 2;
+// A stored value is zero when both halves of its bit pattern are zero once
+// the sign bit is masked (-0 counts as zero, NaN does not). The tests run on
+// the integer pipes: FP64 compares would compete with the arithmetic for
+// the FP64 pipe.
+__device__ __forceinline__ bool zero_bits(double v) {
+    return ((__double2hiint(v) & 0x7fffffff) | __double2loint(v)) == 0;
 }
-__device__ __forceinline__ uint8_t stored_type(float re, float im) {
-    const int r = __float_as_int(re), i = __float_as_int(im);
-    if ((i & 0x7fffffff) != 0) return 4;
-    if ((r & 0x7fffffff) == 0) return 0;
-    return r == 0x3f800000 ? 1 : 2;
+__device__ __forceinline__ bool zero_bits(float v) { return (__float_as_int(v) & 0x7fffffff) == 0; }
+
+// acc += a * v for one stored diagonal, with warp-uniform control flow: a
+// lane whose value is zero adds fma(0, v, acc) = acc, so no lane branches on
+// its own value. The warp skips the diagonal when it is zero on every lane
+// and the imaginary half when every lane's value is real. (Per-lane branches
+// on the value's type are predicated, and predicated-off FP64 instructions
+// still occupy the FP64 pipe.)
+template <typename R>
+__device__ __forceinline__ void stored_mac(amp_t<R>& acc, amp_t<R> a, amp_t<R> v) {
+    const bool cplx = !zero_bits(a.y);
+    const bool nz = cplx || !zero_bits(a.x);
+    if (!__any_sync(0xffffffffu, nz)) return;
+    acc.x = fma(a.x, v.x, acc.x);
+    acc.y = fma(a.x, v.y, acc.y);
+    if (__any_sync(0xffffffffu, cplx)) {
+        acc.x = fma(-a.y, v.y, acc.x);
+        acc.y = fma(a.y, v.x, acc.y);
+    }
 }
 
+// Offsets and value starts of up to STORED_PARAM_D diagonals, passed by
+// value so that no thread waits on a load before it can address x and the
+// values; ops with more diagonals read them from device memory.
+constexpr int STORED_PARAM_D = 16;
+struct StoredDiags {
+    int64_t off[STORED_PARAM_D];
+    int64_t start[STORED_PARAM_D];
+};
+
+// Algorithm 2 over the stored diagonals. Each thread takes G rows (grouped
+// by the row map so that a block holds every row its targets couple) and
+// walks the diagonals in stored order, issuing a diagonal's value and x
+// loads together. (Issuing several diagonals' loads before using any of
+// them was measured slower: the extra registers cost more occupancy than
+// the shorter dependency chain gained.) Threads past N keep running with
+// zero values so that every warp vote sees full warps.
 template <typename R, int G>
 __global__ void __launch_bounds__(256)
 k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* __restrict__ offs,
               const int64_t* __restrict__ starts, const amp_t<R>* __restrict__ vals,
-              const __grid_constant__ RowMap map) {
+              const __grid_constant__ RowMap map, const __grid_constant__ StoredDiags sd) {
     using A = amp_t<R>;
     const int64_t T = blockDim.x;
     const int64_t j0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
+    const bool by_value = D <= STORED_PARAM_D;
     int64_t row[G];
     A acc[G];
-    bool first[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
         const int64_t j = j0 + u * T;
         row[u] = j < N ? map_row(j, map) : int64_t(-1);
         acc[u].x = R(0);
         acc[u].y = R(0);
-        first[u] = true;
     }
     for (int q = 0; q < D; ++q) {
-        const int64_t d = offs[q];
+        const int64_t d = by_value ? sd.off[q] : offs[q];
+        const int64_t st = by_value ? sd.start[q] : starts[q];
         const int64_t len = N - (d < 0 ? -d : d);
         const int64_t shift = d < 0 ? -d : 0;
-        const A* v = vals + starts[q];
-        // value and x loads issued together (no dependent round trip); x is
-        // read for every row in the diagonal's range, used where A_d(i) != 0
         A a[G], xv[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
             const int64_t p = row[u] - shift;
             if (row[u] >= 0 && p >= 0 && p < len) {
-                a[u] = ld_stream(v + p);
+                a[u] = ld_stream(vals + st + p);
                 xv[u] = x[row[u] + d];
             } else {
                 a[u].x = R(0);
@@ -531,11 +553,7 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
             }
         }
 #pragma unroll
-        for (int u = 0; u < G; ++u) {
-            const uint8_t t = stored_type(a[u].x, a[u].y);
-            if (t == 0) continue;
-            mac_typed<R>(acc[u], first[u], t, a[u].x, a[u].y, xv[u]);
-        }
+        for (int u = 0; u < G; ++u) stored_mac<R>(acc[u], a[u], xv[u]);
     }
 #pragma unroll
     for (int u = 0; u < G; ++u)
@@ -607,15 +625,26 @@ diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStrea
     }
     const int64_t blocks = (N + int64_t(threads) * G - 1) / (int64_t(threads) * G);
     const int D = (int)op->offsets.size();
+    StoredDiags sd;
+    std::memset(&sd, 0, sizeof(sd));
+    for (int q = 0; q < D && q < STORED_PARAM_D; ++q) {
+        sd.off[q] = op->offsets[size_t(q)];
+        sd.start[q] = op->starts[size_t(q)];
+    }
+    if (D == 0) {
+        // the zero operator: y = 0
+        DIAQ_CUDA(cudaMemsetAsync(y, 0, size_t(N) * amp_bytes(op->dtype), s));
+        return DIAQ_OK;
+    }
     DIAQ_PRELAUNCH("k_stored_spmv");
     if (op->dtype == DIAQ_C128)
         k_stored_spmv<double, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
             reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), N, D, op->d_offsets,
-            op->d_starts, reinterpret_cast<const double2*>(op->d_values), map);
+            op->d_starts, reinterpret_cast<const double2*>(op->d_values), map, sd);
     else
         k_stored_spmv<float, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
             reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), N, D, op->d_offsets,
-            op->d_starts, reinterpret_cast<const float2*>(op->d_values), map);
+            op->d_starts, reinterpret_cast<const float2*>(op->d_values), map, sd);
     DIAQ_CUDA(cudaGetLastError());
     return DIAQ_OK;
 }

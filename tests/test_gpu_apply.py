@@ -126,6 +126,29 @@ def test_raw_diaq_apply(api):
         assert op.info()["class"] == "raw"
 
 
+@pytest.mark.parametrize("n_diag", [1, 2, 3, 4, 5, 15, 16, 17, 40])
+def test_raw_diaq_apply_diagonal_counts(api, n_diag):
+    """Stored SpMV with zero, one, real and complex entries, across the
+    switch from offsets passed by value (up to 16 diagonals) to offsets read
+    from device memory."""
+    n = 10
+    N = 1 << n
+    idx = sorted(int(d) for d in RNG.choice(np.arange(-N + 1, N), size=n_diag, replace=False))
+    vals = [RNG.standard_normal(N - abs(d)) + 1j * RNG.standard_normal(N - abs(d)) for d in idx]
+    for v in vals:
+        v[::5] = 0.0
+        v[1::7] = 1.0
+        v[2::9] = RNG.standard_normal(len(v[2::9]))  # real entries
+    x = synth.random_state(n, RNG)
+    want = oracle.diaq_matvec(idx, vals, x)
+    scale = max(1.0, float(np.max(np.abs(want))))
+    for dtype, tol in ((torch.complex128, TOL_C128), (torch.complex64, 5e-6)):
+        op = api.build_diaq(n, idx, vals, dtype=dtype)
+        y = torch.empty(N, dtype=dtype, device="cuda")
+        api.apply(op, dev(x, dtype), y)
+        assert maxerr(host(y), want) <= tol * scale * n_diag, (n_diag, dtype)
+
+
 def test_fuse_gate_ops(api):
     n = 10
     for trial in range(5):
