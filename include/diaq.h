@@ -105,6 +105,9 @@ typedef struct {
     int32_t targets[DIAQ_MAX_K];
     int64_t n_diagonals;     /* full-system DiaQ diagonals of the op */
     int64_t stored_bytes;    /* device bytes of materialised diagonals (0 if on-the-fly) */
+    int32_t real_values;     /* 1 if every entry of the op is real (imaginary part 0): gate
+                                ops with a real matrix, raw ops given real values, products
+                                of such ops; the stored SpMV then skips the imaginary half */
 } diaq_op_info;
 
 /* ------------------------------------------------------------------------
@@ -214,11 +217,15 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
  * pass. diaq_op_apply_bytes reports the bytes either way. */
 diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t stream);
 
-/* Algorithmic HBM bytes of one diaq_apply of op into *bytes: out of place
- * (in_place = 0) 2 N s for on-the-fly ops and 2 N s + s sum_d (N - |d|) for
- * stored ops (s = bytes per amplitude); in place (on-the-fly ops only,
- * DIAQ_ERR_ARG for stored) N / 2^k x (columns read + rows written) x s when
- * the op has identity rows, else 2 N s. Host only. */
+/* Algorithmic HBM bytes of one diaq_apply of op into *bytes (s = bytes per
+ * amplitude). Out of place (in_place = 0): 2 N s for on-the-fly ops; for
+ * stored ops 2 N s plus s x the stored values the SpMV reads, which for a
+ * gate op on k <= 3 targets are N / 2^k x (the diagonals each local row
+ * class can use, summed over the 2^k classes): the zeros the format stores
+ * where a diagonal crosses rows of another class are not read. Raw ops and
+ * k > 3 read every stored value, s sum_d (N - |d|). In place (on-the-fly ops
+ * only, DIAQ_ERR_ARG for stored) N / 2^k x (columns read + rows written) x s
+ * when the op has identity rows, else 2 N s. Host only. */
 diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
 
 /* Run ops[0..count-1] in order on a state: psi_in -> psi_out. psi_in and

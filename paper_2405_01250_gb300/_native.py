@@ -51,6 +51,7 @@ class diaq_op_info(ctypes.Structure):
         ("targets", ctypes.c_int32 * DIAQ_MAX_K),
         ("n_diagonals", ctypes.c_int64),
         ("stored_bytes", ctypes.c_int64),
+        ("real_values", ctypes.c_int32),
     ]
 
 

@@ -119,6 +119,7 @@ class Op:
             "class": N.CLASSES[inf.op_class], "k": inf.k,
             "targets": tuple(inf.targets[a] for a in range(inf.k)),
             "n_diagonals": inf.n_diagonals, "stored_bytes": inf.stored_bytes,
+            "real_values": bool(inf.real_values),
         }
 
     def apply_bytes(self, in_place: bool = False) -> int:

@@ -480,20 +480,22 @@ __device__ __forceinline__ bool zero_bits(double v) {
 }
 __device__ __forceinline__ bool zero_bits(float v) { return (__float_as_int(v) & 0x7fffffff) == 0; }
 
-// acc += a * v for one stored diagonal, with warp-uniform control flow: a
-// lane whose value is zero adds fma(0, v, acc) = acc, so no lane branches on
-// its own value. The warp skips the diagonal when it is zero on every lane
-// and the imaginary half when every lane's value is real. (Per-lane branches
-// on the value's type are predicated, and predicated-off FP64 instructions
-// still occupy the FP64 pipe.)
-template <typename R>
+// acc += a * v for one stored diagonal of a raw op, with warp-uniform
+// control flow: a lane whose value is zero adds fma(0, v, acc) = acc, so no
+// lane branches on its own value. The warp skips the diagonal when it is
+// zero on every lane, and the imaginary half when every lane's value is real
+// (CPLX = false: the op's values are all real, so there is no imaginary
+// half). The skip is nested around the imaginary half on purpose: measured,
+// without that nesting the compiler predicates the whole skip, and
+// predicated-off FP64 instructions still occupy the FP64 pipe.
+template <typename R, bool CPLX>
 __device__ __forceinline__ void stored_mac(amp_t<R>& acc, amp_t<R> a, amp_t<R> v) {
-    const bool cplx = !zero_bits(a.y);
+    const bool cplx = CPLX && !zero_bits(a.y);
     const bool nz = cplx || !zero_bits(a.x);
     if (!__any_sync(0xffffffffu, nz)) return;
     acc.x = fma(a.x, v.x, acc.x);
     acc.y = fma(a.x, v.y, acc.y);
-    if (__any_sync(0xffffffffu, cplx)) {
+    if (CPLX && __any_sync(0xffffffffu, cplx)) {
         acc.x = fma(-a.y, v.y, acc.x);
         acc.y = fma(a.y, v.x, acc.y);
     }
@@ -502,20 +504,41 @@ __device__ __forceinline__ void stored_mac(amp_t<R>& acc, amp_t<R> a, amp_t<R> v
 // Offsets and value starts of up to STORED_PARAM_D diagonals, passed by
 // value so that no thread waits on a load before it can address x and the
 // values; ops with more diagonals read them from device memory.
+//
+// For a gate op on k <= STORED_CLS_K targets, also the diagonals each local
+// row class can use: a row whose target bits are c (in the row map's local
+// numbering) has A[i][i+d] != 0 only for d = off[c2] - off[c], and that
+// column is always inside the state. cls[c][e] (e < ecount) is the stored
+// index q of such a diagonal, in stored order, or -1 past the class's own
+// count.
 constexpr int STORED_PARAM_D = 16;
+constexpr int STORED_CLS_K = 3;
+constexpr int STORED_THREADS = 256;  // launch shape of k_stored_spmv
+constexpr int STORED_G = 2;          // rows per thread
 struct StoredDiags {
     int64_t off[STORED_PARAM_D];
     int64_t start[STORED_PARAM_D];
+    int ecount;  // 0: no class table (raw ops, k > STORED_CLS_K)
+    int8_t cls[1 << STORED_CLS_K][1 << STORED_CLS_K];
 };
 
 // Algorithm 2 over the stored diagonals. Each thread takes G rows (grouped
-// by the row map so that a block holds every row its targets couple) and
-// walks the diagonals in stored order, issuing a diagonal's value and x
-// loads together. (Issuing several diagonals' loads before using any of
-// them was measured slower: the extra registers cost more occupancy than
-// the shorter dependency chain gained.) Threads past N keep running with
+// by the row map so that a block holds every row its targets couple).
+//
+// CLS (gate ops, k <= 3): each row walks only the diagonals of its local row
+// class (at most 2^k, from the class table) and multiplies them without
+// testing the values: the class is warp-uniform under the row map, so no
+// warp diverges or votes, and each row does its own multiply-adds only.
+//
+// Otherwise (raw ops): each row walks every diagonal in stored order, with
+// the warp-uniform skips of stored_mac. Threads past N keep running with
 // zero values so that every warp vote sees full warps.
-template <typename R, int G>
+//
+// Both issue a diagonal's value and x loads together. (Issuing several
+// diagonals' loads before using any of them was measured slower: the extra
+// registers cost more occupancy than the shorter dependency chain gained.)
+// CPLX = false only for ops whose stored values are all real.
+template <typename R, int G, bool CPLX, bool CLS>
 __global__ void __launch_bounds__(256)
 k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* __restrict__ offs,
               const int64_t* __restrict__ starts, const amp_t<R>* __restrict__ vals,
@@ -525,24 +548,31 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
     const int64_t j0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
     const bool by_value = D <= STORED_PARAM_D;
     int64_t row[G];
+    int cls[G];
     A acc[G];
 #pragma unroll
     for (int u = 0; u < G; ++u) {
         const int64_t j = j0 + u * T;
         row[u] = j < N ? map_row(j, map) : int64_t(-1);
+        cls[u] = CLS ? int((j >> map.L) & ((int64_t(1) << map.k) - 1)) : 0;
         acc[u].x = R(0);
         acc[u].y = R(0);
     }
-    for (int q = 0; q < D; ++q) {
-        const int64_t d = by_value ? sd.off[q] : offs[q];
-        const int64_t st = by_value ? sd.start[q] : starts[q];
-        const int64_t len = N - (d < 0 ? -d : d);
-        const int64_t shift = d < 0 ? -d : 0;
+    const int E = CLS ? sd.ecount : D;
+    for (int e = 0; e < E; ++e) {
         A a[G], xv[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            const int64_t p = row[u] - shift;
-            if (row[u] >= 0 && p >= 0 && p < len) {
+            const int q = CLS ? int(sd.cls[cls[u]][e]) : e;
+            bool ok = row[u] >= 0 && q >= 0;
+            int64_t d = 0, p = 0, st = 0;
+            if (ok) {
+                d = CLS || by_value ? sd.off[q] : offs[q];
+                st = CLS || by_value ? sd.start[q] : starts[q];
+                p = row[u] - (d < 0 ? -d : 0);
+                ok = p >= 0 && p < N - (d < 0 ? -d : d);
+            }
+            if (ok) {
                 a[u] = ld_stream(vals + st + p);
                 xv[u] = x[row[u] + d];
             } else {
@@ -553,7 +583,18 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
             }
         }
 #pragma unroll
-        for (int u = 0; u < G; ++u) stored_mac<R>(acc[u], a[u], xv[u]);
+        for (int u = 0; u < G; ++u) {
+            if (CLS) {
+                acc[u].x = fma(a[u].x, xv[u].x, acc[u].x);
+                acc[u].y = fma(a[u].x, xv[u].y, acc[u].y);
+                if (CPLX) {
+                    acc[u].x = fma(-a[u].y, xv[u].y, acc[u].x);
+                    acc[u].y = fma(a[u].y, xv[u].x, acc[u].y);
+                }
+            } else {
+                stored_mac<R, CPLX>(acc[u], a[u], xv[u]);
+            }
+        }
     }
 #pragma unroll
     for (int u = 0; u < G; ++u)
@@ -614,9 +655,56 @@ static RowMap make_rowmap(const GateDesc& g, int n, int threads, int G) {
     return m;
 }
 
+// Class table of a gate op on k <= STORED_CLS_K targets (row map local
+// numbering): for each local row class c, the stored diagonals
+// d = off[c2] - off[c] present in the op, in stored order. Returns the sum
+// of the classes' counts, or -1 when the op takes the generic path (raw
+// ops, k > STORED_CLS_K, more than STORED_PARAM_D diagonals).
+static int stored_class_table(const diaq_op_s* op, const RowMap& map, int D, StoredDiags* sd) {
+    if (op->op_class == DIAQ_CLASS_RAW || map.k < 1 || map.k > STORED_CLS_K || D > STORED_PARAM_D) return -1;
+    std::memset(sd->cls, -1, sizeof(sd->cls));
+    sd->ecount = 0;
+    const int K = 1 << map.k;
+    int total = 0;
+    for (int c = 0; c < K; ++c) {
+        int e = 0;
+        for (int q = 0; q < D; ++q)
+            for (int c2 = 0; c2 < K; ++c2)
+                if (op->offsets[size_t(q)] == map.off[c2] - map.off[c]) {
+                    sd->cls[c][e++] = int8_t(q);
+                    break;
+                }
+        sd->ecount = std::max(sd->ecount, e);
+        total += e;
+    }
+    return total;
+}
+
+template <typename R, int G>
+static void stored_launch(bool cplx, bool cls, dim3 grid, int threads, cudaStream_t s, const void* x, void* y,
+                          int64_t N, int D, const diaq_op_s* op, const RowMap& map, const StoredDiags& sd) {
+    using A = amp_t<R>;
+    const A* xa = reinterpret_cast<const A*>(x);
+    A* ya = reinterpret_cast<A*>(y);
+    const A* va = reinterpret_cast<const A*>(op->d_values);
+    const int64_t* o = op->d_offsets;
+    const int64_t* t = op->d_starts;
+    if (cls) {
+        if (cplx)
+            k_stored_spmv<R, G, true, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+        else
+            k_stored_spmv<R, G, false, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    } else {
+        if (cplx)
+            k_stored_spmv<R, G, true, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+        else
+            k_stored_spmv<R, G, false, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    }
+}
+
 diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStream_t s) {
     const int64_t N = int64_t(1) << op->n;
-    const int threads = 256, G = 2;
+    const int threads = STORED_THREADS, G = STORED_G;
     RowMap map;
     if (op->op_class == DIAQ_CLASS_RAW) {
         std::memset(&map, 0, sizeof(map));
@@ -625,28 +713,38 @@ diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStrea
     }
     const int64_t blocks = (N + int64_t(threads) * G - 1) / (int64_t(threads) * G);
     const int D = (int)op->offsets.size();
+    if (D == 0) {
+        // the zero operator: y = 0
+        DIAQ_CUDA(cudaMemsetAsync(y, 0, size_t(N) * amp_bytes(op->dtype), s));
+        return DIAQ_OK;
+    }
     StoredDiags sd;
     std::memset(&sd, 0, sizeof(sd));
     for (int q = 0; q < D && q < STORED_PARAM_D; ++q) {
         sd.off[q] = op->offsets[size_t(q)];
         sd.start[q] = op->starts[size_t(q)];
     }
-    if (D == 0) {
-        // the zero operator: y = 0
-        DIAQ_CUDA(cudaMemsetAsync(y, 0, size_t(N) * amp_bytes(op->dtype), s));
-        return DIAQ_OK;
-    }
+    const bool cls = stored_class_table(op, map, D, &sd) >= 0;
     DIAQ_PRELAUNCH("k_stored_spmv");
+    const dim3 grid((unsigned)blocks);
+    const bool cplx = !op->real_values;
     if (op->dtype == DIAQ_C128)
-        k_stored_spmv<double, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
-            reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), N, D, op->d_offsets,
-            op->d_starts, reinterpret_cast<const double2*>(op->d_values), map, sd);
+        stored_launch<double, G>(cplx, cls, grid, threads, s, x, y, N, D, op, map, sd);
     else
-        k_stored_spmv<float, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
-            reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), N, D, op->d_offsets,
-            op->d_starts, reinterpret_cast<const float2*>(op->d_values), map, sd);
+        stored_launch<float, G>(cplx, cls, grid, threads, s, x, y, N, D, op, map, sd);
     DIAQ_CUDA(cudaGetLastError());
     return DIAQ_OK;
+}
+
+int64_t stored_values_read(const diaq_op_s* op) {
+    const int D = (int)op->offsets.size();
+    if (op->op_class == DIAQ_CLASS_RAW || D == 0) return op->stored_elems;
+    const RowMap map = make_rowmap(op->gate, op->n, STORED_THREADS, STORED_G);
+    StoredDiags sd;
+    std::memset(&sd, 0, sizeof(sd));
+    const int total = stored_class_table(op, map, D, &sd);
+    if (total < 0) return op->stored_elems;
+    return (int64_t(1) << (op->n - map.k)) * int64_t(total);
 }
 
 diaq_status launch_materialise(diaq_op_s* op, cudaStream_t s) {

@@ -387,6 +387,7 @@ static diaq_status alloc_stored(diaq_op_s* op) {
 // Finish a gate-structured op: class, offsets, device data.
 static diaq_status finish_gate_op(diaq_op_s* op, const std::vector<uint8_t>* pattern, cudaStream_t s) {
     op->op_class = classify(op->gate.m, op->gate.k);
+    op->real_values = std::all_of(op->gate.m.begin(), op->gate.m.end(), [](const cplx& v) { return v.imag() == 0.0; });
     op->offsets = full_offsets(op->gate, pattern);
     if (op->variant == DIAQ_ONTHEFLY) {
         if (op->gate.k > 3) DIAQ_TRY(upload_matrix(op));
@@ -568,6 +569,8 @@ diaq_status diaq_build_diaq(int32_t n_qubits, int64_t count, const int64_t* indi
         return cuda_fail(e, "cudaGetDevice");
     }
     for (auto& p : idx) op->offsets.push_back(p.first);
+    op->real_values = true;
+    for (int64_t t = 0; t < pos && op->real_values; ++t) op->real_values = values[2 * t + 1] == 0.0;
     diaq_status s = alloc_stored(op);
     if (s == DIAQ_OK) {
         // host staging in the op's precision, sorted order
@@ -627,6 +630,7 @@ diaq_status diaq_op_query(diaq_op_t op, diaq_op_info* info) {
     for (int a = 0; a < info->k; ++a) info->targets[a] = op->gate.targets[a];
     info->n_diagonals = int64_t(op->offsets.size());
     info->stored_bytes = op->variant == DIAQ_STORED ? op->stored_elems * int64_t(amp_bytes(op->dtype)) : 0;
+    info->real_values = op->real_values ? 1 : 0;
     return DIAQ_OK;
 }
 
@@ -704,6 +708,7 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
         c->op_class = DIAQ_CLASS_RAW;
         c->device = ops[0]->device;
         const diaq_op_s* right = cur ? cur : ops[0];
+        c->real_values = ops[i]->real_values && right->real_values;
         diaq_status st = launch_spgemm(ops[i], right, c, s);
         if (cur) {
             free_op_memory(cur);
@@ -727,6 +732,7 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
         c->op_class = DIAQ_CLASS_RAW;
         c->device = ops[0]->device;
         c->offsets = ops[0]->offsets;
+        c->real_values = ops[0]->real_values;
         diaq_status st = alloc_stored(c);
         if (st == DIAQ_OK) {
             cudaError_t e = cudaMemcpyAsync(c->d_values, ops[0]->d_values, size_t(c->stored_elems) * amp_bytes(c->dtype),
@@ -771,7 +777,7 @@ diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes) 
     const int64_t s = int64_t(amp_bytes(op->dtype));
     if (op->variant == DIAQ_STORED) {
         if (in_place) return fail(DIAQ_ERR_ARG, "stored ops cannot run in place");
-        *bytes = 2 * N * s + op->stored_elems * s;
+        *bytes = 2 * N * s + stored_values_read(op) * s;
     } else if (in_place) {
         *bytes = inplace_bytes(op->n, op->dtype, op->gate);
     } else {
@@ -805,6 +811,7 @@ static diaq_status prune_with_counts(const diaq_op_s* src, const std::vector<int
     c->variant = DIAQ_STORED;
     c->op_class = DIAQ_CLASS_RAW;
     c->device = src->device;
+    c->real_values = src->real_values;
     std::vector<int32_t> keep;
     for (size_t q = 0; q < src->offsets.size(); ++q)
         if (counts[q] > 0) {
@@ -873,6 +880,7 @@ diaq_status diaq_unitary_chain(const diaq_gate* gates, int32_t n_gates, const do
             C->variant = DIAQ_STORED;
             C->op_class = DIAQ_CLASS_RAW;
             C->device = g->device;
+            C->real_values = g->real_values && U->real_values;
             st = launch_spgemm(g, U, C, s);  // C = G_t U (Algorithm 1)
             drop(U);
             drop(g);

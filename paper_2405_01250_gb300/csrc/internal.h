@@ -100,6 +100,7 @@ struct diaq_op_s {
     int64_t* d_starts = nullptr;         // element start of each diagonal
     std::vector<int64_t> starts;         // host copy of d_starts
     int64_t stored_elems = 0;
+    bool real_values = false;            // every stored value has imaginary part 0
     // device copy of the local matrix for k > 3 (dtype complex, then types)
     void* d_matrix = nullptr;
 };
@@ -122,6 +123,10 @@ diaq_status launch_onthefly(const diaq_op_s* op, const void* x, void* y, cudaStr
 diaq_status launch_gate_local(int n, diaq_dtype dt, const GateDesc& g, const void* d_matrix,
                               const void* x, void* y, cudaStream_t s);
 diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStream_t s);
+// Stored values one diaq_apply of a stored op reads: for a gate op on at
+// most 3 targets only the diagonals of each row's local class
+// (N/2^k x the class table's entries), else every stored value.
+int64_t stored_values_read(const diaq_op_s* op);
 diaq_status launch_materialise(diaq_op_s* op, cudaStream_t s);
 diaq_status launch_raw_upload(diaq_op_s* op, const double* host_values, cudaStream_t s);
 diaq_status launch_spgemm(const diaq_op_s* a, const diaq_op_s* b, diaq_op_s* c, cudaStream_t s);

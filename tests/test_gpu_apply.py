@@ -103,10 +103,12 @@ def test_classes(api):
     n = 6
     cases = {"diagonal": synth.cphase(0.3), "permutation": synth.SWAP, "real": synth.H,
              "monomial": np.array([[0, -1j], [1j, 0]]), "general": synth.haar_u2(RNG)}
+    real = {"diagonal": False, "permutation": True, "real": True, "monomial": False, "general": False}
     for want, m in cases.items():
         k = int(math.log2(m.shape[0]))
         op = api.build(synth.Gate(tuple(range(k)), m), n)
         assert op.info()["class"] == want
+        assert op.info()["real_values"] == real[want]
 
 
 def test_raw_diaq_apply(api):
@@ -126,15 +128,17 @@ def test_raw_diaq_apply(api):
         assert op.info()["class"] == "raw"
 
 
+@pytest.mark.parametrize("real", [False, True])
 @pytest.mark.parametrize("n_diag", [1, 2, 3, 4, 5, 15, 16, 17, 40])
-def test_raw_diaq_apply_diagonal_counts(api, n_diag):
-    """Stored SpMV with zero, one, real and complex entries, across the
+def test_raw_diaq_apply_diagonal_counts(api, n_diag, real):
+    """Stored SpMV with zero, one, real and complex entries (or real entries
+    only, which take the kernel without the imaginary half), across the
     switch from offsets passed by value (up to 16 diagonals) to offsets read
     from device memory."""
     n = 10
     N = 1 << n
     idx = sorted(int(d) for d in RNG.choice(np.arange(-N + 1, N), size=n_diag, replace=False))
-    vals = [RNG.standard_normal(N - abs(d)) + 1j * RNG.standard_normal(N - abs(d)) for d in idx]
+    vals = [RNG.standard_normal(N - abs(d)) + (0 if real else 1j) * RNG.standard_normal(N - abs(d)) for d in idx]
     for v in vals:
         v[::5] = 0.0
         v[1::7] = 1.0
@@ -194,6 +198,22 @@ def test_fuse_raw_ops_on_device(api):
     y = torch.empty(N, dtype=torch.complex128, device="cuda")
     api.apply(f, dev(x), y)
     assert maxerr(host(y), P @ x) <= 1e-11 * max(1.0, float(np.max(np.abs(P @ x))))
+    # real operands give a real product (applied without the imaginary half);
+    # one complex operand makes it complex again
+    rops = [api.build_diaq(n, list(range(-3, 4)), [RNG.standard_normal(N - abs(d)) for d in range(-3, 4)])
+            for _ in range(2)]
+    rm = [np.zeros((N, N), dtype=np.complex128) for _ in range(2)]
+    for o, A in zip(rops, rm):
+        for q, d in enumerate(o.offsets()):
+            t = np.arange(N - abs(d))
+            A[max(0, -d) + t, max(0, d) + t] = o.diagonal(q)
+    assert all(o.info()["real_values"] for o in rops) and not ops[1].info()["real_values"]
+    for pair, want, real in (((rops[0], rops[1]), rm[1] @ rm[0], True), ((rops[0], ops[1]), mats[1] @ rm[0], False)):
+        f = api.fuse(list(pair))
+        assert f.info()["real_values"] == real
+        assert f.prune().info()["real_values"] == real
+        api.apply(f, dev(x), y)
+        assert maxerr(host(y), want @ x) <= 1e-11 * max(1.0, float(np.max(np.abs(want @ x))))
 
 
 @pytest.mark.parametrize("variant", ["stored", "onthefly"])

@@ -95,6 +95,18 @@ def test_apply_bytes_accounting(api):
     assert st.apply_bytes(in_place=False) == 2 * N * 16 + st.info()["stored_bytes"]
     with pytest.raises(Exception):
         st.apply_bytes(in_place=True)
+    # stored H on qubit q: each row reads its own two entries (main diagonal
+    # and the one to its partner), not the zeros stored where the diagonals
+    # +-2^q cross rows of the other class
+    for q in (0, 5, 11):
+        st = api.build(synth.Gate((q,), synth.H), n, variant="stored")
+        assert st.info()["stored_bytes"] == 16 * (3 * N - 2 * (1 << q))
+        assert st.apply_bytes() == 2 * N * 16 + 2 * N * 16
+    # a dense two-qubit gate: four entries per row; raw ops read every value
+    st = api.build(synth.Gate((4, 9), synth.haar_u2(RNG, 4)), n, variant="stored")
+    assert st.apply_bytes() == 2 * N * 16 + 4 * N * 16
+    raw = api.build_diaq(n, [-3, 0, 5], [np.ones(N - 3), np.ones(N), np.ones(N - 5)])
+    assert raw.apply_bytes() == 2 * N * 16 + 16 * (3 * N - 8)
 
 
 def test_identity_gate_in_place_leaves_state(api):
