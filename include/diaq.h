@@ -214,7 +214,13 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
  * Section III-A) reads only the local columns its other rows use and writes
  * only those rows: a controlled phase or CZ moves a quarter of the bytes of
  * a full pass, a CNOT or SWAP half. The result is bit-identical to the full
- * pass. diaq_op_apply_bytes reports the bytes either way. */
+ * pass. diaq_op_apply_bytes reports the bytes either way.
+ *
+ * Stored ops: each row sums its diagonals' terms in index order. For a gate
+ * op on k <= 3 targets a row reads only the diagonals its local row class
+ * can use (the others hold zeros in that row). A stored zero that is read
+ * is multiplied, not skipped, as in a dense product: a non-finite amplitude
+ * that meets one gives NaN. */
 diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t stream);
 
 /* Algorithmic HBM bytes of one diaq_apply of op into *bytes (s = bytes per
