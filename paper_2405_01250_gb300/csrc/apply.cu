@@ -480,6 +480,14 @@ __device__ __forceinline__ bool zero_bits(double v) {
 }
 __device__ __forceinline__ bool zero_bits(float v) { return (__float_as_int(v) & 0x7fffffff) == 0; }
 
+// -v when neg, else v, by flipping the sign bit with an integer operation.
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+    return __hiloint2double(__double2hiint(v) ^ (neg ? int(0x80000000) : 0), __double2loint(v));
+}
+__device__ __forceinline__ float flip_sign(float v, bool neg) {
+    return __int_as_float(__float_as_int(v) ^ (neg ? int(0x80000000) : 0));
+}
+
 // acc += a * v for one stored diagonal of a raw op, with warp-uniform
 // control flow: a lane whose value is zero adds fma(0, v, acc) = acc, so no
 // lane branches on its own value. The warp skips the diagonal when it is
@@ -505,30 +513,44 @@ __device__ __forceinline__ void stored_mac(amp_t<R>& acc, amp_t<R> a, amp_t<R> v
 // value so that no thread waits on a load before it can address x and the
 // values; ops with more diagonals read them from device memory.
 //
-// For a gate op on k <= STORED_CLS_K targets, also the diagonals each local
-// row class can use: a row whose target bits are c (in the row map's local
-// numbering) has A[i][i+d] != 0 only for d = off[c2] - off[c], and that
-// column is always inside the state. cls[c][e] (e < ecount) is the stored
-// index q of such a diagonal, in stored order, or -1 past the class's own
-// count.
+// For a gate op on k <= STORED_CLS_K targets, also the terms of each local
+// row class: a row whose target bits are c (the matrix's local row index)
+// has A[i][i+d] = M[c][c2] for d = off[c2] - off[c], that column is always
+// inside the state, and every other entry of the row is zero. cls[c][e]
+// (e < ecount) codes the term of one entry M[c][c2] != 0 as (q << 1) | h:
+// the stored diagonal q and, for ops whose entries are each real or
+// imaginary (STORED_TERMS_HALF), whether the term multiplies the value's
+// imaginary part (h = 1). Entries M[c][c2] = 0 have no term. 0xff marks the
+// end of a class's terms.
 constexpr int STORED_PARAM_D = 16;
 constexpr int STORED_CLS_K = 3;
 constexpr int STORED_THREADS = 256;  // launch shape of k_stored_spmv
 constexpr int STORED_G = 2;          // rows per thread
+// Kind of the terms, fixed per op: all values real (2 FMAs per term); each
+// value real or imaginary (2 FMAs, the half chosen per term); complex values
+// (4 FMAs per term).
+constexpr int STORED_TERMS_REAL = 0;
+constexpr int STORED_TERMS_HALF = 1;
+constexpr int STORED_TERMS_COMPLEX = 2;
 struct StoredDiags {
     int64_t off[STORED_PARAM_D];
     int64_t start[STORED_PARAM_D];
     int ecount;  // 0: no class table (raw ops, k > STORED_CLS_K)
-    int8_t cls[1 << STORED_CLS_K][1 << STORED_CLS_K];
+    uint8_t cls[1 << STORED_CLS_K][1 << STORED_CLS_K];
 };
 
 // Algorithm 2 over the stored diagonals. Each thread takes G rows (grouped
 // by the row map so that a block holds every row its targets couple).
 //
-// CLS (gate ops, k <= 3): each row walks only the diagonals of its local row
-// class (at most 2^k, from the class table) and multiplies them without
-// testing the values: the class is warp-uniform under the row map, so no
-// warp diverges or votes, and each row does its own multiply-adds only.
+// CLS (gate ops, k <= 3): each row walks only the terms of its local row
+// class (from the class table) and multiplies them without testing the
+// values: the class is warp-uniform under the row map, so no warp diverges
+// or votes, and each row does its own multiply-adds only. The FMAs per term
+// follow the op's KIND; for STORED_TERMS_HALF the half a term multiplies is
+// chosen with integer selects and a sign flip, never with a branch (a
+// branch around FP64 work is predicated by the compiler, and predicated-off
+// FP64 instructions still occupy the FP64 pipe). Measured, splitting a
+// complex entry into two half terms was slower than one 4-FMA term.
 //
 // Otherwise (raw ops): each row walks every diagonal in stored order, with
 // the warp-uniform skips of stored_mac. Threads past N keep running with
@@ -537,8 +559,9 @@ struct StoredDiags {
 // Both issue a diagonal's value and x loads together. (Issuing several
 // diagonals' loads before using any of them was measured slower: the extra
 // registers cost more occupancy than the shorter dependency chain gained.)
-// CPLX = false only for ops whose stored values are all real.
-template <typename R, int G, bool CPLX, bool CLS>
+// KIND = STORED_TERMS_REAL only for ops whose stored values are all real;
+// STORED_TERMS_HALF only with CLS.
+template <typename R, int G, int KIND, bool CLS>
 __global__ void __launch_bounds__(256)
 k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* __restrict__ offs,
               const int64_t* __restrict__ starts, const amp_t<R>* __restrict__ vals,
@@ -561,10 +584,13 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
     const int E = CLS ? sd.ecount : D;
     for (int e = 0; e < E; ++e) {
         A a[G], xv[G];
+        bool imag_half[G];
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            const int q = CLS ? int(sd.cls[cls[u]][e]) : e;
-            bool ok = row[u] >= 0 && q >= 0;
+            const int code = CLS ? int(sd.cls[cls[u]][e]) : (e << 1);
+            const int q = code >> 1;
+            imag_half[u] = (code & 1) != 0;
+            bool ok = row[u] >= 0 && code != 0xff;
             int64_t d = 0, p = 0, st = 0;
             if (ok) {
                 d = CLS || by_value ? sd.off[q] : offs[q];
@@ -584,15 +610,25 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
         }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
-            if (CLS) {
+            if (CLS && KIND == STORED_TERMS_REAL) {
                 acc[u].x = fma(a[u].x, xv[u].x, acc[u].x);
                 acc[u].y = fma(a[u].x, xv[u].y, acc[u].y);
-                if (CPLX) {
-                    acc[u].x = fma(-a[u].y, xv[u].y, acc[u].x);
-                    acc[u].y = fma(a[u].y, xv[u].x, acc[u].y);
-                }
+            } else if (CLS && KIND == STORED_TERMS_COMPLEX) {
+                acc[u].x = fma(a[u].x, xv[u].x, acc[u].x);
+                acc[u].x = fma(-a[u].y, xv[u].y, acc[u].x);
+                acc[u].y = fma(a[u].x, xv[u].y, acc[u].y);
+                acc[u].y = fma(a[u].y, xv[u].x, acc[u].y);
+            } else if (CLS) {
+                // real half: acc += re(a) (x.x, x.y); imaginary half:
+                // acc += im(a) (-x.y, x.x)
+                const bool h = imag_half[u];
+                const R m = h ? a[u].y : a[u].x;
+                const R x0 = flip_sign(h ? xv[u].y : xv[u].x, h);
+                const R x1 = h ? xv[u].x : xv[u].y;
+                acc[u].x = fma(m, x0, acc[u].x);
+                acc[u].y = fma(m, x1, acc[u].y);
             } else {
-                stored_mac<R, CPLX>(acc[u], a[u], xv[u]);
+                stored_mac<R, KIND != STORED_TERMS_REAL>(acc[u], a[u], xv[u]);
             }
         }
     }
@@ -655,33 +691,46 @@ static RowMap make_rowmap(const GateDesc& g, int n, int threads, int G) {
     return m;
 }
 
-// Class table of a gate op on k <= STORED_CLS_K targets (row map local
-// numbering): for each local row class c, the stored diagonals
-// d = off[c2] - off[c] present in the op, in stored order. Returns the sum
-// of the classes' counts, or -1 when the op takes the generic path (raw
+// Class table of a gate op on k <= STORED_CLS_K targets: for each local row
+// class c, one term per entry M[c][c2] != 0 (diagonal d = off[c2] - off[c]),
+// in stored order, and the op's term kind in *kind. *values_read (if not
+// NULL) gets the number of stored values the SpMV reads, N / 2^k x the
+// non-zero entries. Returns false when the op takes the generic path (raw
 // ops, k > STORED_CLS_K, more than STORED_PARAM_D diagonals).
-static int stored_class_table(const diaq_op_s* op, const RowMap& map, int D, StoredDiags* sd) {
-    if (op->op_class == DIAQ_CLASS_RAW || map.k < 1 || map.k > STORED_CLS_K || D > STORED_PARAM_D) return -1;
-    std::memset(sd->cls, -1, sizeof(sd->cls));
-    sd->ecount = 0;
+static bool stored_class_table(const diaq_op_s* op, const RowMap& map, int D, StoredDiags* sd, int* kind,
+                               int64_t* values_read) {
+    if (op->op_class == DIAQ_CLASS_RAW || map.k < 1 || map.k > STORED_CLS_K || D > STORED_PARAM_D) return false;
     const int K = 1 << map.k;
-    int total = 0;
+    bool any_imag = false, any_complex = false;
+    for (const cplx& m : op->gate.m) {
+        any_imag |= m.imag() != 0.0;
+        any_complex |= m.real() != 0.0 && m.imag() != 0.0;
+    }
+    *kind = any_complex ? STORED_TERMS_COMPLEX : any_imag ? STORED_TERMS_HALF : STORED_TERMS_REAL;
+    std::memset(sd->cls, 0xff, sizeof(sd->cls));
+    sd->ecount = 0;
+    int64_t entries = 0;
     for (int c = 0; c < K; ++c) {
         int e = 0;
         for (int q = 0; q < D; ++q)
             for (int c2 = 0; c2 < K; ++c2)
                 if (op->offsets[size_t(q)] == map.off[c2] - map.off[c]) {
-                    sd->cls[c][e++] = int8_t(q);
+                    const cplx m = op->gate.m[size_t(c) * K + c2];
+                    if (m.real() != 0.0 || m.imag() != 0.0) {
+                        const int h = *kind == STORED_TERMS_HALF && m.imag() != 0.0 ? 1 : 0;
+                        sd->cls[c][e++] = uint8_t((q << 1) | h);
+                        ++entries;
+                    }
                     break;
                 }
         sd->ecount = std::max(sd->ecount, e);
-        total += e;
     }
-    return total;
+    if (values_read) *values_read = (int64_t(1) << (op->n - map.k)) * entries;
+    return true;
 }
 
 template <typename R, int G>
-static void stored_launch(bool cplx, bool cls, dim3 grid, int threads, cudaStream_t s, const void* x, void* y,
+static void stored_launch(int kind, bool cls, dim3 grid, int threads, cudaStream_t s, const void* x, void* y,
                           int64_t N, int D, const diaq_op_s* op, const RowMap& map, const StoredDiags& sd) {
     using A = amp_t<R>;
     const A* xa = reinterpret_cast<const A*>(x);
@@ -689,17 +738,16 @@ static void stored_launch(bool cplx, bool cls, dim3 grid, int threads, cudaStrea
     const A* va = reinterpret_cast<const A*>(op->d_values);
     const int64_t* o = op->d_offsets;
     const int64_t* t = op->d_starts;
-    if (cls) {
-        if (cplx)
-            k_stored_spmv<R, G, true, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
-        else
-            k_stored_spmv<R, G, false, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
-    } else {
-        if (cplx)
-            k_stored_spmv<R, G, true, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
-        else
-            k_stored_spmv<R, G, false, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
-    }
+    if (cls && kind == STORED_TERMS_REAL)
+        k_stored_spmv<R, G, STORED_TERMS_REAL, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    else if (cls && kind == STORED_TERMS_HALF)
+        k_stored_spmv<R, G, STORED_TERMS_HALF, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    else if (cls)
+        k_stored_spmv<R, G, STORED_TERMS_COMPLEX, true><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    else if (kind == STORED_TERMS_REAL)
+        k_stored_spmv<R, G, STORED_TERMS_REAL, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
+    else
+        k_stored_spmv<R, G, STORED_TERMS_COMPLEX, false><<<grid, threads, 0, s>>>(xa, ya, N, D, o, t, va, map, sd);
 }
 
 diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStream_t s) {
@@ -724,14 +772,14 @@ diaq_status launch_stored(const diaq_op_s* op, const void* x, void* y, cudaStrea
         sd.off[q] = op->offsets[size_t(q)];
         sd.start[q] = op->starts[size_t(q)];
     }
-    const bool cls = stored_class_table(op, map, D, &sd) >= 0;
+    int kind = op->real_values ? STORED_TERMS_REAL : STORED_TERMS_COMPLEX;
+    const bool cls = stored_class_table(op, map, D, &sd, &kind, nullptr);
     DIAQ_PRELAUNCH("k_stored_spmv");
     const dim3 grid((unsigned)blocks);
-    const bool cplx = !op->real_values;
     if (op->dtype == DIAQ_C128)
-        stored_launch<double, G>(cplx, cls, grid, threads, s, x, y, N, D, op, map, sd);
+        stored_launch<double, G>(kind, cls, grid, threads, s, x, y, N, D, op, map, sd);
     else
-        stored_launch<float, G>(cplx, cls, grid, threads, s, x, y, N, D, op, map, sd);
+        stored_launch<float, G>(kind, cls, grid, threads, s, x, y, N, D, op, map, sd);
     DIAQ_CUDA(cudaGetLastError());
     return DIAQ_OK;
 }
@@ -742,9 +790,10 @@ int64_t stored_values_read(const diaq_op_s* op) {
     const RowMap map = make_rowmap(op->gate, op->n, STORED_THREADS, STORED_G);
     StoredDiags sd;
     std::memset(&sd, 0, sizeof(sd));
-    const int total = stored_class_table(op, map, D, &sd);
-    if (total < 0) return op->stored_elems;
-    return (int64_t(1) << (op->n - map.k)) * int64_t(total);
+    int kind = 0;
+    int64_t values_read = 0;
+    if (!stored_class_table(op, map, D, &sd, &kind, &values_read)) return op->stored_elems;
+    return values_read;
 }
 
 diaq_status launch_materialise(diaq_op_s* op, cudaStream_t s) {

@@ -81,6 +81,27 @@ def test_stored_variant(api, dtype, k):
             _check(api, n, t, synth.random_gate(k, RNG, kind), dtype, "stored")
 
 
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_stored_real_or_imaginary_entries(api, dtype):
+    """Stored gate ops whose entries are each real or purely imaginary (RX,
+    Y, iSWAP and products of such) take the kernel that multiplies one half
+    of each value; ops with a complex entry and all-real ops the others."""
+    rx = np.array([[math.cos(0.35), -1j * math.sin(0.35)], [-1j * math.sin(0.35), math.cos(0.35)]])
+    y = np.array([[0, -1j], [1j, 0]])
+    x = np.array([[0, 1], [1, 0]], dtype=complex)
+    iswap = np.array([[1, 0, 0, 0], [0, 0, 1j, 0], [0, 1j, 0, 0], [0, 0, 0, 1]])
+    gates = [rx, y, iswap, np.kron(y, rx), np.kron(np.kron(y, x), rx), np.kron(rx, iswap)]
+    n = 10
+    for m in gates:
+        assert np.all((m.real == 0) | (m.imag == 0))
+        k = int(math.log2(m.shape[0]))
+        for _ in range(2):
+            t = [int(q) for q in RNG.choice(n, size=k, replace=False)]
+            _check(api, n, t, m, dtype, "stored")
+        op = api.build(synth.Gate(tuple(range(k)), m), n, dtype=dtype, variant="stored")
+        assert not op.info()["real_values"]
+
+
 def test_stored_diagonals_match_oracle(api):
     """Builder (stored): full-system offsets and every diagonal's values."""
     for n, k in ((5, 1), (6, 2), (7, 3)):

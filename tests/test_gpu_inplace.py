@@ -102,6 +102,12 @@ def test_apply_bytes_accounting(api):
         st = api.build(synth.Gate((q,), synth.H), n, variant="stored")
         assert st.info()["stored_bytes"] == 16 * (3 * N - 2 * (1 << q))
         assert st.apply_bytes() == 2 * N * 16 + 2 * N * 16
+    # zero entries are not read: SWAP and a controlled phase one entry per
+    # row, RX two
+    for g, per_row in ((synth.Gate((2, 8), synth.SWAP), 1), (synth.Gate((2, 8), synth.cphase(0.4)), 1),
+                       (synth.Gate((6,), np.array([[0.8, -0.6j], [-0.6j, 0.8]])), 2)):
+        st = api.build(g, n, variant="stored")
+        assert st.apply_bytes() == 2 * N * 16 + per_row * N * 16, g.name
     # a dense two-qubit gate: four entries per row; raw ops read every value
     st = api.build(synth.Gate((4, 9), synth.haar_u2(RNG, 4)), n, variant="stored")
     assert st.apply_bytes() == 2 * N * 16 + 4 * N * 16
