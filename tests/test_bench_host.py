@@ -1,0 +1,112 @@
+"""Host logic of bench.py's measurement contract, on CPU: the clock record
+taken during the timed region (median SM clock, max clock, throttle reasons
+seen), the whole-job throughput, the peak used as the roofline denominator,
+and the rule that a committed DRAM-traffic figure is reported only while the
+kernel source it was taken on is unchanged."""
+
+import json
+import os
+import shutil
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _DoneProc:
+    """Stands in for the finished nvidia-smi process."""
+
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+    def kill(self):
+        pass
+
+
+def _sampler(lines):
+    s = bench.ClockSampler(0)
+    s.proc = _DoneProc()
+    s.lines = list(lines)
+    return s
+
+
+def test_clock_record_median_max_and_reasons():
+    lines = [
+        "2070, 2070, 900.5, Not Active, Not Active, Not Active, Not Active",
+        "2055, 2070, 1300.0, Not Active, Not Active, Not Active, Active",
+        "2070, 2070, 1350.2, Not Active, Not Active, Not Active, Active",
+        "1980, 2070, 1390.0, Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, 10, Not Active, Not Active, Not Active, Not Active",
+    ]
+    rec = _sampler(lines).stop()
+    assert rec["samples"] == 4
+    assert rec["sm_mhz"] == pytest.approx(2062.5)  # median of 2070, 2055, 2070, 1980
+    assert rec["sm_max_mhz"] == 2070
+    assert rec["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_record_without_samples_or_tool():
+    rec = _sampler([]).stop()
+    assert rec["sm_mhz"] is None and rec["samples"] == 0 and rec["reasons"] == []
+    s = bench.ClockSampler(0)  # never started: no nvidia-smi
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_whole_job_throughput_counts_every_rank_over_the_slowest_time():
+    # one rank: 8 GB in 1 s
+    assert bench.aggregate(8e9, 1000.0, 1) == pytest.approx(8.0)
+    # four replicas, the slowest took 2 s: 4 x 8 GB / 2 s
+    assert bench.aggregate(8e9, 2000.0, 4) == pytest.approx(16.0)
+    assert bench.reduce_max(3.5, 1) == 3.5
+
+
+def _fake_root(tmp_path):
+    csrc = tmp_path / "paper_2405_01250_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("apply.cu", "common.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_2405_01250_gb300", "csrc", f), csrc / f)
+    (tmp_path / "profiles").mkdir()
+    return tmp_path
+
+
+def test_traffic_reported_only_for_the_source_it_was_taken_on(tmp_path, monkeypatch):
+    root = _fake_root(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench._traffic("cp_c128") is None  # no record at all
+    h = bench._kernel_source_hash()
+    rec = {"cp_c128": {"bytes_per_launch": 8.3e9, "source_hash": h}}
+    (root / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    assert bench._traffic("cp_c128") == 8.3e9
+    assert bench._traffic("other_kernel") is None
+    # any change to the kernel source invalidates the figure
+    with open(root / "paper_2405_01250_gb300" / "csrc" / "apply.cu", "a") as f:
+        f.write("\n// edited\n")
+    assert bench._kernel_source_hash() != h
+    assert bench._traffic("cp_c128") is None
+
+
+def test_committed_traffic_record_is_well_formed():
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        d = json.load(f)
+    e = d["cp_c128"]
+    assert len(e["source_hash"]) == 16
+    # traffic is a DRAM measurement of one 28-qubit launch: close to, and not
+    # far above, the algorithmic 2 x 2^28 x 16 bytes
+    alg = 2 * (1 << 28) * 16
+    assert 0.9 * alg <= e["bytes_per_launch"] <= 1.1 * alg
+    assert os.path.exists(os.path.join(ROOT, e["profile"]))
+
+
+def test_peak_is_measured_when_present_else_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench._peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6779.0, "bf16_tflops": 1900.0}))
+    assert bench._peaks() == (6779.0, "measured")
