@@ -193,6 +193,37 @@ def test_gate_diaq_matches_dense_extraction(n, k):
             np.testing.assert_allclose(a, b, atol=1e-15)
 
 
+@pytest.mark.parametrize("n,k", [(5, 1), (6, 2), (7, 3), (8, 3)])
+def test_row_class_structure_of_gate_diagonals(n, k):
+    """A row i whose target bits are c (t[0] most significant) holds, in the
+    DiaQ form of a gate, exactly the entries M[c][c2] != 0, on the diagonals
+    d = off(c2) - off(c) with off(c) = sum_a bit_a(c) 2^t[a], and zeros on
+    every other stored diagonal. (A stored SpMV may therefore give each row
+    only the terms of its class, Section II-C's embedding.)"""
+    for kind in ("dense", "sparse", "perm", "diag"):
+        targets = [int(t) for t in RNG.choice(n, size=k, replace=False)]
+        m = synth.random_gate(k, RNG, kind)
+        offs, vals = oracle.gate_diaq(n, targets, m)
+        K = 1 << k
+
+        def off(c):
+            return sum(((c >> (k - 1 - a)) & 1) << targets[a] for a in range(k))
+
+        def local(i):
+            return sum(((i >> targets[a]) & 1) << (k - 1 - a) for a in range(k))
+
+        for i in range(1 << n):
+            c = local(i)
+            want = {off(c2) - off(c): m[c, c2] for c2 in range(K) if m[c, c2] != 0}
+            got = {}
+            for d, v in zip(offs.tolist(), vals):
+                if 0 <= i + d < (1 << n):
+                    a = v[i - max(0, -d)]
+                    if a != 0:
+                        got[d] = a
+            assert got == want, (i, c)
+
+
 def test_diaq_matvec_matches_dense():
     N = 37  # not a power of two: the DiaQ product is defined for any square matrix
     A = np.zeros((N, N), dtype=np.complex128)
