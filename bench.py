@@ -68,6 +68,17 @@ def reduce_max(value: float, world: int) -> float:
     return float(t.item())
 
 
+def qft_config(n: int, n_ops: int, world: int) -> dict:
+    """The workload both arms report: one step is the QFT-n circuit's n_ops
+    DiaQ ops in complex128 plus the FP64 norm (the reference arm times a
+    bounded sample of those ops per step and says so in its cpu_baseline)."""
+    state = (1 << n) * 16
+    return {"workload": f"qft-{n} complex128, on-the-fly DiaQ apply of {n_ops} ops + FP64 norm",
+            "qubits": n, "ops_per_step": n_ops, "state_bytes": state,
+            "l2": f"inputs larger than L2 ({state / 2**30:g} GiB state vs 129 MB L2); no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def aggregate(bytes_per_rank: float, ms_max: float, world: int) -> float:
     """Whole-job GB/s: every rank runs the same replica, so the units
     processed are world x one rank's, over the slowest rank's time."""
@@ -321,10 +332,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 (f64 arithmetic)", "data": "synthetic",
-        "config": {"workload": f"qft-{n} complex128, on-the-fly DiaQ apply of {len(ops)} ops + FP64 norm",
-                   "qubits": n, "ops_per_step": len(ops), "state_bytes": N * 16,
-                   "l2": "inputs larger than L2 (4 GiB state vs 129 MB L2); no flush", "parallelism":
-                   "replicas" if world > 1 else "single GPU"},
+        "config": qft_config(n, len(ops), world),
         "gates_per_s": world * len(ops) * args.steps / (ms_total / 1e3),
         "apply_only_gbs": len(ops) * bytes_op / (apply_ms / 1e3) / 1e9,
         "per_class": per_class,
@@ -686,9 +694,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128 (f64 arithmetic)", "data": "synthetic",
-        "config": {"workload": f"qft-{n} complex128, FP64 CPU oracle, {per_step} ops per step", "qubits": n},
+        "config": qft_config(n, len(circ.gates), world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                         "sample": f"{per_step} qft-{n} ops per step"},
+                         "sample": f"{per_step} of the {len(circ.gates)} qft-{n} ops per step, FP64 oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

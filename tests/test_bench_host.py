@@ -110,3 +110,22 @@ def test_peak_is_measured_when_present_else_fallback(tmp_path, monkeypatch):
     assert bench._peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6779.0, "bf16_tflops": 1900.0}))
     assert bench._peaks() == (6779.0, "measured")
+
+
+def test_reference_arm_reports_the_same_config_as_the_gpu_arm():
+    """The oracle arm runs a bounded sample of the same QFT workload and
+    prints the GPU arm's config (both come from qft_config); its sampling is
+    stated in cpu_baseline."""
+    import argparse
+
+    import synth
+    args = argparse.Namespace(qubits=10, ref_gates=3, steps=1, warmup=0)
+    line = bench.run_reference(args, 0, 1)
+    circ, _ = synth.qft(10, seed=0)
+    assert line["config"] == bench.qft_config(10, len(circ.gates), 1)
+    assert line["config"]["ops_per_step"] == 10 + 45 + 5
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["higher_is_better"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and "3 of the 60" in line["cpu_baseline"]["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert bench.qft_config(28, 420, 1)["l2"] == "inputs larger than L2 (4 GiB state vs 129 MB L2); no flush"
+    assert bench.qft_config(28, 420, 4)["parallelism"] == "replicas"
