@@ -224,6 +224,39 @@ def test_row_class_structure_of_gate_diagonals(n, k):
             assert got == want, (i, c)
 
 
+def test_embed_matches_kron_with_swaps():
+    """Gate matrices on a union target space (union[0] most significant),
+    against numpy.kron: adjacent targets are I (x) M (x) I; non-adjacent or
+    reversed targets are the adjacent case conjugated by SWAPs."""
+    I2 = np.eye(2)
+    swap = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=complex)
+    u = [7, 4, 1]  # qubit labels; bit 2, 1, 0 of the local index
+    m1 = synth.random_gate(1, RNG, "dense")
+    m2 = synth.random_gate(2, RNG, "dense")
+    np.testing.assert_allclose(oracle.embed(u, [4], m1), np.kron(np.kron(I2, m1), I2), atol=1e-15)
+    np.testing.assert_allclose(oracle.embed(u, [7], m1), np.kron(m1, np.eye(4)), atol=1e-15)
+    np.testing.assert_allclose(oracle.embed(u, [7, 4], m2), np.kron(m2, I2), atol=1e-15)
+    np.testing.assert_allclose(oracle.embed(u, [4, 1], m2), np.kron(I2, m2), atol=1e-15)
+    # targets (7, 1): move qubit 1 next to 7 with a SWAP of the two low bits
+    s01 = np.kron(I2, swap)
+    np.testing.assert_allclose(oracle.embed(u, [7, 1], m2), s01 @ np.kron(m2, I2) @ s01, atol=1e-15)
+    # reversed order (4, 7): the matrix with its two bits exchanged
+    np.testing.assert_allclose(oracle.embed(u, [4, 7], m2), np.kron(swap @ m2 @ swap, I2), atol=1e-15)
+
+
+def test_fidelity_and_error_helpers():
+    zero = np.array([1, 0], dtype=complex)
+    plus = np.array([1, 1], dtype=complex) / math.sqrt(2)
+    one = np.array([0, 1], dtype=complex)
+    assert oracle.fidelity(zero, zero) == pytest.approx(1.0)
+    assert oracle.fidelity(zero, one) == 0.0
+    assert oracle.fidelity(zero, plus) == pytest.approx(0.5)
+    assert oracle.fidelity(3j * plus, plus) == pytest.approx(1.0)  # global phase and scale drop out
+    assert oracle.max_abs_err(zero, plus) == pytest.approx(1 / math.sqrt(2))  # |0 - 1/sqrt(2)| of amplitude 1
+    assert oracle.max_abs_err(np.array([1 + 1j, 2]), np.array([1, 2])) == pytest.approx(1.0)
+    assert oracle.max_abs_err(np.array([]), np.array([])) == 0.0
+
+
 def test_diaq_matvec_matches_dense():
     N = 37  # not a power of two: the DiaQ product is defined for any square matrix
     A = np.zeros((N, N), dtype=np.complex128)
