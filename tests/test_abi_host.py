@@ -151,3 +151,40 @@ def test_device_entry_points_fail_loudly_without_gpu(api):
     from paper_2405_01250_gb300._native import DiaqError
     with pytest.raises(DiaqError):
         api.build(synth.Gate((0,), synth.H), 4, stream=0)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of include/diaq.h has the same size and field offsets in
+    C (gcc, from the header itself) as in the ctypes binding."""
+    import subprocess
+
+    from paper_2405_01250_gb300 import _native as N
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = open(os.path.join(root, "include", "diaq.h")).read()
+    structs = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(diaq_\w+);", hdr, re.S):
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        fields = re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
+        structs[name] = fields
+    assert set(structs) == {"diaq_gate", "diaq_op_info", "diaq_plan_tuning", "diaq_apply_tuning",
+                            "diaq_fusion_tuning", "diaq_batch_tuning"}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "diaq.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    c_layout = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        c_layout[(a, b)] = int(v)
+    for name, fields in structs.items():
+        cls = getattr(N, name)
+        assert [f[0] for f in cls._fields_] == fields, name
+        assert ctypes.sizeof(cls) == c_layout[(name, "size")], name
+        for f in fields:
+            assert getattr(cls, f).offset == c_layout[(name, f)], (name, f)
