@@ -188,3 +188,48 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert ctypes.sizeof(cls) == c_layout[(name, "size")], name
         for f in fields:
             assert getattr(cls, f).offset == c_layout[(name, f)], (name, f)
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the header declares has a binding entry with the same
+    number of arguments, each of the same kind (32-bit integer or enum,
+    64-bit integer, double, pointer or handle), and the same return kind."""
+    import ctypes as C
+
+    from paper_2405_01250_gb300 import _native as N
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    hdr = re.sub(r"/\*.*?\*/", "", open(os.path.join(root, "include", "diaq.h")).read(), flags=re.S)
+    protos = re.findall(r"(diaq_status|const char\s*\*)\s*(diaq_\w+)\s*\(([^;]*?)\)\s*;", hdr, re.S)
+    assert len(protos) == len(N.SIGNATURES)
+
+    def c_kind(decl):
+        decl = " ".join(decl.split())
+        if "*" in decl or re.match(r"(const )?diaq_\w+_t\b", decl):
+            return "ptr"
+        base = decl.split()[0] if not decl.startswith("const ") else decl.split()[1]
+        if base in ("int32_t", "int", "diaq_dtype", "diaq_variant"):
+            return "i32"
+        if base == "int64_t":
+            return "i64"
+        if base == "double":
+            return "f64"
+        raise AssertionError(f"unclassified C parameter type: {decl}")
+
+    def py_kind(t):
+        if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+            return "ptr"
+        if C.sizeof(t) == 4 and t in (C.c_int32, C.c_int):
+            return "i32"
+        if t is C.c_int64:
+            return "i64"
+        if t is C.c_double:
+            return "f64"
+        raise AssertionError(f"unclassified ctypes type: {t}")
+
+    for ret, name, params in protos:
+        assert name in N.SIGNATURES, name
+        res, args = N.SIGNATURES[name]
+        params = params.strip()
+        kinds = [] if params in ("", "void") else [c_kind(p) for p in params.split(",")]
+        assert [py_kind(a) for a in args] == kinds, name
+        assert (res is C.c_char_p) == ret.startswith("const char"), name
