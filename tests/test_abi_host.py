@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(api):
     assert "sm_103a" in api.version()
 
 
-@pytest.mark.parametrize("n,k", [(3, 1), (6, 2), (8, 3), (5, 2)])
+@pytest.mark.parametrize("n,k", [(3, 1), (6, 2), (8, 3), (5, 2), (7, 4), (8, 5), (8, 6)])
 def test_gate_offsets_match_oracle(api, n, k):
     for kind in ("dense", "sparse", "perm", "diag", "monomial"):
         t = [int(q) for q in RNG.choice(n, size=k, replace=False)]
