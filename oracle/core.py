@@ -17,8 +17,12 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   (>= 99.8 %, Section III-A), equality with sequential application.
 * expect, norm2, apply_pauli_sum  pinned: basis-state and |+> special cases,
   GHZ correlators, dense Pauli matrices (<= 8 qubits).
-* energy, param_shift_grad ..... pinned: closed-form single-rotation energies,
-  central finite differences, dense-matrix derivative.
+* energy, param_shift_grad ..... pinned: closed-form single-rotation energies
+  (RX, RY, RZ), central finite differences, dense-matrix derivative.
+* gate_matrix, pauli_local ..... pinned: scipy.linalg.expm of the full-system
+  Pauli operator assembled from X/Z masks, for one- to three-letter
+  generators (asymmetric ones included) on non-adjacent and reversed
+  targets; a reversed Kronecker order and a flipped sine sign are rejected.
 """
 
 from __future__ import annotations

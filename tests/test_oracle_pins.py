@@ -398,15 +398,126 @@ def test_single_rotation_closed_forms(gen, obs_x, obs_z):
             assert abs(e - math.sin(t)) < 1e-15 and abs(de - math.cos(t)) < 1e-15
 
 
-def test_param_shift_vs_fd_and_dense_derivative():
-    circ = synth.ansatz(n=4, layers=2, seed=5)
-    obs = synth.ansatz_observable(4)
-    psi0 = synth.basis_state(4, 0)
+def test_z_rotation_closed_form():
+    """RZ(t)|+> = (e^{-it/2}|0> + e^{it/2}|1>)/sqrt(2): <X> = cos t, <Y> = sin t,
+    and the parameter-shift derivatives -sin t, cos t."""
+    plus = np.array([1, 1], dtype=np.complex128) / math.sqrt(2)
+    ox = synth.Observable(np.array([1], np.uint64), np.array([0], np.uint64), np.array([1.0]))
+    oy = synth.Observable(np.array([1], np.uint64), np.array([1], np.uint64), np.array([1.0]))
+    for t in (0.0, 0.4, 2.2, 5.1):
+        circ = _single_rotation("Z", t)
+        assert abs(oracle.energy(circ, ox, plus) - math.cos(t)) < 1e-15
+        assert abs(oracle.energy(circ, oy, plus) - math.sin(t)) < 1e-15
+        assert abs(oracle.param_shift_grad(circ, ox, plus)[0] + math.sin(t)) < 1e-15
+        assert abs(oracle.param_shift_grad(circ, oy, plus)[0] - math.cos(t)) < 1e-15
+
+
+def _masks_of(gen, targets):
+    """(xmask, zmask) of a Pauli string whose letter a acts on qubit targets[a]."""
+    return synth.pauli_masks({q: ch for q, ch in zip(targets, gen)})
+
+
+# Parametric generators on non-adjacent and reversed targets of a 6-qubit
+# register, including strings whose letters differ (so a reversed Kronecker
+# order changes the operator).
+ROTATIONS = [("Z", (4,)), ("X", (1,)), ("Y", (5,)), ("XY", (5, 1)), ("ZX", (0, 3)), ("YZ", (2, 4)),
+             ("ZXY", (5, 0, 3)), ("XZ", (1, 0)), ("YX", (3, 5)), ("ZYX", (1, 4, 2))]
+
+
+def _rotation_pin_error(gen, targets, a, n=6, seed=0):
+    """max |oracle - reference| for exp(-i a/2 P) on `targets`, where the
+    reference is scipy's matrix exponential of the full-system Pauli
+    operator assembled from masks by dense_pauli (numpy.kron over qubits,
+    no use of the oracle's pauli_local): once for the gate's local matrix
+    (the operator on a k-qubit register, t[0] = its most significant bit)
+    and once for its action on a random state."""
+    from scipy.linalg import expm
+    k = len(targets)
+    g = synth.Gate(tuple(targets), None, param=0, gen=gen)
+    th = np.array([a])
+    m = oracle.gate_matrix(g, th)
+    # local register: letter a of gen on local bit k-1-a
+    lx, lz = _masks_of(gen, [k - 1 - i for i in range(k)])
+    m_ref = expm(-0.5j * a * dense_pauli(k, lx, lz))
+    err_local = float(np.max(np.abs(m - m_ref)))
+    xm, zm = _masks_of(gen, targets)
+    U = expm(-0.5j * a * dense_pauli(n, xm, zm))
+    psi = synth.random_state(n, np.random.default_rng(seed))
+    err_apply = float(np.max(np.abs(oracle.apply_gate(psi, list(targets), m) - U @ psi)))
+    err_tensor = float(np.max(np.abs(dense_apply_tensor(psi, list(targets), m) - U @ psi)))
+    return max(err_local, err_apply, err_tensor)
+
+
+@pytest.mark.parametrize("gen,targets", ROTATIONS)
+def test_rotation_matrices_match_expm_of_dense_pauli(gen, targets):
+    """Reading R12 (the paper has no rotations): exp(-i a/2 P) for Pauli
+    strings on arbitrary target placements, against scipy.linalg.expm."""
+    for a in (0.37, 1.9, -2.6, 5.5):
+        assert _rotation_pin_error(gen, targets, a) < 1e-13
+
+
+def test_rotation_pin_rejects_reversed_kronecker_order(monkeypatch):
+    """Planted mistake: a pauli_local that takes the Kronecker factors in
+    reverse order. The expm pin rejects it for every string whose letters
+    differ, and (rightly) cannot tell for palindromes."""
+    import oracle.core as core
+    good = core.pauli_local
+
+    def reversed_order(gen):
+        return good(gen[::-1])
+
+    monkeypatch.setattr(core, "pauli_local", reversed_order)
+    for gen, targets in ROTATIONS:
+        err = _rotation_pin_error(gen, targets, 1.3)
+        if gen != gen[::-1]:
+            assert err > 1e-2, (gen, err)
+        else:
+            assert err < 1e-13
+    # a dropped sign of the sine term is rejected for every generator
+    monkeypatch.setattr(core, "pauli_local", good)
+    monkeypatch.setattr(core, "math", _NegSinMath())
+    for gen, targets in ROTATIONS:
+        assert _rotation_pin_error(gen, targets, 1.3) > 1e-2, gen
+
+
+class _NegSinMath:
+    """math with sin negated (a planted sign error in exp(-i a/2 P))."""
+
+    def __getattr__(self, name):
+        return getattr(math, name)
+
+    @staticmethod
+    def sin(x):
+        return -math.sin(x)
+
+
+def _multi_letter_circuit(n=4, seed=9):
+    """A small circuit of fixed gates and rotations with multi-letter,
+    asymmetric generators on reversed and non-adjacent targets."""
+    rng = np.random.default_rng(seed)
+    gates = [synth.Gate((0,), synth.H), synth.Gate((2,), synth.H),
+             synth.Gate((3, 1), None, param=0, gen="XY"),
+             synth.Gate((0, 2), None, param=1, gen="ZX", scale=0.5),
+             synth.Gate((1, 3), synth.random_gate(2, rng, "dense")),
+             synth.Gate((2, 0, 3), None, param=2, gen="YZX"),
+             synth.Gate((1,), None, param=0, gen="Z", scale=-1.5)]
+    return synth.Circuit(n, gates, theta=rng.uniform(0, 2 * math.pi, size=3))
+
+
+@pytest.mark.parametrize("which", ["ansatz", "multi_letter"])
+def test_param_shift_vs_fd_and_dense_derivative(which):
+    n = 4
+    if which == "ansatz":
+        circ = synth.ansatz(n=n, layers=2, seed=5)
+    else:
+        circ = _multi_letter_circuit(n)
+    obs = synth.ansatz_observable(n)
+    psi0 = synth.basis_state(n, 0)
     g_ps = oracle.param_shift_grad(circ, obs, psi0)
     g_fd = oracle.fd_grad(circ, obs, psi0, h=1e-4)
     assert np.max(np.abs(g_ps - g_fd)) < 1e-6
-    # dense derivative: dU/da = -i/2 P U for each occurrence, full matrices
-    n = 4
+    # dense derivative: dU/da = -i/2 P U for each occurrence, full matrices,
+    # with P the full-system Pauli operator assembled from masks
     N = 1 << n
     Hm = sum(c * dense_pauli(n, int(x), int(z)) for x, z, c in zip(obs.xmask, obs.zmask, obs.coeff))
 
@@ -419,7 +530,7 @@ def test_param_shift_vs_fd_and_dense_derivative():
     for i, g in enumerate(circ.gates):
         if not g.parametric:
             continue
-        P = full(synth.Gate(g.targets, oracle.pauli_local(g.gen)), None)
+        P = dense_pauli(n, *_masks_of(g.gen, g.targets))
         U = np.eye(N, dtype=complex)
         dU = np.eye(N, dtype=complex)
         for j, M in enumerate(mats):
