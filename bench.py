@@ -731,6 +731,13 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    launched = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus != launched:
+        # one process per GPU: N GPUs need N ranks (torchrun --nproc-per-node N)
+        print(f"bench.py --gpus {args.gpus} needs {args.gpus} ranks, but WORLD_SIZE is {launched}: launch it as "
+              f"python -m torch.distributed.run --nproc-per-node {args.gpus} bench.py --gpus {args.gpus} ...",
+              file=sys.stderr)
+        sys.exit(2)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -560,14 +560,18 @@ diaq_status diaq_debug_inject_alloc_failure(int32_t after);
  * not pay for allocation - and keeps its partial sums in a fixed array
  * compiled into the library instead.
  *
+ * It runs the same two kernels on the same grid as diaq_norm, so the two
+ * return the same bits on the same device.
+ *
  * Limit: the reduction uses min(ceil(N / 1024), 8 x SM count) blocks and
  * needs one double per block plus one; if that exceeds
  * DIAQ_NOALLOC_SCRATCH_DOUBLES the call returns DIAQ_ERR_UNSUPPORTED
  * (only on devices with more than 511 SMs).
  *
- * Set-up: the first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Sharing: all calls on a device use the same
+ * Set-up: every call looks up the array's device address in the current
+ * context (cudaGetSymbolAddress, with the state's device current); the first
+ * call on a device also loads the library's device code there, so make that
+ * first call before any stream capture. Sharing: all calls on a device use the same
  * array, which keeps the last call's contents; every slot a call reads it
  * has written itself, so nothing needs clearing, but calls whose work
  * overlaps on the GPU (different streams, or host threads racing on one

@@ -165,6 +165,12 @@ diaq_status run_expect(const void* psi, int n, diaq_dtype dt, const PauliGroups&
 diaq_status run_pauli_apply(const void* psi, void* lam, int n, diaq_dtype dt, const PauliGroups& pg,
                             cudaStream_t s);
 diaq_status run_norm(const void* psi, int n, diaq_dtype dt, double* out, cudaStream_t s);
+// The two kernels of the norm on caller-provided scratch: the block partials
+// in scratch[0, norm_partials(n)) and the total in scratch[norm_partials(n)].
+// diaq_norm and diaq_norm_noalloc both run exactly this (same grid, same
+// per-thread order and block tree), so they return the same bits.
+int norm_partials(int n);
+diaq_status launch_norm(const void* psi, int n, diaq_dtype dt, double* scratch, cudaStream_t s);
 
 // Adjoint reverse step for one gate: optional gradient partial
 // Im <lam|P|psi> into partial[blockIdx] and, then, psi <- U^dag psi,

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -22,13 +23,23 @@
 
 namespace diaq {
 
+// SM count of the current device, looked up once per device ordinal (it
+// does not change while the process runs, whatever happens to contexts).
 static int sm_count() {
-    static int sms = 0;
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> cache[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    if (dev >= kMaxDevices) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }
+    int sms = cache[dev].load(std::memory_order_relaxed);
     if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 1;
+        cache[dev].store(sms, std::memory_order_relaxed);
     }
     return sms;
 }
@@ -64,41 +75,49 @@ diaq_status launch_sum_rows(const double* partials, int rows, int cols, double* 
 }
 
 // ---------------------------------------------------------------------------
-// Norm: sum |psi_i|^2.
+// Norm: sum |psi_i|^2. complex128 accumulates in FP64; complex64 forms each
+// |psi_i|^2 in FP32 and sums a thread's share with Kahan compensation
+// (Acc<float>), so the FP64 pipe is used only from the block sum on.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_norm(const amp_t<R>* __restrict__ psi, int64_t N, double* part) {
     __shared__ double warps[32];
-    double acc = 0.0;
+    Acc<R> acc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const amp_t<R> v = ld_stream(psi + i);
-        if constexpr (sizeof(R) == 8) {
-            acc = fma(double(v.x), double(v.x), acc);
-            acc = fma(double(v.y), double(v.y), acc);
-        } else {
-            acc += double(fmaf(v.x, v.x, v.y * v.y));
-        }
+        acc.add_dot(v.x, v.x, v.y, v.y);
     }
-    acc = block_sum(acc, warps);
-    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    const double t = block_sum(acc.value(), warps);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+int norm_partials(int n) { return reduce_blocks((int64_t(1) << n) / 4); }
+
+diaq_status launch_norm(const void* psi, int n, diaq_dtype dt, double* scratch, cudaStream_t s) {
+    const int64_t N = int64_t(1) << n;
+    const int P = norm_partials(n);
+    DIAQ_PRELAUNCH("k_norm");
+    if (dt == DIAQ_C128)
+        k_norm<double><<<P, 256, 0, s>>>(reinterpret_cast<const double2*>(psi), N, scratch);
+    else
+        k_norm<float><<<P, 256, 0, s>>>(reinterpret_cast<const float2*>(psi), N, scratch);
+    DIAQ_CUDA(cudaGetLastError());
+    return launch_sum_rows(scratch, 1, P, scratch + P, s);
 }
 
 diaq_status run_norm(const void* psi, int n, diaq_dtype dt, double* out, cudaStream_t s) {
-    const int64_t N = int64_t(1) << n;
-    const int P = reduce_blocks(N / 4);
+    const int P = norm_partials(n);
     double* d = nullptr;
     cudaError_t e = cudaMallocAsync((void**)&d, sizeof(double) * (P + 1), s);
     if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(norm partials): %s", cudaGetErrorString(e));
-    DIAQ_PRELAUNCH("k_norm");
-    if (dt == DIAQ_C128)
-        k_norm<double><<<P, 256, 0, s>>>(reinterpret_cast<const double2*>(psi), N, d);
-    else
-        k_norm<float><<<P, 256, 0, s>>>(reinterpret_cast<const float2*>(psi), N, d);
-    DIAQ_CUDA(cudaGetLastError());
-    DIAQ_TRY(launch_sum_rows(d, 1, P, d + P, s));
-    DIAQ_CUDA(cudaMemcpyAsync(out, d + P, sizeof(double), cudaMemcpyDeviceToHost, s));
-    DIAQ_CUDA(cudaFreeAsync(d, s));
+    diaq_status st = launch_norm(psi, n, dt, d, s);
+    if (st == DIAQ_OK) {
+        e = cudaMemcpyAsync(out, d + P, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync(norm)");
+    }
+    cudaFreeAsync(d, s);
+    if (st != DIAQ_OK) return st;
     DIAQ_CUDA(cudaStreamSynchronize(s));
     return DIAQ_OK;
 }

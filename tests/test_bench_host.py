@@ -129,3 +129,18 @@ def test_reference_arm_reports_the_same_config_as_the_gpu_arm():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert bench.qft_config(28, 420, 1)["l2"] == "inputs larger than L2 (4 GiB state vs 129 MB L2); no flush"
     assert bench.qft_config(28, 420, 4)["parallelism"] == "replicas"
+
+
+def test_gpus_flag_must_match_the_launched_ranks():
+    """bench.py --gpus N runs one rank per GPU: without N ranks (WORLD_SIZE)
+    it refuses, before any GPU work, instead of reporting one replica."""
+    import subprocess
+    env = dict(os.environ)
+    env.pop("WORLD_SIZE", None)
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "4", "--steps", "1"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert p.returncode == 2 and "needs 4 ranks" in p.stderr
+    env["WORLD_SIZE"] = "2"
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "1", "--impl", "reference"],
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert p.returncode == 2 and "WORLD_SIZE is 2" in p.stderr
