@@ -36,3 +36,35 @@ def qft_amplitudes(n: int, j: int, ks: np.ndarray) -> np.ndarray:
     ks = np.asarray(ks, dtype=np.uint64)
     ph = ((np.uint64(j) * ks) % np.uint64(N)).astype(np.float64) / N
     return np.exp(2j * np.pi * ph) / math.sqrt(N)
+
+
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def c64_gate_bound(k: int) -> float:
+    """Worst-case growth of the 2-norm error vector, in units of FP32's unit
+    roundoff u, when a k-qubit unitary M (stored in FP32) is applied in
+    complex64 to a state of 2-norm 1. Each output row sums 2^k complex
+    products, i.e. 2^(k+1) real products per real component, so its rounding
+    error is at most gamma_{2^(k+1)+1} * (|M||x|)_r; rounding the entries of
+    M to FP32 adds u |M| |x| (sqrt(2) for the two parts). Over a group of 2^k
+    rows the 2-norm of |M||x| is at most ||M||_F ||x|| = 2^(k/2) ||x||, and
+    the groups are orthogonal, so the whole state's error grows by at most
+    ((2^(k+1) + 1) * 1.01 + sqrt(2)) * 2^(k/2) * u."""
+    return ((2 ** (k + 1) + 1) * 1.01 + math.sqrt(2.0)) * 2.0 ** (k / 2.0)
+
+
+def c64_circuit_bound(ks) -> float:
+    """Bound B on ||psi_c64 - psi_exact||_2 (hence on the largest amplitude
+    error) for a circuit of unitary gates on k_i qubits applied in complex64
+    to a unit state: the error of gate l is carried forward unchanged in norm
+    by the later (unitary) gates, so the per-gate bounds add. Gates whose
+    entries are all 0 or +-1 (CZ, CNOT, SWAP) are exact in FP32 and pass
+    k = 0 here."""
+    return 1.01 * U32 * sum(c64_gate_bound(k) for k in ks if k > 0)
+
+
+def fidelity_loss_bound(b: float) -> float:
+    """For unit a and b = a + d with ||d|| <= B: 1 - |<a|b>|^2 / ||b||^2 =
+    (||d||^2 - |<a|d>|^2) / ||b||^2 <= B^2 / (1 - B)^2."""
+    return b * b / (1.0 - b) ** 2
