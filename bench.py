@@ -345,25 +345,31 @@ def run_ours(args, rank, world):
     # free the QFT buffers before the secondary workloads
     del a, b, x0, ops
     torch.cuda.empty_cache()
-    extras = {}
-    if not args.no_adjoint:
-        extras["adjoint"] = bench_adjoint(api)
-    if not args.no_batch:
-        extras["batch"] = bench_batch(api, count=args.batch_count)
-    if not args.no_tfim:
-        extras["tfim"] = bench_tfim(api, n=args.tfim_qubits)
-    if not args.no_unitary:
-        extras["unitary"] = bench_unitary(api)
-    if args.random:
-        extras["random"] = bench_random(api, n=args.random_qubits)
-    if extras:
-        out["extras"] = extras
+    refs = {}
     if rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(n, circ, j, budget_s=args.cpu_seconds)
+        if not args.no_refs:
+            refs = oracle_references(batch_count=args.batch_count)
+            out["cpu_baseline_random"] = refs.pop("random_cpu")
+    extras = {}
+    if not args.no_adjoint:
+        extras["adjoint"] = bench_adjoint(api, refs=refs.get("adjoint"))
+    if not args.no_batch:
+        extras["batch"] = bench_batch(api, count=args.batch_count, refs=refs.get("batch"))
+    if not args.no_tfim:
+        extras["tfim"] = bench_tfim(api, n=args.tfim_qubits, ref=refs.get("tfim"), ref_mag=refs.get("tfim_mag"))
+    if not args.no_unitary:
+        extras["unitary"] = bench_unitary(api)
+    if not args.no_random:
+        extras["random"] = bench_random(api, *REF_RANDOM, ref=refs.get("random"))
+    if args.random_30:
+        extras["random_30"] = bench_random_30(api, n=30)
+    if extras:
+        out["extras"] = extras
     return out
 
 
-def bench_adjoint(api, n=20, layers=8, reps=3):
+def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     """Ansatz-20 energy + full gradient (320 parameters) by the adjoint sweep,
     complex128 and complex64, against the plain FP64 path: the
     parameter-shift gradient with one launch per gate (2 circuit
@@ -375,6 +381,7 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
     obs = synth.ansatz_observable(n)
     out = {"workload": f"ansatz-{n}, {layers} layers, {circ.n_params} parameters, {len(circ.gates)} gates"}
     grads = {}
+    energies_grads = {}
     for name, dt in (("c128", torch.complex128), ("c64", torch.complex64)):
         p0 = torch.zeros(1 << n, dtype=dt, device="cuda")
         p0[0] = 1
@@ -387,6 +394,7 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
             e, g = api.adjoint_grad(circ.gates, circ.theta, obs.xmask, obs.zmask, obs.coeff, p0, wp, wl)
         el = (time.perf_counter() - t0) / reps
         grads[name] = g
+        energies_grads[f"adjoint_{name}"] = (e, g)
         out[f"adjoint_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3, "energy": e,
                                   "launches_per_gradient": 2 * len(circ.gates) + 4 + circ.n_params}
     # the same sweep recorded once as a CUDA graph and replayed per theta
@@ -412,12 +420,28 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
             e, gw = plan.run(circ.theta)
         elw = (time.perf_counter() - t0) / r
         w, ln, nb = plan.sweep()
+        energies_grads[f"adjoint_autotuned_{name}"] = (e, gw)
         out[f"adjoint_autotuned_{name}"] = {
             "window": w, "lanes": ln, "launches_per_sweep": nb, "grads_per_s": 1.0 / elw,
             "ms_per_gradient": elw * 1e3, "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(gw - grads[name]))),
             "device_ms_by_sweep": {f"w{tw}_l{tl}": m for tw, tl, m in tune["tried"]}}
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
+    for name in ("c128", "c64"):
+        # what the graph plan and the window-fused sweep add over the
+        # one-launch-per-gate adjoint sweep (the same algorithm)
+        out[f"speedup_graph_vs_launch_adjoint_{name}"] = (out[f"adjoint_graph_{name}"]["grads_per_s"]
+                                                         / out[f"adjoint_{name}"]["grads_per_s"])
+        out[f"speedup_autotuned_vs_launch_adjoint_{name}"] = (out[f"adjoint_autotuned_{name}"]["grads_per_s"]
+                                                             / out[f"adjoint_{name}"]["grads_per_s"])
+    if refs is not None:
+        p = refs["params"]
+        out["vs_oracle"] = {"reference": f"FP64 oracle energy and parameter-shift gradient at {len(p)} sampled "
+                                         "parameters (cpu_baseline leg)"}
+        for key in ("adjoint_c128", "adjoint_c64", "adjoint_autotuned_c128", "adjoint_autotuned_c64"):
+            e, g = energies_grads[key]
+            out["vs_oracle"][key] = {"energy_abs_err": abs(e - refs["energy"]),
+                                     "grad_max_abs_err": float(np.max(np.abs(g[p] - refs["grad"])))}
     # plain FP64 path: one circuit evaluation = 472 applies + expectation
     ops = [api.build(g, n, theta=circ.theta) for g in circ.gates]
     x = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
@@ -452,7 +476,7 @@ def bench_adjoint(api, n=20, layers=8, reps=3):
     return out
 
 
-def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "c128")):
+def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "c128"), refs=None):
     """QAOA MaxCut batch: `count` circuits on random 3-regular graphs,
     n in {14..22}, p = 4: energy + 8-parameter gradient per circuit in one
     persistent launch replayed from a CUDA graph (launch shape chosen by the
@@ -487,6 +511,13 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
             E, G = b.run(theta)
         el = (time.perf_counter() - t0) / reps
         energies[name] = E
+        if refs:
+            out.setdefault("vs_oracle", {"reference": f"FP64 oracle energies and parameter-shift gradients of "
+                                                      f"{len(refs)} 14-qubit instances (cpu_baseline leg)",
+                                         "instances": sorted(int(i) for i in refs)})
+            out["vs_oracle"][name] = {
+                "energy_max_abs_err": max(abs(E[i] - refs[i][0]) for i in refs),
+                "grad_max_abs_err": max(float(np.max(np.abs(G[i] - refs[i][1]))) for i in refs)}
         q = b.query()
         out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
                                   "cluster": q["cluster"], "threads": q["threads"], "window": b.sweep()[0],
@@ -515,7 +546,7 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
     return out
 
 
-def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7):
+def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7, ref=None, ref_mag=None):
     """Trotterised 1D transverse-field Ising model (the paper's
     Hamiltonian-simulation workload): `steps` first-order Trotter steps of
     ZZ bond rotations and X field rotations, in place, complex128 and
@@ -550,6 +581,23 @@ def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7):
                      "magnetisation": mags[name], "norm": api.norm(x)}
         del ops, x
     out["c64_vs_c128_magnetisation_diff"] = abs(mags["c64"] - mags["c128"])
+    if ref is not None:
+        # the same Trotter circuit at REF_TFIM qubits against the FP64 oracle
+        m = REF_TFIM
+        cc = synth.tfim(m, steps, dt, J=J, h=h)
+        ob = synth.magnetisation_observable(m)
+        chk = {"qubits": m, "reference": "FP64 oracle (cpu_baseline leg)"}
+        for name, dt_ in (("c128", torch.complex128), ("c64", torch.complex64)):
+            ops = [api.build(g, m, dtype=dt_, theta=cc.theta) for g in cc.gates]
+            x = torch.zeros(1 << m, dtype=dt_, device="cuda")
+            x[0] = 1
+            for op in ops:
+                api.apply(op, x, x)
+            rec = state_errors(x.cpu().numpy(), ref)
+            rec["magnetisation_abs_err_vs_oracle"] = abs(api.expect(x, ob.xmask, ob.zmask, ob.coeff).real - ref_mag)
+            chk[name] = rec
+            del ops, x
+        out["check_vs_oracle"] = chk
     return out
 
 
@@ -579,17 +627,73 @@ def bench_unitary(api):
     return out
 
 
-def bench_random(api, n=30, depth=40):
+def _c64_bound(ks) -> float:
+    """Worst-case 2-norm error bound of a complex64 circuit of unitary gates
+    on k_i qubits (k = 0 for gates whose entries are 0 or +-1, applied
+    exactly): per gate ((2^(k+1) + 1) 1.01 + sqrt 2) 2^(k/2) units of 2^-24,
+    summed over the gates (each later gate is unitary)."""
+    u = 2.0 ** -24
+    return 1.01 * u * sum(((2 ** (k + 1) + 1) * 1.01 + math.sqrt(2.0)) * 2.0 ** (k / 2.0) for k in ks if k > 0)
+
+
+def bench_random(api, n=24, depth=40, ref=None):
     """Random layered circuit (Haar U(2) on every qubit + CZ on a random
-    matching per layer), complex64 vs complex128, one pass each; fusion depth
-    chosen by the autotuner for complex64; fidelity and max amplitude error of
-    complex64 against the complex128 result (the complex128 path matches the
-    FP64 oracle to 1e-12 at every size the oracle reaches)."""
+    matching per layer) at the largest size the oracle runs in seconds: one
+    in-place pass in complex64 and complex128, plain and with
+    commutation-aware fusion (max K 3, depth 6), each with its fidelity and
+    max amplitude error against the FP64 oracle's state (and, for
+    complex64, the worst-case rounding bound). The state (128 or 256 MiB)
+    is about the size of L2, so the times here are not an HBM figure; the
+    30-qubit line gives that."""
     import torch
     import synth
     circ = synth.random_layered(n, depth, seed=0)
     N = 1 << n
-    out = {"workload": f"random-{n} depth {depth}: {len(circ.gates)} gates"}
+    out = {"workload": f"random-{n} depth {depth}: {len(circ.gates)} gates, in place",
+           "reference": "FP64 oracle (cpu_baseline leg)" if ref is not None else None}
+    for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+        for fused in (False, True):
+            if fused:
+                ops = api.build_fused(circ.gates, n, 3, 6, dtype=dt, commuting=True)
+                ks = [op.info()["k"] for op in ops]
+            else:
+                ops = [api.build(g, n, dtype=dt) for g in circ.gates]
+                ks = [0 if g.name == "cz" else g.k for g in circ.gates]
+            x = torch.zeros(N, dtype=dt, device="cuda")
+            for rep in range(2):  # the first pass warms up
+                x.zero_()
+                x[0] = 1
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for op in ops:
+                    api.apply(op, x, x)
+                torch.cuda.synchronize()
+                el = time.perf_counter() - t0
+            key = name + ("_fused" if fused else "")
+            rec = {"ops": len(ops), "s_per_circuit": el, "gates_per_s": len(circ.gates) / el, "norm": api.norm(x)}
+            if ref is not None:
+                rec.update(state_errors(x.cpu().numpy(), ref))
+            if name == "c64":
+                b = _c64_bound(ks)
+                rec["max_abs_err_bound"] = b
+                rec["infidelity_bound"] = b * b / (1.0 - b) ** 2
+            out[key] = rec
+            del ops, x
+    return out
+
+
+def bench_random_30(api, n=30, depth=40):
+    """Random layered circuit at 30 qubits (8 or 16 GiB state), complex64
+    vs complex128, one pass each; fusion depth chosen by the autotuner for
+    complex64. The oracle does not run at this size, so the complex64 state
+    is compared with the complex128 GPU state, which matches the oracle to
+    1e-12 wherever the oracle runs (24 qubits in the random line)."""
+    import torch
+    import synth
+    circ = synth.random_layered(n, depth, seed=0)
+    N = 1 << n
+    out = {"workload": f"random-{n} depth {depth}: {len(circ.gates)} gates",
+           "reference": "complex128 GPU state (oracle-pinned at <= 24 qubits)"}
     res = {}
     for name, dt, s in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
         ops = [api.build(g, n, dtype=dt) for g in circ.gates]
@@ -614,9 +718,6 @@ def bench_random(api, n=30, depth=40):
     out["c64_max_abs_err_vs_c128"] = float((a - b).abs().max().item())
     del b
     res.pop("c64")
-    # fusion (commutation-aware grouping, the DIA x DIA product of Algorithm 1
-    # on each group): the autotuner times each depth for max_k 2 and 3 on
-    # the first five layers; the best plan then runs the whole circuit
     w = torch.zeros(N, dtype=torch.complex64, device="cuda")
     w[0] = 1
     prefix = circ.gates[: 5 * (n + n // 2)]
@@ -661,6 +762,59 @@ def cpu_baseline(n, circ, j, budget_s=12.0):
     el = time.perf_counter() - t0
     return {"value": done * 2 * N * 16 / el / 1e9, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": f"first {done} of {len(circ.gates)} ops of qft-{n} (complex128), {el:.1f} s"}
+
+
+# Sizes of the oracle reference runs behind the precision fields of the
+# secondary workloads (each a few seconds to ~20 s on the host cores).
+REF_RANDOM = (24, 40)      # random layered: qubits, depth
+REF_TFIM = 22              # TFIM qubits (10 Trotter steps, as the timed line)
+REF_ADJOINT_PARAMS = 8     # Ansatz-20 parameters checked by parameter shift
+REF_BATCH_INSTANCES = 4    # 14-qubit QAOA instances of the batch checked
+
+
+def oracle_references(batch_count=256):
+    """Part of the cpu_baseline leg (rank 0, outside every timed region):
+    the FP64 oracle's results that the secondary workloads' GPU results are
+    compared with (fidelity and max amplitude error of final states; energy
+    and sampled gradient entries). Also times the oracle on the random
+    layered circuit."""
+    import oracle
+    import synth
+    refs = {}
+    n, depth = REF_RANDOM
+    circ = synth.random_layered(n, depth, seed=0)
+    t0 = time.perf_counter()
+    refs["random"] = oracle.run_circuit(circ, synth.basis_state(n, 0))
+    el = time.perf_counter() - t0
+    refs["random_cpu"] = {"gates_per_s": len(circ.gates) / el, "s_per_circuit": el, "cores": oracle.threads(),
+                          "kind": "oracle", "sample": f"random-{n} depth {depth}, whole circuit, complex128"}
+    tc = synth.tfim(REF_TFIM, 10, 0.1, J=1.0, h=0.7)
+    refs["tfim"] = oracle.run_circuit(tc, synth.basis_state(REF_TFIM, 0), tc.theta)
+    refs["tfim_mag"] = oracle.expect(refs["tfim"], synth.magnetisation_observable(REF_TFIM)).real
+    ac = synth.ansatz(n=20, layers=8, seed=0)
+    ao = synth.ansatz_observable(20)
+    a0 = synth.basis_state(20, 0)
+    params = np.linspace(0, ac.n_params - 1, REF_ADJOINT_PARAMS).astype(int)
+    refs["adjoint"] = {"energy": oracle.energy(ac, ao, a0), "params": params,
+                       "grad": oracle.param_shift_grad(ac, ao, a0, params=params)[params]}
+    inst = synth.qaoa_batch(batch_count, seed=0)
+    picked = [i for i, (c, _) in enumerate(inst) if c.n == 14][:REF_BATCH_INSTANCES]
+    refs["batch"] = {}
+    for i in picked:
+        c, o = inst[i]
+        p0 = synth.basis_state(c.n, 0)
+        refs["batch"][i] = (oracle.energy(c, o, p0), oracle.param_shift_grad(c, o, p0))
+    return refs
+
+
+def state_errors(got, want) -> dict:
+    """Fidelity |<a|b>|^2 / (<a|a><b|b>) and max amplitude error of a GPU
+    state against the oracle's (numpy on the host copies)."""
+    a = np.asarray(want, dtype=np.complex128)
+    b = np.asarray(got, dtype=np.complex128)
+    f = abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+    return {"fidelity_vs_oracle": float(f), "infidelity_vs_oracle": float(1.0 - f),
+            "max_abs_err_vs_oracle": float(np.max(np.abs(a - b)))}
 
 
 def run_reference(args, rank, world):
@@ -726,8 +880,9 @@ def main():
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--batch-window", type=int, default=0)
     ap.add_argument("--batch-lanes", type=int, default=1)
-    ap.add_argument("--random", action="store_true", help="also run the random layered circuit (slow in c128)")
-    ap.add_argument("--random-qubits", type=int, default=30)
+    ap.add_argument("--no-random", action="store_true", help="skip the random layered circuit at 24 qubits")
+    ap.add_argument("--random-30", action="store_true", help="also run the random layered circuit at 30 qubits")
+    ap.add_argument("--no-refs", action="store_true", help="skip the oracle reference runs of the precision fields")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

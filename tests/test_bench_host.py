@@ -144,3 +144,20 @@ def test_gpus_flag_must_match_the_launched_ranks():
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "1", "--impl", "reference"],
                        capture_output=True, text=True, env=env, timeout=120)
     assert p.returncode == 2 and "WORLD_SIZE is 2" in p.stderr
+
+
+def test_precision_fields_helpers():
+    """The bench's state comparison and complex64 bound agree with the test
+    suite's (gpu_util) and with the oracle's error measures."""
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import gpu_util
+    import oracle
+    ks = [1, 0, 2, 3, 1, 0]
+    assert bench._c64_bound(ks) == pytest.approx(gpu_util.c64_circuit_bound(ks), rel=1e-15)
+    rng = np.random.default_rng(0)
+    a = rng.standard_normal(64) + 1j * rng.standard_normal(64)
+    b = a + 1e-6 * (rng.standard_normal(64) + 1j * rng.standard_normal(64))
+    e = bench.state_errors(b, a)
+    assert e["fidelity_vs_oracle"] == pytest.approx(oracle.fidelity(a, b), rel=1e-14)
+    assert e["max_abs_err_vs_oracle"] == oracle.max_abs_err(a, b)
