@@ -19,6 +19,11 @@ Parity status of each function (what pins it, in ``tests/test_oracle_pins.py``):
   GHZ correlators, dense Pauli matrices (<= 8 qubits).
 * energy, param_shift_grad ..... pinned: closed-form single-rotation energies
   (RX, RY, RZ), central finite differences, dense-matrix derivative.
+* cdf, sample .................. pinned: exact rational inverse-CDF draws on
+  states with dyadic probabilities (every sum exact), GHZ and basis-state
+  outcomes, zero-probability outcomes never drawn, empirical frequencies
+  against |psi|^2 (chi-square), planted mistakes (>= for >, reversed
+  order, no normalisation) rejected.
 * gate_matrix, pauli_local ..... pinned: scipy.linalg.expm of the full-system
   Pauli operator assembled from X/Z masks, for one- to three-letter
   generators (asymmetric ones included) on non-adjacent and reversed
@@ -38,7 +43,7 @@ __all__ = [
     "lib", "threads", "set_threads", "apply_gate", "gate_matrix", "run_circuit",
     "gate_diaq", "dense_to_diaq", "diaq_matvec", "embed", "fuse", "norm2",
     "expect", "apply_pauli_sum", "energy", "param_shift_grad", "fd_grad",
-    "fidelity", "max_abs_err", "pauli_local",
+    "fidelity", "max_abs_err", "pauli_local", "cdf", "sample",
 ]
 
 _LIB = None
@@ -66,6 +71,8 @@ def lib():
         L.oracle_norm2.argtypes = [ctypes.c_int, dp]
         L.oracle_norm2.restype = ctypes.c_double
         L.oracle_apply_pauli_sum.argtypes = [ctypes.c_int, dp, i64, u64p, u64p, dp, dp]
+        L.oracle_cdf.argtypes = [ctypes.c_int, dp, dp]
+        L.oracle_sample.argtypes = [ctypes.c_int, dp, i64, dp, i64p]
         _LIB = L
     return _LIB
 
@@ -356,6 +363,31 @@ def fd_grad(circ, obs, psi0, theta=None, h: float = 1e-4, params=None) -> np.nda
         tm[p] -= h
         g[p] = (energy(circ, obs, psi0, tp) - energy(circ, obs, psi0, tm)) / (2 * h)
     return g
+
+
+# --------------------------------------------------------------------------
+# Shots (Section VII: every benchmark runs 1024 shots): Born-rule sampling
+# --------------------------------------------------------------------------
+
+
+def cdf(psi) -> np.ndarray:
+    """cdf_i = sum_{j <= i} |psi_j|^2, summed in index order in FP64."""
+    psi = _c128(psi)
+    out = np.empty(psi.shape[0], dtype=np.float64)
+    lib().oracle_cdf(_nq(psi), _dp(psi.view(np.float64)), _dp(out))
+    return out
+
+
+def sample(psi, uniforms) -> np.ndarray:
+    """One basis-state index per uniform u: the smallest i with
+    cdf_i > u * cdf_{N-1} (u clamped to [0, 1]; the largest i of non-zero
+    probability when none exceeds it; -1 for a zero state)."""
+    psi = _c128(psi)
+    u = np.ascontiguousarray(np.asarray(uniforms, dtype=np.float64))
+    out = np.empty(u.shape[0], dtype=np.int64)
+    lib().oracle_sample(_nq(psi), _dp(psi.view(np.float64)), u.shape[0], _dp(u),
+                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return out
 
 
 # --------------------------------------------------------------------------

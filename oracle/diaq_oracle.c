@@ -306,3 +306,71 @@ void oracle_apply_pauli_sum(int n, const double* psi, int64_t n_terms, const uin
         }
     }
 }
+
+/*
+ * Shots: Born-rule sampling of basis states, the measurement behind a run's
+ * shots (Section VII runs every benchmark for 1024 shots). Basis state i is
+ * drawn with probability |psi_i|^2 / sum_j |psi_j|^2, by the inverse of the
+ * cumulative distribution in index order:
+ *
+ *   cdf_i = sum_{j <= i} |psi_j|^2, summed in index order, with
+ *           |psi_j|^2 = re*re + im*im;
+ *   r     = u * cdf_{N-1} for the shot's uniform u (clamped to [0, 1]);
+ *   outcome = the smallest i with cdf_i > r, or, when no cdf_i exceeds r
+ *             (u = 1), the largest i with |psi_i|^2 > 0; -1 when the state
+ *             has zero norm.
+ *
+ * cdf is non-decreasing, so the smallest such i is found by bisection.
+ */
+void oracle_cdf(int n, const double* psi, double* cdf) {
+    const int64_t N = (int64_t)1 << n;
+    double s = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        const double p = psi[2 * i] * psi[2 * i] + psi[2 * i + 1] * psi[2 * i + 1];
+        s = s + p;
+        cdf[i] = s;
+    }
+}
+
+void oracle_sample(int n, const double* psi, int64_t shots, const double* u, int64_t* out) {
+    const int64_t N = (int64_t)1 << n;
+    double* cdf = (double*)malloc(sizeof(double) * (size_t)N);
+    if (!cdf) {
+        for (int64_t s = 0; s < shots; ++s) out[s] = -2;
+        return;
+    }
+    oracle_cdf(n, psi, cdf);
+    const double total = cdf[N - 1];
+    int64_t last_pos = -1;
+    for (int64_t i = N - 1; i >= 0; --i) {
+        const double prev = i ? cdf[i - 1] : 0.0;
+        if (cdf[i] > prev) {
+            last_pos = i;
+            break;
+        }
+    }
+    for (int64_t s = 0; s < shots; ++s) {
+        double v = u[s];
+        if (!(v > 0.0)) v = 0.0; /* also maps NaN to 0 */
+        if (v > 1.0) v = 1.0;
+        const double r = v * total;
+        if (!(total > 0.0)) {
+            out[s] = -1;
+            continue;
+        }
+        if (!(cdf[N - 1] > r)) {
+            out[s] = last_pos;
+            continue;
+        }
+        int64_t lo = 0, hi = N - 1; /* invariant: cdf[hi] > r */
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > r)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        out[s] = lo;
+    }
+    free(cdf);
+}
