@@ -300,6 +300,33 @@ diaq_status diaq_apply_pauli_sum(const void* psi, void* lambda, int32_t n_qubits
                                  diaq_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Shots - Section VII runs every benchmark for 1024 shots: basis states
+ * drawn from the final state with the Born-rule probabilities.
+ * ------------------------------------------------------------------------ */
+
+/* Draw n_shots basis-state indices from psi: outcome i with probability
+ * |psi_i|^2 / ||psi||^2, by the inverse of the cumulative distribution in
+ * index order. Shot s takes the caller's uniform u = uniforms[s] (clamped to
+ * [0, 1]; NaN counts as 0), forms r = u ||psi||^2 and returns the smallest i
+ * whose running sum of |psi|^2 exceeds r; when none does (u = 1) it returns
+ * the largest i of non-zero probability. An outcome of zero probability is
+ * never drawn; a state of zero norm gives -1 for every shot.
+ *
+ * The running sums are FP64 (complex64: exact FP32 squares summed as FP32
+ * pairs, about 48 bits, per 16 amplitudes) over a tree of sequential sums,
+ * so where r lies within rounding of a boundary of the cumulative
+ * distribution the outcome may be the neighbouring index of a plain
+ * left-to-right sum; on states whose sums are exact (e.g. dyadic
+ * probabilities) the outcome is exactly that of the definition.
+ *
+ * psi: device state (16-byte aligned). uniforms: device array of n_shots
+ * doubles. out_indices: device array of n_shots int64 (8-byte aligned both).
+ * 0 <= n_shots <= 2^31. Allocates (N / 2048) x 1.004 doubles of device
+ * scratch on `stream` and frees it there; does not synchronise. */
+diaq_status diaq_sample(const void* psi, int32_t n_qubits, diaq_dtype dtype, const double* uniforms,
+                        int64_t n_shots, int64_t* out_indices, diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint gradient (not in the paper; the adjoint-state method for
  * E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U_L ... U_1 psi0).
  * ------------------------------------------------------------------------ */

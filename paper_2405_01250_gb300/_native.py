@@ -93,6 +93,7 @@ SIGNATURES = {
                                             _dp, _vp]),
     "diaq_adjoint_grad": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int32, _u64p, _u64p,
                                          _dp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int, _dp, _dp, _vp]),
+    "diaq_sample": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp]),
     "diaq_norm_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
     "diaq_debug_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int32]),
 }

@@ -23,7 +23,7 @@ __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
     "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
-    "build_fused", "AdjointPlan", "plan_fusion_commuting",
+    "build_fused", "AdjointPlan", "plan_fusion_commuting", "sample",
 ]
 
 
@@ -254,6 +254,26 @@ def norm(psi: torch.Tensor, stream=None) -> float:
     check(lib().diaq_norm(ctypes.c_void_p(psi.data_ptr()), _nq(psi), _dtype_code(psi.dtype), ctypes.byref(out),
                           _stream(stream)))
     return out.value
+
+
+def sample(psi: torch.Tensor, uniforms, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Born-rule shots of psi (diaq_sample): one basis-state index per
+    uniform in [0, 1). uniforms: a float64 CUDA tensor, or host values that
+    are copied to the device first. Returns a CUDA int64 tensor."""
+    _check_state(psi, "psi")
+    if not (isinstance(uniforms, torch.Tensor) and uniforms.is_cuda):
+        uniforms = torch.as_tensor(np.asarray(uniforms, dtype=np.float64)).to(psi.device)
+    if uniforms.dtype != torch.float64 or not uniforms.is_contiguous():
+        raise ValueError("uniforms must be a contiguous float64 tensor")
+    shots = uniforms.numel()
+    if out is None:
+        out = torch.empty(shots, dtype=torch.int64, device=psi.device)
+    if out.dtype != torch.int64 or out.numel() != shots or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous CUDA int64 tensor with one entry per uniform")
+    check(lib().diaq_sample(ctypes.c_void_p(psi.data_ptr()), _nq(psi), _dtype_code(psi.dtype),
+                            ctypes.c_void_p(uniforms.data_ptr()), shots, ctypes.c_void_p(out.data_ptr()),
+                            _stream(stream)))
+    return out
 
 
 def _terms(xmask, zmask, coeff):
