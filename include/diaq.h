@@ -327,6 +327,90 @@ diaq_status diaq_sample(const void* psi, int32_t n_qubits, diaq_dtype dtype, con
                         int64_t n_shots, int64_t* out_indices, diaq_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Sharded state - a state vector larger than one device's memory is split
+ * across devices (Section II-A; Section VI names the multi-node backend,
+ * diaq-mpi). The 2^n amplitudes are split by the top g bits of the physical
+ * basis index into 2^g shards of 2^(n-g) amplitudes: shard s holds physical
+ * indices s 2^(n-g) .. (s+1) 2^(n-g) - 1. Logical qubits are mapped to
+ * physical bits (0 .. n-g-1 local, n-g .. n-1 global); a gate runs in every
+ * shard on its targets' physical positions once they are all local, and a
+ * target on a global bit G is first exchanged with a local bit l: every
+ * shard pair (s with bit G clear, s | 2^G) trades the half of s whose local
+ * bit l is 1 for the half of its partner whose local bit l is 0.
+ * ------------------------------------------------------------------------ */
+
+typedef enum {
+    DIAQ_SHARD_APPLY = 0,      /* run gates[gate] in every shard on local positions targets[] */
+    DIAQ_SHARD_EXCHANGE = 1,   /* trade halves across global bit global_bit and local bit local_bit */
+    DIAQ_SHARD_LOCAL_SWAP = 2  /* SWAP of local positions targets[0], targets[1] in every shard */
+} diaq_shard_step_kind;
+
+typedef struct {
+    int32_t kind;                 /* diaq_shard_step_kind */
+    int32_t gate;                 /* APPLY: index into the gate array; else -1 */
+    int32_t k;                    /* APPLY: the gate's k; LOCAL_SWAP: 2 */
+    int32_t targets[DIAQ_MAX_K];  /* local physical positions (targets[0] most significant, as the gate's) */
+    int32_t global_bit;           /* EXCHANGE: bit of the shard index (0 .. g-1); else -1 */
+    int32_t local_bit;            /* EXCHANGE: local physical bit traded with it; else -1 */
+} diaq_shard_step;
+
+/* The step list of a circuit on 2^global_bits shards, starting from the
+ * identity map. Before each gate, every target held on a global bit is
+ * exchanged with the local bit whose logical qubit is next used furthest
+ * ahead (never one of the gate's targets). With restore != 0 the list ends
+ * with exchanges and local SWAPs that return every logical qubit to its own
+ * physical bit. Two calls: steps == NULL reports *n_steps; then pass cap >=
+ * *n_steps entries. final_map (may be NULL, n_qubits entries) receives the
+ * physical bit of each logical qubit after the last step. Every gate must
+ * fit in a shard (k <= n - g; DIAQ_ERR_UNSUPPORTED otherwise);
+ * 0 <= global_bits <= 16. Host only. */
+diaq_status diaq_shard_schedule(const diaq_gate* gates, int32_t n_gates, int32_t n_qubits, int32_t global_bits,
+                                int32_t restore, diaq_shard_step* steps, int32_t cap, int32_t* n_steps,
+                                int32_t* final_map);
+
+/* EXCHANGE between two shards in one address space, in place: the
+ * amplitudes of lo_shard (the shard with global bit clear) whose local bit
+ * local_bit is 1 trade places with those of hi_shard (its partner) whose
+ * local bit is 0. Device buffers of 2^n_local amplitudes, not overlapping. */
+diaq_status diaq_shard_swap(void* lo_shard, void* hi_shard, int32_t n_local, diaq_dtype dtype, int32_t local_bit,
+                            diaq_stream_t stream);
+
+/* EXCHANGE between ranks: buf (2^(n_local-1) amplitudes, device) receives, in
+ * index order, the amplitudes of shard whose local bit local_bit equals
+ * value; diaq_shard_unpack writes such a buffer back to those positions. A
+ * rank whose shard has the global bit clear packs value 1 and its partner
+ * value 0; they swap buffers (e.g. NCCL send/recv) and each unpacks what it
+ * received with the value it packed. */
+diaq_status diaq_shard_pack(const void* shard, int32_t n_local, diaq_dtype dtype, int32_t local_bit, int32_t value,
+                            void* buf, diaq_stream_t stream);
+diaq_status diaq_shard_unpack(const void* buf, void* shard, int32_t n_local, diaq_dtype dtype, int32_t local_bit,
+                              int32_t value, diaq_stream_t stream);
+
+/* Run a circuit on 2^global_bits shards held in this process (shards[s]:
+ * device buffers of 2^(n - global_bits) amplitudes, not overlapping, on the
+ * current device), in place, by the steps of diaq_shard_schedule: on-the-fly
+ * ops on the local positions and diaq_shard_swap for exchanges. theta is read
+ * for parametric gates. final_map as in diaq_shard_schedule (identity when
+ * restore != 0). Synchronises `stream`. */
+diaq_status diaq_sharded_simulate(const diaq_gate* gates, int32_t n_gates, const double* theta, int32_t n_qubits,
+                                  int32_t global_bits, diaq_dtype dtype, void* const* shards, int32_t restore,
+                                  int32_t* final_map, diaq_stream_t stream);
+
+/* ||psi||^2 of a sharded state: diaq_norm of each shard, then one FP64 sum
+ * over the shards in shard order. */
+diaq_status diaq_sharded_norm(void* const* shards, int32_t n_qubits, int32_t global_bits, diaq_dtype dtype,
+                              double* out, diaq_stream_t stream);
+
+/* <psi| sum_t c_t P_t |psi> of a sharded state (terms as in diaq_expect, in
+ * logical qubits; map: physical bit of each logical qubit, NULL for the
+ * identity). X and Y letters must sit on local bits (DIAQ_ERR_UNSUPPORTED
+ * otherwise: exchange the qubit first); a Z on global bit G weighs shard s by
+ * (-1)^(bit G of s). Per-shard FP64 sums, then one sum over the shards. */
+diaq_status diaq_sharded_expect(void* const* shards, int32_t n_qubits, int32_t global_bits, diaq_dtype dtype,
+                                const int32_t* map, int32_t n_terms, const uint64_t* xmask, const uint64_t* zmask,
+                                const double* coeff, double* out, diaq_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint gradient (not in the paper; the adjoint-state method for
  * E(theta) = <psi(theta)|H|psi(theta)>, psi(theta) = U_L ... U_1 psi0).
  * ------------------------------------------------------------------------ */

@@ -180,6 +180,34 @@ SIGNATURES.update({
     "diaq_batch_query": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i64p]),
 })
 
+class diaq_shard_step(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("gate", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("targets", ctypes.c_int32 * DIAQ_MAX_K),
+        ("global_bit", ctypes.c_int32),
+        ("local_bit", ctypes.c_int32),
+    ]
+
+
+SHARD_APPLY, SHARD_EXCHANGE, SHARD_LOCAL_SWAP = 0, 1, 2
+
+SIGNATURES.update({
+    "diaq_shard_schedule": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.POINTER(diaq_shard_step), ctypes.c_int32, _i32p, _i32p]),
+    "diaq_shard_swap": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _vp]),
+    "diaq_shard_pack": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, _vp, _vp]),
+    "diaq_shard_unpack": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                         _vp]),
+    "diaq_sharded_simulate": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int,
+                                             ctypes.POINTER(_vp), ctypes.c_int32, _i32p, _vp]),
+    "diaq_sharded_norm": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32, ctypes.c_int, _dp,
+                                         _vp]),
+    "diaq_sharded_expect": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.c_int32, ctypes.c_int, _i32p,
+                                           ctypes.c_int32, _u64p, _u64p, _dp, _dp, _vp]),
+})
+
 _LIB = None
 
 

@@ -23,7 +23,8 @@ __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
     "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
-    "build_fused", "AdjointPlan", "plan_fusion_commuting", "sample",
+    "build_fused", "AdjointPlan", "plan_fusion_commuting", "sample", "shard_schedule", "ShardedState",
+    "ShardRank", "TorchDistTransport",
 ]
 
 
@@ -648,3 +649,187 @@ class DiaqEnergy(torch.autograd.Function):
     def backward(ctx, grad_out):
         (g,) = ctx.saved_tensors
         return grad_out * g, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# Sharded state (diaq_shard_* / diaq_sharded_*): 2^g shards split by the top
+# g bits of the physical basis index, qubits remapped by exchanges.
+# ---------------------------------------------------------------------------
+
+
+def shard_schedule(gates, n_qubits: int, global_bits: int, restore: bool = True) -> tuple:
+    """Step list of diaq_shard_schedule as dicts, and the final map
+    (physical bit of each logical qubit). Host only."""
+    arr, keep = _gate_array(gates)
+    cnt = ctypes.c_int32(0)
+    check(lib().diaq_shard_schedule(arr, len(gates), n_qubits, global_bits, int(bool(restore)), None, 0,
+                                    ctypes.byref(cnt), None))
+    steps = (N.diaq_shard_step * max(1, cnt.value))()
+    fmap = (ctypes.c_int32 * n_qubits)()
+    check(lib().diaq_shard_schedule(arr, len(gates), n_qubits, global_bits, int(bool(restore)), steps, cnt.value,
+                                    ctypes.byref(cnt), fmap))
+    out = []
+    for i in range(cnt.value):
+        s = steps[i]
+        out.append({"kind": ("apply", "exchange", "local_swap")[s.kind], "gate": s.gate,
+                    "targets": tuple(s.targets[a] for a in range(s.k)), "global_bit": s.global_bit,
+                    "local_bit": s.local_bit})
+    return out, list(fmap)
+
+
+def _shard_ptrs(shards):
+    return (ctypes.c_void_p * len(shards))(*[t.data_ptr() for t in shards])
+
+
+class ShardedState:
+    """2^global_bits shards of one state on the current device (one process),
+    each a CUDA tensor of 2^(n - global_bits) amplitudes. Shard s holds the
+    physical indices s 2^(n-g) .. (s+1) 2^(n-g) - 1; `map` gives the physical
+    bit of each logical qubit (identity after a run with restore)."""
+
+    def __init__(self, n_qubits: int, global_bits: int, dtype=torch.complex128, shards=None):
+        self.n, self.g = int(n_qubits), int(global_bits)
+        self.n_local = self.n - self.g
+        self.dtype = dtype
+        if shards is None:
+            shards = [torch.zeros(1 << self.n_local, dtype=dtype, device="cuda") for _ in range(1 << self.g)]
+        if len(shards) != 1 << self.g:
+            raise ValueError("need 2^global_bits shards")
+        for t in shards:
+            _check_state(t, "shard")
+            if t.numel() != 1 << self.n_local or t.dtype != dtype:
+                raise ValueError("every shard holds 2^(n - global_bits) amplitudes of the state's dtype")
+        self.shards = list(shards)
+        self.map = list(range(self.n))
+
+    @classmethod
+    def from_full(cls, psi: torch.Tensor, global_bits: int) -> "ShardedState":
+        n = _nq(psi)
+        parts = [c.clone() for c in psi.reshape(1 << global_bits, -1)]
+        return cls(n, global_bits, psi.dtype, parts)
+
+    def simulate(self, gates, theta=None, restore: bool = True, stream=None) -> "ShardedState":
+        if self.map != list(range(self.n)):
+            raise ValueError("the state's qubits are remapped; run from the identity map")
+        arr, keep = _gate_array(gates)
+        th = None if theta is None else np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        fmap = (ctypes.c_int32 * self.n)()
+        check(lib().diaq_sharded_simulate(arr, len(gates), _dptr(th) if th is not None else None, self.n, self.g,
+                                          _dtype_code(self.dtype), _shard_ptrs(self.shards), int(bool(restore)), fmap,
+                                          _stream(stream)))
+        self.map = list(fmap)
+        return self
+
+    def norm(self, stream=None) -> float:
+        out = ctypes.c_double(0)
+        check(lib().diaq_sharded_norm(_shard_ptrs(self.shards), self.n, self.g, _dtype_code(self.dtype),
+                                      ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def expect(self, xmask, zmask, coeff, stream=None) -> complex:
+        xm, zm, cc = _terms(xmask, zmask, coeff)
+        m = (ctypes.c_int32 * self.n)(*self.map)
+        out = np.zeros(2)
+        check(lib().diaq_sharded_expect(_shard_ptrs(self.shards), self.n, self.g, _dtype_code(self.dtype), m, len(xm),
+                                        xm.ctypes.data_as(N._u64p), zm.ctypes.data_as(N._u64p), _dptr(cc), _dptr(out),
+                                        _stream(stream)))
+        return complex(out[0], out[1])
+
+    def physical(self) -> torch.Tensor:
+        """The shards concatenated in shard order (physical index order)."""
+        return torch.cat(self.shards)
+
+
+class TorchDistTransport:
+    """Pairwise buffer exchange between ranks with torch.distributed
+    (NCCL for CUDA tensors, gloo for CPU tensors): send `send` to `partner`
+    and receive its buffer into `recv`."""
+
+    def exchange(self, partner: int, send: torch.Tensor, recv: torch.Tensor) -> None:
+        import torch.distributed as dist
+        ops = [dist.P2POp(dist.isend, send, partner), dist.P2POp(dist.irecv, recv, partner)]
+        for w in dist.batch_isend_irecv(ops):
+            w.wait()
+
+
+class ShardRank:
+    """One rank's shard of a state over 2^global_bits ranks (rank r holds
+    shard r) and its steps of diaq_shard_schedule: gates run on the shard in
+    place; an exchange packs the half this rank gives away
+    (diaq_shard_pack), trades buffers with the partner through a transport,
+    and unpacks what it received (diaq_shard_unpack)."""
+
+    def __init__(self, rank: int, n_qubits: int, global_bits: int, shard: torch.Tensor):
+        self.rank, self.n, self.g = int(rank), int(n_qubits), int(global_bits)
+        self.n_local = self.n - self.g
+        _check_state(shard, "shard")
+        if shard.numel() != 1 << self.n_local:
+            raise ValueError("the shard holds 2^(n - global_bits) amplitudes")
+        self.shard = shard
+        self.send = torch.empty(1 << (self.n_local - 1), dtype=shard.dtype, device=shard.device)
+        self.recv = torch.empty_like(self.send)
+        self._ops = {}
+
+    def plan(self, gates, theta=None, restore: bool = True) -> list:
+        steps, self.final_map = shard_schedule(gates, self.n, self.g, restore)
+        swap = _SwapGate()
+        self._ops = {}
+        for i, s in enumerate(steps):
+            if s["kind"] == "exchange":
+                continue
+            g = gates[s["gate"]] if s["kind"] == "apply" else swap
+            self._ops[i] = build(_Retargeted(g, s["targets"]), self.n_local, dtype=self.shard.dtype, theta=theta)
+        return steps
+
+    def apply_step(self, i: int, step: dict) -> None:
+        apply(self._ops[i], self.shard, self.shard)
+
+    def partner(self, step: dict) -> int:
+        return self.rank ^ (1 << step["global_bit"])
+
+    def _value(self, step: dict) -> int:
+        return 1 - ((self.rank >> step["global_bit"]) & 1)
+
+    def pack(self, step: dict, stream=None) -> torch.Tensor:
+        check(lib().diaq_shard_pack(ctypes.c_void_p(self.shard.data_ptr()), self.n_local, _dtype_code(self.shard.dtype),
+                                    step["local_bit"], self._value(step), ctypes.c_void_p(self.send.data_ptr()),
+                                    _stream(stream)))
+        return self.send
+
+    def unpack(self, step: dict, stream=None) -> None:
+        check(lib().diaq_shard_unpack(ctypes.c_void_p(self.recv.data_ptr()), ctypes.c_void_p(self.shard.data_ptr()),
+                                      self.n_local, _dtype_code(self.shard.dtype), step["local_bit"],
+                                      self._value(step), _stream(stream)))
+
+    def run(self, gates, theta=None, restore: bool = True, transport=None) -> list:
+        """All steps on this rank; the other ranks run the same call."""
+        transport = transport or TorchDistTransport()
+        steps = self.plan(gates, theta, restore)
+        for i, s in enumerate(steps):
+            if s["kind"] == "exchange":
+                self.pack(s)
+                torch.cuda.current_stream().synchronize()
+                transport.exchange(self.partner(s), self.send, self.recv)
+                self.unpack(s)
+            else:
+                self.apply_step(i, s)
+        return self.final_map
+
+
+class _Retargeted:
+    """A gate object with its targets replaced (same matrix or generator)."""
+
+    def __init__(self, g, targets):
+        self.targets = tuple(targets)
+        self.matrix = getattr(g, "matrix", None)
+        self.param = int(getattr(g, "param", -1))
+        self.gen = getattr(g, "gen", "")
+        self.scale = float(getattr(g, "scale", 1.0))
+
+
+class _SwapGate:
+    targets = (1, 0)
+    matrix = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+    param = -1
+    gen = ""
+    scale = 1.0

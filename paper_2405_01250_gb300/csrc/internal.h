@@ -111,6 +111,11 @@ namespace diaq {
 // Kernel launchers (apply.cu, reduce.cu, adjoint.cu)
 // ---------------------------------------------------------------------------
 inline size_t amp_bytes(diaq_dtype dt) { return dt == DIAQ_C128 ? 16 : 8; }
+// SM count of the current device (cached per device ordinal).
+int device_sm_count();
+// In-place trade of the bit-l = 1 half of lo with the bit-l = 0 half of hi
+// (two shards of n_local qubits; shard.cu).
+diaq_status launch_shard_swap(void* lo, void* hi, int n_local, diaq_dtype dt, int l, cudaStream_t s);
 
 // Launch tuning knobs, filled by the autotuner (defaults otherwise).
 struct LaunchCfg {

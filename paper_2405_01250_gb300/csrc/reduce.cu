@@ -25,7 +25,7 @@ namespace diaq {
 
 // SM count of the current device, looked up once per device ordinal (it
 // does not change while the process runs, whatever happens to contexts).
-static int sm_count() {
+int device_sm_count() {
     constexpr int kMaxDevices = 64;
     static std::atomic<int> cache[kMaxDevices];
     int dev = 0;
@@ -46,7 +46,7 @@ static int sm_count() {
 
 static int reduce_blocks(int64_t work_items) {
     const int64_t want = (work_items + 255) / 256;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, int64_t(sm_count()) * 8));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, int64_t(device_sm_count()) * 8));
 }
 
 template <typename R>
@@ -341,7 +341,7 @@ diaq_status run_pauli_apply(const void* psi, void* lam, int n, diaq_dtype dt, co
     void* gm = nullptr;
     DevGroups G;
     DIAQ_TRY(upload_groups(pg, s, &gm, &G));
-    const int P = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, int64_t(sm_count()) * 16));
+    const int P = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, int64_t(device_sm_count()) * 16));
     DIAQ_PRELAUNCH("k_pauli_apply");
     if (dt == DIAQ_C128)
         k_pauli_apply<double><<<P, 256, 0, s>>>(reinterpret_cast<const double2*>(psi),

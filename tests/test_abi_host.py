@@ -167,7 +167,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         fields = re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*;", body)
         structs[name] = fields
     assert set(structs) == {"diaq_gate", "diaq_op_info", "diaq_plan_tuning", "diaq_apply_tuning",
-                            "diaq_fusion_tuning", "diaq_batch_tuning"}
+                            "diaq_fusion_tuning", "diaq_batch_tuning", "diaq_shard_step"}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "diaq.h"', "int main(void) {"]
     for name, fields in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
