@@ -214,7 +214,9 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
  * Section III-A) reads only the local columns its other rows use and writes
  * only those rows: a controlled phase or CZ moves a quarter of the bytes of
  * a full pass, a CNOT or SWAP half. The result is bit-identical to the full
- * pass. diaq_op_apply_bytes reports the bytes either way.
+ * pass. diaq_op_apply_bytes reports the bytes either way. A diagonal op of
+ * 4..6 qubits (e.g. a fused run of controlled phases) multiplies each row by
+ * its one entry; in place it skips the rows whose entry is exactly 1.
  *
  * Stored ops: each row sums its diagonals' terms in index order. For a gate
  * op on k <= 3 targets a row reads only the diagonals its local row class
@@ -231,7 +233,8 @@ diaq_status diaq_apply(diaq_op_t op, const void* x, void* y, diaq_stream_t strea
  * where a diagonal crosses rows of another class are not read. Raw ops and
  * k > 3 read every stored value, s sum_d (N - |d|). In place (on-the-fly ops
  * only, DIAQ_ERR_ARG for stored) N / 2^k x (columns read + rows written) x s
- * when the op has identity rows, else 2 N s. Host only. */
+ * when the op has identity rows (k <= 3; for a diagonal op of 4..6 qubits
+ * 2 s N / 2^k x the entries that are not exactly 1), else 2 N s. Host only. */
 diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
 
 /* Run ops[0..count-1] in order on a state: psi_in -> psi_out. psi_in and
@@ -239,9 +242,25 @@ diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
  * data are copied in and out on `stream` inside the call. work0 and work1
  * are caller-owned device state buffers (work1 may be NULL when every op is
  * on-the-fly). On-the-fly ops run in place in work0 (with the identity-row
- * skip of diaq_apply). Synchronises `stream` before returning. */
+ * skip of diaq_apply). Host copies overlap the first and last ops as in
+ * diaq_simulate_timed. Synchronises `stream` before returning. */
 diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
                           void* work0, void* work1, diaq_stream_t stream);
+
+/* diaq_simulate with the host copies overlapped and timed. When psi_in is
+ * host memory and ops[0] is an on-the-fly op of k <= 3 qubits, the input is
+ * copied in 16 slices (its groups split by their top 4 non-target bits, a
+ * few contiguous runs each) on a second stream, and ops[0] runs on each
+ * slice as soon as it has arrived; when psi_out is host memory and the last
+ * op is such an op, it runs slice by slice and each finished slice is
+ * copied out while the next is computed. The result is the same as
+ * diaq_simulate's. timeline_ms (host, 3 floats, may be NULL) receives, from
+ * the start of the call's device work, the time at which the input copy
+ * was complete, the last op was done, and the output copy was complete (the
+ * legs overlap). Creates and destroys two streams and a few events per
+ * call; synchronises `stream`. */
+diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
+                                void* work0, void* work1, diaq_stream_t stream, float* timeline_ms);
 
 /* ------------------------------------------------------------------------
  * Unitary simulation - Section II-A (a circuit's unitary as the product of
@@ -313,7 +332,8 @@ diaq_status diaq_apply_pauli_sum(const void* psi, void* lambda, int32_t n_qubits
  * never drawn; a state of zero norm gives -1 for every shot.
  *
  * The running sums are FP64 (complex64: exact FP32 squares summed as FP32
- * pairs, about 48 bits, per 16 amplitudes) over a tree of sequential sums,
+ * pairs, about 48 bits, per 16 amplitudes) over a tree of sequential sums
+ * (runs of 16 amplitudes, segs of 16 runs, tiles of 16 segs, groups of 256),
  * so where r lies within rounding of a boundary of the cumulative
  * distribution the outcome may be the neighbouring index of a plain
  * left-to-right sum; on states whose sums are exact (e.g. dyadic
@@ -321,8 +341,9 @@ diaq_status diaq_apply_pauli_sum(const void* psi, void* lambda, int32_t n_qubits
  *
  * psi: device state (16-byte aligned). uniforms: device array of n_shots
  * doubles. out_indices: device array of n_shots int64 (8-byte aligned both).
- * 0 <= n_shots <= 2^31. Allocates (N / 2048) x 1.004 doubles of device
- * scratch on `stream` and frees it there; does not synchronise. */
+ * 0 <= n_shots <= 2^31. Allocates about (N / 4096) x 273 doubles of device
+ * scratch (the tree's running sums) on `stream` and frees it there; does
+ * not synchronise. */
 diaq_status diaq_sample(const void* psi, int32_t n_qubits, diaq_dtype dtype, const double* uniforms,
                         int64_t n_shots, int64_t* out_indices, diaq_stream_t stream);
 
@@ -548,6 +569,17 @@ diaq_status diaq_plan_fusion(const diaq_gate* gates, int32_t n_gates, int32_t ma
  * unchanged. Host only. */
 diaq_status diaq_plan_fusion_commuting(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
                                        int32_t* order, int32_t* group_of_pos, int32_t* n_groups);
+
+/* Group consecutive gates so that every group is either one gate that is
+ * not diagonal or a run of diagonal gates (fixed matrices with zeros off the
+ * diagonal, or rotations with only I and Z letters; Section III-A: such
+ * gates hold their values on the principal diagonal, and so does their
+ * product) whose union of targets has at most max_k qubits and which holds
+ * at most max_depth gates. A run of controlled phases then fuses into one
+ * diagonal op, which diaq_apply multiplies row by row, while the gates
+ * between runs stay separate. Output as diaq_plan_fusion. Host only. */
+diaq_status diaq_plan_fusion_diagonal(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
+                                      int32_t* group_of_gate, int32_t* n_groups);
 
 /* For each fusion depth 1..max_depth: plan (diaq_plan_fusion, or
  * diaq_plan_fusion_commuting when `commuting` is non-zero), build and fuse

@@ -87,6 +87,8 @@ SIGNATURES = {
     "diaq_unitary_chain": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
                                           _i64p, _i64p, _vp, ctypes.POINTER(_op)]),
     "diaq_simulate": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "diaq_simulate_timed": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                           ctypes.POINTER(ctypes.c_float)]),
     "diaq_norm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
     "diaq_expect": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _u64p, _u64p, _dp, _dp, _vp]),
     "diaq_apply_pauli_sum": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32, _u64p, _u64p,
@@ -155,6 +157,7 @@ SIGNATURES.update({
     "diaq_plan_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
     "diaq_plan_fusion_commuting": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
                                                   _i32p]),
+    "diaq_plan_fusion_diagonal": (ctypes.c_int, [_gp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p]),
     "diaq_autotune_fusion": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, _vp,
                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(diaq_fusion_tuning), _vp]),

@@ -23,7 +23,7 @@ __all__ = [
     "Op", "build", "build_diaq", "fuse", "apply", "simulate", "norm", "expect", "apply_pauli_sum",
     "adjoint_grad", "gate_offsets", "diaq_matmul_host", "fuse_gates_host", "version", "gate_struct",
     "DiaqError", "DiaqEnergy", "Batch", "autotune_apply", "set_apply_launch", "plan_fusion", "autotune_fusion",
-    "build_fused", "AdjointPlan", "plan_fusion_commuting", "sample", "shard_schedule", "ShardedState",
+    "build_fused", "AdjointPlan", "plan_fusion_commuting", "sample", "shard_schedule", "ShardedState", "plan_fusion_diagonal",
     "ShardRank", "TorchDistTransport",
 ]
 
@@ -241,12 +241,17 @@ def unitary_chain(gates, n_qubits: int, dtype=torch.complex128, theta=None, prun
     return Op(h.value), nd, nz
 
 
-def simulate(ops, psi_in, psi_out, work0: torch.Tensor, work1: torch.Tensor | None = None, stream=None):
-    """Run ops in order; psi_in / psi_out may be host (numpy / CPU tensor) or device."""
+def simulate(ops, psi_in, psi_out, work0: torch.Tensor, work1: torch.Tensor | None = None, stream=None,
+             timeline: bool = False):
+    """Run ops in order; psi_in / psi_out may be host (numpy / CPU tensor) or
+    device. With timeline=True returns (psi_out, [input copied, last op done,
+    output copied] in ms from the start of the call's device work)."""
     arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
-    check(lib().diaq_simulate(arr, len(ops), _ptr(psi_in), _ptr(psi_out), _ptr(work0),
-                              _ptr(work1) if work1 is not None else None, _stream(stream)))
-    return psi_out
+    tl = (ctypes.c_float * 3)()
+    check(lib().diaq_simulate_timed(arr, len(ops), _ptr(psi_in), _ptr(psi_out), _ptr(work0),
+                                    _ptr(work1) if work1 is not None else None, _stream(stream),
+                                    tl if timeline else None))
+    return (psi_out, [tl[0], tl[1], tl[2]]) if timeline else psi_out
 
 
 def norm(psi: torch.Tensor, stream=None) -> float:
@@ -421,13 +426,27 @@ def plan_fusion_commuting(gates, max_k: int, max_depth: int) -> tuple:
     return order[:len(gates)].tolist(), grp[:len(gates)].tolist()
 
 
+def plan_fusion_diagonal(gates, max_k: int, max_depth: int) -> list:
+    """Group index per gate: runs of diagonal gates fuse, other gates stay
+    alone (diaq_plan_fusion_diagonal)."""
+    arr, keep = _gate_array(gates)
+    grp = np.zeros(max(1, len(gates)), dtype=np.int32)
+    ng = ctypes.c_int32(0)
+    check(lib().diaq_plan_fusion_diagonal(arr, len(gates), max_k, max_depth, grp.ctypes.data_as(N._i32p),
+                                          ctypes.byref(ng)))
+    return grp[: len(gates)].tolist()
+
+
 def build_fused(gates, n_qubits: int, max_k: int, max_depth: int, dtype=torch.complex128, variant="onthefly",
-                theta=None, stream=None, commuting: bool = False) -> list:
+                theta=None, stream=None, commuting: bool = False, diagonal: bool = False) -> list:
     """Ops for a circuit with gates fused per plan_fusion (consecutive
-    groups) or, with commuting=True, per plan_fusion_commuting."""
+    groups), per plan_fusion_commuting (commuting=True) or per
+    plan_fusion_diagonal (diagonal=True: runs of diagonal gates only)."""
     if commuting:
         order, grp = plan_fusion_commuting(gates, max_k, max_depth)
         gates = [gates[i] for i in order]
+    elif diagonal:
+        grp = plan_fusion_diagonal(gates, max_k, max_depth)
     else:
         grp = plan_fusion(gates, max_k, max_depth)
     ops, i = [], 0

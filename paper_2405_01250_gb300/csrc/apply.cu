@@ -35,7 +35,8 @@ namespace diaq {
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 struct SmallGateArgs {
-    int64_t n_groups;
+    int64_t g_base;              // first group of the launch
+    int64_t n_groups;            // one past the last group
     int st[K];                   // targets, ascending
     int64_t off[1 << K];         // full-system offset of local index c
     R re[1 << (2 * K)];
@@ -64,7 +65,7 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
     constexpr int D = 1 << K;
     using A = amp_t<R>;
     const int64_t T = blockDim.x;
-    const int64_t g0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
+    const int64_t g0 = a.g_base + (int64_t)blockIdx.x * T * G + threadIdx.x;
     A v[G][D];
     int64_t b[G];
 #pragma unroll
@@ -306,10 +307,11 @@ LaunchCfg& launch_cfg(diaq_dtype dt, int k) {
 
 template <typename R, int K, int G>
 static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void* y, int threads,
-                                  cudaStream_t s) {
+                                  int64_t g_begin, int64_t g_end, cudaStream_t s) {
     SmallGateArgs<R, K> a;
     std::memset(&a, 0, sizeof(a));
-    a.n_groups = int64_t(1) << (n - K);
+    a.g_base = g_begin;
+    a.n_groups = g_end;
     sorted_targets(g, a.st);
     local_offsets(g, a.off);
     constexpr int DD = 1 << (2 * K);
@@ -339,7 +341,8 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
         if (diag) a.pattern = 3;
     }
     const int64_t per_block = int64_t(threads) * G;
-    const int64_t blocks = (a.n_groups + per_block - 1) / per_block;
+    const int64_t blocks = (g_end - g_begin + per_block - 1) / per_block;
+    if (blocks <= 0) return DIAQ_OK;
     DIAQ_PRELAUNCH("k_apply_small");
     k_apply_small<R, K, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
         reinterpret_cast<const amp_t<R>*>(x), reinterpret_cast<amp_t<R>*>(y), a);
@@ -349,14 +352,32 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
 
 template <typename R, int K>
 static diaq_status launch_small(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y,
-                                cudaStream_t s) {
+                                int64_t g_begin, int64_t g_end, cudaStream_t s) {
     const LaunchCfg& cfg = launch_cfg(dt, K);
     const int G = cfg.groups > 0 ? cfg.groups : default_groups(dt, K);
     const int threads = cfg.threads;
     switch (G) {
-        case 1: return launch_small_G<R, K, 1>(n, g, x, y, threads, s);
-        case 2: return launch_small_G<R, K, 2>(n, g, x, y, threads, s);
-        default: return launch_small_G<R, K, 4>(n, g, x, y, threads, s);
+        case 1: return launch_small_G<R, K, 1>(n, g, x, y, threads, g_begin, g_end, s);
+        case 2: return launch_small_G<R, K, 2>(n, g, x, y, threads, g_begin, g_end, s);
+        default: return launch_small_G<R, K, 4>(n, g, x, y, threads, g_begin, g_end, s);
+    }
+}
+
+// Groups [g_begin, g_end) of a k <= 3 gate (all of them: 0, 2^(n-k)).
+diaq_status launch_gate_local_range(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y,
+                                    int64_t g_begin, int64_t g_end, cudaStream_t s) {
+    if (g.k < 1 || g.k > 3) return fail(DIAQ_ERR_UNSUPPORTED, "group ranges need k <= 3 (k = %d)", g.k);
+    if (dt == DIAQ_C128) {
+        switch (g.k) {
+            case 1: return launch_small<double, 1>(n, dt, g, x, y, g_begin, g_end, s);
+            case 2: return launch_small<double, 2>(n, dt, g, x, y, g_begin, g_end, s);
+            default: return launch_small<double, 3>(n, dt, g, x, y, g_begin, g_end, s);
+        }
+    }
+    switch (g.k) {
+        case 1: return launch_small<float, 1>(n, dt, g, x, y, g_begin, g_end, s);
+        case 2: return launch_small<float, 2>(n, dt, g, x, y, g_begin, g_end, s);
+        default: return launch_small<float, 3>(n, dt, g, x, y, g_begin, g_end, s);
     }
 }
 
@@ -427,20 +448,8 @@ diaq_status upload_matrix(diaq_op_s* op) {
 
 diaq_status launch_gate_local(int n, diaq_dtype dt, const GateDesc& g, const void* d_matrix,
                               const void* x, void* y, cudaStream_t s) {
-    if (g.k <= 3) {
-        if (dt == DIAQ_C128) {
-            switch (g.k) {
-                case 1: return launch_small<double, 1>(n, dt, g, x, y, s);
-                case 2: return launch_small<double, 2>(n, dt, g, x, y, s);
-                default: return launch_small<double, 3>(n, dt, g, x, y, s);
-            }
-        }
-        switch (g.k) {
-            case 1: return launch_small<float, 1>(n, dt, g, x, y, s);
-            case 2: return launch_small<float, 2>(n, dt, g, x, y, s);
-            default: return launch_small<float, 3>(n, dt, g, x, y, s);
-        }
-    }
+    if (g.k <= 3) return launch_gate_local_range(n, dt, g, x, y, 0, int64_t(1) << (n - g.k), s);
+    if (is_diagonal(g)) return launch_diag(n, dt, g, x, y, s);
     if (!d_matrix) return fail(DIAQ_ERR_ARG, "k = %d op has no device matrix", g.k);
     return dt == DIAQ_C128 ? launch_large<double>(n, dt, g, d_matrix, x, y, s)
                            : launch_large<float>(n, dt, g, d_matrix, x, y, s);

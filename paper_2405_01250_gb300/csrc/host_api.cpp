@@ -927,8 +927,85 @@ static int mem_kind(const void* p) {
     return 0;
 }
 
-diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out, void* work0,
-                          void* work1, diaq_stream_t stream) {
+// The slices of an op (on the fly, k <= 3) for copies that overlap it: its
+// 2^(n-k) groups split into 2^b ranges by the top b non-target bits. Slice
+// s holds the amplitudes whose b highest non-target bits equal s; in memory
+// that is one contiguous run of 2^L amplitudes (L the lowest of those bits)
+// per setting of the targets above L.
+namespace {
+struct Slice {
+    int64_t g_begin, g_end;
+    std::vector<int64_t> runs;  // first amplitude of each run
+};
+struct SlicePlan {
+    int64_t run_len = 0;
+    std::vector<Slice> slices;
+};
+
+bool plan_slices(const diaq_op_s* op, int b, SlicePlan* out) {
+    if (op->variant != DIAQ_ONTHEFLY || op->op_class == DIAQ_CLASS_RAW) return false;
+    const int n = op->n, k = op->gate.k;
+    if (k < 1 || k > 3 || n - k < b + 1) return false;
+    std::vector<int> nt, above;
+    for (int q = 0; q < n; ++q) {
+        bool t = false;
+        for (int a = 0; a < k; ++a) t |= op->gate.targets[a] == q;
+        if (!t) nt.push_back(q);
+    }
+    const int L = nt[size_t(n - k - b)];
+    for (int a = 0; a < k; ++a)
+        if (op->gate.targets[a] > L) above.push_back(op->gate.targets[a]);
+    const int64_t per = (int64_t(1) << (n - k)) >> b;
+    out->run_len = int64_t(1) << L;
+    out->slices.assign(size_t(1) << b, Slice{});
+    for (int64_t s = 0; s < (int64_t(1) << b); ++s) {
+        Slice& sl = out->slices[size_t(s)];
+        sl.g_begin = s * per;
+        sl.g_end = sl.g_begin + per;
+        int64_t base = 0;
+        for (int i = 0; i < b; ++i)
+            if ((s >> i) & 1) base |= int64_t(1) << nt[size_t(n - k - b + i)];
+        for (int64_t c = 0; c < (int64_t(1) << above.size()); ++c) {
+            int64_t st = base;
+            for (size_t j = 0; j < above.size(); ++j)
+                if ((c >> j) & 1) st |= int64_t(1) << above[j];
+            sl.runs.push_back(st);
+        }
+    }
+    return true;
+}
+
+// An on-the-fly op in place on groups [g0, g1) (k <= 3), or on all of them.
+diaq_status run_inplace(const diaq_op_s* op, void* x, int64_t g0, int64_t g1, cudaStream_t s) {
+    bool done = false;
+    DIAQ_TRY(launch_inplace_skip_range(op, x, g0, g1, s, &done));
+    if (done) return DIAQ_OK;
+    if (op->gate.k <= 3) return launch_gate_local_range(op->n, op->dtype, op->gate, x, x, g0, g1, s);
+    return launch_onthefly(op, x, x, s);
+}
+
+// Streams and events of one diaq_simulate call, released on every path.
+struct SimResources {
+    cudaStream_t cin = nullptr, cout = nullptr;
+    std::vector<cudaEvent_t> events;
+    cudaEvent_t make(bool timing) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, timing ? cudaEventDefault : cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        events.push_back(e);
+        return e;
+    }
+    ~SimResources() {
+        if (cin) cudaStreamSynchronize(cin);
+        if (cout) cudaStreamSynchronize(cout);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        if (cin) cudaStreamDestroy(cin);
+        if (cout) cudaStreamDestroy(cout);
+    }
+};
+}  // namespace
+
+diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out, void* work0,
+                                void* work1, diaq_stream_t stream, float* timeline_ms) {
     clear_error_device();
     if (count < 0 || (count && !ops)) return fail(DIAQ_ERR_ARG, "bad op list");
     if (!psi_in || !psi_out || !work0) return fail(DIAQ_ERR_ARG, "NULL state or work buffer");
@@ -943,26 +1020,131 @@ diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_i
     }
     if (any_stored && !work1) return fail(DIAQ_ERR_ARG, "stored ops need a second work buffer");
     if (mem_kind(work0) != 1 || (work1 && mem_kind(work1) != 1)) return fail(DIAQ_ERR_ARG, "work buffers must be device memory");
-    const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
+    const size_t s_amp = amp_bytes(dt);
+    const size_t bytes = (size_t(1) << n) * s_amp;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const cudaMemcpyKind kin = mem_kind(psi_in) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    DIAQ_CUDA(cudaMemcpyAsync(work0, psi_in, bytes, kin, s));
+    const bool in_host = !mem_kind(psi_in), out_host = !mem_kind(psi_out);
+    // host copies overlap the first op (input) and the last op (output),
+    // slice by slice, when those ops run in place on the fly with k <= 3
+    constexpr int kSliceBits = 4;
+    SlicePlan pin, pout;
+    const bool pipe_in = in_host && plan_slices(ops[0], kSliceBits, &pin);
+    const bool pipe_out = out_host && plan_slices(ops[count - 1], kSliceBits, &pout) && (count > 1 || pipe_in);
+    SimResources R;
+    const bool timing = timeline_ms != nullptr;
+    cudaEvent_t t_start = nullptr, t_in = nullptr, t_compute = nullptr, t_end = nullptr;
+    if (timing) {
+        t_start = R.make(true);
+        t_in = R.make(true);
+        t_compute = R.make(true);
+        t_end = R.make(true);
+        if (!t_start || !t_in || !t_compute || !t_end) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+        DIAQ_CUDA(cudaEventRecord(t_start, s));
+    }
+    if (pipe_in || pipe_out) {
+        cudaEvent_t e0 = R.make(false);
+        if (!e0) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+        DIAQ_CUDA(cudaStreamCreateWithFlags(&R.cin, cudaStreamNonBlocking));
+        DIAQ_CUDA(cudaStreamCreateWithFlags(&R.cout, cudaStreamNonBlocking));
+        // the copies start after the work already queued on `stream`
+        DIAQ_CUDA(cudaEventRecord(e0, s));
+        DIAQ_CUDA(cudaStreamWaitEvent(R.cin, e0, 0));
+        DIAQ_CUDA(cudaStreamWaitEvent(R.cout, e0, 0));
+    }
+    int first = 0, last = count;  // ops [first, last) run whole below
+    bool out_sent = false;        // the output copy is already queued
+    if (pipe_in) {
+        const size_t run_bytes = size_t(pin.run_len) * s_amp;
+        std::vector<cudaEvent_t> got(pin.slices.size());
+        for (size_t j = 0; j < pin.slices.size(); ++j) {
+            for (int64_t r : pin.slices[j].runs)
+                DIAQ_CUDA(cudaMemcpyAsync(static_cast<char*>(work0) + size_t(r) * s_amp,
+                                          static_cast<const char*>(psi_in) + size_t(r) * s_amp, run_bytes,
+                                          cudaMemcpyHostToDevice, R.cin));
+            got[j] = R.make(false);
+            if (!got[j]) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+            DIAQ_CUDA(cudaEventRecord(got[j], R.cin));
+        }
+        if (timing) DIAQ_CUDA(cudaEventRecord(t_in, R.cin));
+        const bool also_out = pipe_out && count == 1;
+        const size_t out_run_bytes = size_t(pout.run_len) * s_amp;
+        for (size_t j = 0; j < pin.slices.size(); ++j) {
+            DIAQ_CUDA(cudaStreamWaitEvent(s, got[j], 0));
+            DIAQ_TRY(run_inplace(ops[0], work0, pin.slices[j].g_begin, pin.slices[j].g_end, s));
+            if (also_out) {  // one op: each slice leaves as soon as it is done
+                cudaEvent_t done = R.make(false);
+                if (!done) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+                DIAQ_CUDA(cudaEventRecord(done, s));
+                DIAQ_CUDA(cudaStreamWaitEvent(R.cout, done, 0));
+                for (int64_t r : pout.slices[j].runs)
+                    DIAQ_CUDA(cudaMemcpyAsync(static_cast<char*>(psi_out) + size_t(r) * s_amp,
+                                              static_cast<const char*>(work0) + size_t(r) * s_amp, out_run_bytes,
+                                              cudaMemcpyDeviceToHost, R.cout));
+            }
+        }
+        first = 1;
+        out_sent = also_out;
+    } else {
+        const cudaMemcpyKind kin = in_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+        DIAQ_CUDA(cudaMemcpyAsync(work0, psi_in, bytes, kin, s));
+        if (timing) DIAQ_CUDA(cudaEventRecord(t_in, s));
+    }
+    if (pipe_out && !out_sent) last = count - 1;
     void* cur = work0;
     void* other = work1;
-    for (int i = 0; i < count; ++i) {
+    for (int i = first; i < last; ++i) {
         if (ops[i]->variant == DIAQ_ONTHEFLY) {
-            bool done = false;
-            DIAQ_TRY(launch_inplace_skip(ops[i], cur, s, &done));
-            if (!done) DIAQ_TRY(launch_onthefly(ops[i], cur, cur, s));
+            DIAQ_TRY(run_inplace(ops[i], cur, 0, ops[i]->gate.k <= 3 ? int64_t(1) << (n - ops[i]->gate.k) : 0, s));
         } else {
             DIAQ_TRY(launch_stored(ops[i], cur, other, s));
             std::swap(cur, other);
         }
     }
-    const cudaMemcpyKind kout = mem_kind(psi_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    DIAQ_CUDA(cudaMemcpyAsync(psi_out, cur, bytes, kout, s));
+    if (pipe_out && !out_sent) {
+        // the last op (on the fly) runs in place on the current buffer,
+        // slice by slice, and each slice goes out as soon as it is done
+        const size_t run_bytes = size_t(pout.run_len) * s_amp;
+        for (size_t j = 0; j < pout.slices.size(); ++j) {
+            DIAQ_TRY(run_inplace(ops[count - 1], cur, pout.slices[j].g_begin, pout.slices[j].g_end, s));
+            cudaEvent_t done = R.make(false);
+            if (!done) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+            DIAQ_CUDA(cudaEventRecord(done, s));
+            DIAQ_CUDA(cudaStreamWaitEvent(R.cout, done, 0));
+            for (int64_t r : pout.slices[j].runs)
+                DIAQ_CUDA(cudaMemcpyAsync(static_cast<char*>(psi_out) + size_t(r) * s_amp,
+                                          static_cast<const char*>(cur) + size_t(r) * s_amp, run_bytes,
+                                          cudaMemcpyDeviceToHost, R.cout));
+        }
+    }
+    if (timing) DIAQ_CUDA(cudaEventRecord(t_compute, s));
+    if (pipe_out) {
+        cudaEvent_t copied = R.make(false);
+        if (!copied) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+        DIAQ_CUDA(cudaEventRecord(copied, R.cout));
+        DIAQ_CUDA(cudaStreamWaitEvent(s, copied, 0));
+    } else {
+        const cudaMemcpyKind kout = out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        DIAQ_CUDA(cudaMemcpyAsync(psi_out, cur, bytes, kout, s));
+    }
+    if (R.cin) {  // nothing on `stream` may outlive this call's input copies
+        cudaEvent_t in_done = R.make(false);
+        if (!in_done) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
+        DIAQ_CUDA(cudaEventRecord(in_done, R.cin));
+        DIAQ_CUDA(cudaStreamWaitEvent(s, in_done, 0));
+    }
+    if (timing) DIAQ_CUDA(cudaEventRecord(t_end, s));
     DIAQ_CUDA(cudaStreamSynchronize(s));
+    if (timing) {
+        DIAQ_CUDA(cudaEventElapsedTime(&timeline_ms[0], t_start, t_in));
+        DIAQ_CUDA(cudaEventElapsedTime(&timeline_ms[1], t_start, t_compute));
+        DIAQ_CUDA(cudaEventElapsedTime(&timeline_ms[2], t_start, t_end));
+    }
     return DIAQ_OK;
+}
+
+diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out, void* work0,
+                          void* work1, diaq_stream_t stream) {
+    return diaq_simulate_timed(ops, count, psi_in, psi_out, work0, work1, stream, nullptr);
 }
 
 static diaq_status check_state(const void* psi, int n, diaq_dtype dt) {

@@ -25,7 +25,8 @@ namespace diaq {
 
 template <typename R, int K>
 struct RowsArgs {
-    int64_t n_groups;
+    int64_t g_base;         // first group of the launch
+    int64_t n_groups;       // one past the last group
     int st[K];              // targets, ascending
     int64_t off[1 << K];    // full-system offset of local index c
     uint32_t ld_mask;       // local columns read by the changed rows
@@ -41,7 +42,7 @@ k_apply_rows(amp_t<R>* x, const __grid_constant__ RowsArgs<R, K> a) {
     constexpr int D = 1 << K;
     using A = amp_t<R>;
     const int64_t T = blockDim.x;
-    const int64_t g0 = (int64_t)blockIdx.x * T * G + threadIdx.x;
+    const int64_t g0 = a.g_base + (int64_t)blockIdx.x * T * G + threadIdx.x;
     A v[G][D];
     int64_t b[G];
     // every load of a group precedes its stores: the group is read whole
@@ -110,7 +111,7 @@ void inplace_masks(const GateDesc& g, diaq_dtype dt, uint32_t* ld_mask, uint32_t
 int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g) {
     const int64_t N = int64_t(1) << n;
     const int64_t s = int64_t(amp_bytes(dt));
-    if (g.k > 3) return 2 * N * s;
+    if (g.k > 3) return is_diagonal(g) ? diag_inplace_bytes(n, dt, g) : 2 * N * s;
     uint32_t ld, st;
     inplace_masks(g, dt, &ld, &st);
     const uint32_t full = (1u << (1 << g.k)) - 1u;
@@ -119,10 +120,12 @@ int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g) {
 }
 
 template <typename R, int K, int G>
-static diaq_status launch_rows_G(int n, const GateDesc& g, uint32_t ld, uint32_t stm, void* x, cudaStream_t s) {
+static diaq_status launch_rows_G(int n, const GateDesc& g, uint32_t ld, uint32_t stm, void* x, int64_t g_begin,
+                                 int64_t g_end, cudaStream_t s) {
     RowsArgs<R, K> a;
     std::memset(&a, 0, sizeof(a));
-    a.n_groups = int64_t(1) << (n - K);
+    a.g_base = g_begin;
+    a.n_groups = g_end;
     for (int i = 0; i < K; ++i) a.st[i] = g.targets[i];
     std::sort(a.st, a.st + K);
     for (int c = 0; c < (1 << K); ++c) {
@@ -141,7 +144,8 @@ static diaq_status launch_rows_G(int n, const GateDesc& g, uint32_t ld, uint32_t
     }
     const int threads = 256;
     const int64_t per_block = int64_t(threads) * G;
-    const int64_t blocks = (a.n_groups + per_block - 1) / per_block;
+    const int64_t blocks = (g_end - g_begin + per_block - 1) / per_block;
+    if (blocks <= 0) return DIAQ_OK;
     DIAQ_PRELAUNCH("k_apply_rows");
     k_apply_rows<R, K, G><<<dim3((unsigned)blocks), threads, 0, s>>>(reinterpret_cast<amp_t<R>*>(x), a);
     DIAQ_CUDA(cudaGetLastError());
@@ -149,17 +153,25 @@ static diaq_status launch_rows_G(int n, const GateDesc& g, uint32_t ld, uint32_t
 }
 
 template <typename R>
-static diaq_status launch_rows(int n, const GateDesc& g, uint32_t ld, uint32_t st, void* x, cudaStream_t s) {
+static diaq_status launch_rows(int n, const GateDesc& g, uint32_t ld, uint32_t st, void* x, int64_t g_begin,
+                               int64_t g_end, cudaStream_t s) {
     // groups per thread: enough independent loads in flight, registers bounded
     constexpr bool dbl = sizeof(R) == 8;
     switch (g.k) {
-        case 1: return launch_rows_G<R, 1, 4>(n, g, ld, st, x, s);
-        case 2: return launch_rows_G<R, 2, dbl ? 2 : 4>(n, g, ld, st, x, s);
-        default: return launch_rows_G<R, 3, dbl ? 1 : 2>(n, g, ld, st, x, s);
+        case 1: return launch_rows_G<R, 1, 4>(n, g, ld, st, x, g_begin, g_end, s);
+        case 2: return launch_rows_G<R, 2, dbl ? 2 : 4>(n, g, ld, st, x, g_begin, g_end, s);
+        default: return launch_rows_G<R, 3, dbl ? 1 : 2>(n, g, ld, st, x, g_begin, g_end, s);
     }
 }
 
 diaq_status launch_inplace_skip(const diaq_op_s* op, void* x, cudaStream_t s, bool* launched) {
+    return op->gate.k >= 1 && op->gate.k <= 3
+               ? launch_inplace_skip_range(op, x, 0, int64_t(1) << (op->n - op->gate.k), s, launched)
+               : launch_inplace_skip_range(op, x, 0, 0, s, launched);
+}
+
+diaq_status launch_inplace_skip_range(const diaq_op_s* op, void* x, int64_t g_begin, int64_t g_end, cudaStream_t s,
+                                      bool* launched) {
     *launched = false;
     if (op->variant != DIAQ_ONTHEFLY || op->op_class == DIAQ_CLASS_RAW || op->gate.k > 3) return DIAQ_OK;
     uint32_t ld, st;
@@ -168,8 +180,8 @@ diaq_status launch_inplace_skip(const diaq_op_s* op, void* x, cudaStream_t s, bo
     if (st == full) return DIAQ_OK;  // every row changes: the full kernel is the right one
     *launched = true;
     if (st == 0) return DIAQ_OK;     // the identity: nothing changes in place
-    return op->dtype == DIAQ_C128 ? launch_rows<double>(op->n, op->gate, ld, st, x, s)
-                                  : launch_rows<float>(op->n, op->gate, ld, st, x, s);
+    return op->dtype == DIAQ_C128 ? launch_rows<double>(op->n, op->gate, ld, st, x, g_begin, g_end, s)
+                                  : launch_rows<float>(op->n, op->gate, ld, st, x, g_begin, g_end, s);
 }
 
 }  // namespace diaq

@@ -149,10 +149,24 @@ diaq_status launch_gather_diagonals(const diaq_op_s* src, const std::vector<int3
 // no identity row or is not a k <= 3 on-the-fly gate op; the caller then
 // runs the full kernel.
 diaq_status launch_inplace_skip(const diaq_op_s* op, void* x, cudaStream_t s, bool* launched);
+// The same on the groups [g_begin, g_end) only (a group: the 2^k amplitudes
+// that share their non-target bits, numbered by those bits).
+diaq_status launch_inplace_skip_range(const diaq_op_s* op, void* x, int64_t g_begin, int64_t g_end, cudaStream_t s,
+                                      bool* launched);
+// On-the-fly apply of a k <= 3 gate on the groups [g_begin, g_end) only.
+diaq_status launch_gate_local_range(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y,
+                                    int64_t g_begin, int64_t g_end, cudaStream_t s);
 // Local columns read and local rows written by that kernel.
 void inplace_masks(const GateDesc& g, diaq_dtype dt, uint32_t* ld_mask, uint32_t* st_mask);
 // Algorithmic bytes of one in-place on-the-fly apply of g.
 int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
+
+// Diagonal ops of 4..6 qubits (diag.cu): one table lookup and one complex
+// multiply per row; in place (x == y) rows whose entry is exactly 1 are
+// skipped.
+bool is_diagonal(const GateDesc& g);
+diaq_status launch_diag(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y, cudaStream_t s);
+int64_t diag_inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
 
 // Pauli-sum terms grouped by X mask, prepared on the host.
 struct PauliGroups {

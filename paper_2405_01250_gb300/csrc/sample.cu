@@ -5,30 +5,36 @@
 // uniform u per shot: the smallest i whose running sum of |psi|^2 exceeds
 // r = u * ||psi||^2.
 //
-// No cumulative array is written. The state is read once to build a sum
-// tree of fixed fan-out whose every node is the SEQUENTIAL sum, in index
-// order, of its children:
-//   run   16 consecutive amplitudes            (one thread)
-//   seg   32 runs = 512 amplitudes             (one warp)
-//   tile  4 segs  = 2048 amplitudes            (one block; totals stored)
-//   level 256 nodes of the level below         (stored, up to the single total)
-// A shot then descends from the total: at each node it walks the children's
-// running sum and enters the first child whose running sum exceeds the
-// shot's remaining r, subtracting the sum before it. Inside a tile the seg,
-// run and amplitude sums are recomputed with the same operation sequence as
-// the tile pass, so they reproduce its totals bit for bit.
+// No cumulative array of N entries is written. One pass over the state
+// builds a tree of sums in which every node is the SEQUENTIAL sum, in index
+// order, of its children, and stores each group of siblings as inclusive
+// running sums (prefixes):
+//   run    16 consecutive amplitudes                (one thread; not stored)
+//   seg    16 runs = 256 amplitudes                 (run prefixes stored)
+//   tile   16 segs = 4096 amplitudes, one block     (seg prefixes stored)
+//   level  groups of 256 nodes of the level below   (prefixes stored, up to one node)
+// A shot descends from the total: in each group it binary-searches the
+// first prefix that exceeds its remaining r, subtracts the prefix before it,
+// and finally walks the 16 amplitudes of one run with the same operation
+// sequence as the tile pass, which reproduces the stored run prefix bit for
+// bit. Prefixes are non-negative doubles, so they are compared as their
+// 64-bit patterns on the integer pipe.
 //
-// Because every running sum is sequential, a child of zero total leaves it
-// unchanged, so a zero-probability outcome is never entered. When rounding
-// leaves the remaining r at or above a node's own total (or u = 1), the
-// descent takes the node's last child of non-zero total, then the last one
-// below that, and so on: the outcome still has non-zero probability.
+// Because every running sum is sequential, a child of zero total leaves its
+// prefix unchanged, so a zero-probability outcome is never entered. When
+// rounding leaves the remaining r at or above a group's last prefix (or
+// u = 1), the descent takes the group's last child of non-zero total, then
+// the last one below that, and so on: the outcome still has non-zero
+// probability.
 //
-// Sums: complex128 accumulates re^2 then im^2 with FP64 fused multiply-adds
+// Cost. complex128 accumulates re^2 then im^2 with FP64 fused multiply-adds
 // (two FP64 instructions per amplitude, the fewest for |psi|^2 in FP64);
 // complex64 keeps each run as an unevaluated FP32 pair hi + lo fed with the
 // exact squares (two-product and two-sum, about 48 bits), converted to FP64
-// once per run, so the FP64 pipe is not used per amplitude.
+// once per run. The sequential sums above the runs are done by one thread
+// per group, so a tile spends 32 warp-wide FP64 additions on them, not one
+// per lane: on this GPU a warp-wide FP64 instruction occupies the SM's FP64
+// pipe for about 19 cycles whatever its active mask.
 
 #include <cuda_runtime.h>
 
@@ -40,14 +46,14 @@
 namespace diaq {
 namespace {
 
-constexpr int kRun = 16;                            // amplitudes per run
-constexpr int kSegRuns = 32;                        // runs per seg (one per lane)
-constexpr int kSeg = kRun * kSegRuns;               // 512 amplitudes
-constexpr int kTileSegs = 4;                        // segs per tile (one per warp)
-constexpr int kTile = kSeg * kTileSegs;             // 2048 amplitudes
-constexpr int kFan = 256;                           // children per node above the tiles
-constexpr int kMaxLevels = 8;                       // 2^34 / 2048 = 2^23 tiles -> 4 levels
-constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRun = 16;                  // amplitudes per run
+constexpr int kSegRuns = 16;              // runs per seg
+constexpr int kTileSegs = 16;             // segs per tile
+constexpr int kTileRuns = kSegRuns * kTileSegs;   // 256 runs: one per thread
+constexpr int kTile = kRun * kTileRuns;   // 4096 amplitudes
+constexpr int kWarpRuns = 32;             // runs staged by one warp
+constexpr int kFan = 256;                 // group size above the tiles
+constexpr int kMaxLevels = 8;             // 2^34 / 4096 = 2^22 tiles -> 4 levels
 
 // Running sum of |psi_i|^2 over one run, in one fixed operation sequence
 // shared by the tile pass and the descent.
@@ -90,195 +96,178 @@ __device__ __forceinline__ double2 zero_amp<double>() { return make_double2(0.0,
 template <>
 __device__ __forceinline__ float2 zero_amp<float>() { return make_float2(0.0f, 0.0f); }
 
-// Sequential sum over the warp's lanes, in lane order, of one value per
-// lane; every lane gets the total.
-__device__ __forceinline__ double lane_ordered_sum(double v) {
-    double s = 0.0;
+// Ordering of non-negative doubles by their bit patterns.
+__device__ __forceinline__ long long key(double v) { return __double_as_longlong(v); }
+
+// Running sums of 16 values in place, sequential from acc: loads first, then
+// the chain of additions in registers, then the stores.
+__device__ __forceinline__ double prefix16(double* v, double acc) {
+    double x[16];
 #pragma unroll
-    for (int l = 0; l < 32; ++l) s = __dadd_rn(s, __shfl_sync(kFull, v, l));
-    return s;
+    for (int t = 0; t < 16; ++t) x[t] = v[t];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        acc = __dadd_rn(acc, x[t]);
+        x[t] = acc;
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = x[t];
+    return acc;
+}
+
+template <typename R>
+constexpr int tile_smem_bytes() {
+    return 8 * kWarpRuns * (kRun + 1) * int(sizeof(amp_t<R>));
 }
 
 // ---------------------------------------------------------------------------
-// Tile pass: one block of 4 warps per 2048 amplitudes. Each warp stages its
-// seg in shared memory with coalesced loads (one padding amplitude per run
-// keeps the per-lane reads free of bank conflicts), then lane l sums run l.
+// Tile pass: one block of 256 threads per 4096 amplitudes. Each warp stages
+// its 512 amplitudes in shared memory with coalesced loads (one padding
+// amplitude per run keeps the per-lane reads free of bank conflicts); thread
+// t then sums run t. Threads 0..15 form the run prefixes of seg t, thread 0
+// the seg prefixes of the tile.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(128) k_sample_tiles(const amp_t<R>* __restrict__ psi, int64_t N,
+__global__ void __launch_bounds__(256) k_sample_tiles(const amp_t<R>* __restrict__ psi, int64_t N,
+                                                      double* __restrict__ run_pre, double* __restrict__ seg_pre,
                                                       double* __restrict__ tile_tot) {
-    __shared__ amp_t<R> stage[kTileSegs][kSegRuns][kRun + 1];
-    __shared__ double seg_tot[kTileSegs];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using A = amp_t<R>;
+    A(*stage)[kWarpRuns][kRun + 1] = reinterpret_cast<A(*)[kWarpRuns][kRun + 1]>(smem_raw);
+    __shared__ double rp[kTileRuns];
+    __shared__ double sp[kTileSegs];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t seg_base = (int64_t)blockIdx.x * kTile + (int64_t)warp * kSeg;
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * (kWarpRuns * kRun);
+    // all 16 loads in flight before the first shared-memory store
+    A v[kRun];
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+        const int64_t i = base + 32 * j + lane;
+        v[j] = i < N ? ld_stream(psi + i) : zero_amp<R>();
+    }
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
         const int g = 32 * j + lane;
-        const int64_t i = seg_base + g;
-        stage[warp][g / kRun][g % kRun] = i < N ? ld_stream(psi + i) : zero_amp<R>();
+        stage[warp][g / kRun][g % kRun] = v[j];
     }
     __syncwarp();
     RunSum<R> rs;
 #pragma unroll
     for (int e = 0; e < kRun; ++e) rs.add(stage[warp][lane][e]);
-    const double seg = lane_ordered_sum(rs.value());
-    if (lane == 0) seg_tot[warp] = seg;
+    rp[threadIdx.x] = rs.value();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int s = 0; s < kTileSegs; ++s) t = __dadd_rn(t, seg_tot[s]);
-        tile_tot[blockIdx.x] = t;
-    }
+    static_assert(kSegRuns == 16 && kTileSegs == 16, "prefix16 walks groups of 16");
+    if (threadIdx.x < kTileSegs) sp[threadIdx.x] = prefix16(rp + threadIdx.x * kSegRuns, 0.0);
+    __syncthreads();
+    run_pre[(int64_t)blockIdx.x * kTileRuns + threadIdx.x] = rp[threadIdx.x];
+    if (threadIdx.x == 0) tile_tot[blockIdx.x] = prefix16(sp, 0.0);
+    __syncthreads();
+    if (threadIdx.x < kTileSegs) seg_pre[(int64_t)blockIdx.x * kTileSegs + threadIdx.x] = sp[threadIdx.x];
 }
 
-// One level up: parent j = sequential sum of children [256 j, 256 j + 256).
-__global__ void __launch_bounds__(128) k_sample_level(const double* __restrict__ child, int64_t n_child,
-                                                      double* __restrict__ parent, int64_t n_parent) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n_parent) return;
-    const int64_t b = j * kFan, e = b + kFan < n_child ? b + kFan : n_child;
-    double s = 0.0;
-    for (int64_t c = b; c < e; ++c) s = __dadd_rn(s, child[c]);
-    parent[j] = s;
+// One level up: group j of 256 values becomes their running sums (pre) and
+// its total (parent[j]). One block per group, coalesced loads.
+__global__ void __launch_bounds__(256) k_sample_level(const double* __restrict__ child, int64_t n_child,
+                                                      double* __restrict__ pre, double* __restrict__ parent) {
+    __shared__ double v[kFan];
+    const int64_t c = (int64_t)blockIdx.x * kFan + threadIdx.x;
+    v[threadIdx.x] = c < n_child ? child[c] : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // values past the end are 0 and leave the running sum unchanged
+        double acc = 0.0;
+        for (int t = 0; t < kFan; t += 16) acc = prefix16(v + t, acc);
+        parent[blockIdx.x] = acc;
+    }
+    __syncthreads();
+    if (c < n_child) pre[c] = v[threadIdx.x];
 }
 
 struct Levels {
-    const double* lv[kMaxLevels];  // lv[0]: tile totals ... lv[m-1]: the total (one node)
-    int64_t count[kMaxLevels];
+    const double* pre[kMaxLevels];  // pre[L]: running sums of level L within groups of 256
+    int64_t count[kMaxLevels];      // nodes at level L (level 0: tiles); count[m-1] == 1
+    const double* total;            // the single node above level m-2 (or the tile total if m == 1)
+    const double* run_pre;          // per tile: 256 run prefixes (within segs)
+    const double* seg_pre;          // per tile: 16 seg prefixes
     int m;
 };
 
-// Among stored children [b, e): the first whose running sum exceeds r (r
-// becomes the remainder past the children before it), else - and from then
-// on, take_last - the last child of non-zero total. Warp-uniform: every
-// lane walks the same sequence. Returns -1 if every child is zero.
-__device__ int64_t pick_stored(const double* __restrict__ v, int64_t b, int64_t e, double& r, bool& take_last) {
-    const int lane = threadIdx.x & 31;
-    double prefix = 0.0;
-    int64_t last_pos = -1;
-    for (int64_t c0 = b; c0 < e; c0 += 32) {
-        const int64_t c = c0 + lane;
-        const double mine = c < e ? v[c] : 0.0;
-        const unsigned pos = __ballot_sync(kFull, mine > 0.0);
-        if (pos) last_pos = c0 + 31 - __clz((int)pos);
-        if (take_last) continue;
-        const int cnt = e - c0 < 32 ? (int)(e - c0) : 32;
-        for (int k = 0; k < cnt; ++k) {
-            const double x = __shfl_sync(kFull, mine, k);
-            const double np = __dadd_rn(prefix, x);
-            if (np > r) {
-                r = __dsub_rn(r, prefix);
-                return c0 + k;
-            }
-            prefix = np;
+// In the running sums pre[b .. e) (non-decreasing, pre[e-1] the group total):
+// the first position whose running sum exceeds r, or - when none does, and
+// whenever take_last is set - the position where the running sum last
+// increased (the last child of non-zero total); -1 if the group total is 0.
+// r becomes the remainder past the positions before the chosen one.
+__device__ int64_t pick(const double* __restrict__ pre, int64_t b, int64_t e, double& r, bool& take_last) {
+    const long long last = key(pre[e - 1]);
+    if (last == 0) return -1;
+    int64_t lo = b, hi = e - 1;
+    if (!take_last && key(r) < last) {  // smallest c with pre[c] > r
+        const long long kr = key(r);
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (key(pre[mid]) > kr)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+    } else {  // smallest c with pre[c] == pre[e-1]
+        take_last = true;
+        while (lo < hi) {
+            const int64_t mid = lo + ((hi - lo) >> 1);
+            if (key(pre[mid]) >= last)
+                hi = mid;
+            else
+                lo = mid + 1;
         }
     }
-    take_last = true;
-    return last_pos;
+    if (lo > b) r = __dsub_rn(r, pre[lo - 1]);
+    return lo;
 }
 
-// Inside one tile: seg (recomputed), run (the lanes' run sums), amplitude.
-template <typename R>
-__device__ int64_t pick_in_tile(const amp_t<R>* __restrict__ psi, int64_t N, int64_t tile, double r,
-                                bool take_last) {
-    const int lane = threadIdx.x & 31;
-    const int64_t tile_base = tile * kTile;
-    // the seg: its lanes' run sums stay in registers once chosen
-    double run = 0.0;
-    int seg = -1;
-    {
-        double prefix = 0.0;
-        int last_seg = -1;
-        double last_run = 0.0;
-        for (int s = 0; s < kTileSegs; ++s) {
-            const int64_t base = tile_base + (int64_t)s * kSeg + (int64_t)lane * kRun;
-            RunSum<R> rs;
-            for (int e = 0; e < kRun; ++e) rs.add(base + e < N ? psi[base + e] : zero_amp<R>());
-            const double my_run = rs.value();
-            const double tot = lane_ordered_sum(my_run);
-            if (tot > 0.0) {
-                last_seg = s;
-                last_run = my_run;
-            }
-            if (!take_last) {
-                const double np = __dadd_rn(prefix, tot);
-                if (np > r) {
-                    r = __dsub_rn(r, prefix);
-                    seg = s;
-                    run = my_run;
-                    break;
-                }
-                prefix = np;
-            }
-        }
-        if (seg < 0) {
-            take_last = true;
-            seg = last_seg;
-            run = last_run;
-        }
-    }
-    if (seg < 0) return -1;
-    // the run
-    int L = -1;
-    {
-        double prefix = 0.0;
-        int last_l = -1;
-        for (int k = 0; k < 32; ++k) {
-            const double x = __shfl_sync(kFull, run, k);
-            if (x > 0.0) last_l = k;
-            if (!take_last && L < 0) {
-                const double np = __dadd_rn(prefix, x);
-                if (np > r) {
-                    r = __dsub_rn(r, prefix);
-                    L = k;
-                } else {
-                    prefix = np;
-                }
-            }
-        }
-        if (L < 0) {
-            take_last = true;
-            L = last_l;
-        }
-    }
-    if (L < 0) return -1;
-    // the amplitude: the run's running sum, element by element
-    const int64_t base = tile_base + (int64_t)seg * kSeg + (int64_t)L * kRun;
-    RunSum<R> rs;
-    double prev = 0.0;
-    int last_e = -1;
-    for (int e = 0; e < kRun; ++e) {
-        rs.add(base + e < N ? psi[base + e] : zero_amp<R>());
-        const double cur = rs.value();
-        if (!take_last && cur > r) return base + e;
-        if (cur > prev) last_e = e;
-        prev = cur;
-    }
-    return last_e < 0 ? -1 : base + last_e;
-}
-
-// One warp per shot.
+// One thread per shot.
 template <typename R>
 __global__ void __launch_bounds__(128) k_sample_search(const amp_t<R>* __restrict__ psi, int64_t N, Levels lv,
                                                        const double* __restrict__ uniforms, int64_t shots,
                                                        int64_t* __restrict__ out) {
-    const int64_t shot = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (shot >= shots) return;  // whole warps leave together
+    const int64_t shot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (shot >= shots) return;
     double u = uniforms[shot];
     if (!(u > 0.0)) u = 0.0;  // also maps NaN to 0
     if (u > 1.0) u = 1.0;
-    double r = __dmul_rn(u, lv.lv[lv.m - 1][0]);
+    double r = __dmul_rn(u, *lv.total);
     bool take_last = false;
-    int64_t node = 0;
-    for (int L = lv.m - 2; L >= 0; --L) {
+    int64_t node = 0, idx = -1;
+    for (int L = lv.m - 2; L >= 0 && node >= 0; --L) {
         const int64_t b = node * kFan;
         const int64_t e = b + kFan < lv.count[L] ? b + kFan : lv.count[L];
-        node = pick_stored(lv.lv[L], b, e, r, take_last);
-        if (node < 0) break;
+        node = pick(lv.pre[L], b, e, r, take_last);
     }
-    // with a single tile (lv.m == 1) the descent starts inside it
-    const int64_t idx = node >= 0 ? pick_in_tile<R>(psi, N, node, r, take_last) : -1;
-    if ((threadIdx.x & 31) == 0) out[shot] = idx;
+    if (node >= 0) {  // node: the tile
+        const int64_t seg = pick(lv.seg_pre + node * kTileSegs, 0, kTileSegs, r, take_last);
+        if (seg >= 0) {
+            const double* rpre = lv.run_pre + node * kTileRuns + seg * kSegRuns;
+            const int64_t run = pick(rpre, 0, kSegRuns, r, take_last);
+            if (run >= 0) {
+                const int64_t first = node * kTile + (seg * kSegRuns + run) * kRun;
+                RunSum<R> rs;
+                long long prev = 0;
+                int last_e = -1;
+                const long long kr = key(r);
+                for (int e = 0; e < kRun; ++e) {
+                    rs.add(first + e < N ? psi[first + e] : zero_amp<R>());
+                    const long long cur = key(rs.value());
+                    if (!take_last && cur > kr) {
+                        idx = first + e;
+                        break;
+                    }
+                    if (cur > prev) last_e = e;
+                    prev = cur;
+                }
+                if (idx < 0 && last_e >= 0) idx = first + last_e;
+            }
+        }
+    }
+    out[shot] = idx;
 }
 
 }  // namespace
@@ -300,38 +289,59 @@ extern "C" diaq_status diaq_sample(const void* psi, int32_t n_qubits, diaq_dtype
     if ((reinterpret_cast<uintptr_t>(uniforms) | reinterpret_cast<uintptr_t>(out_indices)) & 7)
         return fail(DIAQ_ERR_ARG, "uniforms and out_indices must be 8-byte aligned");
     const int64_t N = int64_t(1) << n_qubits;
+    const int64_t tiles = (N + kTile - 1) / kTile;
+    // scratch: run prefixes, seg prefixes, then per level its running sums
+    // and the totals of its groups (the next level's nodes)
     Levels lv{};
-    int64_t off[kMaxLevels];
-    int64_t total = 0;
-    int64_t count = (N + kTile - 1) / kTile;
-    lv.m = 0;
-    for (;;) {
-        lv.count[lv.m] = count;
-        off[lv.m] = total;
-        total += count;
-        ++lv.m;
-        if (count == 1) break;
-        count = (count + kFan - 1) / kFan;
+    int64_t count[kMaxLevels + 1];
+    int m = 0;
+    for (int64_t c = tiles;; c = (c + kFan - 1) / kFan) {
+        count[m++] = c;
+        if (c == 1) break;
     }
+    int64_t total_doubles = tiles * (kTileRuns + kTileSegs) + count[0];
+    for (int L = 0; L + 1 < m; ++L) total_doubles += count[L] + count[L + 1];
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double* scratch = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * total, s);
+    cudaError_t e = cudaMallocAsync((void**)&scratch, sizeof(double) * total_doubles, s);
     if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(sample tree, %lld doubles): %s",
-                                      (long long)total, cudaGetErrorString(e));
-    for (int l = 0; l < lv.m; ++l) lv.lv[l] = scratch + off[l];
+                                      (long long)total_doubles, cudaGetErrorString(e));
+    double* run_pre = scratch;
+    double* seg_pre = run_pre + tiles * kTileRuns;
+    double* node_tot = seg_pre + tiles * kTileSegs;  // level 0 totals (tiles)
+    double* cursor = node_tot + count[0];
+    lv.m = m;
+    lv.run_pre = run_pre;
+    lv.seg_pre = seg_pre;
+    for (int L = 0; L < m; ++L) lv.count[L] = count[L];
+    const double* level_tot = node_tot;
     diaq_status st = DIAQ_OK;
-    if (dtype == DIAQ_C128)
-        k_sample_tiles<double><<<(unsigned)lv.count[0], 128, 0, s>>>(reinterpret_cast<const double2*>(psi), N, scratch);
-    else
-        k_sample_tiles<float><<<(unsigned)lv.count[0], 128, 0, s>>>(reinterpret_cast<const float2*>(psi), N, scratch);
-    e = cudaGetLastError();
-    for (int l = 1; l < lv.m && e == cudaSuccess; ++l) {
-        k_sample_level<<<(unsigned)((lv.count[l] + 127) / 128), 128, 0, s>>>(lv.lv[l - 1], lv.count[l - 1],
-                                                                             scratch + off[l], lv.count[l]);
-        e = cudaGetLastError();
+    if (dtype == DIAQ_C128) {
+        constexpr int sm = tile_smem_bytes<double>();
+        e = cudaFuncSetAttribute(k_sample_tiles<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess)
+            k_sample_tiles<double><<<(unsigned)tiles, 256, sm, s>>>(reinterpret_cast<const double2*>(psi), N, run_pre,
+                                                                     seg_pre, node_tot);
+    } else {
+        constexpr int sm = tile_smem_bytes<float>();
+        e = cudaFuncSetAttribute(k_sample_tiles<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess)
+            k_sample_tiles<float><<<(unsigned)tiles, 256, sm, s>>>(reinterpret_cast<const float2*>(psi), N, run_pre,
+                                                                    seg_pre, node_tot);
     }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    for (int L = 0; L + 1 < m && e == cudaSuccess; ++L) {
+        double* pre = cursor;
+        double* parent = cursor + count[L];
+        cursor = parent + count[L + 1];
+        k_sample_level<<<(unsigned)count[L + 1], kFan, 0, s>>>(level_tot, count[L], pre, parent);
+        e = cudaGetLastError();
+        lv.pre[L] = pre;
+        level_tot = parent;
+    }
+    lv.total = level_tot;
     if (e == cudaSuccess) {
-        const unsigned blocks = (unsigned)((n_shots + 3) / 4);
+        const unsigned blocks = (unsigned)((n_shots + 127) / 128);
         if (dtype == DIAQ_C128)
             k_sample_search<double><<<blocks, 128, 0, s>>>(reinterpret_cast<const double2*>(psi), N, lv, uniforms,
                                                            n_shots, out_indices);

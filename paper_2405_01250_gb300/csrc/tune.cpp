@@ -158,6 +158,54 @@ diaq_status diaq_plan_fusion(const diaq_gate* gates, int32_t n_gates, int32_t ma
     return DIAQ_OK;
 }
 
+// A gate whose operator is diagonal in the computational basis: a fixed
+// matrix with exact zeros off the diagonal, or a rotation whose generator
+// has only I and Z letters.
+static bool gate_is_diagonal(const diaq_gate& g) {
+    if (g.param >= 0) {
+        for (int a = 0; a < g.k; ++a)
+            if (!strchr("IiZz", g.gen[a])) return false;
+        return true;
+    }
+    if (!g.m) return false;
+    const int D = 1 << g.k;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c)
+            if (r != c && (g.m[2 * (r * D + c)] != 0.0 || g.m[2 * (r * D + c) + 1] != 0.0)) return false;
+    return true;
+}
+
+diaq_status diaq_plan_fusion_diagonal(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
+                                      int32_t* group_of_gate, int32_t* n_groups) {
+    clear_error();
+    if (n_gates < 0 || (n_gates && (!gates || !group_of_gate)) || !n_groups) return fail(DIAQ_ERR_ARG, "bad arrays");
+    if (max_k < 1 || max_k > DIAQ_MAX_K) return fail(DIAQ_ERR_ARG, "max_k = %d outside [1, %d]", max_k, DIAQ_MAX_K);
+    if (max_depth < 1) return fail(DIAQ_ERR_ARG, "max_depth = %d < 1", max_depth);
+    int grp = -1, depth = 0;
+    bool open_diag = false;  // the current group is a run of diagonal gates
+    std::vector<int> uni;
+    for (int i = 0; i < n_gates; ++i) {
+        const diaq_gate& g = gates[i];
+        if (g.k < 1 || g.k > DIAQ_MAX_K) return fail(DIAQ_ERR_ARG, "gate %d has k = %d", i, g.k);
+        if (g.k > max_k) return fail(DIAQ_ERR_ARG, "gate %d (k = %d) exceeds max_k = %d", i, g.k, max_k);
+        const bool diag = gate_is_diagonal(g);
+        std::vector<int> u = uni;
+        for (int a = 0; a < g.k; ++a)
+            if (std::find(u.begin(), u.end(), g.targets[a]) == u.end()) u.push_back(g.targets[a]);
+        if (!diag || !open_diag || depth >= max_depth || int(u.size()) > max_k) {
+            ++grp;
+            depth = 0;
+            u.assign(g.targets, g.targets + g.k);
+        }
+        open_diag = diag;
+        uni = u;
+        ++depth;
+        group_of_gate[i] = grp;
+    }
+    *n_groups = grp + 1;
+    return DIAQ_OK;
+}
+
 diaq_status diaq_plan_fusion_commuting(const diaq_gate* gates, int32_t n_gates, int32_t max_k, int32_t max_depth,
                                        int32_t* order, int32_t* group_of_pos, int32_t* n_groups) {
     clear_error();

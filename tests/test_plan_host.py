@@ -103,3 +103,42 @@ def test_plan_fusion_commuting_valid_and_exact(api):
     circ = synth.random_layered(30, 4, seed=0)
     _, grp = api.plan_fusion_commuting(circ.gates, 2, 4)
     assert max(grp) + 1 == 60
+
+
+def test_plan_fusion_diagonal_keeps_classes_apart(api):
+    """Runs of diagonal gates (fixed diagonal matrices, Z-only rotations)
+    fuse within max_k qubits and max_depth gates; every other gate is a
+    group of its own; the fused circuit equals the original (oracle)."""
+    import oracle
+    rng = np.random.default_rng(5)
+    n = 8
+    circ, j = synth.qft(n, seed=2)
+    extra = [synth.Gate((1, 4), None, param=0, gen="ZZ"), synth.Gate((3,), None, param=0, gen="Z"),
+             synth.Gate((2, 5), None, param=0, gen="ZX"), synth.Gate((0, 6), synth.CZ)]
+    gates = list(circ.gates[:10]) + extra + list(circ.gates[10:])
+    theta = np.array([0.37])
+    diag = [g.matrix is None and set(g.gen) <= {"Z", "I"} or
+            (g.matrix is not None and np.count_nonzero(g.matrix - np.diag(np.diag(g.matrix))) == 0) for g in gates]
+    for max_k, depth in ((2, 64), (4, 3), (6, 64)):
+        grp = api.plan_fusion_diagonal(gates, max_k, depth)
+        assert grp[0] == 0 and all(b - a in (0, 1) for a, b in zip(grp, grp[1:]))
+        for gi in set(grp):
+            members = [i for i in range(len(gates)) if grp[i] == gi]
+            if len(members) > 1:
+                assert all(diag[i] for i in members)
+                assert len(members) <= depth
+                assert len({q for i in members for q in gates[i].targets}) <= max_k
+        psi = synth.random_state(n, rng)
+        want = psi
+        for g in gates:
+            want = oracle.apply_gate(want, g.targets, oracle.gate_matrix(g, theta))
+        got = psi
+        for gi in sorted(set(grp)):
+            members = [gates[i] for i in range(len(gates)) if grp[i] == gi]
+            union, F = oracle.fuse([(m.targets, oracle.gate_matrix(m, theta)) for m in members])
+            got = oracle.apply_gate(got, list(union), F)
+        assert np.max(np.abs(got - want)) < 1e-13
+    # QFT-28: 28 H, 87 runs of controlled phases (5 per run beside the
+    # shared target, 6 qubits), 14 SWAPs
+    c28, _ = synth.qft(28, seed=0)
+    assert max(api.plan_fusion_diagonal(c28.gates, 6, 64)) + 1 == 28 + 87 + 14
