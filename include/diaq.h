@@ -687,6 +687,24 @@ diaq_status diaq_batch_query(diaq_batch_t b, int32_t* cluster, int32_t* threads,
  * Process-wide. */
 diaq_status diaq_debug_inject_alloc_failure(int32_t after);
 
+/* Debug bounds checks. The library's debug build (libdiaq_gb300_dbg.so,
+ * compiled with -DDIAQ_DEBUG_BOUNDS; the normal build has no checks) checks
+ * the amplitude and table indices its kernels compute before each access;
+ * a failing check skips that access and records the first failure (site and
+ * index) on the device.
+ *
+ * diaq_debug_bounds_enabled: *enabled = 1 in the debug build, 0 otherwise.
+ * diaq_debug_bounds_check: reads the recorded failure (clearing it when
+ * clear != 0) into *word (may be NULL; 0 when none) and returns DIAQ_OK, or
+ * DIAQ_ERR_BOUNDS with the site and index in diaq_last_error(). In the
+ * normal build it always returns DIAQ_OK. Call it after synchronising.
+ * diaq_debug_bounds_status: the status and message for a recorded word
+ * (host only, no GPU needed): bit 63 set, bits 48..62 the site, bits 0..47
+ * the index. */
+diaq_status diaq_debug_bounds_enabled(int32_t* enabled);
+diaq_status diaq_debug_bounds_check(int32_t clear, uint64_t* word);
+diaq_status diaq_debug_bounds_status(uint64_t word);
+
 /* ------------------------------------------------------------------------
  * Allocation-free norm (the paper has no counterpart: this is a deployment
  * variant of diaq_norm).

@@ -10,7 +10,11 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libdiaq_gb300.so")
+# DIAQ_DEBUG_BOUNDS=1 selects the debug build, whose kernels check every
+# computed index (diaq_debug_bounds_check reports a failure)
+DEBUG_BOUNDS = os.environ.get("DIAQ_DEBUG_BOUNDS", "0") == "1"
+LIB_PATH = os.path.join(HERE, "_build_dbg" if DEBUG_BOUNDS else "_build",
+                        "libdiaq_gb300_dbg.so" if DEBUG_BOUNDS else "libdiaq_gb300.so")
 
 DIAQ_MAX_K = 6
 DIAQ_MAX_QUBITS = 34
@@ -98,6 +102,9 @@ SIGNATURES = {
     "diaq_sample": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _vp, ctypes.c_int64, _vp, _vp]),
     "diaq_norm_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),
     "diaq_debug_inject_alloc_failure": (ctypes.c_int, [ctypes.c_int32]),
+    "diaq_debug_bounds_enabled": (ctypes.c_int, [_i32p]),
+    "diaq_debug_bounds_check": (ctypes.c_int, [ctypes.c_int32, _u64p]),
+    "diaq_debug_bounds_status": (ctypes.c_int, [ctypes.c_uint64]),
 }
 
 class diaq_batch_tuning(ctypes.Structure):

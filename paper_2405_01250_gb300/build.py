@@ -23,6 +23,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdiaq_gb300.so")
+# the debug build: every kernel checks its computed indices (-DDIAQ_DEBUG_BOUNDS)
+DBG_DIR = os.path.join(HERE, "_build_dbg")
+DBG_LIB = os.path.join(DBG_DIR, "libdiaq_gb300_dbg.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -52,25 +55,30 @@ def _stale(lib: str) -> bool:
     return any(os.path.getmtime(p) > t for p in cu + cpp + hdr + [os.path.abspath(__file__)])
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and not _stale(LIB):
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug_bounds: bool = None) -> str:
+    """Build the library (or, with debug_bounds, its index-checking debug
+    build; default: the one DIAQ_DEBUG_BOUNDS=1 selects)."""
+    if debug_bounds is None:
+        debug_bounds = os.environ.get("DIAQ_DEBUG_BOUNDS", "0") == "1"
+    out_dir, lib = (DBG_DIR, DBG_LIB) if debug_bounds else (OUT_DIR, LIB)
+    if not force and not _stale(lib):
+        return lib
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     cu, cpp, _ = _sources()
-    common = ["-O3", "-std=c++17", f"-I{INCLUDE}", f"-I{CSRC}"]
+    common = ["-O3", "-std=c++17", f"-I{INCLUDE}", f"-I{CSRC}"] + (["-DDIAQ_DEBUG_BOUNDS"] if debug_bounds else [])
     jobs = []
     objs = []
     for src in cu:
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, "-gencode", GENCODE, "-lineinfo", "-Xcompiler", "-fPIC", "-c", src, "-o", obj] + common
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]
         jobs.append(cmd)
         objs.append(obj)
     for src in cpp:
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = ["g++", "-fPIC", "-Wall", "-c", src, "-o", obj, f"-I{os.path.join(cuda, 'include')}"] + common
         jobs.append(cmd)
         objs.append(obj)
@@ -88,7 +96,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{p.stdout}\n{p.stderr}")
         if (verbose or ptxas_info) and (p.stdout or p.stderr):
             print(p.stdout + p.stderr, flush=True)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     link = [nvcc, "-shared", "-cudart", "shared", "-gencode", GENCODE, "-o", tmp] + objs + [
         "-Xlinker", "-rpath", "-Xlinker", os.path.join(cuda, "lib64"),
         "-Xlinker", "-rpath", "-Xlinker", os.path.join(cuda, "lib"),
@@ -96,9 +104,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     p = subprocess.run(link, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(link)}\n{p.stdout}\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, ptxas_info="--ptxas" in sys.argv,
+                debug_bounds=True if "--debug-bounds" in sys.argv else None))

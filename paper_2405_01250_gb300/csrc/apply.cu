@@ -25,8 +25,11 @@
 #include <cstring>
 #include <vector>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(apply)
 
 namespace diaq {
 
@@ -37,6 +40,7 @@ template <typename R, int K>
 struct SmallGateArgs {
     int64_t g_base;              // first group of the launch
     int64_t n_groups;            // one past the last group
+    int64_t N;                   // amplitudes of the state
     int st[K];                   // targets, ascending
     int64_t off[1 << K];         // full-system offset of local index c
     R re[1 << (2 * K)];
@@ -72,6 +76,8 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
     for (int j = 0; j < G; ++j) {
         const int64_t g = g0 + j * T;
         b[j] = g < a.n_groups ? insert_zeros<K>(g, a.st) : int64_t(-1);
+        // every row of the group lies in [b, b + off[D-1]]
+        if (b[j] >= 0 && !DIAQ_BOUNDS_OK(b[j] + a.off[D - 1], a.N, BS_APPLY_SMALL)) b[j] = -1;
         if (b[j] >= 0) {
 #pragma unroll
             for (int c = 0; c < D; ++c) v[j][c] = ld_stream(x + b[j] + a.off[c]);
@@ -222,6 +228,7 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
 // ---------------------------------------------------------------------------
 struct LargeGateArgs {
     int64_t n_groups;
+    int64_t N;
     int k;
     int st[DIAQ_MAX_K];
     int64_t off[1 << DIAQ_MAX_K];
@@ -256,7 +263,14 @@ k_apply_large(const amp_t<R>* x, amp_t<R>* y, const void* dmat, const __grid_con
         for (int e = threadIdx.x; e < per; e += blockDim.x) {
             const int gi = e % B, c = e / B;
             const int64_t g = ch * B + gi;
-            if (g < a.n_groups) xs[c * B + gi] = ld_stream(x + insert_zeros_rt(g, a.st, k) + a.off[c]);
+            if (g < a.n_groups) {
+                const int64_t i = insert_zeros_rt(g, a.st, k) + a.off[c];
+                A v;
+                v.x = R(0);
+                v.y = R(0);
+                if (DIAQ_BOUNDS_OK(i, a.N, BS_APPLY_LARGE)) v = ld_stream(x + i);
+                xs[c * B + gi] = v;
+            }
         }
         __syncthreads();
         for (int e = threadIdx.x; e < per; e += blockDim.x) {
@@ -269,7 +283,8 @@ k_apply_large(const amp_t<R>* x, amp_t<R>* y, const void* dmat, const __grid_con
             bool first = true;
             for (int c = 0; c < D; ++c)
                 mac_typed<R>(acc, first, mty[r * D + c], mre[r * D + c], mim[r * D + c], xs[c * B + gi]);
-            st_stream(y + insert_zeros_rt(g, a.st, k) + a.off[r], acc);
+            const int64_t i = insert_zeros_rt(g, a.st, k) + a.off[r];
+            if (DIAQ_BOUNDS_OK(i, a.N, BS_APPLY_LARGE)) st_stream(y + i, acc);
         }
         __syncthreads();
     }
@@ -312,6 +327,7 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
     std::memset(&a, 0, sizeof(a));
     a.g_base = g_begin;
     a.n_groups = g_end;
+    a.N = int64_t(1) << n;
     sorted_targets(g, a.st);
     local_offsets(g, a.off);
     constexpr int DD = 1 << (2 * K);
@@ -395,6 +411,7 @@ static diaq_status launch_large(int n, diaq_dtype dt, const GateDesc& g, const v
     std::memset(&a, 0, sizeof(a));
     a.k = g.k;
     a.n_groups = int64_t(1) << (n - g.k);
+    a.N = int64_t(1) << n;
     sorted_targets(g, a.st);
     local_offsets(g, a.off);
     const int B = 32;
@@ -607,6 +624,7 @@ k_stored_spmv(const amp_t<R>* x, amp_t<R>* y, int64_t N, int D, const int64_t* _
                 p = row[u] - (d < 0 ? -d : 0);
                 ok = p >= 0 && p < N - (d < 0 ? -d : d);
             }
+            if (ok) ok = DIAQ_BOUNDS_OK(row[u] + d, N, BS_STORED_X) && DIAQ_BOUNDS_OK(row[u], N, BS_STORED_VALUE);
             if (ok) {
                 a[u] = ld_stream(vals + st + p);
                 xv[u] = x[row[u] + d];
@@ -673,7 +691,7 @@ k_materialise(amp_t<R>* vals, int64_t N, const int64_t* __restrict__ offs,
         A v;
         v.x = R(0);
         v.y = R(0);
-        if (((i ^ j) & ~ma.tmask) == 0) {
+        if (((i ^ j) & ~ma.tmask) == 0 && DIAQ_BOUNDS_OK(j, N, BS_MATERIALISE)) {
             int r = 0, c = 0;
             for (int a = 0; a < k; ++a) {
                 r |= int((i >> ma.t[a]) & 1) << (k - 1 - a);
@@ -884,6 +902,7 @@ k_spgemm(amp_t<R>* cvals, const int64_t* __restrict__ c_offs, const int64_t* __r
             const int64_t a = a_offs[qa], b = b_offs[qb];
             const int64_t m = i + a;
             if (m < 0 || m >= N || m + b < 0 || m + b >= N) continue;
+            if (!DIAQ_BOUNDS_OK(i - (a < 0 ? -a : 0), N - (a < 0 ? -a : a), BS_SPGEMM)) continue;
             const A av = avals[a_starts[qa] + (i - (a < 0 ? -a : 0))];
             const A bv = bvals[b_starts[qb] + (m - (b < 0 ? -b : 0))];
             acc.x = fma(av.x, bv.x, acc.x);

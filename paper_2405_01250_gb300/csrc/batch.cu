@@ -26,12 +26,15 @@
 #include <numeric>
 #include <vector>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
 #include "rot.cuh"
 #include "win.cuh"
 
 namespace cg = cooperative_groups;
+
+DIAQ_BOUNDS_TU(batch)
 
 namespace diaq {
 
@@ -209,6 +212,7 @@ __device__ __noinline__ void team_fixed_u(amp_t<R>* __restrict__ psi, amp_t<R>* 
         for (int u = 0; u < U; ++u) {
             const int64_t gi = g0 + int64_t(u) * nthreads;
             b[u] = gi < G ? insert_zeros<K>(gi, st) : int64_t(-1);
+            if (b[u] >= 0 && !DIAQ_BOUNDS_OK(b[u] + off[D - 1], int64_t(1) << n, BS_WINDOW)) b[u] = -1;
             if (b[u] >= 0) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) p[u][c] = psi[b[u] + off[c]];
@@ -469,9 +473,12 @@ __global__ void __launch_bounds__(WIN_THREADS) k_batch_win(const BatchArgs a, co
             const int64_t G = int64_t(1) << (I.n - w.nq);
             for (int64_t g = tid; g < G; g += nthreads) {
                 const int64_t base = insert_zeros_rt(g, w.q, w.nq);
-                for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
+                const bool ok = DIAQ_BOUNDS_OK(base + w.off[D - 1], N, BS_WINDOW);
+                if (ok)
+                    for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
                 for (int i = 0; i < w.count; ++i) win_apply<R>(ops[i], cp, nullptr, D, T, nullptr);
-                for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
+                if (ok)
+                    for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
             }
             team_sync(C);
         }
@@ -493,14 +500,19 @@ __global__ void __launch_bounds__(WIN_THREADS) k_batch_win(const BatchArgs a, co
             const int64_t G = int64_t(1) << (I.n - w.nq);
             for (int64_t g = tid; g < G; g += nthreads) {
                 const int64_t base = insert_zeros_rt(g, w.q, w.nq);
-                for (int e2 = 0; e2 < D; ++e2) cp[e2 * T] = psi[base + w.off[e2]];
-                for (int e2 = 0; e2 < D; ++e2) cl[e2 * T] = lam[base + w.off[e2]];
+                const bool ok = DIAQ_BOUNDS_OK(base + w.off[D - 1], N, BS_WINDOW);
+                if (ok)
+                    for (int e2 = 0; e2 < D; ++e2) cp[e2 * T] = psi[base + w.off[e2]];
+                if (ok)
+                    for (int e2 = 0; e2 < D; ++e2) cl[e2 * T] = lam[base + w.off[e2]];
                 for (int i = w.count - 1; i >= 0; --i) {
                     const WinOp<R>& o = ops[i];
                     win_apply<R>(o, cp, cl, D, T, o.j >= 0 ? sa + o.j * T + t : nullptr);
                 }
-                for (int e2 = 0; e2 < D; ++e2) psi[base + w.off[e2]] = cp[e2 * T];
-                for (int e2 = 0; e2 < D; ++e2) lam[base + w.off[e2]] = cl[e2 * T];
+                if (ok)
+                    for (int e2 = 0; e2 < D; ++e2) psi[base + w.off[e2]] = cp[e2 * T];
+                if (ok)
+                    for (int e2 = 0; e2 < D; ++e2) lam[base + w.off[e2]] = cl[e2 * T];
             }
             for (int j = 0; j < w.np; ++j) {
                 const double v = block_sum(sa[j * T + t].value(), warps);
@@ -583,8 +595,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 4) k_batch_win_l(const BatchArgs 
                 A* gl = sl + gs * SD;
                 for (int64_t g0 = int64_t(rank) * GPC; g0 < G; g0 += int64_t(C) * GPC) {
                     const int64_t g = g0 + gs;
-                    const bool valid = g < G;
-                    const int64_t base = valid ? insert_zeros_rt(g, w.q, w.nq) : 0;
+                    const int64_t base = g < G ? insert_zeros_rt(g, w.q, w.nq) : 0;
+                    const bool valid = g < G && DIAQ_BOUNDS_OK(base + w.off[D - 1], int64_t(1) << I.n, BS_WINDOW);
                     if (valid) {
                         for (int e2 = li; e2 < D; e2 += L) gp[e2] = psi[base + w.off[e2]];
                         if (rev)
@@ -1549,8 +1561,8 @@ __global__ void __launch_bounds__(WIN_THREADS, 4) k_plan_win_l(amp_t<R>* psi, am
     // lane of a warp reaches each __syncwarp
     for (int64_t g0 = int64_t(blockIdx.x) * GPC; g0 < G; g0 += int64_t(gridDim.x) * GPC) {
         const int64_t g = g0 + gs;
-        const bool valid = g < G;
-        const int64_t base = valid ? insert_zeros_rt(g, w.q, w.nq) : 0;
+        const int64_t base = g < G ? insert_zeros_rt(g, w.q, w.nq) : 0;
+        const bool valid = g < G && DIAQ_BOUNDS_OK(base + w.off[D - 1], int64_t(1) << n, BS_WINDOW);
         if (valid) {
             for (int e = li; e < D; e += L) gp[e] = psi[base + w.off[e]];
             if (rev)
@@ -1639,8 +1651,10 @@ __global__ void __launch_bounds__(WIN_THREADS) k_plan_win(amp_t<R>* psi, amp_t<R
     A* cl = sl + t;
     for (int64_t g = int64_t(blockIdx.x) * T + t; g < G; g += int64_t(gridDim.x) * T) {
         const int64_t base = insert_zeros_rt(g, w.q, w.nq);
-        for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
-        if (rev)
+        const bool ok = DIAQ_BOUNDS_OK(base + w.off[D - 1], int64_t(1) << n, BS_WINDOW);
+        if (ok)
+            for (int e = 0; e < D; ++e) cp[e * T] = psi[base + w.off[e]];
+        if (rev && ok)
             for (int e = 0; e < D; ++e) cl[e * T] = lam[base + w.off[e]];
         if (!rev) {
             for (int i = 0; i < w.count; ++i) win_apply<R>(ops[i], cp, nullptr, D, T, nullptr);
@@ -1650,8 +1664,9 @@ __global__ void __launch_bounds__(WIN_THREADS) k_plan_win(amp_t<R>* psi, amp_t<R
                 win_apply<R>(o, cp, cl, D, T, o.j >= 0 ? sa + o.j * T + t : nullptr);
             }
         }
-        for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
-        if (rev)
+        if (ok)
+            for (int e = 0; e < D; ++e) psi[base + w.off[e]] = cp[e * T];
+        if (rev && ok)
             for (int e = 0; e < D; ++e) lam[base + w.off[e]] = cl[e * T];
     }
     if (rev) {

@@ -21,8 +21,11 @@
 #include <algorithm>
 #include <cstring>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(diag)
 
 namespace diaq {
 namespace {
@@ -51,7 +54,7 @@ __global__ void __launch_bounds__(256) k_apply_diag(const amp_t<R>* x, amp_t<R>*
         for (int u = 0; u < kDiagUnroll; ++u) {
             const int64_t i = i0 + u * T;
             int cc = -1;
-            if (i < a.N) {
+            if (i < a.N && DIAQ_BOUNDS_OK(i, a.N, BS_APPLY_DIAG)) {
                 cc = 0;
                 for (int q = 0; q < a.k; ++q) cc = (cc << 1) | int((i >> a.t[q]) & 1);
                 if (((a.one >> cc) & 1) && INPLACE) cc = -1;  // unchanged: no read, no write

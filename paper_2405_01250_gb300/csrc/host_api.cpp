@@ -13,8 +13,10 @@
 #include <map>
 #include <new>
 #include <string>
+#include <mutex>
 #include <vector>
 
+#include "bounds.cuh"
 #include "internal.h"
 
 namespace diaq {
@@ -325,6 +327,49 @@ cudaError_t inj_malloc_host(void** p, size_t n) {
 }
 }  // namespace diaq
 
+// ---------------------------------------------------------------------------
+// Debug bounds checks (the build with -DDIAQ_DEBUG_BOUNDS)
+// ---------------------------------------------------------------------------
+extern "C" diaq_status diaq_debug_bounds_enabled(int32_t* enabled) {
+    clear_error();
+    if (!enabled) return fail(DIAQ_ERR_ARG, "enabled is NULL");
+#ifdef DIAQ_DEBUG_BOUNDS
+    *enabled = 1;
+#else
+    *enabled = 0;
+#endif
+    return DIAQ_OK;
+}
+
+extern "C" diaq_status diaq_debug_bounds_status(uint64_t word) {
+    clear_error();
+    if (word == 0) return DIAQ_OK;
+    static const char* names[] = {"?", "on-the-fly apply (k <= 3)", "in-place row skip", "on-the-fly apply (k >= 4)",
+                                  "diagonal op", "stored SpMV row", "stored SpMV column", "materialise",
+                                  "expectation", "Pauli-sum apply", "rotation", "sampling tile pass",
+                                  "sampling descent", "shard move", "DiaQ product", "window sweep"};
+    if (word == ~uint64_t(0)) return fail(DIAQ_ERR_CUDA, "a bounds word could not be read from the device");
+    const int site = int((word >> 48) & 0x7fff);
+    const uint64_t idx = word & 0xffffffffffffull;
+    const int64_t sidx = (idx >> 47) ? int64_t(idx | ~0xffffffffffffull) : int64_t(idx);  // sign-extend 48 bits
+    return fail(DIAQ_ERR_BOUNDS, "device index check failed in %s (site %d): index %lld", site < BS_SITES ? names[site] : "?",
+                site, (long long)sidx);
+}
+
+extern "C" diaq_status diaq_debug_bounds_check(int32_t clear, uint64_t* word) {
+    clear_error();
+    unsigned long long first = 0;
+    unsigned long long (*const tus[])(bool) = {bounds_word_apply, bounds_word_inplace, bounds_word_diag,
+                                               bounds_word_reduce, bounds_word_batch, bounds_word_sample,
+                                               bounds_word_shard};
+    for (auto f : tus) {
+        const unsigned long long w = f(clear != 0);
+        if (w && !first) first = w;
+    }
+    if (word) *word = first;
+    return diaq_debug_bounds_status(first);
+}
+
 extern "C" diaq_status diaq_debug_inject_alloc_failure(int32_t after) {
     clear_error();
     if (after < -1) return fail(DIAQ_ERR_ARG, "after = %d: use -1 (off) or >= 0", after);
@@ -347,6 +392,8 @@ static diaq_status check_op(diaq_op_t op) {
 
 static diaq_status free_op_memory(diaq_op_s* op) {
     cudaError_t first = cudaSuccess;
+    // the stored values return to the pool (cudaFree waits for the device
+    // first, as for the other buffers)
     for (void* p : {op->d_values, static_cast<void*>(op->d_offsets), static_cast<void*>(op->d_starts), op->d_matrix}) {
         if (!p) continue;
         const cudaError_t e = cudaFree(p);
@@ -359,7 +406,32 @@ static diaq_status free_op_memory(diaq_op_s* op) {
     return first == cudaSuccess ? DIAQ_OK : cuda_fail(first, "cudaFree(op memory)");
 }
 
-static diaq_status alloc_stored(diaq_op_s* op) {
+// Stored diagonals come from a library-owned stream-ordered pool per device
+// that keeps up to 32 GiB of released memory for reuse, so the build,
+// apply, release cycle of a circuit of stored ops (up to 12 GiB each at 28
+// qubits) does not return to the operating system between ops. Memory above
+// that threshold goes back at the next synchronisation.
+static diaq_status values_pool(int dev, cudaMemPool_t* out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return fail(DIAQ_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        DIAQ_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t keep = uint64_t(32) << 30;
+        DIAQ_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+        pools[dev] = p;
+    }
+    *out = pools[dev];
+    return DIAQ_OK;
+}
+
+static diaq_status alloc_stored(diaq_op_s* op, cudaStream_t s) {
     const int64_t N = int64_t(1) << op->n;
     op->starts.resize(op->offsets.size());
     int64_t tot = 0;
@@ -369,17 +441,22 @@ static diaq_status alloc_stored(diaq_op_s* op) {
     }
     op->stored_elems = tot;
     const size_t bytes = size_t(std::max<int64_t>(tot, 1)) * amp_bytes(op->dtype);
-    cudaError_t e = cudaMalloc(&op->d_values, bytes);
-    if (e != cudaSuccess)
-        return fail(DIAQ_ERR_ALLOC, "cudaMalloc of %zu bytes for stored diagonals failed: %s", bytes,
+    cudaMemPool_t pool = nullptr;
+    DIAQ_TRY(values_pool(op->device, &pool));
+    cudaError_t e = inject_now() ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(&op->d_values, bytes, pool, s);
+    if (e != cudaSuccess) {
+        op->d_values = nullptr;
+        return fail(DIAQ_ERR_ALLOC, "allocation of %zu bytes for stored diagonals failed: %s", bytes,
                     cudaGetErrorString(e));
+    }
     const size_t ob = std::max<size_t>(op->offsets.size(), 1) * sizeof(int64_t);
     if ((e = cudaMalloc((void**)&op->d_offsets, ob)) != cudaSuccess ||
         (e = cudaMalloc((void**)&op->d_starts, ob)) != cudaSuccess)
         return fail(DIAQ_ERR_ALLOC, "cudaMalloc for diagonal indices failed: %s", cudaGetErrorString(e));
     if (!op->offsets.empty()) {
-        DIAQ_CUDA(cudaMemcpy(op->d_offsets, op->offsets.data(), op->offsets.size() * 8, cudaMemcpyHostToDevice));
-        DIAQ_CUDA(cudaMemcpy(op->d_starts, op->starts.data(), op->starts.size() * 8, cudaMemcpyHostToDevice));
+        // ordered on the build stream (the host vectors live as long as the op)
+        DIAQ_CUDA(cudaMemcpyAsync(op->d_offsets, op->offsets.data(), op->offsets.size() * 8, cudaMemcpyHostToDevice, s));
+        DIAQ_CUDA(cudaMemcpyAsync(op->d_starts, op->starts.data(), op->starts.size() * 8, cudaMemcpyHostToDevice, s));
     }
     return DIAQ_OK;
 }
@@ -393,7 +470,7 @@ static diaq_status finish_gate_op(diaq_op_s* op, const std::vector<uint8_t>* pat
         if (op->gate.k > 3) DIAQ_TRY(upload_matrix(op));
         return DIAQ_OK;
     }
-    DIAQ_TRY(alloc_stored(op));
+    DIAQ_TRY(alloc_stored(op, s));
     return launch_materialise(op, s);
 }
 
@@ -571,7 +648,7 @@ diaq_status diaq_build_diaq(int32_t n_qubits, int64_t count, const int64_t* indi
     for (auto& p : idx) op->offsets.push_back(p.first);
     op->real_values = true;
     for (int64_t t = 0; t < pos && op->real_values; ++t) op->real_values = values[2 * t + 1] == 0.0;
-    diaq_status s = alloc_stored(op);
+    diaq_status s = alloc_stored(op, static_cast<cudaStream_t>(stream));
     if (s == DIAQ_OK) {
         // host staging in the op's precision, sorted order
         const size_t ab = amp_bytes(dtype);
@@ -733,7 +810,7 @@ diaq_status diaq_fuse(const diaq_op_t* ops, int32_t count, diaq_variant variant,
         c->device = ops[0]->device;
         c->offsets = ops[0]->offsets;
         c->real_values = ops[0]->real_values;
-        diaq_status st = alloc_stored(c);
+        diaq_status st = alloc_stored(c, s);
         if (st == DIAQ_OK) {
             cudaError_t e = cudaMemcpyAsync(c->d_values, ops[0]->d_values, size_t(c->stored_elems) * amp_bytes(c->dtype),
                                             cudaMemcpyDeviceToDevice, s);
@@ -818,7 +895,7 @@ static diaq_status prune_with_counts(const diaq_op_s* src, const std::vector<int
             keep.push_back(int32_t(q));
             c->offsets.push_back(src->offsets[q]);
         }
-    diaq_status st = alloc_stored(c);
+    diaq_status st = alloc_stored(c, s);
     if (st == DIAQ_OK) st = launch_gather_diagonals(src, keep, c, s);
     if (st != DIAQ_OK) {
         free_op_memory(c);

@@ -18,8 +18,11 @@
 #include <algorithm>
 #include <cstring>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(inplace)
 
 namespace diaq {
 
@@ -27,6 +30,7 @@ template <typename R, int K>
 struct RowsArgs {
     int64_t g_base;         // first group of the launch
     int64_t n_groups;       // one past the last group
+    int64_t N;              // amplitudes of the state
     int st[K];              // targets, ascending
     int64_t off[1 << K];    // full-system offset of local index c
     uint32_t ld_mask;       // local columns read by the changed rows
@@ -51,6 +55,7 @@ k_apply_rows(amp_t<R>* x, const __grid_constant__ RowsArgs<R, K> a) {
     for (int j = 0; j < G; ++j) {
         const int64_t g = g0 + j * T;
         b[j] = g < a.n_groups ? insert_zeros<K>(g, a.st) : int64_t(-1);
+        if (b[j] >= 0 && !DIAQ_BOUNDS_OK(b[j] + a.off[D - 1], a.N, BS_APPLY_ROWS)) b[j] = -1;
         if (b[j] >= 0) {
 #pragma unroll
             for (int c = 0; c < D; ++c)
@@ -126,6 +131,7 @@ static diaq_status launch_rows_G(int n, const GateDesc& g, uint32_t ld, uint32_t
     std::memset(&a, 0, sizeof(a));
     a.g_base = g_begin;
     a.n_groups = g_end;
+    a.N = int64_t(1) << n;
     for (int i = 0; i < K; ++i) a.st[i] = g.targets[i];
     std::sort(a.st, a.st + K);
     for (int c = 0; c < (1 << K); ++c) {

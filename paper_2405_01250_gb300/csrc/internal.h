@@ -168,6 +168,17 @@ bool is_diagonal(const GateDesc& g);
 diaq_status launch_diag(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y, cudaStream_t s);
 int64_t diag_inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
 
+// Debug bounds words, one per translation unit with checks (bounds.cuh);
+// each returns the first failure recorded there (0: none; ~0: unreadable)
+// and clears it when asked. In the normal build they return 0.
+unsigned long long bounds_word_apply(bool clear);
+unsigned long long bounds_word_inplace(bool clear);
+unsigned long long bounds_word_diag(bool clear);
+unsigned long long bounds_word_reduce(bool clear);
+unsigned long long bounds_word_batch(bool clear);
+unsigned long long bounds_word_sample(bool clear);
+unsigned long long bounds_word_shard(bool clear);
+
 // Pauli-sum terms grouped by X mask, prepared on the host.
 struct PauliGroups {
     std::vector<uint64_t> xmask;         // one per group

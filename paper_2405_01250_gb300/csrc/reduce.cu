@@ -18,8 +18,11 @@
 #include <cstring>
 #include <vector>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(reduce)
 
 namespace diaq {
 
@@ -248,7 +251,9 @@ k_expect(const amp_t<R>* __restrict__ psi, int64_t N, const DevGroups G, double*
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += stride) {
         const double2 pj = to_d2<R>(psi[j]);
         for (int g = 0; g < G.n_groups; ++g) {
-            const double2 pk = to_d2<R>(psi[j ^ (int64_t)G.xmask[g]]);
+            const int64_t jk = j ^ (int64_t)G.xmask[g];
+            if (!DIAQ_BOUNDS_OK(jk, N, BS_EXPECT)) continue;
+            const double2 pk = to_d2<R>(psi[jk]);
             // w = conj(pk) * pj
             const double wr = pk.x * pj.x + pk.y * pj.y;
             const double wi = pk.x * pj.y - pk.y * pj.x;
@@ -312,6 +317,7 @@ k_pauli_apply(const amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int6
         R lr = R(0), li = R(0);
         for (int g = 0; g < G.n_groups; ++g) {
             const uint64_t j = (uint64_t)i ^ G.xmask[g];
+            if (!DIAQ_BOUNDS_OK(int64_t(j), N, BS_PAULI_APPLY)) continue;
             const amp_t<R> p = psi[j];
             // W_g(j) in the state's precision
             R wr = R(0), wi = R(0);

@@ -11,6 +11,7 @@
 // an indexed load; the angle enters as three numbers (cos, kappa).
 #pragma once
 
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace diaq {
@@ -76,6 +77,7 @@ __device__ __noinline__ double rot_groups_u(amp_t<R>* __restrict__ psi, amp_t<R>
         for (int u = 0; u < U; ++u) {
             const int64_t gi = g0 + int64_t(u) * nthreads;
             b[u] = gi < G ? insert_zeros<K>(gi, st) : int64_t(-1);
+            if (b[u] >= 0 && !DIAQ_BOUNDS_OK(b[u] + off[D - 1], int64_t(1) << n, BS_ROTATION)) b[u] = -1;
             if (b[u] >= 0) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) p[u][c] = psi[b[u] + off[c]];

@@ -40,8 +40,11 @@
 
 #include <algorithm>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(sample)
 
 namespace diaq {
 namespace {
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(256) k_sample_tiles(const amp_t<R>* __restrict
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
         const int64_t i = base + 32 * j + lane;
-        v[j] = i < N ? ld_stream(psi + i) : zero_amp<R>();
+        v[j] = i < N && DIAQ_BOUNDS_OK(i, N, BS_SAMPLE_TILES) ? ld_stream(psi + i) : zero_amp<R>();
     }
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
@@ -242,6 +245,7 @@ __global__ void __launch_bounds__(128) k_sample_search(const amp_t<R>* __restric
         const int64_t e = b + kFan < lv.count[L] ? b + kFan : lv.count[L];
         node = pick(lv.pre[L], b, e, r, take_last);
     }
+    if (node >= 0 && !DIAQ_BOUNDS_OK(node, lv.count[0], BS_SAMPLE_SEARCH)) node = -1;
     if (node >= 0) {  // node: the tile
         const int64_t seg = pick(lv.seg_pre + node * kTileSegs, 0, kTileSegs, r, take_last);
         if (seg >= 0) {

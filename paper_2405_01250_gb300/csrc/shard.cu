@@ -17,8 +17,11 @@
 
 #include <algorithm>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+
+DIAQ_BOUNDS_TU(shard)
 
 namespace diaq {
 namespace {
@@ -35,6 +38,7 @@ __global__ void __launch_bounds__(256) k_shard_swap(amp_t<R>* __restrict__ lo_sh
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride) {
         const int64_t a = with_bit(t, l, 1), b = with_bit(t, l, 0);
+        if (!DIAQ_BOUNDS_OK(a, 2 * half, BS_SHARD_MOVE)) continue;
         const amp_t<R> va = ld_stream(lo_shard + a);
         const amp_t<R> vb = ld_stream(hi_shard + b);
         st_stream(lo_shard + a, vb);
@@ -47,7 +51,8 @@ __global__ void __launch_bounds__(256) k_shard_pack(const amp_t<R>* __restrict__
                                                     int64_t half, int l, int value) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride)
-        st_stream(buf + t, ld_stream(shard + with_bit(t, l, value)));
+        if (DIAQ_BOUNDS_OK(with_bit(t, l, value), 2 * half, BS_SHARD_MOVE))
+            st_stream(buf + t, ld_stream(shard + with_bit(t, l, value)));
 }
 
 template <typename R>
@@ -55,7 +60,8 @@ __global__ void __launch_bounds__(256) k_shard_unpack(const amp_t<R>* __restrict
                                                       int64_t half, int l, int value) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += stride)
-        st_stream(shard + with_bit(t, l, value), ld_stream(buf + t));
+        if (DIAQ_BOUNDS_OK(with_bit(t, l, value), 2 * half, BS_SHARD_MOVE))
+            st_stream(shard + with_bit(t, l, value), ld_stream(buf + t));
 }
 
 int move_blocks(int64_t half) {

@@ -209,7 +209,7 @@ def test_binding_signatures_match_the_header():
         base = decl.split()[0] if not decl.startswith("const ") else decl.split()[1]
         if base in ("int32_t", "int", "diaq_dtype", "diaq_variant"):
             return "i32"
-        if base == "int64_t":
+        if base in ("int64_t", "uint64_t"):
             return "i64"
         if base == "double":
             return "f64"
@@ -220,7 +220,7 @@ def test_binding_signatures_match_the_header():
             return "ptr"
         if C.sizeof(t) == 4 and t in (C.c_int32, C.c_int):
             return "i32"
-        if t is C.c_int64:
+        if t in (C.c_int64, C.c_uint64):
             return "i64"
         if t is C.c_double:
             return "f64"
@@ -233,3 +233,35 @@ def test_binding_signatures_match_the_header():
         kinds = [] if params in ("", "void") else [c_kind(p) for p in params.split(",")]
         assert [py_kind(a) for a in args] == kinds, name
         assert (res is C.c_char_p) == ret.startswith("const char"), name
+
+
+def test_debug_bounds_status_plumbing():
+    """The debug build's status path on the CPU: the recorded word decodes to
+    DIAQ_ERR_BOUNDS with the site and the index (negative indices included);
+    an empty word is DIAQ_OK; the normal build reports its checks as off and
+    the debug build as on."""
+    import ctypes as C
+    import subprocess
+    import sys
+
+    from paper_2405_01250_gb300 import _native as N
+    L = N.lib()
+    assert L.diaq_debug_bounds_status(0) == 0
+    site, idx = 6, 123456789
+    w = (1 << 63) | (site << 48) | idx
+    assert L.diaq_debug_bounds_status(w) == 6
+    msg = L.diaq_last_error().decode()
+    assert "stored SpMV column" in msg and "123456789" in msg
+    neg = (1 << 63) | (10 << 48) | ((-5) & 0xFFFFFFFFFFFF)
+    assert L.diaq_debug_bounds_status(neg) == 6 and "index -5" in L.diaq_last_error().decode()
+    on = C.c_int32(7)
+    assert L.diaq_debug_bounds_enabled(C.byref(on)) == 0
+    assert on.value == (1 if N.DEBUG_BOUNDS else 0)
+    # the debug build compiles and reports its checks as on (in a fresh process)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import ctypes, sys; sys.path.insert(0, %r); "
+            "from paper_2405_01250_gb300 import build as B; p = B.build(debug_bounds=True); "
+            "L = ctypes.CDLL(p); v = ctypes.c_int32(0); "
+            "assert L.diaq_debug_bounds_enabled(ctypes.byref(v)) == 0 and v.value == 1; print('dbg ok')" % root)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=900)
+    assert "dbg ok" in out.stdout, out.stderr[-2000:]
