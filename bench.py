@@ -520,6 +520,51 @@ def bench_sample(api, psi, n, j, stream, shots=1024, reps=10):
     return out
 
 
+# FP64 instructions per amplitude of the complex128 sweep kernels, per gate
+# kind: a Pauli rotation 4 forward (cos x + kappa x', a product and an FMA
+# per part) and 10 reverse (U^dag on psi and lambda, and the 2-FMA gradient
+# term); a fixed real gate (H) 4 forward, 8 reverse; CZ and other sign or
+# permutation gates 0; a diagonal run (weight form) 4 forward, 11 reverse
+# (2 for Im conj(l) p, 1 for W t, 8 for D^dag on both states); a chunk-form
+# run of r rotations over c byte tables 4 (c - 1) + 4 forward and
+# 4 (c - 1) + 2 + r + 8 reverse. The Pauli-sum lambda: 2 per term (the
+# signed weights) and 4 per X-mask group, plus 2 for the energy. The reverse
+# sweep stops at the earliest gate with a gradient term.
+def fp64_per_amp(gates, obs, runs, chunks_run=None):
+    """(forward, reverse, lambda) FP64 instructions per amplitude of one
+    energy + gradient of `gates`; with runs=True the diagonal runs are
+    counted as the library forms them (chunks_run: (rotations, byte tables)
+    of each chunk-form run in place of its member gates, or the weight form
+    for runs of one-parameter rotations)."""
+    def kind(g):
+        if g.param >= 0:
+            return "zrot" if set(g.gen) <= {"Z", "I"} else "rot"
+        m = np.asarray(g.matrix)
+        if np.count_nonzero(m - np.diag(np.diag(m))) == 0 and np.all(np.isin(np.diag(m), [1, -1])):
+            return "sign"
+        return "fixed"
+    ks = [kind(g) for g in gates]
+    first = next((i for i, k in enumerate(ks) if k in ("rot", "zrot")), len(ks))
+    fwd = rev = 0
+    for i, k in enumerate(ks):
+        if runs and k in ("zrot", "sign"):
+            continue  # counted with the runs below
+        fwd += {"rot": 4, "zrot": 4, "fixed": 4, "sign": 0}[k]
+        if i >= first:
+            rev += {"rot": 10, "zrot": 10, "fixed": 8, "sign": 0}[k]
+    if runs:
+        for r_rot, c in (chunks_run or []):
+            if c == 0:  # weight form
+                fwd += 4
+                rev += 11
+            else:
+                fwd += 4 * (c - 1) + 4
+                rev += 4 * (c - 1) + 2 + r_rot + 8
+    groups = len(set(int(x) for x in obs.xmask))
+    lam = 2 * len(obs.coeff) + 4 * groups + 2
+    return fwd, rev, lam
+
+
 def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     """Ansatz-20 energy + full gradient (320 parameters) by the adjoint sweep,
     complex128 and complex64, against the plain FP64 path: the
@@ -578,6 +623,36 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
             "device_ms_by_sweep": {f"w{tw}_l{tl}": m for tw, tl, m in tune["tried"]}}
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
+    # the same plan, gate by gate (diagonal runs off), complex128
+    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=torch.complex128)
+    on, n_runs, steps = plan.runs()
+    plan.set_runs(False)
+    for _ in range(2):
+        plan.run(circ.theta)
+    t0 = time.perf_counter()
+    for _ in range(3 * reps):
+        e, g = plan.run(circ.theta)
+    el_off = (time.perf_counter() - t0) / (3 * reps)
+    plan.close()
+    out["adjoint_gate_by_gate_graph_c128"] = {"ms_per_gradient": el_off * 1e3, "grads_per_s": 1.0 / el_off}
+    # FP64 floor of a complex128 gradient (FP64-bound: the 16 MiB states stay in L2)
+    N = 1 << n
+    chunks = (n + 7) // 8
+    f0, r0, l0 = fp64_per_amp(circ.gates, obs, runs=False)
+    f1, r1, l1 = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers)
+    best = out["adjoint_autotuned_c128"]["ms_per_gradient"]
+    out["roofline_c128"] = {
+        "bound": "fp64", "unit": "FP64 instructions", "peak_instr_per_s": FP64_INSTR_PER_S,
+        "peak_source": "measured FP64 probe (independent DFMA chains), not MEASURED_PEAKS.json",
+        "diagonal_runs": n_runs, "launches_per_direction": steps,
+        "fp64_instr_per_gradient": (f1 + r1 + l1) * N, "floor_ms": (f1 + r1 + l1) * N / FP64_INSTR_PER_S * 1e3,
+        "achieved_ms": best, "frac": (f1 + r1 + l1) * N / FP64_INSTR_PER_S * 1e3 / best,
+        "gate_by_gate_fp64_instr_per_gradient": (f0 + r0 + l0) * N,
+        "gate_by_gate_floor_ms": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3,
+        "frac_of_gate_by_gate_floor": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3 / best,
+        "bytes_per_gradient": N * 16 * (2 * steps + 4 * steps + 2),
+        "note": "per amplitude: rotation 4 forward / 10 reverse; chunk-form diagonal run (RZ layer + CZ ladder) "
+                "4 (c - 1) + 4 forward, 4 (c - 1) + 10 + r reverse; lambda 2 per term + 4 per X group"}
     for name in ("c128", "c64"):
         # what the graph plan and the window-fused sweep add over the
         # one-launch-per-gate adjoint sweep (the same algorithm)
@@ -670,7 +745,7 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
                 "energy_max_abs_err": max(abs(E[i] - refs[i][0]) for i in refs),
                 "grad_max_abs_err": max(float(np.max(np.abs(G[i] - refs[i][1]))) for i in refs)}
         q = b.query()
-        out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
+        out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3, "diagonal_runs": b.runs()[1],
                                   "cluster": q["cluster"], "threads": q["threads"], "window": b.sweep()[0],
                                   "lanes": b.sweep()[1],
                                   "teams": q["teams"],
@@ -691,6 +766,23 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
             e_plain.append(e)
         el = time.perf_counter() - t0
         out["plain_fp64_per_circuit"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3}
+        # FP64 floor of the complex128 batch (sum over circuits of N x
+        # instructions per amplitude, gate by gate and with the cost layers
+        # as weight-form diagonal runs)
+        fl0 = fl1 = 0.0
+        for c, o in inst:
+            f0, r0, l0 = fp64_per_amp(c.gates, o, runs=False)
+            f1, r1, l1 = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4)
+            fl0 += (1 << c.n) * (f0 + r0 + l0)
+            fl1 += (1 << c.n) * (f1 + r1 + l1)
+        bt = out["batched_c128"]["ms_per_batch"]
+        out["roofline_c128"] = {
+            "bound": "fp64", "unit": "FP64 instructions", "peak_instr_per_s": FP64_INSTR_PER_S,
+            "peak_source": "measured FP64 probe (independent DFMA chains), not MEASURED_PEAKS.json",
+            "fp64_instr_per_batch": fl1, "floor_ms": fl1 / FP64_INSTR_PER_S * 1e3, "achieved_ms": bt,
+            "frac": fl1 / FP64_INSTR_PER_S * 1e3 / bt, "gate_by_gate_fp64_instr_per_batch": fl0,
+            "gate_by_gate_floor_ms": fl0 / FP64_INSTR_PER_S * 1e3,
+            "frac_of_gate_by_gate_floor": fl0 / FP64_INSTR_PER_S * 1e3 / bt}
         out["batched_c128_vs_plain_max_abs_energy_diff"] = float(np.max(np.abs(np.array(e_plain) - energies["c128"])))
         out["speedup_batched_c128_vs_plain"] = out["batched_c128"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]
         out["speedup_batched_c64_vs_plain"] = out["batched_c64"]["circuits_per_s"] / out["plain_fp64_per_circuit"]["circuits_per_s"]

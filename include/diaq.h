@@ -489,6 +489,23 @@ diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, i
 
 diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, int32_t* lanes, int32_t* n_blocks);
 
+/* Diagonal runs of the per-gate sweep (window 0; on by default). Runs of
+ * Z-type rotations (generators of I and Z letters), fixed single-qubit
+ * diagonal gates and CZs - after moving the other gates that act on none of
+ * a run's qubits ahead of it, which changes neither the operator nor any
+ * gradient term - are applied as one diagonal operator (Section III-A:
+ * such gates live on the principal diagonal, as does their product) in one
+ * launch each way: a table lookup per amplitude when the run's rotations
+ * share one parameter (a QAOA cost layer: the phase depends only on
+ * W(i) = sum_g z_g(i)), a product of per-byte tables and the CZ sign when
+ * they act on single qubits (an ansatz layer's RZs and CZ ladder). Each
+ * rotation's gradient term, sum_i z_g(i) Im(conj(lambda_i) psi_i), is the
+ * same anywhere inside the run. on = 0 applies every gate separately.
+ * Re-records the graph. get_runs: whether runs are on, how many the circuit
+ * has, and the launches per sweep direction. */
+diaq_status diaq_adjoint_plan_set_runs(diaq_adjoint_plan_t p, int32_t on);
+diaq_status diaq_adjoint_plan_get_runs(diaq_adjoint_plan_t p, int32_t* on, int32_t* n_runs, int32_t* n_steps);
+
 #define DIAQ_PLAN_TUNE_MAX 8
 
 typedef struct {
@@ -663,6 +680,16 @@ diaq_status diaq_batch_get_window(diaq_batch_t b, int32_t* window);
 diaq_status diaq_batch_set_sweep(diaq_batch_t b, int32_t window, int32_t lanes);
 
 diaq_status diaq_batch_get_sweep(diaq_batch_t b, int32_t* window, int32_t* lanes);
+
+/* Diagonal runs of the per-gate team kernel (window 0; on by default), as in
+ * diaq_adjoint_plan_set_runs but in the weight form only: a run of Z-type
+ * rotations that share one parameter and scale (a QAOA cost layer) is one
+ * pass with a phase table indexed by W(i) = sum_g z_g(i), and its gradient
+ * term sum_i W(i) Im(conj(lambda_i) psi_i). Other diagonal gates run one by
+ * one. Recaptures the graph. get_runs: whether runs are on and how many the
+ * batch's circuits hold. */
+diaq_status diaq_batch_set_runs(diaq_batch_t b, int32_t on);
+diaq_status diaq_batch_get_runs(diaq_batch_t b, int32_t* on, int32_t* n_runs);
 
 /* Time every team shape that fits - window 0 with cluster in {1,2,4,8} x
  * threads in {64,128,256}, and windows 3, 4, 5 at 1 and 4 lanes with

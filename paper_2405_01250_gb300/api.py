@@ -533,6 +533,16 @@ class AdjointPlan:
         """window 0 (per gate) or 2..5, with 1 or 4 threads per group (diaq_adjoint_plan_set_sweep)."""
         check(lib().diaq_adjoint_plan_set_sweep(self.handle, int(window), int(lanes)))
 
+    def set_runs(self, on: bool) -> None:
+        """Diagonal runs of the per-gate sweep on or off (diaq_adjoint_plan_set_runs)."""
+        check(lib().diaq_adjoint_plan_set_runs(self.handle, int(bool(on))))
+
+    def runs(self) -> tuple:
+        """(on, runs in the circuit, launches per sweep direction)."""
+        a, b, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_runs(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return bool(a.value), b.value, c.value
+
     def sweep(self) -> tuple:
         """(window, lanes, launches per sweep)."""
         w, ln, nb = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
@@ -627,6 +637,16 @@ class Batch:
         w, ln = ctypes.c_int32(0), ctypes.c_int32(0)
         check(lib().diaq_batch_get_sweep(self.handle, ctypes.byref(w), ctypes.byref(ln)))
         return w.value, ln.value
+
+    def set_runs(self, on: bool):
+        """Diagonal runs of the per-gate team kernel on or off (diaq_batch_set_runs)."""
+        check(lib().diaq_batch_set_runs(self.handle, int(bool(on))))
+
+    def runs(self) -> tuple:
+        """(on, diagonal runs in the batch's circuits)."""
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_batch_get_runs(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return bool(a.value), b.value
 
     def set_window(self, window: int):
         """0: one pass per gate; 2..5: window-fused blocks (diaq_batch_set_window)."""

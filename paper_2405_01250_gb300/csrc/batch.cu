@@ -29,6 +29,7 @@
 #include "bounds.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "phase.cuh"
 #include "rot.cuh"
 #include "win.cuh"
 
@@ -56,6 +57,8 @@ struct BGate {
 struct BInst {
     int32_t n;
     int32_t gate_begin, gate_end;
+    int32_t exec_begin, exec_end;    // execution list of the per-gate kernel (gates and diagonal runs)
+    int32_t exec_rev_begin;          // the reverse sweep stops here: the earliest entry with a gradient term
     int32_t block_begin, block_end;  // window blocks of the instance (window-fused kernel)
     int32_t param_begin, n_params;
     int32_t term_begin, term_end;
@@ -72,6 +75,8 @@ struct BTerm {
 struct BatchArgs {
     const BInst* inst;
     const BGate* gates;
+    const int32_t* exec;       // gate index, or -1 - run index
+    const PhaseRun* runs;      // diagonal runs (weight form)
     const BTerm* terms;
     const int32_t* sched;      // instance ids, team-major: sched[team_first[c] .. team_first[c+1])
     const int32_t* team_first;
@@ -307,6 +312,7 @@ template <typename R>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     using A = amp_t<R>;
     __shared__ StepMats<R> mats;
+    __shared__ PhaseTables<PR_TAB_WEIGHT> ptab;
     __shared__ double warps[32];
     __shared__ double ang[3];
     const int C = a.C;
@@ -331,7 +337,16 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
         }
         team_sync(C);
         // forward sweep
-        for (int gi = I.gate_begin; gi < I.gate_end; ++gi) {
+        for (int x = I.exec_begin; x < I.exec_end; ++x) {
+            const int gi = a.exec[x];
+            if (gi < 0) {  // a diagonal run: one pass with its phase table
+                const PhaseRun& run = a.runs[-1 - gi];
+                phase_tables<PR_TAB_WEIGHT>(run, th, false, I.n, &ptab);
+                double acc[1];
+                phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
+                team_sync(C);
+                continue;
+            }
             const BGate& g = a.gates[gi];
             if (threadIdx.x == 0) {
                 if (g.param >= 0) rot_angle(g, th, false, &ang[0], &ang[1], &ang[2]);
@@ -356,7 +371,21 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
         if (threadIdx.x == 0) part[0 * C + rank] = es;
         team_sync(C);
         // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
-        for (int gi = I.gate_end - 1; gi >= I.gate_begin; --gi) {
+        for (int x = I.exec_end - 1; x >= I.exec_rev_begin; --x) {
+            const int gi = a.exec[x];
+            if (gi < 0) {  // a diagonal run: its gradient sum, then D^dag on psi and lam
+                const PhaseRun& run = a.runs[-1 - gi];
+                phase_tables<PR_TAB_WEIGHT>(run, th, true, I.n, &ptab);
+                double acc[1];
+                phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, lam, I.n, run, ptab, tid, nthreads, acc);
+                const double sum = block_sum(acc[0], warps);
+                if (threadIdx.x == 0) {
+                    part[int64_t(run.rot_slot[0]) * C + rank] = sum;
+                    for (int g2 = 1; g2 < run.n_rot; ++g2) part[int64_t(run.rot_slot[g2]) * C + rank] = 0.0;
+                }
+                team_sync(C);
+                continue;
+            }
             const BGate& g = a.gates[gi];
             if (threadIdx.x == 0) {
                 if (g.param >= 0) rot_angle(g, th, true, &ang[0], &ang[1], &ang[2]);
@@ -702,7 +731,15 @@ struct diaq_batch_s {
     int lanes = 1;  // threads per group of the window-fused kernel (1 or WIN_LANES)
     WinBlock* d_blocks = nullptr;
     WinGate* d_wg = nullptr;
+    // execution lists of the per-gate kernel, with or without diagonal runs
+    bool runs_on = true;
+    int n_runs = 0;
+    std::vector<int32_t> exec_list;
+    std::vector<PhaseRun> runs;
+    int32_t* d_exec = nullptr;
+    PhaseRun* d_runs = nullptr;
 };
+
 
 // Rotation shape of a parametric gate from its generator letters.
 static void fill_rot(BGate* B) {
@@ -726,6 +763,112 @@ static void fill_rot(BGate* B) {
                 if ((c >> (k - 1 - a)) & 1) o += int64_t(1) << B->t[a];
         B->rot.off[c] = o;
     }
+}
+
+// Diagonal runs (phase.cuh) of one circuit's gates [0, n_gates): Z-type
+// rotations (generators of I and Z letters), fixed single-qubit diagonal
+// gates and CZs gather into a run; a gate of any other kind that acts on
+// none of the run's qubits moves ahead of it (it commutes with every
+// member), one that shares a qubit closes the run. A run of at least two
+// gates that fits the weight form (one shared parameter and scale, no fixed
+// gate) or, with chunks_ok, the chunk form (single-qubit rotations) becomes
+// one step; any other run is executed gate by gate in its order. exec
+// receives the execution order: gate_base + gate index, or -1 - run index
+// (runs appended to *runs).
+static void plan_phase_runs(const BGate* gates, int n_gates, int gate_base, bool chunks_ok, std::vector<int32_t>* exec,
+                            std::vector<PhaseRun>* runs) {
+    auto zrot = [](const BGate& g, uint64_t* z) {
+        if (g.param < 0) return false;
+        uint64_t m = 0;
+        for (int a = 0; a < g.k; ++a) {
+            if (g.pauli[a] != 0 && g.pauli[a] != 3) return false;
+            if (g.pauli[a] == 3) m |= uint64_t(1) << g.t[a];
+        }
+        *z = m;
+        return true;
+    };
+    auto fix1 = [](const BGate& g) {
+        return g.param < 0 && g.k == 1 && g.re[1] == 0.0 && g.im[1] == 0.0 && g.re[2] == 0.0 && g.im[2] == 0.0;
+    };
+    auto cz = [](const BGate& g) {
+        if (g.param >= 0 || g.k != 2) return false;
+        for (int e = 0; e < 16; ++e) {
+            const double want = (e == 0 || e == 5 || e == 10) ? 1.0 : (e == 15 ? -1.0 : 0.0);
+            if (g.re[e] != want || g.im[e] != 0.0) return false;
+        }
+        return true;
+    };
+    std::vector<int> members;
+    uint64_t run_q = 0;
+    auto flush = [&]() {
+        if (members.empty()) return;
+        PhaseRun r = {};
+        bool weight = members.size() >= 2 && int(members.size()) <= PR_MAX_ROT;
+        bool chunk = chunks_ok && members.size() >= 2;
+        int nr = 0;
+        for (int i : members) {
+            const BGate& g = gates[i];
+            uint64_t z = 0;
+            if (zrot(g, &z)) {
+                const BGate& f = gates[members[0]];
+                weight &= g.param == f.param && g.scale == f.scale && f.param >= 0;
+                chunk &= __builtin_popcountll(z) == 1 && nr < PR_MAX_CROT;
+                if (nr < PR_MAX_ROT) {
+                    r.rot_param[nr] = g.param;
+                    r.rot_scale[nr] = g.scale;
+                    r.rot_z[nr] = z;
+                    r.rot_slot[nr] = g.slot;
+                }
+                ++nr;
+            } else if (fix1(g)) {
+                weight = false;
+                if (r.n_fix1 >= PR_MAX_FIX1) {
+                    chunk = false;
+                    continue;
+                }
+                r.fix1_q[r.n_fix1] = g.t[0];
+                r.fix1_re[2 * r.n_fix1] = g.re[0];
+                r.fix1_im[2 * r.n_fix1] = g.im[0];
+                r.fix1_re[2 * r.n_fix1 + 1] = g.re[3];
+                r.fix1_im[2 * r.n_fix1 + 1] = g.im[3];
+                ++r.n_fix1;
+            } else {  // a CZ
+                weight = false;
+                if (r.n_cz >= PR_MAX_CZ) {
+                    chunk = false;
+                    continue;
+                }
+                r.cz[r.n_cz++] = (uint64_t(1) << g.t[0]) | (uint64_t(1) << g.t[1]);
+            }
+        }
+        r.n_rot = nr;
+        weight &= nr >= 2;
+        if (weight || chunk) {
+            r.kind = weight ? PR_WEIGHT : PR_CHUNKS;
+            exec->push_back(-1 - int32_t(runs->size()));
+            runs->push_back(r);
+        } else {
+            for (int i : members) exec->push_back(gate_base + i);
+        }
+        members.clear();
+        run_q = 0;
+    };
+    for (int i = 0; i < n_gates; ++i) {
+        const BGate& g = gates[i];
+        uint64_t q = uint64_t(1) << g.t[0];
+        if (g.k == 2) q |= uint64_t(1) << g.t[1];
+        uint64_t z = 0;
+        if (zrot(g, &z) || fix1(g) || cz(g)) {
+            members.push_back(i);
+            run_q |= q;
+        } else if (members.empty() || !(q & run_q)) {
+            exec->push_back(gate_base + i);
+        } else {
+            flush();
+            exec->push_back(gate_base + i);
+        }
+    }
+    flush();
 }
 
 // Window blocks of at most `window` qubits and WIN_MAXG gates for the gates
@@ -795,6 +938,8 @@ static void batch_free(diaq_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->d_blocks) cudaFree(b->d_blocks);
     if (b->d_wg) cudaFree(b->d_wg);
+    if (b->d_exec) cudaFree(b->d_exec);
+    if (b->d_runs) cudaFree(b->d_runs);
     for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
                     b->d_arena, static_cast<void*>(b->d_theta), static_cast<void*>(b->d_partials),
                     static_cast<void*>(b->d_out), static_cast<void*>(b->d_sched), static_cast<void*>(b->d_team_first)})
@@ -810,6 +955,43 @@ static diaq_status upload(T** d, const std::vector<T>& h) {
     if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMalloc(%zu) for batch tables: %s", bytes, cudaGetErrorString(e));
     if (!h.empty()) DIAQ_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     return DIAQ_OK;
+}
+
+// The per-gate kernel's execution list of every instance (gates, or weight
+// form diagonal runs when runs_on), instance ranges in inst, uploaded with
+// the instance records.
+static diaq_status batch_exec(diaq_batch_s* b) {
+    b->exec_list.clear();
+    b->runs.clear();
+    for (BInst& I : b->inst) {
+        I.exec_begin = int32_t(b->exec_list.size());
+        if (b->runs_on) {
+            plan_phase_runs(b->gates.data() + I.gate_begin, I.gate_end - I.gate_begin, I.gate_begin, false, &b->exec_list,
+                            &b->runs);
+        } else {
+            for (int g = I.gate_begin; g < I.gate_end; ++g) b->exec_list.push_back(g);
+        }
+        I.exec_end = int32_t(b->exec_list.size());
+        // nothing below the earliest parametric entry feeds a gradient term
+        I.exec_rev_begin = I.exec_end;
+        for (int x = I.exec_begin; x < I.exec_end; ++x) {
+            const int32_t e = b->exec_list[size_t(x)];
+            if (e < 0 || b->gates[size_t(e)].param >= 0) {
+                I.exec_rev_begin = x;
+                break;
+            }
+        }
+    }
+    b->n_runs = int(b->runs.size());
+    for (void* q : {static_cast<void*>(b->d_exec), static_cast<void*>(b->d_runs), static_cast<void*>(b->d_inst)})
+        if (q) cudaFree(q);
+    b->d_exec = nullptr;
+    b->d_runs = nullptr;
+    b->d_inst = nullptr;
+    if (b->exec_list.empty()) b->exec_list.push_back(0);
+    DIAQ_TRY(upload(&b->d_exec, b->exec_list));
+    if (!b->runs.empty()) DIAQ_TRY(upload(&b->d_runs, b->runs));
+    return upload(&b->d_inst, b->inst);
 }
 
 template <typename R>
@@ -882,6 +1064,8 @@ static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
     BatchArgs a;
     a.inst = b->d_inst;
     a.gates = b->d_gates;
+    a.exec = b->d_exec;
+    a.runs = b->d_runs;
     a.terms = b->d_terms;
     a.sched = b->d_sched;
     a.team_first = b->d_team_first;
@@ -1153,7 +1337,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
     b->arena_elems = arena;
     // host tables validated; from here on the device is needed
     if (st == DIAQ_OK && (e = cudaGetDevice(&b->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
-    if (st == DIAQ_OK) st = upload(&b->d_inst, b->inst);
+    if (st == DIAQ_OK) st = batch_exec(b);
     if (st == DIAQ_OK) st = upload(&b->d_gates, b->gates);
     if (st == DIAQ_OK) st = upload(&b->d_terms, b->terms);
     if (st == DIAQ_OK) {
@@ -1202,6 +1386,28 @@ diaq_status diaq_batch_set_launch(diaq_batch_t b, int32_t cluster, int32_t threa
     if (b->window > 0 && threads != WIN_THREADS)
         return fail(DIAQ_ERR_ARG, "the window-fused kernel runs %d threads per block (got %d)", WIN_THREADS, threads);
     return configure(b, cluster, threads, nullptr);
+}
+
+diaq_status diaq_batch_set_runs(diaq_batch_t b, int32_t on) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    DIAQ_CUDA(cudaDeviceSynchronize());
+    if (b->exec) {  // it uses the lists replaced below
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->runs_on = on != 0;
+    DIAQ_TRY(batch_exec(b));
+    return configure(b, b->C, b->threads, nullptr);
+}
+
+diaq_status diaq_batch_get_runs(diaq_batch_t b, int32_t* on, int32_t* n_runs) {
+    clear_error();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (on) *on = b->runs_on ? 1 : 0;
+    if (n_runs) *n_runs = b->n_runs;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_batch_set_window(diaq_batch_t b, int32_t window) {
@@ -1438,6 +1644,42 @@ __global__ void k_plan_finish(const BGate* gates, int n_gates, const double* row
     for (int g = 0; g < n_gates; ++g) {
         const BGate& G = gates[g];
         if (G.slot >= 0) out[1 + G.param] += G.scale * rows[G.slot];
+    }
+}
+
+// A diagonal run (phase.cuh) of the plan: forward D psi, or reverse with the
+// run's gradient rows (P columns) and D^dag on psi and lambda.
+template <typename R, bool REV>
+__global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam, const PhaseRun* __restrict__ run,
+                                                    const double* __restrict__ theta, int n, double* part, int P) {
+    __shared__ PhaseTables<PR_TAB_ALL> tb;
+    __shared__ PhaseRun rs;
+    __shared__ double warps[32];
+    {
+        const int* src = reinterpret_cast<const int*>(run);
+        int* dst = reinterpret_cast<int*>(&rs);
+        for (int i = threadIdx.x; i < int(sizeof(PhaseRun) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    phase_tables<PR_TAB_ALL>(rs, theta, REV, n, &tb);
+    double acc[PR_MAX_CROT];
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    phase_run_sweep<R, true, PR_TAB_ALL>(psi, REV ? lam : nullptr, n, rs, tb, tid, nth, acc);
+    if (!REV) return;
+    if (rs.kind == PR_WEIGHT) {
+        // the run's sum in the first member's row, zeros in the others' (same
+        // parameter and scale, so the finish sums the same total)
+        const double v = block_sum(acc[0], warps);
+        if (threadIdx.x == 0) {
+            part[int64_t(rs.rot_slot[0]) * P + blockIdx.x] = v;
+            for (int g = 1; g < rs.n_rot; ++g) part[int64_t(rs.rot_slot[g]) * P + blockIdx.x] = 0.0;
+        }
+    } else {
+        for (int g = 0; g < rs.n_rot; ++g) {
+            const double v = block_sum(acc[g], warps);
+            if (threadIdx.x == 0) part[int64_t(rs.rot_slot[g]) * P + blockIdx.x] = v;
+        }
     }
 }
 
@@ -1706,12 +1948,19 @@ struct diaq_adjoint_plan_s {
     int lanes = 1;                   // threads per group of the window-fused kernel (1 or WIN_LANES)
     std::vector<WinBlock> blocks;
     WinGate* d_wg = nullptr;
+    // diagonal runs of the per-gate sweep (window 0)
+    bool runs_on = true;
+    std::vector<int32_t> run_order;  // gate index, or -1 - run index
+    std::vector<PhaseRun> runs;
+    PhaseRun* d_runs = nullptr;
 };
 
 static void plan_free(diaq_adjoint_plan_s* p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->d_wg) cudaFree(p->d_wg);
     p->d_wg = nullptr;
+    if (p->d_runs) cudaFree(p->d_runs);
+    p->d_runs = nullptr;
     for (void* q : {static_cast<void*>(p->d_gates), static_cast<void*>(p->d_terms), static_cast<void*>(p->d_angles),
                     p->d_psi, p->d_lam, static_cast<void*>(p->d_theta), static_cast<void*>(p->d_part),
                     static_cast<void*>(p->d_rows), static_cast<void*>(p->d_out)})
@@ -1747,7 +1996,18 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
         for (size_t b = p->blocks.size(); b-- > 0;) block(p->blocks[b], lam);
         DIAQ_CUDA(cudaGetLastError());
     } else {
-        for (int g = 0; g < p->n_gates; ++g) {
+        std::vector<int32_t> order;
+        if (p->runs_on) {
+            order = p->run_order;
+        } else {
+            for (int g = 0; g < p->n_gates; ++g) order.push_back(g);
+        }
+        for (int32_t g : order) {
+            if (g < 0) {
+                k_plan_phase<R, false><<<p->P, 256, 0, s>>>(psi, nullptr, p->d_runs + (-1 - g), p->d_theta, p->n,
+                                                            nullptr, p->P);
+                continue;
+            }
             const BGate& G = p->gates[size_t(g)];
             if (G.param >= 0)
                 launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, s);
@@ -1755,7 +2015,20 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
                 DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
         }
         k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
-        for (int g = p->n_gates - 1; g >= 0; --g) {
+        // nothing below the earliest parametric entry feeds a gradient term
+        size_t stop = order.size();
+        for (size_t oi = 0; oi < order.size(); ++oi)
+            if (order[oi] < 0 || p->gates[size_t(order[oi])].param >= 0) {
+                stop = oi;
+                break;
+            }
+        for (size_t oi = order.size(); oi-- > stop;) {
+            const int32_t g = order[oi];
+            if (g < 0) {
+                k_plan_phase<R, true><<<p->P, 256, 0, s>>>(psi, lam, p->d_runs + (-1 - g), p->d_theta, p->n,
+                                                           p->d_part, p->P);
+                continue;
+            }
             const BGate& G = p->gates[size_t(g)];
             if (G.param >= 0) {
                 launch_plan_rot<R>(G, psi, lam, p->d_gates + g, p->d_angles + g, p->n,
@@ -1939,6 +2212,10 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
     }
     const size_t ab = amp_bytes(dtype), N = size_t(1) << n_qubits;
     if (st == DIAQ_OK) st = upload(&p->d_gates, p->gates);
+    if (st == DIAQ_OK) {
+        plan_phase_runs(p->gates.data(), n_gates, 0, true, &p->run_order, &p->runs);
+        if (!p->runs.empty()) st = upload(&p->d_runs, p->runs);
+    }
     if (st == DIAQ_OK) st = upload(&p->d_terms, terms);
     if (st == DIAQ_OK &&
         ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_angles), sizeof(RotAngles) * size_t(std::max(n_gates, 1)))) != cudaSuccess ||
@@ -2022,6 +2299,27 @@ diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, i
         return st;
     }
     return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_set_runs(diaq_adjoint_plan_t p, int32_t on) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    int dev = -1;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
+    DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    p->runs_on = on != 0;
+    return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_runs(diaq_adjoint_plan_t p, int32_t* on, int32_t* n_runs, int32_t* n_steps) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (on) *on = p->runs_on ? 1 : 0;
+    if (n_runs) *n_runs = int32_t(p->runs.size());
+    if (n_steps) *n_steps = p->runs_on ? int32_t(p->run_order.size()) : p->n_gates;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, int32_t* lanes, int32_t* n_blocks) {

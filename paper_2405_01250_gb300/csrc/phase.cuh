@@ -1,0 +1,182 @@
+// Diagonal runs of the adjoint sweep. Z-type rotations exp(-i a/2 Z_g)
+// (a generator of I and Z letters) and fixed diagonal gates hold their
+// values on the principal diagonal (Section III-A), so a run of them is one
+// diagonal operator, the product of their diagonals (what Algorithm 1's
+// product of such DiaQ matrices gives), applied in one pass:
+//   psi_i <- exp(-i sum_g a_g z_g(i) / 2) d(i) psi_i,
+// z_g(i) = (-1)^popc(i & Z_g), d(i) the fixed gates' product. Every gate of
+// the run commutes with every other and with each generator Z_g, so the
+// gradient term of rotation g at its own position equals the one at the end
+// of the run: Im <lambda|Z_g|psi> = sum_i z_g(i) Im(conj(lambda_i) psi_i),
+// with the same Im(conj(lambda_i) psi_i) for every member.
+//
+// Two forms, chosen on the host:
+//  * weight (PR_WEIGHT): every rotation shares one parameter and scale and
+//    there is no fixed gate (a QAOA cost layer): the phase depends only on
+//    the integer W(i) = sum_g z_g(i) in [-T, T], looked up in a table of
+//    2T + 1 entries; the run's gradient term is sum_i W(i) t_i.
+//  * chunks (PR_CHUNKS): every rotation acts on one qubit, fixed gates are
+//    single-qubit diagonals or CZs (an ansatz layer's RZs and CZ ladder):
+//    the phase is a product of one table entry per 8 qubits of i (the
+//    factors of the qubits in that byte) and the CZ sign; the gradient term
+//    of a rotation on qubit q is sum_i (-1)^(bit q of i) t_i.
+// Tables are built per block in shared memory from theta on the device, so
+// a recorded graph serves every theta.
+#pragma once
+
+#include "common.cuh"
+
+namespace diaq {
+
+constexpr int PR_WEIGHT = 1;
+constexpr int PR_CHUNKS = 2;
+constexpr int PR_MAX_ROT = 48;     // rotations per run (weight form)
+constexpr int PR_MAX_CROT = 24;    // rotations per run (chunk form: one accumulator each)
+constexpr int PR_MAX_CZ = 64;
+constexpr int PR_MAX_FIX1 = 16;
+constexpr int PR_CHUNK_BITS = 8;
+constexpr int PR_MAX_CHUNKS = (DIAQ_MAX_QUBITS + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
+
+struct PhaseRun {
+    int32_t kind;                   // PR_WEIGHT or PR_CHUNKS
+    int32_t n_rot;
+    int32_t rot_param[PR_MAX_ROT];  // parameter index (instance-relative)
+    double rot_scale[PR_MAX_ROT];   // a_g = scale * theta[param]
+    uint64_t rot_z[PR_MAX_ROT];     // Z mask (chunk form: one bit)
+    int32_t rot_slot[PR_MAX_ROT];   // gradient row (weight form: rot_slot[0] for the run)
+    int32_t n_cz;
+    uint64_t cz[PR_MAX_CZ];         // the two bits of each CZ
+    int32_t n_fix1;
+    int32_t fix1_q[PR_MAX_FIX1];    // qubit of a fixed single-qubit diagonal gate
+    double fix1_re[2 * PR_MAX_FIX1], fix1_im[2 * PR_MAX_FIX1];  // its entries for bit 0 and bit 1
+};
+
+// Shared-memory tables of one run and direction: weight form entry W + T;
+// chunk form entry c * 256 + v. E entries: PR_TAB_WEIGHT holds the weight
+// form only, PR_TAB_ALL both forms.
+constexpr int PR_TAB_WEIGHT = 2 * PR_MAX_ROT + 1;
+constexpr int PR_TAB_ALL = PR_MAX_CHUNKS * 256;
+
+template <int E>
+struct PhaseTables {
+    double re[E];
+    double im[E];
+};
+
+// Build the tables (all threads of the block take part; synchronises).
+// rev: the conjugate (U^dag). n: qubits of the state.
+template <int E>
+__device__ __forceinline__ void phase_tables(const PhaseRun& r, const double* theta, bool rev, int n,
+                                             PhaseTables<E>* tb) {
+    const double sg = rev ? 1.0 : -1.0;  // U = exp(-i a/2 ...), U^dag = exp(+i a/2 ...)
+    if (r.kind == PR_WEIGHT) {
+        const int T = r.n_rot;
+        const double a = r.rot_scale[0] * theta[r.rot_param[0]];
+        for (int e = threadIdx.x; e <= 2 * T; e += blockDim.x) {
+            double s, c;
+            sincos(sg * 0.5 * a * double(e - T), &s, &c);
+            tb->re[e] = c;
+            tb->im[e] = s;
+        }
+    } else if (E >= PR_TAB_ALL) {
+        const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
+        for (int e = threadIdx.x; e < chunks * 256; e += blockDim.x) {
+            const int c = e >> 8, v = e & 255;
+            double ang = 0.0;
+            for (int g = 0; g < r.n_rot; ++g) {
+                const int q = __ffsll((long long)r.rot_z[g]) - 1;
+                if ((q >> 3) != c) continue;
+                const double z = ((v >> (q & 7)) & 1) ? -1.0 : 1.0;
+                ang += 0.5 * r.rot_scale[g] * theta[r.rot_param[g]] * z;
+            }
+            double s, co;
+            sincos(sg * ang, &s, &co);
+            double xr = co, xi = s;
+            for (int f = 0; f < r.n_fix1; ++f) {
+                const int q = r.fix1_q[f];
+                if ((q >> 3) != c) continue;
+                const int b = (v >> (q & 7)) & 1;
+                const double dr = r.fix1_re[2 * f + b], di = rev ? -r.fix1_im[2 * f + b] : r.fix1_im[2 * f + b];
+                const double tr = xr * dr - xi * di;
+                xi = xr * di + xi * dr;
+                xr = tr;
+            }
+            tb->re[e] = xr;
+            tb->im[e] = xi;
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
+    amp_t<R> o;
+    o.x = fma(a.x, b.x, -a.y * b.y);
+    o.y = fma(a.x, b.y, a.y * b.x);
+    return o;
+}
+
+// One run over a grid-stride share [tid, N) of the state. Forward
+// (lam == nullptr): psi <- D psi. Reverse: the gradient terms first, then
+// psi <- D^dag psi, lam <- D^dag lam (tables built for the direction).
+// Gradient terms go to acc[]: weight form acc[0] (the run's sum
+// sum_i W(i) t_i); chunk form (CHUNKS only) one per rotation.
+template <typename R, bool CHUNKS, int E>
+__device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
+                                             const PhaseRun& r, const PhaseTables<E>& tb, int64_t tid, int64_t nth,
+                                             double* acc) {
+    using A = amp_t<R>;
+    const int64_t N = int64_t(1) << n;
+    const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
+    Acc<R> a_w;
+    Acc<R> a_c[CHUNKS ? PR_MAX_CROT : 1];
+    for (int64_t i = tid; i < N; i += nth) {
+        A ph;
+        int w = 0;
+        if (!CHUNKS || r.kind == PR_WEIGHT) {
+            for (int g = 0; g < r.n_rot; ++g) w += (__popcll(uint64_t(i) & r.rot_z[g]) & 1) ? -1 : 1;
+            ph.x = R(tb.re[w + r.n_rot]);
+            ph.y = R(tb.im[w + r.n_rot]);
+        } else {
+            R pr = R(tb.re[i & 255]), pi = R(tb.im[i & 255]);
+            for (int c = 1; c < chunks; ++c) {
+                const int e = (c << 8) | int((i >> (8 * c)) & 255);
+                const R qr = R(tb.re[e]), qi = R(tb.im[e]);
+                const R tr = fma(pr, qr, -pi * qi);
+                pi = fma(pr, qi, pi * qr);
+                pr = tr;
+            }
+            int neg = 0;
+            for (int k = 0; k < r.n_cz; ++k) neg ^= __popcll(uint64_t(i) & r.cz[k]) == 2;
+            ph.x = neg ? -pr : pr;
+            ph.y = neg ? -pi : pi;
+        }
+        const A p = psi[i];
+        if (lam) {
+            const A l = lam[i];
+            const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
+            if (!CHUNKS || r.kind == PR_WEIGHT) {
+                if constexpr (sizeof(R) == 8) {
+                    a_w.s = fma(double(w), t, a_w.s);
+                } else {
+                    a_w.add(R(w) * t);
+                }
+            } else {
+#pragma unroll
+                for (int g = 0; g < (CHUNKS ? PR_MAX_CROT : 1); ++g) {
+                    if (g >= r.n_rot) break;
+                    a_c[g].add((uint64_t(i) & r.rot_z[g]) ? -t : t);
+                }
+            }
+            lam[i] = cmul<R>(ph, l);
+        }
+        psi[i] = cmul<R>(ph, p);
+    }
+    if (!CHUNKS || r.kind == PR_WEIGHT) {
+        acc[0] = a_w.value();
+    } else {
+        for (int g = 0; g < r.n_rot && g < (CHUNKS ? PR_MAX_CROT : 1); ++g) acc[g] = a_c[g].value();
+    }
+}
+
+}  // namespace diaq
