@@ -540,12 +540,14 @@ def bench_sample(api, psi, n, j, stream, shots=1024, reps=10):
 # 4 (c - 1) + 2 + r + 8 reverse. The Pauli-sum lambda: 2 per term (the
 # signed weights) and 4 per X-mask group, plus 2 for the energy. The reverse
 # sweep stops at the earliest gate with a gradient term.
-def fp64_per_amp(gates, obs, runs, chunks_run=None):
+def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False):
     """(forward, reverse, lambda) FP64 instructions per amplitude of one
     energy + gradient of `gates`; with runs=True the diagonal runs are
     counted as the library forms them (chunks_run: (rotations, byte tables)
     of each chunk-form run in place of its member gates, or the weight form
-    for runs of one-parameter rotations)."""
+    for runs of one-parameter rotations); with scaled=True rotations take
+    the scaled form (one fused multiply-add per real component: 2 forward,
+    2 + 2 + 2 reverse)."""
     def kind(g):
         if g.param >= 0:
             return "zrot" if set(g.gen) <= {"Z", "I"} else "rot"
@@ -559,9 +561,10 @@ def fp64_per_amp(gates, obs, runs, chunks_run=None):
     for i, k in enumerate(ks):
         if runs and k in ("zrot", "sign"):
             continue  # counted with the runs below
-        fwd += {"rot": 4, "zrot": 4, "fixed": 4, "sign": 0}[k]
+        rot_f, rot_r = (2, 6) if scaled else (4, 10)
+        fwd += {"rot": rot_f, "zrot": rot_f, "fixed": 4, "sign": 0}[k]
         if i >= first:
-            rev += {"rot": 10, "zrot": 10, "fixed": 8, "sign": 0}[k]
+            rev += {"rot": rot_r, "zrot": rot_r, "fixed": 8, "sign": 0}[k]
     if runs:
         for r_rot, c in (chunks_run or []):
             if c == 0:  # weight form
@@ -570,8 +573,20 @@ def fp64_per_amp(gates, obs, runs, chunks_run=None):
             else:
                 fwd += 4 * (c - 1) + 4
                 rev += 4 * (c - 1) + 2 + r_rot + 8
-    groups = len(set(int(x) for x in obs.xmask))
-    lam = 2 * len(obs.coeff) + 4 * groups + 2
+    # lambda = H psi: per group of equal X masks the weight comes from a
+    # table (no FP64 work when the coefficients are equal, else one complex
+    # addition per further chunk of 8 terms), then 2 (real weight) or 4
+    # multiply-adds; plus 2 for the energy
+    grp = {}
+    for x, z, c in zip(obs.xmask, obs.zmask, np.real(np.asarray(obs.coeff))):
+        ny = bin(int(x) & int(z)).count("1") % 4
+        kappa = complex(float(c)) * (1j ** ny)
+        grp.setdefault(int(x), []).append(kappa)
+    lam = 2
+    for ks in grp.values():
+        equal = all(k == ks[0] for k in ks)
+        real = all(k.imag == 0 for k in ks)
+        lam += (2 if real else 4) + (0 if equal else 2 * ((len(ks) + 7) // 8 - 1))
     return fwd, rev, lam
 
 
@@ -633,36 +648,51 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
             "device_ms_by_sweep": {f"w{tw}_l{tl}": m for tw, tl, m in tune["tried"]}}
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
-    # the same plan, gate by gate (diagonal runs off), complex128
-    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=torch.complex128)
-    on, n_runs, steps = plan.runs()
-    plan.set_runs(False)
-    for _ in range(2):
-        plan.run(circ.theta)
-    t0 = time.perf_counter()
-    for _ in range(3 * reps):
-        e, g = plan.run(circ.theta)
-    el_off = (time.perf_counter() - t0) / (3 * reps)
-    plan.close()
+    # the same plan, complex128: gate by gate (diagonal runs off), and with
+    # the rotations unscaled
+    def timed_plan(runs, scaled):
+        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n,
+                               dtype=torch.complex128)
+        plan.set_runs(runs)
+        plan.set_scaled(scaled)
+        info = plan.runs(), plan.scaled()
+        for _ in range(2):
+            plan.run(circ.theta)
+        t0 = time.perf_counter()
+        for _ in range(3 * reps):
+            plan.run(circ.theta)
+        el = (time.perf_counter() - t0) / (3 * reps)
+        plan.close()
+        return el, info
+
+    el_off, _ = timed_plan(False, True)
     out["adjoint_gate_by_gate_graph_c128"] = {"ms_per_gradient": el_off * 1e3, "grads_per_s": 1.0 / el_off}
+    el_us, ((on, n_runs, steps), _) = timed_plan(True, False)
+    out["adjoint_unscaled_graph_c128"] = {"ms_per_gradient": el_us * 1e3, "grads_per_s": 1.0 / el_us}
     # FP64 floor of a complex128 gradient (FP64-bound: the 16 MiB states stay in L2)
     N = 1 << n
     chunks = (n + 7) // 8
-    f0, r0, l0 = fp64_per_amp(circ.gates, obs, runs=False)
-    f1, r1, l1 = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers)
     best = out["adjoint_autotuned_c128"]["ms_per_gradient"]
+    scaled_best = out["adjoint_autotuned_c128"]["window"] == 0
+    f0, r0, l0 = fp64_per_amp(circ.gates, obs, runs=False)
+    fu, ru, lu = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers)
+    f1, r1, l1 = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers, scaled=scaled_best)
     out["roofline_c128"] = {
         "bound": "fp64", "unit": "FP64 instructions", "peak_instr_per_s": FP64_INSTR_PER_S,
         "peak_source": "measured FP64 probe (independent DFMA chains), not MEASURED_PEAKS.json",
-        "diagonal_runs": n_runs, "launches_per_direction": steps,
+        "diagonal_runs": n_runs, "launches_per_direction": steps, "scaled_rotations": scaled_best,
         "fp64_instr_per_gradient": (f1 + r1 + l1) * N, "floor_ms": (f1 + r1 + l1) * N / FP64_INSTR_PER_S * 1e3,
         "achieved_ms": best, "frac": (f1 + r1 + l1) * N / FP64_INSTR_PER_S * 1e3 / best,
+        "unscaled_fp64_instr_per_gradient": (fu + ru + lu) * N,
+        "unscaled_floor_ms": (fu + ru + lu) * N / FP64_INSTR_PER_S * 1e3,
+        "frac_of_unscaled_floor": (fu + ru + lu) * N / FP64_INSTR_PER_S * 1e3 / best,
         "gate_by_gate_fp64_instr_per_gradient": (f0 + r0 + l0) * N,
         "gate_by_gate_floor_ms": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3,
         "frac_of_gate_by_gate_floor": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3 / best,
         "bytes_per_gradient": N * 16 * (2 * steps + 4 * steps + 2),
-        "note": "per amplitude: rotation 4 forward / 10 reverse; chunk-form diagonal run (RZ layer + CZ ladder) "
-                "4 (c - 1) + 4 forward, 4 (c - 1) + 10 + r reverse; lambda 2 per term + 4 per X group"}
+        "note": "per amplitude: rotation 2 forward / 6 reverse scaled (4 / 10 unscaled); chunk-form diagonal run "
+                "(RZ layer + CZ ladder) 4 (c - 1) + 4 forward, 4 (c - 1) + 10 + r reverse; lambda 2 per real term "
+                "group (weights from tables) + 2 for the energy"}
     for name in ("c128", "c64"):
         # what the graph plan and the window-fused sweep add over the
         # one-launch-per-gate adjoint sweep (the same algorithm)
@@ -755,7 +785,19 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
                 "energy_max_abs_err": max(abs(E[i] - refs[i][0]) for i in refs),
                 "grad_max_abs_err": max(float(np.max(np.abs(G[i] - refs[i][1]))) for i in refs)}
         q = b.query()
-        out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3, "diagonal_runs": b.runs()[1],
+        unscaled_ms = None
+        if b.scaled()[1]:  # the same batch with the rotations unscaled
+            b.set_scaled(False)
+            b.run(theta)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                b.run(theta)
+            unscaled_ms = (time.perf_counter() - t0) / reps * 1e3
+            b.set_scaled(True)
+        out[f"batched_{name}"] = {"circuits_per_s": count / el, "ms_per_batch": el * 1e3,
+                                  "scaled": b.scaled()[1], "unscaled_ms_per_batch": unscaled_ms,
+                                  "diagonal_runs": b.runs()[1],
                                   "cluster": q["cluster"], "threads": q["threads"], "window": b.sweep()[0],
                                   "lanes": b.sweep()[1],
                                   "teams": q["teams"],
@@ -779,18 +821,25 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
         # FP64 floor of the complex128 batch (sum over circuits of N x
         # instructions per amplitude, gate by gate and with the cost layers
         # as weight-form diagonal runs)
-        fl0 = fl1 = 0.0
+        scaled_best = out["batched_c128"]["scaled"]
+        fl0 = flu = fl1 = 0.0
         for c, o in inst:
             f0, r0, l0 = fp64_per_amp(c.gates, o, runs=False)
-            f1, r1, l1 = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4)
+            fu, ru, lu = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4)
+            f1, r1, l1 = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4, scaled=scaled_best)
             fl0 += (1 << c.n) * (f0 + r0 + l0)
+            flu += (1 << c.n) * (fu + ru + lu)
             fl1 += (1 << c.n) * (f1 + r1 + l1)
         bt = out["batched_c128"]["ms_per_batch"]
         out["roofline_c128"] = {
             "bound": "fp64", "unit": "FP64 instructions", "peak_instr_per_s": FP64_INSTR_PER_S,
             "peak_source": "measured FP64 probe (independent DFMA chains), not MEASURED_PEAKS.json",
+            "scaled_rotations": scaled_best,
             "fp64_instr_per_batch": fl1, "floor_ms": fl1 / FP64_INSTR_PER_S * 1e3, "achieved_ms": bt,
-            "frac": fl1 / FP64_INSTR_PER_S * 1e3 / bt, "gate_by_gate_fp64_instr_per_batch": fl0,
+            "frac": fl1 / FP64_INSTR_PER_S * 1e3 / bt,
+            "unscaled_fp64_instr_per_batch": flu, "unscaled_floor_ms": flu / FP64_INSTR_PER_S * 1e3,
+            "frac_of_unscaled_floor": flu / FP64_INSTR_PER_S * 1e3 / bt,
+            "gate_by_gate_fp64_instr_per_batch": fl0,
             "gate_by_gate_floor_ms": fl0 / FP64_INSTR_PER_S * 1e3,
             "frac_of_gate_by_gate_floor": fl0 / FP64_INSTR_PER_S * 1e3 / bt}
         out["batched_c128_vs_plain_max_abs_energy_diff"] = float(np.max(np.abs(np.array(e_plain) - energies["c128"])))

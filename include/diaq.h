@@ -487,7 +487,24 @@ diaq_status diaq_adjoint_plan_set_window(diaq_adjoint_plan_t p, int32_t window);
  * sweeps). lanes is ignored for window 0. */
 diaq_status diaq_adjoint_plan_set_sweep(diaq_adjoint_plan_t p, int32_t window, int32_t lanes);
 
+/* Current window and lanes, and the launches per sweep direction: window
+ * blocks, or with window 0 the execution entries (gates, or gates and
+ * diagonal runs when runs are on). */
 diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, int32_t* lanes, int32_t* n_blocks);
+
+/* Scaled rotations of the per-gate complex128 sweep (window 0; on by
+ * default). A rotation U = cos(a/2) I + kappa P is applied as U / sigma,
+ * sigma the larger in magnitude of cos(a/2) and kappa, whose rows need one
+ * fused multiply-add per real component instead of two FP64 instructions
+ * (FP64 is the bound of complex128 sweeps on this GPU); the factor
+ * prod(1 / sigma) that the states then carry is tracked on the device and
+ * divided out of the energy and of every gradient term. Results equal the
+ * unscaled sweep up to rounding. Active only for complex128 plans whose
+ * forward and reverse rotation count is at most 960 (the states grow by at
+ * most sqrt(2) per rotation); on = 0 turns it off. Re-records the graph.
+ * get_scaled: whether it is requested and whether it is active. */
+diaq_status diaq_adjoint_plan_set_scaled(diaq_adjoint_plan_t p, int32_t on);
+diaq_status diaq_adjoint_plan_get_scaled(diaq_adjoint_plan_t p, int32_t* on, int32_t* active);
 
 /* Diagonal runs of the per-gate sweep (window 0; on by default). Runs of
  * Z-type rotations (generators of I and Z letters), fixed single-qubit
@@ -690,6 +707,14 @@ diaq_status diaq_batch_get_sweep(diaq_batch_t b, int32_t* window, int32_t* lanes
  * batch's circuits hold. */
 diaq_status diaq_batch_set_runs(diaq_batch_t b, int32_t on);
 diaq_status diaq_batch_get_runs(diaq_batch_t b, int32_t* on, int32_t* n_runs);
+
+/* Scaled rotations of the per-gate team kernel, as diaq_adjoint_plan_set_scaled
+ * (complex128, window 0, every circuit within 480 parametric gates; on by
+ * default); each team tracks its circuit's factor and rescales the energy
+ * and the gradient terms it writes. Recaptures the graph. get_scaled:
+ * requested and active. */
+diaq_status diaq_batch_set_scaled(diaq_batch_t b, int32_t on);
+diaq_status diaq_batch_get_scaled(diaq_batch_t b, int32_t* on, int32_t* active);
 
 /* Time every team shape that fits - window 0 with cluster in {1,2,4,8} x
  * threads in {64,128,256}, and windows 3, 4, 5 at 1 and 4 lanes with

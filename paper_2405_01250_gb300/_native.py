@@ -185,6 +185,10 @@ SIGNATURES.update({
     "diaq_adjoint_plan_get_window": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_adjoint_plan_set_runs": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_adjoint_plan_get_runs": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "diaq_adjoint_plan_set_scaled": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_get_scaled": (ctypes.c_int, [_vp, _i32p, _i32p]),
+    "diaq_batch_set_scaled": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_batch_get_scaled": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_batch_create": (ctypes.c_int, [ctypes.c_int32, _i32p, _i32p, _gp, _i32p, _i32p, _u64p, _u64p, _dp,
                                          ctypes.c_int, ctypes.POINTER(_vp)]),
     "diaq_batch_destroy": (ctypes.c_int, [_vp]),

@@ -537,6 +537,16 @@ class AdjointPlan:
         """Diagonal runs of the per-gate sweep on or off (diaq_adjoint_plan_set_runs)."""
         check(lib().diaq_adjoint_plan_set_runs(self.handle, int(bool(on))))
 
+    def set_scaled(self, on: bool) -> None:
+        """Scaled rotations of the per-gate complex128 sweep on or off (diaq_adjoint_plan_set_scaled)."""
+        check(lib().diaq_adjoint_plan_set_scaled(self.handle, int(bool(on))))
+
+    def scaled(self) -> tuple:
+        """(requested, active) for the scaled rotations (diaq_adjoint_plan_get_scaled)."""
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_scaled(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return bool(a.value), bool(b.value)
+
     def runs(self) -> tuple:
         """(on, runs in the circuit, launches per sweep direction)."""
         a, b, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
@@ -641,6 +651,16 @@ class Batch:
     def set_runs(self, on: bool):
         """Diagonal runs of the per-gate team kernel on or off (diaq_batch_set_runs)."""
         check(lib().diaq_batch_set_runs(self.handle, int(bool(on))))
+
+    def set_scaled(self, on: bool):
+        """Scaled rotations of the per-gate complex128 team kernel on or off (diaq_batch_set_scaled)."""
+        check(lib().diaq_batch_set_scaled(self.handle, int(bool(on))))
+
+    def scaled(self) -> tuple:
+        """(requested, active) for the scaled rotations (diaq_batch_get_scaled)."""
+        a, b = ctypes.c_int32(0), ctypes.c_int32(0)
+        check(lib().diaq_batch_get_scaled(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return bool(a.value), bool(b.value)
 
     def runs(self) -> tuple:
         """(on, diagonal runs in the batch's circuits)."""

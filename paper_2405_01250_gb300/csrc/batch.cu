@@ -67,9 +67,21 @@ struct BInst {
     int64_t part_off;        // first partial (doubles), rows of C columns
 };
 
+// Rotation applications (forward and reverse) up to which the scaled form
+// (rot_groups_s) needs no renormalisation: the stored states grow by at most
+// sqrt(2) per rotation, so they, and the products of psi and lambda behind
+// the energy and the gradient terms, stay below 2^960 << 2^1023.
+constexpr int DIAQ_SCALED_MAX_ROT = 960;
+
 struct BTerm {
     uint64_t x, z;
     double kr, ki;  // coefficient times i^{#Y}
+    // group header, valid on the first term of each group of equal X masks
+    // (lambda_tables): the group's term count, how its weight is looked up
+    // (0: by the number of terms of odd parity, every coefficient equal;
+    // 1: per chunk of 8 terms by their parity bits, chunk values summed),
+    // its first table entry, and whether every weight is real
+    int32_t gn, gmode, gtab, greal;
 };
 
 struct BatchArgs {
@@ -77,13 +89,16 @@ struct BatchArgs {
     const BGate* gates;
     const int32_t* exec;       // gate index, or -1 - run index
     const PhaseRun* runs;      // diagonal runs (weight form)
+    const double2* ptabs;      // their phase tables: (run, direction) at (2 run + dir) PR_TAB_WEIGHT
     const BTerm* terms;
+    const double2* ltab;       // weight tables of the observables' term groups (lambda_tables)
     const int32_t* sched;      // instance ids, team-major: sched[team_first[c] .. team_first[c+1])
     const int32_t* team_first;
     const double* theta;
     void* arena;
     double* partials;
     int C;                     // blocks per team (cluster size)
+    int scaled;                // rotations in the scaled form (rot_groups_s; complex128)
 };
 
 // ---------------------------------------------------------------------------
@@ -280,32 +295,73 @@ __device__ __forceinline__ void rot_angle(const BGate& g, const double* theta, b
 }
 
 // (H psi)_i for terms sorted by X mask: per group of equal masks the signed
-// weight W = sum_t kappa_t (-1)^{popc((i ^ x) & z_t)} is summed first, then
-// multiplied once by psi[i ^ x]. Arithmetic in the state's precision.
+// weight W = sum_t kappa_t (-1)^{popc((i ^ x) & z_t)} times psi[i ^ x]. W
+// takes no floating-point work: it depends only on the parity bits of the
+// group's terms, and is read from the group's table (lambda_tables) - by
+// the number of odd parities when the coefficients are equal (a sum of ZZ
+// couplings with one weight), else per chunk of 8 terms by their parity
+// bits, the chunks' values summed. A real W (real coefficients, even Y
+// counts) then costs two fused multiply-adds. Arithmetic in the state's
+// precision.
 template <typename R>
-__device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, int t0, int t1,
-                                                      int64_t i) {
+__device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, const double2* tab,
+                                                      int t0, int t1, int64_t i) {
     using A = amp_t<R>;
     R lr = R(0), li = R(0);
     int t = t0;
     while (t < t1) {
-        const uint64_t x = terms[t].x;
-        const uint64_t j = uint64_t(i) ^ x;
-        R wr = R(0), wi = R(0);
-        for (; t < t1 && terms[t].x == x; ++t) {
-            const bool neg = (__popcll(j & terms[t].z) & 1) != 0;
-            const R kr = R(terms[t].kr), ki = R(terms[t].ki);
-            wr += neg ? -kr : kr;
-            wi += neg ? -ki : ki;
+        const BTerm& h = terms[t];
+        const uint64_t j = uint64_t(i) ^ h.x;
+        const int gn = h.gn;
+        R wr, wi;
+        if (h.gmode == 0) {
+            int m = 0;
+            for (int u = t; u < t + gn; ++u) m += __popcll(j & terms[u].z) & 1;
+            const double2 w = tab[h.gtab + m];
+            wr = R(w.x);
+            wi = R(w.y);
+        } else {
+            wr = R(0);
+            wi = R(0);
+            for (int c = 0; 8 * c < gn; ++c) {
+                int bits = 0;
+                const int u1 = min(t + 8 * c + 8, t + gn);
+                for (int u = t + 8 * c; u < u1; ++u) bits |= (__popcll(j & terms[u].z) & 1) << (u - t - 8 * c);
+                const double2 w = tab[h.gtab + 256 * c + bits];
+                if (c == 0) {
+                    wr = R(w.x);
+                    wi = R(w.y);
+                } else {
+                    wr += R(w.x);
+                    wi += R(w.y);
+                }
+            }
         }
         const A pj = psi[j];
-        lr = fma(wr, pj.x, fma(-wi, pj.y, lr));
-        li = fma(wr, pj.y, fma(wi, pj.x, li));
+        if (h.greal) {
+            lr = fma(wr, pj.x, lr);
+            li = fma(wr, pj.y, li);
+        } else {
+            lr = fma(wr, pj.x, fma(-wi, pj.y, lr));
+            li = fma(wr, pj.y, fma(wi, pj.x, li));
+        }
+        t += gn;
     }
     A o;
     o.x = lr;
     o.y = li;
     return o;
+}
+
+// Phase tables of every diagonal run, both directions, once per replay:
+// block (run, direction) writes its table at out + (2 run + dir) stride.
+__global__ void __launch_bounds__(256) k_phase_tables(const PhaseRun* __restrict__ runs, const double* __restrict__ theta,
+                                                      int n, int stride, double2* __restrict__ out) {
+    const PhaseRun& r = runs[blockIdx.x];
+    const bool rev = blockIdx.y != 0;
+    const int E = min(phase_entries(r, n), stride);
+    double2* dst = out + (int64_t(blockIdx.x) * 2 + blockIdx.y) * stride;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) dst[e] = phase_entry(r, theta + r.param_base, rev, e);
 }
 
 template <typename R>
@@ -315,7 +371,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     __shared__ PhaseTables<PR_TAB_WEIGHT> ptab;
     __shared__ double warps[32];
     __shared__ double ang[3];
+    __shared__ double sang[2];  // scaled form: m1, V's coefficient
     const int C = a.C;
+    const bool scaled = sizeof(R) == 8 && a.scaled != 0;
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
     const int team = blockIdx.x / C;
     const int64_t tid = int64_t(rank) * blockDim.x + threadIdx.x;
@@ -328,6 +386,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
         const int64_t N = int64_t(1) << I.n;
         const double* th = a.theta + I.param_begin;
         double* part = a.partials + I.part_off;
+        // scaled form: the stored states are the true ones / inv_s (thread 0
+        // tracks it; the energy and every partial are multiplied by inv_s^2)
+        double inv_s = 1.0;
         // |0...0>
         for (int64_t i = tid; i < N; i += nthreads) {
             A v;
@@ -341,7 +402,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
             const int gi = a.exec[x];
             if (gi < 0) {  // a diagonal run: one pass with its phase table
                 const PhaseRun& run = a.runs[-1 - gi];
-                phase_tables<PR_TAB_WEIGHT>(run, th, false, I.n, &ptab);
+                phase_tables_load<PR_TAB_WEIGHT>(a.ptabs + int64_t(-1 - gi) * 2 * PR_TAB_WEIGHT, 2 * run.n_rot + 1,
+                                                 &ptab);
                 double acc[1];
                 phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
                 team_sync(C);
@@ -349,57 +411,103 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
             }
             const BGate& g = a.gates[gi];
             if (threadIdx.x == 0) {
-                if (g.param >= 0) rot_angle(g, th, false, &ang[0], &ang[1], &ang[2]);
-                else build_step<R>(g, th, false, &mats);
+                if (g.param >= 0) {
+                    rot_angle(g, th, false, &ang[0], &ang[1], &ang[2]);
+                    if (scaled) {
+                        int m1;
+                        double sg;
+                        rot_scaled_coefs(ang[0], ang[1], ang[2], g.rot.ny, &m1, &sang[1], &sg);
+                        sang[0] = m1;
+                        inv_s *= sg;
+                    }
+                } else {
+                    build_step<R>(g, th, false, &mats);
+                }
             }
             __syncthreads();
-            if (g.param >= 0)
-                rot_dispatch<R>(g.k, g.xl, psi, nullptr, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid, nthreads);
-            else
+            if (g.param >= 0) {
+                if constexpr (sizeof(R) == 8) {
+                    if (scaled) {
+                        rot_dispatch_s<R>(g.k, g.xl, psi, nullptr, I.n, g.rot, sang[0] != 0.0, R(sang[1]), tid,
+                                          nthreads);
+                    } else {
+                        rot_dispatch<R>(g.k, g.xl, psi, nullptr, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid,
+                                        nthreads);
+                    }
+                } else {
+                    rot_dispatch<R>(g.k, g.xl, psi, nullptr, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid,
+                                    nthreads);
+                }
+            } else {
                 team_fixed<R>(psi, nullptr, I.n, g, mats, tid, nthreads);
+            }
             team_sync(C);
         }
         // lambda = H psi and the energy Re <psi|lambda>
         Acc<R> e;
         for (int64_t i = tid; i < N; i += nthreads) {
-            const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
+            const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
             lam[i] = o;
             const A pi = psi[i];
             e.add_dot(pi.x, o.x, pi.y, o.y);
         }
         const double es = block_sum(e.value(), warps);
-        if (threadIdx.x == 0) part[0 * C + rank] = es;
+        if (threadIdx.x == 0) part[0 * C + rank] = scaled ? es * (inv_s * inv_s) : es;
         team_sync(C);
         // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
         for (int x = I.exec_end - 1; x >= I.exec_rev_begin; --x) {
             const int gi = a.exec[x];
             if (gi < 0) {  // a diagonal run: its gradient sum, then D^dag on psi and lam
                 const PhaseRun& run = a.runs[-1 - gi];
-                phase_tables<PR_TAB_WEIGHT>(run, th, true, I.n, &ptab);
+                phase_tables_load<PR_TAB_WEIGHT>(a.ptabs + (int64_t(-1 - gi) * 2 + 1) * PR_TAB_WEIGHT,
+                                                 2 * run.n_rot + 1, &ptab);
                 double acc[1];
                 phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, lam, I.n, run, ptab, tid, nthreads, acc);
                 const double sum = block_sum(acc[0], warps);
                 if (threadIdx.x == 0) {
-                    part[int64_t(run.rot_slot[0]) * C + rank] = sum;
+                    part[int64_t(run.rot_slot[0]) * C + rank] = scaled ? sum * (inv_s * inv_s) : sum;
                     for (int g2 = 1; g2 < run.n_rot; ++g2) part[int64_t(run.rot_slot[g2]) * C + rank] = 0.0;
                 }
                 team_sync(C);
                 continue;
             }
             const BGate& g = a.gates[gi];
+            const double pscale = inv_s * inv_s;  // this step's partial is taken before U^dag
             if (threadIdx.x == 0) {
-                if (g.param >= 0) rot_angle(g, th, true, &ang[0], &ang[1], &ang[2]);
-                else build_step<R>(g, th, true, &mats);
+                if (g.param >= 0) {
+                    rot_angle(g, th, true, &ang[0], &ang[1], &ang[2]);
+                    if (scaled) {
+                        int m1;
+                        double sg;
+                        rot_scaled_coefs(ang[0], ang[1], ang[2], g.rot.ny, &m1, &sang[1], &sg);
+                        sang[0] = m1;
+                        inv_s *= sg;
+                    }
+                } else {
+                    build_step<R>(g, th, true, &mats);
+                }
             }
             __syncthreads();
             double v = 0.0;
-            if (g.param >= 0)
-                v = rot_dispatch<R>(g.k, g.xl, psi, lam, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid, nthreads);
-            else
+            if (g.param >= 0) {
+                if constexpr (sizeof(R) == 8) {
+                    if (scaled) {
+                        v = rot_dispatch_s<R>(g.k, g.xl, psi, lam, I.n, g.rot, sang[0] != 0.0, R(sang[1]), tid,
+                                              nthreads);
+                    } else {
+                        v = rot_dispatch<R>(g.k, g.xl, psi, lam, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid,
+                                            nthreads);
+                    }
+                } else {
+                    v = rot_dispatch<R>(g.k, g.xl, psi, lam, I.n, g.rot, R(ang[0]), R(ang[1]), R(ang[2]), tid,
+                                        nthreads);
+                }
+            } else {
                 team_fixed<R>(psi, lam, I.n, g, mats, tid, nthreads);
+            }
             if (g.slot >= 0) {
                 const double sum = block_sum(v, warps);
-                if (threadIdx.x == 0) part[int64_t(g.slot) * C + rank] = sum;
+                if (threadIdx.x == 0) part[int64_t(g.slot) * C + rank] = scaled ? sum * pscale : sum;
             }
             team_sync(C);
         }
@@ -514,7 +622,7 @@ __global__ void __launch_bounds__(WIN_THREADS) k_batch_win(const BatchArgs a, co
         // lambda = H psi and the energy Re <psi|lambda>
         Acc<R> e;
         for (int64_t i = tid; i < N; i += nthreads) {
-            const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
+            const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
             lam[i] = o;
             const A pi = psi[i];
             e.add_dot(pi.x, o.x, pi.y, o.y);
@@ -605,7 +713,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 4) k_batch_win_l(const BatchArgs 
                 // lambda = H psi and the energy Re <psi|lambda>
                 Acc<R> e;
                 for (int64_t i = tid; i < N; i += nthreads) {
-                    const A o = pauli_lambda_elem<R>(psi, a.terms, I.term_begin, I.term_end, i);
+                    const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
                     lam[i] = o;
                     const A pi = psi[i];
                     e.add_dot(pi.x, o.x, pi.y, o.y);
@@ -713,6 +821,8 @@ struct diaq_batch_s {
     BInst* d_inst = nullptr;
     BGate* d_gates = nullptr;
     BTerm* d_terms = nullptr;
+    std::vector<double2> ltab;   // lambda weight tables (lambda_tables)
+    double2* d_ltab = nullptr;
     void* d_arena = nullptr;
     double* d_theta = nullptr;
     double* d_partials = nullptr;
@@ -738,6 +848,11 @@ struct diaq_batch_s {
     std::vector<PhaseRun> runs;
     int32_t* d_exec = nullptr;
     PhaseRun* d_runs = nullptr;
+    double2* d_ptabs = nullptr;  // phase tables of the runs (k_phase_tables)
+    // scaled rotations of the per-gate complex128 kernel: requested (default
+    // on) and possible (every instance within the rotation bound)
+    bool scaled = true;
+    bool scaled_ok = false;
 };
 
 
@@ -845,6 +960,17 @@ static void plan_phase_runs(const BGate* gates, int n_gates, int gate_base, bool
         weight &= nr >= 2;
         if (weight || chunk) {
             r.kind = weight ? PR_WEIGHT : PR_CHUNKS;
+            // CZs inside one chunk of PR_CHUNK_BITS qubits first: their signs
+            // go into that chunk's table, the others are tested per row
+            std::stable_partition(r.cz, r.cz + r.n_cz, [](uint64_t m) {
+                const int lo = __builtin_ctzll(m), hi = 63 - __builtin_clzll(m);
+                return lo / PR_CHUNK_BITS == hi / PR_CHUNK_BITS;
+            });
+            r.n_cz_in = 0;
+            for (int k = 0; k < r.n_cz; ++k) {
+                const int lo = __builtin_ctzll(r.cz[k]), hi = 63 - __builtin_clzll(r.cz[k]);
+                if (lo / PR_CHUNK_BITS == hi / PR_CHUNK_BITS) ++r.n_cz_in;
+            }
             exec->push_back(-1 - int32_t(runs->size()));
             runs->push_back(r);
         } else {
@@ -940,7 +1066,9 @@ static void batch_free(diaq_batch_s* b) {
     if (b->d_wg) cudaFree(b->d_wg);
     if (b->d_exec) cudaFree(b->d_exec);
     if (b->d_runs) cudaFree(b->d_runs);
+    if (b->d_ptabs) cudaFree(b->d_ptabs);
     for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
+                    static_cast<void*>(b->d_ltab),
                     b->d_arena, static_cast<void*>(b->d_theta), static_cast<void*>(b->d_partials),
                     static_cast<void*>(b->d_out), static_cast<void*>(b->d_sched), static_cast<void*>(b->d_team_first)})
         if (p) cudaFree(p);
@@ -957,12 +1085,53 @@ static diaq_status upload(T** d, const std::vector<T>& h) {
     return DIAQ_OK;
 }
 
+// Group headers and weight tables for the terms [t0, t1) of one observable
+// (sorted by X mask; see pauli_lambda_elem), tables appended to *tab.
+static void lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector<double2>* tab) {
+    for (int t = t0; t < t1;) {
+        int u = t;
+        while (u < t1 && terms[size_t(u)].x == terms[size_t(t)].x) ++u;
+        const int gn = u - t;
+        bool equal = true, real = true;
+        for (int v = t; v < u; ++v) {
+            equal &= terms[size_t(v)].kr == terms[size_t(t)].kr && terms[size_t(v)].ki == terms[size_t(t)].ki;
+            real &= terms[size_t(v)].ki == 0.0;
+        }
+        BTerm& h = terms[size_t(t)];
+        h.gn = gn;
+        h.gtab = int32_t(tab->size());
+        h.greal = real ? 1 : 0;
+        if (equal) {  // W = (gn - 2 m) kappa, m terms of odd parity
+            h.gmode = 0;
+            for (int m = 0; m <= gn; ++m) tab->push_back(make_double2(double(gn - 2 * m) * h.kr, double(gn - 2 * m) * h.ki));
+        } else {  // per chunk of 8 terms: the signed sum for each parity pattern
+            h.gmode = 1;
+            for (int c = 0; 8 * c < gn; ++c) {
+                const int len = std::min(8, gn - 8 * c);
+                for (int bits = 0; bits < 256; ++bits) {
+                    double wr = 0.0, wi = 0.0;
+                    if (bits < (1 << len))
+                        for (int e = 0; e < len; ++e) {
+                            const BTerm& q = terms[size_t(t + 8 * c + e)];
+                            const bool neg = (bits >> e) & 1;
+                            wr += neg ? -q.kr : q.kr;
+                            wi += neg ? -q.ki : q.ki;
+                        }
+                    tab->push_back(make_double2(wr, wi));
+                }
+            }
+        }
+        t = u;
+    }
+}
+
 // The per-gate kernel's execution list of every instance (gates, or weight
 // form diagonal runs when runs_on), instance ranges in inst, uploaded with
 // the instance records.
 static diaq_status batch_exec(diaq_batch_s* b) {
     b->exec_list.clear();
     b->runs.clear();
+    int first_run = 0;
     for (BInst& I : b->inst) {
         I.exec_begin = int32_t(b->exec_list.size());
         if (b->runs_on) {
@@ -971,6 +1140,8 @@ static diaq_status batch_exec(diaq_batch_s* b) {
         } else {
             for (int g = I.gate_begin; g < I.gate_end; ++g) b->exec_list.push_back(g);
         }
+        for (size_t r = size_t(first_run); r < b->runs.size(); ++r) b->runs[r].param_base = I.param_begin;
+        first_run = int(b->runs.size());
         I.exec_end = int32_t(b->exec_list.size());
         // nothing below the earliest parametric entry feeds a gradient term
         I.exec_rev_begin = I.exec_end;
@@ -983,14 +1154,24 @@ static diaq_status batch_exec(diaq_batch_s* b) {
         }
     }
     b->n_runs = int(b->runs.size());
-    for (void* q : {static_cast<void*>(b->d_exec), static_cast<void*>(b->d_runs), static_cast<void*>(b->d_inst)})
+    for (void* q : {static_cast<void*>(b->d_exec), static_cast<void*>(b->d_runs), static_cast<void*>(b->d_inst),
+                    static_cast<void*>(b->d_ptabs)})
         if (q) cudaFree(q);
     b->d_exec = nullptr;
     b->d_runs = nullptr;
     b->d_inst = nullptr;
+    b->d_ptabs = nullptr;
     if (b->exec_list.empty()) b->exec_list.push_back(0);
     DIAQ_TRY(upload(&b->d_exec, b->exec_list));
-    if (!b->runs.empty()) DIAQ_TRY(upload(&b->d_runs, b->runs));
+    if (!b->runs.empty()) {
+        DIAQ_TRY(upload(&b->d_runs, b->runs));
+        const size_t bytes = b->runs.size() * 2 * PR_TAB_WEIGHT * sizeof(double2);
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&b->d_ptabs), bytes);
+        if (e != cudaSuccess) {
+            b->d_ptabs = nullptr;
+            return fail(DIAQ_ERR_ALLOC, "cudaMalloc(%zu) for batch phase tables: %s", bytes, cudaGetErrorString(e));
+        }
+    }
     return upload(&b->d_inst, b->inst);
 }
 
@@ -1060,19 +1241,26 @@ static void make_schedule(const diaq_batch_s* b, int teams, std::vector<int32_t>
     first->push_back(int32_t(sched->size()));
 }
 
+static bool batch_scaled_active(const diaq_batch_s* b) {
+    return b->scaled && b->scaled_ok && b->dtype == DIAQ_C128 && b->window == 0;
+}
+
 static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
     BatchArgs a;
     a.inst = b->d_inst;
     a.gates = b->d_gates;
     a.exec = b->d_exec;
     a.runs = b->d_runs;
+    a.ptabs = b->d_ptabs;
     a.terms = b->d_terms;
+    a.ltab = b->d_ltab;
     a.sched = b->d_sched;
     a.team_first = b->d_team_first;
     a.theta = b->d_theta;
     a.arena = b->d_arena;
     a.partials = b->d_partials;
     a.C = b->C;
+    a.scaled = batch_scaled_active(b) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(b->teams * b->C), 1, 1);
     cfg.blockDim = dim3(unsigned(b->threads), 1, 1);
@@ -1100,10 +1288,16 @@ static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
             DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win<double>, a, blk, wg, b->window));
         else
             DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch_win<float>, a, blk, wg, b->window));
-    } else if (b->dtype == DIAQ_C128) {
-        DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<double>, a));
     } else {
-        DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<float>, a));
+        if (b->n_runs > 0) {
+            k_phase_tables<<<dim3(unsigned(b->n_runs), 2), 256, 0, s>>>(b->d_runs, b->d_theta, 0, PR_TAB_WEIGHT,
+                                                                         b->d_ptabs);
+            DIAQ_CUDA(cudaGetLastError());
+        }
+        if (b->dtype == DIAQ_C128)
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<double>, a));
+        else
+            DIAQ_CUDA(cudaLaunchKernelEx(&cfg, k_batch<float>, a));
     }
     const int fb = 128;
     k_batch_finish<<<(b->n_inst + fb - 1) / fb, fb, 0, s>>>(b->d_inst, b->d_gates, b->d_partials, b->C, b->n_inst,
@@ -1305,7 +1499,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
                 st = fail(DIAQ_ERR_ARG, "instance %d term %d acts on a qubit >= %d", i, t, n);
                 break;
             }
-            BTerm T;
+            BTerm T = {};
             T.x = xmask[t];
             T.z = zmask[t];
             const int ny = __builtin_popcountll(xmask[t] & zmask[t]) & 3;
@@ -1324,6 +1518,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
         std::stable_sort(b->terms.begin() + I.term_begin, b->terms.end(),
                          [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
         I.term_end = int32_t(b->terms.size());
+        lambda_tables(b->terms, I.term_begin, I.term_end, &b->ltab);
         I.n_slots = slots;
         I.psi_off = arena;
         arena += ((int64_t(1) << n) + align - 1) / align * align;
@@ -1335,11 +1530,16 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
         b->n_params_total = std::max(b->n_params_total, param_first[i + 1]);
     }
     b->arena_elems = arena;
+    // the scaled form needs every instance's rotation applications (at most
+    // two per parametric gate: forward and reverse) within the bound
+    b->scaled_ok = true;
+    for (const BInst& I : b->inst) b->scaled_ok &= 2 * (I.n_slots - 1) <= DIAQ_SCALED_MAX_ROT;
     // host tables validated; from here on the device is needed
     if (st == DIAQ_OK && (e = cudaGetDevice(&b->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
     if (st == DIAQ_OK) st = batch_exec(b);
     if (st == DIAQ_OK) st = upload(&b->d_gates, b->gates);
     if (st == DIAQ_OK) st = upload(&b->d_terms, b->terms);
+    if (st == DIAQ_OK) st = upload(&b->d_ltab, b->ltab);
     if (st == DIAQ_OK) {
         const size_t bytes = size_t(std::max<int64_t>(arena, 1)) * amp_bytes(dtype);
         if ((e = cudaMalloc(&b->d_arena, bytes)) != cudaSuccess)
@@ -1400,6 +1600,27 @@ diaq_status diaq_batch_set_runs(diaq_batch_t b, int32_t on) {
     b->runs_on = on != 0;
     DIAQ_TRY(batch_exec(b));
     return configure(b, b->C, b->threads, nullptr);
+}
+
+diaq_status diaq_batch_set_scaled(diaq_batch_t b, int32_t on) {
+    clear_error();
+    cudaGetLastError();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    DIAQ_CUDA(cudaDeviceSynchronize());
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->scaled = on != 0;
+    return configure(b, b->C, b->threads, nullptr);
+}
+
+diaq_status diaq_batch_get_scaled(diaq_batch_t b, int32_t* on, int32_t* active) {
+    clear_error();
+    if (!b) return fail(DIAQ_ERR_ARG, "batch is NULL");
+    if (on) *on = b->scaled ? 1 : 0;
+    if (active) *active = batch_scaled_active(b) ? 1 : 0;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_batch_get_runs(diaq_batch_t b, int32_t* on, int32_t* n_runs) {
@@ -1568,6 +1789,10 @@ namespace diaq {
 
 struct RotAngles {
     double cs, kfr, kfi, kar, kai;  // cos(a/2), kappa of U, kappa of U^dag
+    // scaled form (rot_groups_s): U = sigma V per direction
+    int32_t m1;                     // 1: sigma is kappa's non-zero part, 0: sigma = cos(a/2)
+    double cff, cfr;                // V's coefficient, forward and reverse
+    double sgf, sgr;                // sigma, forward and reverse
 };
 
 __global__ void k_plan_angles(const BGate* gates, int n_gates, const double* theta, RotAngles* out) {
@@ -1576,10 +1801,81 @@ __global__ void k_plan_angles(const BGate* gates, int n_gates, const double* the
     RotAngles A;
     rot_angle(gates[g], theta, false, &A.cs, &A.kfr, &A.kfi);
     rot_angle(gates[g], theta, true, &A.cs, &A.kar, &A.kai);
+    int m1r = 0;  // the same form both ways: |cos| and |kappa| do not change
+    rot_scaled_coefs(A.cs, A.kfr, A.kfi, gates[g].rot.ny, &A.m1, &A.cff, &A.sgf);
+    rot_scaled_coefs(A.cs, A.kar, A.kai, gates[g].rot.ny, &m1r, &A.cfr, &A.sgr);
     out[g] = A;
 }
 
-template <typename R, int K, int XL, int KT>
+// Scale bookkeeping of the scaled sweep, one thread, in sweep order. The
+// stored states are the true ones times 1/prod(sigma) of the rotations
+// applied so far (ScaleEvent::FWD / REV multiply inv_s by sigma). Every
+// partial of a reverse step, and the energy after the forward sweep, is
+// taken on states that carry the same factor 1/inv_s in psi and lambda, so
+// scale[slot] = inv_s^2 turns it into the true value.
+struct ScaleEvent {
+    int32_t kind;  // 0 forward rotation (idx: gate), 1 energy, 2 partial slot (idx: slot), 3 reverse rotation
+    int32_t idx;
+};
+
+// One block of 256 threads: thread t takes a contiguous chunk of the
+// events, forms the product of its chunk's factors (all loads in flight at
+// once), an exclusive product scan over the threads gives each chunk its
+// starting inv_s, and each thread then writes its chunk's marks.
+constexpr int kScaleThreads = 256;
+constexpr int kScaleChunk = 8;  // events per thread and pass
+
+__global__ void __launch_bounds__(kScaleThreads) k_plan_scales(const ScaleEvent* __restrict__ ev, int n_ev,
+                                                               const RotAngles* __restrict__ ang, int n_slots,
+                                                               double* scale) {
+    __shared__ double warp_prod[kScaleThreads / 32];
+    __shared__ double carry;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int s = t; s < n_slots; s += kScaleThreads) scale[s] = 1.0;
+    if (t == 0) carry = 1.0;
+    __syncthreads();  // marks below overwrite the defaults
+    for (int base = 0; base < n_ev; base += kScaleThreads * kScaleChunk) {
+        const int e0 = base + t * kScaleChunk;
+        ScaleEvent x[kScaleChunk];
+        double f[kScaleChunk];
+#pragma unroll
+        for (int c = 0; c < kScaleChunk; ++c) {
+            x[c] = e0 + c < n_ev ? ev[e0 + c] : ScaleEvent{-1, -1};  // padding: no factor, no mark
+            f[c] = x[c].kind == 0 ? ang[x[c].idx].sgf : (x[c].kind == 3 ? ang[x[c].idx].sgr : 1.0);
+        }
+        double prod = 1.0;
+#pragma unroll
+        for (int c = 0; c < kScaleChunk; ++c) prod *= f[c];
+        // exclusive scan of the chunk products: within the warp, then over warps
+        double incl = prod;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl *= v;
+        }
+        if (lane == 31) warp_prod[warp] = incl;
+        __syncthreads();
+        double before = carry;
+        for (int w = 0; w < warp; ++w) before *= warp_prod[w];
+        double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = 1.0;
+        double inv_s = before * excl;
+#pragma unroll
+        for (int c = 0; c < kScaleChunk; ++c) {
+            if (x[c].kind == 1) scale[0] = inv_s * inv_s;
+            else if (x[c].kind == 2) scale[x[c].idx] = inv_s * inv_s;
+            inv_s *= f[c];
+        }
+        __syncthreads();
+        if (t == kScaleThreads - 1) carry = inv_s;  // the last thread ends the pass
+        __syncthreads();
+    }
+}
+
+// A Pauli rotation over the whole state, forward (lam == NULL) or reverse
+// with its partial. SC: the scaled form (complex128 plans; the angles carry
+// the form and coefficient of each direction).
+template <typename R, int K, int XL, int KT, int SC>
 __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, const BGate* gate,
                                                   const RotAngles* ang, int n, double* part) {
     __shared__ double warps[32];
@@ -1587,8 +1883,16 @@ __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, 
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
     const RotAngles a = *ang;
     const bool adj = lam != nullptr;  // the reverse sweep applies U^dag
-    const double v = rot_groups<R, K, XL, KT>(psi, lam, n, gate->rot, R(a.cs), R(adj ? a.kar : a.kfr),
-                                          R(adj ? a.kai : a.kfi), tid, nth);
+    double v;
+    if constexpr (SC != 0) {
+        const R cf = R(adj ? a.cfr : a.cff);
+        if (adj) v = rot_groups_sc<R, K, XL, (K == 1 ? 4 : (sizeof(R) == 4 ? 2 : 1)), KT>(psi, lam, n, gate->rot,
+                                                                                     a.m1 != 0, cf, tid, nth);
+        else v = rot_groups_sc<R, K, XL, (K == 1 ? 4 : 2), KT>(psi, nullptr, n, gate->rot, a.m1 != 0, cf, tid, nth);
+    } else {
+        v = rot_groups<R, K, XL, KT>(psi, lam, n, gate->rot, R(a.cs), R(adj ? a.kar : a.kfr), R(adj ? a.kai : a.kfi),
+                                     tid, nth);
+    }
     if (part) {
         const double s = block_sum(v, warps);
         if (threadIdx.x == 0) part[blockIdx.x] = s;
@@ -1597,12 +1901,12 @@ __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, 
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                                     int n_terms, int64_t N, double* part) {
+                                                     const double2* ltab, int n_terms, int64_t N, double* part) {
     using A = amp_t<R>;
     __shared__ double warps[32];
     Acc<R> e;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-        const A o = pauli_lambda_elem<R>(psi, terms, 0, n_terms, i);
+        const A o = pauli_lambda_elem<R>(psi, terms, ltab, 0, n_terms, i);
         lam[i] = o;
         const A pi = psi[i];
         e.add_dot(pi.x, o.x, pi.y, o.y);
@@ -1635,15 +1939,28 @@ __global__ void __launch_bounds__(256) k_plan_rows(const double* __restrict__ pa
     if (threadIdx.x == 0) rows[blockIdx.x] = s;
 }
 
-// out[0] = energy, out[1 + p] = dE/dtheta_p from the row sums, parameter
-// contributions accumulated in gate order.
-__global__ void k_plan_finish(const BGate* gates, int n_gates, const double* rows, int n_params, double* out) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    out[0] = rows[0];
-    for (int p = 0; p < n_params; ++p) out[1 + p] = 0.0;
-    for (int g = 0; g < n_gates; ++g) {
-        const BGate& G = gates[g];
-        if (G.slot >= 0) out[1 + G.param] += G.scale * rows[G.slot];
+// One parametric gate's contribution to its parameter: rows[slot] times the
+// gate's scale (a = scale theta).
+struct FinTerm {
+    int32_t slot;
+    double scale;
+};
+
+// out[0] = energy, out[1 + p] = dE/dtheta_p from the row sums: one thread per
+// parameter sums its gates' contributions (terms[first[p] .. first[p+1]),
+// in gate order); scale (NULL: none) rescales each row of the scaled sweep.
+__global__ void __launch_bounds__(256) k_plan_finish(const FinTerm* __restrict__ terms, const int32_t* __restrict__ first,
+                                                     const double* __restrict__ rows, const double* __restrict__ scale,
+                                                     int n_params, double* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) out[0] = scale ? rows[0] * scale[0] : rows[0];
+    for (int p = t; p < n_params; p += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int e = first[p]; e < first[p + 1]; ++e) {
+            const FinTerm f = terms[e];
+            v += f.scale * (scale ? rows[f.slot] * scale[f.slot] : rows[f.slot]);
+        }
+        out[1 + p] = v;
     }
 }
 
@@ -1651,7 +1968,7 @@ __global__ void k_plan_finish(const BGate* gates, int n_gates, const double* row
 // run's gradient rows (P columns) and D^dag on psi and lambda.
 template <typename R, bool REV>
 __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam, const PhaseRun* __restrict__ run,
-                                                    const double* __restrict__ theta, int n, double* part, int P) {
+                                                    const double2* __restrict__ table, int n, double* part, int P) {
     __shared__ PhaseTables<PR_TAB_ALL> tb;
     __shared__ PhaseRun rs;
     __shared__ double warps[32];
@@ -1661,7 +1978,7 @@ __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam
         for (int i = threadIdx.x; i < int(sizeof(PhaseRun) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
-    phase_tables<PR_TAB_ALL>(rs, theta, REV, n, &tb);
+    phase_tables_load<PR_TAB_ALL>(table, phase_entries(rs, n), &tb);
     double acc[PR_MAX_CROT];
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
@@ -1683,29 +2000,153 @@ __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam
     }
 }
 
-// kappa's form follows from the generator: imaginary for an even Y count
-// (KT = 1), real for an odd one (KT = 2)
-template <typename R, int KT>
-static void launch_plan_rot_kt(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
-                               int n, double* part, int P, cudaStream_t s) {
-    if (g.k == 1) {
-        if (g.xl == 0) k_plan_rot<R, 1, 0, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
-        else k_plan_rot<R, 1, 1, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
-        return;
+// Reverse step of a chunk-form run (an ansatz layer's RZs and CZ ladder)
+// with cheaper gradient terms. The term of a rotation on qubit q is
+// sum_i (-1)^(bit q of i) t_i, t_i = Im(conj(lambda_i) psi_i). In the
+// grid-stride loop i = tid + k nth, and nth = blocks x 256 is a multiple of
+// 2^f (f = trailing zero bits of nth), so bits 0 .. f-1 of i are those of
+// tid: fixed for the thread. The thread therefore sums t_i once (T) and
+// keeps a signed sum per amplitude only for rotations on bits >= f. At the
+// end, the fixed-bit terms come out of T: a Walsh-Hadamard butterfly over
+// the lanes gives sum (-1)^(lane bit q) T for q < 5, the warps' totals
+// signed by their warp bit give q = 5..7, and the block's total signed by
+// its block-index bit gives q = 8 .. f-1. Requires 256 threads per block.
+template <typename R>
+__global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, amp_t<R>* lam,
+                                                               const PhaseRun* __restrict__ run,
+                                                               const double2* __restrict__ table, int n, double* part,
+                                                               int P) {
+    using A = amp_t<R>;
+    __shared__ PhaseTables<PR_TAB_ALL> tb;
+    __shared__ PhaseRun rs;
+    __shared__ double wt[8][6];               // per warp: sum T, then the lane-bit sums S_0 .. S_4
+    __shared__ double wv[8][PR_MAX_CROT];     // per warp: the varying-bit sums
+    __shared__ int vq[PR_MAX_CROT];           // varying-bit rotations: their qubit
+    __shared__ int vg[PR_MAX_CROT];           // ... and their index in the run
+    __shared__ int nv;
+    {
+        const int* src = reinterpret_cast<const int*>(run);
+        int* dst = reinterpret_cast<int*>(&rs);
+        for (int i = threadIdx.x; i < int(sizeof(PhaseRun) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
-    switch (g.xl) {
-        case 0: k_plan_rot<R, 2, 0, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        case 1: k_plan_rot<R, 2, 1, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        case 2: k_plan_rot<R, 2, 2, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
-        default: k_plan_rot<R, 2, 3, KT><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+    const int64_t N = int64_t(1) << n;
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    const int f = __ffsll((long long)nth) - 1;  // bits 0 .. f-1 of i are those of tid
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int c = 0;
+        for (int g = 0; g < rs.n_rot && g < PR_MAX_CROT; ++g) {
+            const int q = __ffsll((long long)rs.rot_z[g]) - 1;
+            if (q >= f) {
+                vq[c] = q;
+                vg[c] = g;
+                ++c;
+            }
+        }
+        nv = c;
+    }
+    phase_tables_load<PR_TAB_ALL>(table, phase_entries(rs, n), &tb);  // synchronises
+    const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
+    const int n_var = nv;
+    Acc<R> tot;
+    Acc<R> av[PR_MAX_CROT];
+    for (int64_t i = tid; i < N; i += nth) {
+        R pr = R(tb.re[i & 255]), pi = R(tb.im[i & 255]);
+        for (int c = 1; c < chunks; ++c) {
+            const int e = (c << 8) | int((i >> (8 * c)) & 255);
+            const R qr = R(tb.re[e]), qi = R(tb.im[e]);
+            const R tr = fma(pr, qr, -pi * qi);
+            pi = fma(pr, qi, pi * qr);
+            pr = tr;
+        }
+        int neg = 0;  // CZs across chunks (the others are in the tables)
+        for (int k = rs.n_cz_in; k < rs.n_cz; ++k) neg ^= __popcll(uint64_t(i) & rs.cz[k]) == 2;
+        A ph;
+        ph.x = neg ? -pr : pr;
+        ph.y = neg ? -pi : pi;
+        const A p = psi[i];
+        const A l = lam[i];
+        const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
+        tot.add(t);
+#pragma unroll
+        for (int j = 0; j < PR_MAX_CROT; ++j) {
+            if (j >= n_var) break;
+            av[j].add(flip_sign(t, ((uint64_t(i) >> vq[j]) & 1) ? 0x80000000u : 0u));
+        }
+        lam[i] = cmul<R>(ph, l);
+        psi[i] = cmul<R>(ph, p);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // lane butterfly: lane m ends with sum_l (-1)^popc(l & m) T_l
+    double w = tot.value();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double v = __shfl_xor_sync(0xffffffffu, w, o);
+        w = (lane & o) ? v - w : w + v;
+    }
+    if (lane == 0) wt[warp][0] = w;
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        if (lane == (1 << q)) wt[warp][1 + q] = w;
+    for (int j = 0; j < n_var; ++j) {
+        double v = av[j].value();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wv[warp][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < rs.n_rot && threadIdx.x < PR_MAX_CROT) {
+        const int g = threadIdx.x;
+        const int q = __ffsll((long long)rs.rot_z[g]) - 1;
+        double v = 0.0;
+        if (q >= f) {
+            int j = 0;
+            while (vg[j] != g) ++j;
+            for (int x = 0; x < 8; ++x) v += wv[x][j];
+        } else if (q < 5) {
+            for (int x = 0; x < 8; ++x) v += wt[x][1 + q];
+        } else if (q < 8) {
+            for (int x = 0; x < 8; ++x) v += ((x >> (q - 5)) & 1) ? -wt[x][0] : wt[x][0];
+        } else {
+            for (int x = 0; x < 8; ++x) v += wt[x][0];
+            if ((blockIdx.x >> (q - 8)) & 1) v = -v;
+        }
+        part[int64_t(rs.rot_slot[g]) * P + blockIdx.x] = v;
     }
 }
 
+// kappa's form follows from the generator: imaginary for an even Y count
+// (KT = 1), real for an odd one (KT = 2)
+template <typename R, int KT, int SC>
+static void launch_plan_rot_kt(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
+                               int n, double* part, int P, cudaStream_t s) {
+    if (g.k == 1) {
+        if (g.xl == 0) k_plan_rot<R, 1, 0, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        else k_plan_rot<R, 1, 1, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part);
+        return;
+    }
+    switch (g.xl) {
+        case 0: k_plan_rot<R, 2, 0, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 1: k_plan_rot<R, 2, 1, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        case 2: k_plan_rot<R, 2, 2, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+        default: k_plan_rot<R, 2, 3, KT, SC><<<P, 256, 0, s>>>(psi, lam, dg, da, n, part); break;
+    }
+}
+
+// scaled: the scaled form (complex128 only)
 template <typename R>
 static void launch_plan_rot(const BGate& g, amp_t<R>* psi, amp_t<R>* lam, const BGate* dg, const RotAngles* da,
-                            int n, double* part, int P, cudaStream_t s) {
-    if (g.rot.ny & 1) launch_plan_rot_kt<R, 2>(g, psi, lam, dg, da, n, part, P, s);
-    else launch_plan_rot_kt<R, 1>(g, psi, lam, dg, da, n, part, P, s);
+                            int n, double* part, int P, bool scaled, cudaStream_t s) {
+    if constexpr (sizeof(R) == 8) {
+        if (scaled) {
+            if (g.rot.ny & 1) launch_plan_rot_kt<R, 2, 1>(g, psi, lam, dg, da, n, part, P, s);
+            else launch_plan_rot_kt<R, 1, 1>(g, psi, lam, dg, da, n, part, P, s);
+            return;
+        }
+    }
+    if (g.rot.ny & 1) launch_plan_rot_kt<R, 2, 0>(g, psi, lam, dg, da, n, part, P, s);
+    else launch_plan_rot_kt<R, 1, 0>(g, psi, lam, dg, da, n, part, P, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1932,6 +2373,7 @@ struct diaq_adjoint_plan_s {
     std::vector<GateDesc> fwd, bwd;  // fixed gates: U and U^dag
     BGate* d_gates = nullptr;
     BTerm* d_terms = nullptr;
+    double2* d_ltab = nullptr;   // lambda weight tables (lambda_tables)
     RotAngles* d_angles = nullptr;
     void* d_psi = nullptr;
     void* d_lam = nullptr;
@@ -1953,21 +2395,110 @@ struct diaq_adjoint_plan_s {
     std::vector<int32_t> run_order;  // gate index, or -1 - run index
     std::vector<PhaseRun> runs;
     PhaseRun* d_runs = nullptr;
+    double2* d_ptabs = nullptr;  // phase tables of the runs: (run, dir) at (2 run + dir) PR_TAB_ALL
+    // scaled rotations of the per-gate complex128 sweep (rot_groups_s):
+    // requested (default on); active when n_events > 0
+    bool scaled = true;
+    FinTerm* d_fin = nullptr;        // gradient terms per parameter, in gate order
+    int32_t* d_fin_first = nullptr;  // n_params + 1 offsets into d_fin
+    ScaleEvent* d_events = nullptr;
+    int n_events = 0;
+    double* d_scale = nullptr;  // n_slots rescale factors
 };
 
+
 static void plan_free(diaq_adjoint_plan_s* p) {
+    if (p->d_ptabs) cudaFree(p->d_ptabs);
+    p->d_ptabs = nullptr;
+    if (p->d_fin) cudaFree(p->d_fin);
+    p->d_fin = nullptr;
+    if (p->d_fin_first) cudaFree(p->d_fin_first);
+    p->d_fin_first = nullptr;
+    if (p->d_events) cudaFree(p->d_events);
+    p->d_events = nullptr;
+    if (p->d_scale) cudaFree(p->d_scale);
+    p->d_scale = nullptr;
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->d_wg) cudaFree(p->d_wg);
     p->d_wg = nullptr;
     if (p->d_runs) cudaFree(p->d_runs);
     p->d_runs = nullptr;
-    for (void* q : {static_cast<void*>(p->d_gates), static_cast<void*>(p->d_terms), static_cast<void*>(p->d_angles),
+    for (void* q : {static_cast<void*>(p->d_gates), static_cast<void*>(p->d_terms), static_cast<void*>(p->d_ltab),
+                    static_cast<void*>(p->d_angles),
                     p->d_psi, p->d_lam, static_cast<void*>(p->d_theta), static_cast<void*>(p->d_part),
                     static_cast<void*>(p->d_rows), static_cast<void*>(p->d_out)})
         if (q) cudaFree(q);
     if (p->h_theta) cudaFreeHost(p->h_theta);
     if (p->h_out) cudaFreeHost(p->h_out);
     if (p->stream) cudaStreamDestroy(p->stream);
+}
+
+// Execution order of the per-gate sweep (gate index, or -1 - run index) and
+// the position of its earliest entry with a gradient term (the reverse
+// sweep stops there).
+static void plan_order(const diaq_adjoint_plan_s* p, std::vector<int32_t>* order, size_t* stop) {
+    order->clear();
+    if (p->runs_on) {
+        *order = p->run_order;
+    } else {
+        for (int g = 0; g < p->n_gates; ++g) order->push_back(g);
+    }
+    *stop = order->size();
+    for (size_t oi = 0; oi < order->size(); ++oi)
+        if ((*order)[oi] < 0 || p->gates[size_t((*order)[oi])].param >= 0) {
+            *stop = oi;
+            break;
+        }
+}
+
+static int plan_rotation_applications(const diaq_adjoint_plan_s* p) {
+    std::vector<int32_t> order;
+    size_t stop = 0;
+    plan_order(p, &order, &stop);
+    int count = 0;
+    for (size_t oi = 0; oi < order.size(); ++oi)
+        if (order[oi] >= 0 && p->gates[size_t(order[oi])].param >= 0) count += oi >= stop ? 2 : 1;
+    return count;
+}
+
+// Scale events of the scaled per-gate sweep, in sweep order (uploaded
+// before the graph is recorded).
+static diaq_status plan_scale_events(diaq_adjoint_plan_s* p) {
+    if (p->d_events) cudaFree(p->d_events);
+    p->d_events = nullptr;
+    p->n_events = 0;
+    if (!p->scaled || p->window > 0 || p->dtype != DIAQ_C128 ||
+        plan_rotation_applications(p) > DIAQ_SCALED_MAX_ROT)
+        return DIAQ_OK;
+    std::vector<int32_t> order;
+    size_t stop = 0;
+    plan_order(p, &order, &stop);
+    std::vector<ScaleEvent> ev;
+    for (int32_t g : order)
+        if (g >= 0 && p->gates[size_t(g)].param >= 0) ev.push_back({0, g});
+    ev.push_back({1, 0});
+    for (size_t oi = order.size(); oi-- > stop;) {
+        const int32_t g = order[oi];
+        if (g < 0) {
+            const PhaseRun& r = p->runs[size_t(-1 - g)];
+            for (int j = 0; j < r.n_rot; ++j) ev.push_back({2, r.rot_slot[j]});
+            continue;
+        }
+        const BGate& G = p->gates[size_t(g)];
+        if (G.param < 0) continue;
+        ev.push_back({2, G.slot});
+        ev.push_back({3, g});
+    }
+    if (!p->d_scale) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p->d_scale), sizeof(double) * size_t(p->n_slots));
+        if (e != cudaSuccess) {
+            p->d_scale = nullptr;
+            return fail(DIAQ_ERR_ALLOC, "adjoint plan scales: %s", cudaGetErrorString(e));
+        }
+    }
+    DIAQ_TRY(upload(&p->d_events, ev));
+    p->n_events = int(ev.size());
+    return DIAQ_OK;
 }
 
 template <typename R>
@@ -1992,47 +2523,51 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
                     psi, l, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
         };
         for (const WinBlock& w : p->blocks) block(w, nullptr);
-        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part);
         for (size_t b = p->blocks.size(); b-- > 0;) block(p->blocks[b], lam);
         DIAQ_CUDA(cudaGetLastError());
     } else {
         std::vector<int32_t> order;
-        if (p->runs_on) {
-            order = p->run_order;
-        } else {
-            for (int g = 0; g < p->n_gates; ++g) order.push_back(g);
-        }
+        size_t stop = 0;
+        plan_order(p, &order, &stop);
+        const bool scaled = p->scaled && p->n_events > 0;
+        if (scaled)
+            k_plan_scales<<<1, kScaleThreads, 0, s>>>(p->d_events, p->n_events, p->d_angles, p->n_slots,
+                                                      p->d_scale);
+        if (p->runs_on && !p->runs.empty())
+            k_phase_tables<<<dim3(unsigned(p->runs.size()), 2), 256, 0, s>>>(p->d_runs, p->d_theta, p->n, PR_TAB_ALL,
+                                                                              p->d_ptabs);
         for (int32_t g : order) {
             if (g < 0) {
-                k_plan_phase<R, false><<<p->P, 256, 0, s>>>(psi, nullptr, p->d_runs + (-1 - g), p->d_theta, p->n,
+                k_plan_phase<R, false><<<p->P, 256, 0, s>>>(psi, nullptr, p->d_runs + (-1 - g),
+                                                            p->d_ptabs + int64_t(-1 - g) * 2 * PR_TAB_ALL, p->n,
                                                             nullptr, p->P);
                 continue;
             }
             const BGate& G = p->gates[size_t(g)];
             if (G.param >= 0)
-                launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, s);
+                launch_plan_rot<R>(G, psi, nullptr, p->d_gates + g, p->d_angles + g, p->n, nullptr, p->P, scaled, s);
             else
                 DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
         }
-        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->n_terms, N, p->d_part);
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part);
         // nothing below the earliest parametric entry feeds a gradient term
-        size_t stop = order.size();
-        for (size_t oi = 0; oi < order.size(); ++oi)
-            if (order[oi] < 0 || p->gates[size_t(order[oi])].param >= 0) {
-                stop = oi;
-                break;
-            }
         for (size_t oi = order.size(); oi-- > stop;) {
             const int32_t g = order[oi];
             if (g < 0) {
-                k_plan_phase<R, true><<<p->P, 256, 0, s>>>(psi, lam, p->d_runs + (-1 - g), p->d_theta, p->n,
-                                                           p->d_part, p->P);
+                const double2* tab = p->d_ptabs + (int64_t(-1 - g) * 2 + 1) * PR_TAB_ALL;
+                if (p->runs[size_t(-1 - g)].kind == PR_CHUNKS)
+                    k_plan_phase_rev_chunks<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_runs + (-1 - g), tab, p->n,
+                                                                     p->d_part, p->P);
+                else
+                    k_plan_phase<R, true><<<p->P, 256, 0, s>>>(psi, lam, p->d_runs + (-1 - g), tab, p->n, p->d_part,
+                                                               p->P);
                 continue;
             }
             const BGate& G = p->gates[size_t(g)];
             if (G.param >= 0) {
                 launch_plan_rot<R>(G, psi, lam, p->d_gates + g, p->d_angles + g, p->n,
-                                   p->d_part + int64_t(G.slot) * p->P, p->P, s);
+                                   p->d_part + int64_t(G.slot) * p->P, p->P, scaled, s);
             } else {
                 DIAQ_TRY(launch_adjoint_step(p->n, p->dtype, p->bwd[size_t(g)], nullptr, psi, lam, nullptr,
                                              adjoint_partials(p->n, p->dtype, G.k), s));
@@ -2040,7 +2575,9 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
         }
     }
     k_plan_rows<<<p->n_slots, 256, 0, s>>>(p->d_part, p->P, p->d_rows);
-    k_plan_finish<<<1, 1, 0, s>>>(p->d_gates, p->n_gates, p->d_rows, p->n_params, p->d_out);
+    k_plan_finish<<<std::max(1, (p->n_params + 255) / 256), 256, 0, s>>>(
+        p->d_fin, p->d_fin_first, p->d_rows, (p->scaled && p->window == 0 && p->n_events > 0) ? p->d_scale : nullptr,
+        p->n_params, p->d_out);
     DIAQ_CUDA(cudaGetLastError());
     DIAQ_CUDA(cudaMemcpyAsync(p->h_out, p->d_out, sizeof(double) * size_t(1 + p->n_params), cudaMemcpyDeviceToHost, s));
     return DIAQ_OK;
@@ -2096,6 +2633,7 @@ static diaq_status plan_capture(diaq_adjoint_plan_s* p) {
         p->exec = nullptr;
     }
     cudaGraph_t graph = nullptr;
+    DIAQ_TRY(plan_scale_events(p));
     DIAQ_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     diaq_status st = p->dtype == DIAQ_C128 ? plan_record<double>(p) : plan_record<float>(p);
     cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
@@ -2183,7 +2721,7 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
             st = fail(DIAQ_ERR_ARG, "Pauli term %d acts on a qubit >= n_qubits", t);
             break;
         }
-        BTerm T;
+        BTerm T = {};
         T.x = xmask[t];
         T.z = zmask[t];
         const int ny = __builtin_popcountll(xmask[t] & zmask[t]) & 3;
@@ -2199,6 +2737,8 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
     }
     std::stable_sort(terms.begin(), terms.end(), [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
     p->n_terms = n_terms;
+    std::vector<double2> ltab;
+    if (st == DIAQ_OK) lambda_tables(terms, 0, int(terms.size()), &ltab);
     cudaError_t e = cudaSuccess;
     if (st == DIAQ_OK && (e = cudaGetDevice(&p->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
     if (st == DIAQ_OK) {
@@ -2213,10 +2753,32 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
     const size_t ab = amp_bytes(dtype), N = size_t(1) << n_qubits;
     if (st == DIAQ_OK) st = upload(&p->d_gates, p->gates);
     if (st == DIAQ_OK) {
+        // gradient terms grouped by parameter, each group in gate order
+        std::vector<int32_t> first(size_t(n_params) + 1, 0);
+        for (const BGate& G : p->gates)
+            if (G.slot >= 0) ++first[size_t(G.param) + 1];
+        for (int q = 0; q < n_params; ++q) first[size_t(q) + 1] += first[size_t(q)];
+        const size_t n_fin = size_t(first[size_t(n_params)]);
+        std::vector<FinTerm> fin(n_fin);
+        std::vector<int32_t> fill(first.begin(), first.end() - 1);
+        for (const BGate& G : p->gates)
+            if (G.slot >= 0) fin[size_t(fill[size_t(G.param)]++)] = {G.slot, G.scale};
+        st = upload(&p->d_fin_first, first);
+        if (st == DIAQ_OK && !fin.empty()) st = upload(&p->d_fin, fin);
+    }
+    if (st == DIAQ_OK) {
         plan_phase_runs(p->gates.data(), n_gates, 0, true, &p->run_order, &p->runs);
         if (!p->runs.empty()) st = upload(&p->d_runs, p->runs);
+        if (st == DIAQ_OK && !p->runs.empty()) {
+            const size_t bytes = p->runs.size() * 2 * PR_TAB_ALL * sizeof(double2);
+            if ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_ptabs), bytes)) != cudaSuccess) {
+                p->d_ptabs = nullptr;
+                st = fail(DIAQ_ERR_ALLOC, "adjoint plan phase tables: %s", cudaGetErrorString(e));
+            }
+        }
     }
     if (st == DIAQ_OK) st = upload(&p->d_terms, terms);
+    if (st == DIAQ_OK) st = upload(&p->d_ltab, ltab);
     if (st == DIAQ_OK &&
         ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_angles), sizeof(RotAngles) * size_t(std::max(n_gates, 1)))) != cudaSuccess ||
          (e = cudaMalloc(&p->d_psi, N * ab)) != cudaSuccess || (e = cudaMalloc(&p->d_lam, N * ab)) != cudaSuccess ||
@@ -2327,7 +2889,29 @@ diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, 
     if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
     if (window) *window = p->window;
     if (lanes) *lanes = p->lanes;
-    if (n_blocks) *n_blocks = p->window > 0 ? int32_t(p->blocks.size()) : p->n_gates;
+    if (n_blocks)
+        *n_blocks = p->window > 0 ? int32_t(p->blocks.size())
+                                  : (p->runs_on ? int32_t(p->run_order.size()) : p->n_gates);
+    return DIAQ_OK;
+}
+
+diaq_status diaq_adjoint_plan_set_scaled(diaq_adjoint_plan_t p, int32_t on) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    int dev = -1;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
+    DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    p->scaled = on != 0;
+    return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_scaled(diaq_adjoint_plan_t p, int32_t* on, int32_t* active) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (on) *on = p->scaled ? 1 : 0;
+    if (active) *active = p->n_events > 0 ? 1 : 0;
     return DIAQ_OK;
 }
 

@@ -46,6 +46,17 @@ template <typename R, bool INPLACE>
 __global__ void __launch_bounds__(256) k_apply_diag(const amp_t<R>* x, amp_t<R>* y,
                                                     const __grid_constant__ DiagArgs<R> a) {
     using A = amp_t<R>;
+    // The entries go to shared memory first: the lanes of a warp index them
+    // by their own row class, and indexed reads of kernel parameters with
+    // different addresses across a warp are served one address at a time.
+    __shared__ A tab[1 << DIAQ_MAX_K];
+    for (int c = threadIdx.x; c < (1 << a.k); c += blockDim.x) {
+        A e;
+        e.x = a.re[c];
+        e.y = a.im[c];
+        tab[c] = e;
+    }
+    __syncthreads();
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < a.N; i0 += T * kDiagUnroll) {
         int c[kDiagUnroll];
@@ -70,7 +81,8 @@ __global__ void __launch_bounds__(256) k_apply_diag(const amp_t<R>* x, amp_t<R>*
                 st_stream(y + i, v[u]);
                 continue;
             }
-            const R mr = a.re[c[u]], mi = a.im[c[u]];
+            const A m = tab[c[u]];
+            const R mr = m.x, mi = m.y;
             A o;
             o.x = mr * v[u].x;
             o.x = fma(-mi, v[u].y, o.x);

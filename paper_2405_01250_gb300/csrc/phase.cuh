@@ -25,6 +25,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "rot.cuh"
 
 namespace diaq {
 
@@ -45,6 +46,8 @@ struct PhaseRun {
     uint64_t rot_z[PR_MAX_ROT];     // Z mask (chunk form: one bit)
     int32_t rot_slot[PR_MAX_ROT];   // gradient row (weight form: rot_slot[0] for the run)
     int32_t n_cz;
+    int32_t n_cz_in;                // chunk form: cz[0 .. n_cz_in) lie inside one chunk (folded into its table)
+    int32_t param_base;             // first parameter of the run's circuit in the theta array
     uint64_t cz[PR_MAX_CZ];         // the two bits of each CZ
     int32_t n_fix1;
     int32_t fix1_q[PR_MAX_FIX1];    // qubit of a fixed single-qubit diagonal gate
@@ -63,47 +66,57 @@ struct PhaseTables {
     double im[E];
 };
 
-// Build the tables (all threads of the block take part; synchronises).
-// rev: the conjugate (U^dag). n: qubits of the state.
-template <int E>
-__device__ __forceinline__ void phase_tables(const PhaseRun& r, const double* theta, bool rev, int n,
-                                             PhaseTables<E>* tb) {
+// Entry e of a run's table for one direction (rev: U^dag), from the
+// parameters theta (the run's circuit's first parameter at theta[0]):
+// weight form W + T = e; chunk form e = c * 256 + v, the product of the
+// factors of the qubits in chunk c for the byte value v, times the signs
+// of the CZs inside that chunk (cz[0 .. n_cz_in)).
+__device__ __forceinline__ double2 phase_entry(const PhaseRun& r, const double* theta, bool rev, int e) {
     const double sg = rev ? 1.0 : -1.0;  // U = exp(-i a/2 ...), U^dag = exp(+i a/2 ...)
+    double s, c;
     if (r.kind == PR_WEIGHT) {
-        const int T = r.n_rot;
         const double a = r.rot_scale[0] * theta[r.rot_param[0]];
-        for (int e = threadIdx.x; e <= 2 * T; e += blockDim.x) {
-            double s, c;
-            sincos(sg * 0.5 * a * double(e - T), &s, &c);
-            tb->re[e] = c;
-            tb->im[e] = s;
-        }
-    } else if (E >= PR_TAB_ALL) {
-        const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
-        for (int e = threadIdx.x; e < chunks * 256; e += blockDim.x) {
-            const int c = e >> 8, v = e & 255;
-            double ang = 0.0;
-            for (int g = 0; g < r.n_rot; ++g) {
-                const int q = __ffsll((long long)r.rot_z[g]) - 1;
-                if ((q >> 3) != c) continue;
-                const double z = ((v >> (q & 7)) & 1) ? -1.0 : 1.0;
-                ang += 0.5 * r.rot_scale[g] * theta[r.rot_param[g]] * z;
-            }
-            double s, co;
-            sincos(sg * ang, &s, &co);
-            double xr = co, xi = s;
-            for (int f = 0; f < r.n_fix1; ++f) {
-                const int q = r.fix1_q[f];
-                if ((q >> 3) != c) continue;
-                const int b = (v >> (q & 7)) & 1;
-                const double dr = r.fix1_re[2 * f + b], di = rev ? -r.fix1_im[2 * f + b] : r.fix1_im[2 * f + b];
-                const double tr = xr * dr - xi * di;
-                xi = xr * di + xi * dr;
-                xr = tr;
-            }
-            tb->re[e] = xr;
-            tb->im[e] = xi;
-        }
+        sincos(sg * 0.5 * a * double(e - r.n_rot), &s, &c);
+        return make_double2(c, s);
+    }
+    const int ch = e >> 8, v = e & 255;
+    double ang = 0.0;
+    for (int g = 0; g < r.n_rot; ++g) {
+        const int q = __ffsll((long long)r.rot_z[g]) - 1;
+        if ((q >> 3) != ch) continue;
+        const double z = ((v >> (q & 7)) & 1) ? -1.0 : 1.0;
+        ang += 0.5 * r.rot_scale[g] * theta[r.rot_param[g]] * z;
+    }
+    sincos(sg * ang, &s, &c);
+    double xr = c, xi = s;
+    for (int f = 0; f < r.n_fix1; ++f) {
+        const int q = r.fix1_q[f];
+        if ((q >> 3) != ch) continue;
+        const int b = (v >> (q & 7)) & 1;
+        const double dr = r.fix1_re[2 * f + b], di = rev ? -r.fix1_im[2 * f + b] : r.fix1_im[2 * f + b];
+        const double tr = xr * dr - xi * di;
+        xi = xr * di + xi * dr;
+        xr = tr;
+    }
+    int neg = 0;
+    const uint64_t full = uint64_t(v) << (8 * ch);
+    for (int k = 0; k < r.n_cz_in; ++k) neg ^= __popcll(full & r.cz[k]) == 2;
+    return neg ? make_double2(-xr, -xi) : make_double2(xr, xi);
+}
+
+// Entries of a run's table: weight form 2T + 1, chunk form chunks x 256.
+__host__ __device__ __forceinline__ int phase_entries(const PhaseRun& r, int n) {
+    return r.kind == PR_WEIGHT ? 2 * r.n_rot + 1 : ((n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS) * 256;
+}
+
+// Copy a run's table, built once per replay in global memory, into the
+// block's shared tables (all threads take part; synchronises).
+template <int E>
+__device__ __forceinline__ void phase_tables_load(const double2* __restrict__ src, int entries, PhaseTables<E>* tb) {
+    for (int e = threadIdx.x; e < entries && e < E; e += blockDim.x) {
+        const double2 v = src[e];
+        tb->re[e] = v.x;
+        tb->im[e] = v.y;
     }
     __syncthreads();
 }
@@ -146,8 +159,8 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
                 pi = fma(pr, qi, pi * qr);
                 pr = tr;
             }
-            int neg = 0;
-            for (int k = 0; k < r.n_cz; ++k) neg ^= __popcll(uint64_t(i) & r.cz[k]) == 2;
+            int neg = 0;  // CZs across chunks (the others are in the tables)
+            for (int k = r.n_cz_in; k < r.n_cz; ++k) neg ^= __popcll(uint64_t(i) & r.cz[k]) == 2;
             ph.x = neg ? -pr : pr;
             ph.y = neg ? -pi : pi;
         }
@@ -165,7 +178,7 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
 #pragma unroll
                 for (int g = 0; g < (CHUNKS ? PR_MAX_CROT : 1); ++g) {
                     if (g >= r.n_rot) break;
-                    a_c[g].add((uint64_t(i) & r.rot_z[g]) ? -t : t);
+                    a_c[g].add(flip_sign(t, (uint64_t(i) & r.rot_z[g]) ? 0x80000000u : 0u));
                 }
             }
             lam[i] = cmul<R>(ph, l);

@@ -118,16 +118,24 @@ __device__ __forceinline__ double prefix16(double* v, double acc) {
     return acc;
 }
 
+// Half a run per staging pass.
+constexpr int kHalf = kRun / 2;
+
 template <typename R>
 constexpr int tile_smem_bytes() {
-    return 8 * kWarpRuns * (kRun + 1) * int(sizeof(amp_t<R>));
+    return 8 * kWarpRuns * (kHalf + 1) * int(sizeof(amp_t<R>));
 }
 
 // ---------------------------------------------------------------------------
-// Tile pass: one block of 256 threads per 4096 amplitudes. Each warp stages
-// its 512 amplitudes in shared memory with coalesced loads (one padding
-// amplitude per run keeps the per-lane reads free of bank conflicts); thread
-// t then sums run t. Threads 0..15 form the run prefixes of seg t, thread 0
+// Tile pass: one block of 256 threads per 4096 amplitudes; warp w owns runs
+// 32 w .. 32 w + 31, lane l run 32 w + l. In two passes the warp stages the
+// first and then the second half of each of its runs in shared memory (load
+// j covers 4 runs, 8 consecutive amplitudes of each: four whole 128-byte
+// segments; one padding amplitude per run keeps the per-lane reads free of
+// bank conflicts), and each lane continues its run's sum over the 8 staged
+// amplitudes, so the sum is sequential in index order as before. Staging
+// half runs halves the shared memory per block, so twice as many blocks
+// fit on an SM. Threads 0..15 then form the run prefixes of seg t, thread 0
 // the seg prefixes of the tile.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -136,27 +144,29 @@ __global__ void __launch_bounds__(256) k_sample_tiles(const amp_t<R>* __restrict
                                                       double* __restrict__ tile_tot) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using A = amp_t<R>;
-    A(*stage)[kWarpRuns][kRun + 1] = reinterpret_cast<A(*)[kWarpRuns][kRun + 1]>(smem_raw);
+    A(*stage)[kWarpRuns][kHalf + 1] = reinterpret_cast<A(*)[kWarpRuns][kHalf + 1]>(smem_raw);
     __shared__ double rp[kTileRuns];
     __shared__ double sp[kTileSegs];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)warp * (kWarpRuns * kRun);
-    // all 16 loads in flight before the first shared-memory store
-    A v[kRun];
-#pragma unroll
-    for (int j = 0; j < kRun; ++j) {
-        const int64_t i = base + 32 * j + lane;
-        v[j] = i < N && DIAQ_BOUNDS_OK(i, N, BS_SAMPLE_TILES) ? ld_stream(psi + i) : zero_amp<R>();
-    }
-#pragma unroll
-    for (int j = 0; j < kRun; ++j) {
-        const int g = 32 * j + lane;
-        stage[warp][g / kRun][g % kRun] = v[j];
-    }
-    __syncwarp();
     RunSum<R> rs;
 #pragma unroll
-    for (int e = 0; e < kRun; ++e) rs.add(stage[warp][lane][e]);
+    for (int half = 0; half < 2; ++half) {
+        // load j: runs 4 j + lane / 8, amplitude half * 8 + lane % 8 of each;
+        // all 8 loads in flight before the first shared-memory store
+        A v[kHalf];
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) {
+            const int64_t i = base + int64_t(kRun) * (4 * j + lane / kHalf) + half * kHalf + lane % kHalf;
+            v[j] = i < N && DIAQ_BOUNDS_OK(i, N, BS_SAMPLE_TILES) ? ld_stream(psi + i) : zero_amp<R>();
+        }
+        if (half) __syncwarp();  // every lane has read the first half
+#pragma unroll
+        for (int j = 0; j < kHalf; ++j) stage[warp][4 * j + lane / kHalf][lane % kHalf] = v[j];
+        __syncwarp();
+#pragma unroll
+        for (int e = 0; e < kHalf; ++e) rs.add(stage[warp][lane][e]);
+    }
     rp[threadIdx.x] = rs.value();
     __syncthreads();
     static_assert(kSegRuns == 16 && kTileSegs == 16, "prefix16 walks groups of 16");

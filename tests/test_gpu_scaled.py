@@ -1,0 +1,149 @@
+"""Scaled rotations of the complex128 adjoint sweep (rot.cuh rot_groups_s):
+each Pauli rotation is applied divided by the larger of |cos(a/2)| and
+|sin(a/2)|, one fused multiply-add per real component, and the factor the
+states then carry is divided out of the energy and of each gradient term.
+Checked against the unscaled sweep and the FP64 oracle's parameter-shift
+gradient for the adjoint plan and the batch: one- and two-qubit generators
+with even and odd Y counts, angles on both sides of |cos| = |sin| and at
+the special angles, runs on and off, and a circuit past the rotation bound
+(where the unscaled form runs)."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GENS1 = ["X", "Y", "Z"]
+GENS2 = ["XX", "XY", "YX", "YY", "ZX", "XZ", "YZ", "ZY", "ZZ", "IX", "YI"]
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2405_01250_gb300 import build as B
+    B.build()
+    from paper_2405_01250_gb300 import api as A
+    return A
+
+
+def _pauli_circuit(n, rng, count, theta=None):
+    """Random Pauli rotations on one and two (possibly reversed,
+    non-adjacent) qubits, with fixed H and CZ gates between them."""
+    g = [synth.Gate((q,), synth.H) for q in range(n)]
+    p = 0
+    for i in range(count):
+        if i % 5 == 4:
+            a, b = rng.choice(n, size=2, replace=False)
+            g.append(synth.Gate((int(a), int(b)), synth.CZ))
+            continue
+        if rng.random() < 0.5:
+            g.append(synth.Gate((int(rng.integers(n)),), None, param=p, gen=GENS1[int(rng.integers(3))],
+                                scale=float(rng.choice([1.0, -0.5, 2.0]))))
+        else:
+            a, b = rng.choice(n, size=2, replace=False)
+            g.append(synth.Gate((int(a), int(b)), None, param=p, gen=GENS2[int(rng.integers(len(GENS2)))]))
+        p += 1
+    th = rng.uniform(0, 2 * math.pi, size=p) if theta is None else theta(p)
+    return synth.Circuit(n, g, theta=th)
+
+
+def _plan(api, circ, obs, n, dtype, scaled, runs=True):
+    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+    plan.set_runs(runs)
+    plan.set_scaled(scaled)
+    state = plan.scaled()
+    e, g = plan.run(circ.theta)
+    plan.close()
+    return e, g, state
+
+
+def _check_vs_oracle(circ, obs, n, e, g):
+    psi0 = synth.basis_state(n, 0)
+    assert abs(e - oracle.energy(circ, obs, psi0)) < 1e-11
+    assert np.max(np.abs(g - oracle.param_shift_grad(circ, obs, psi0))) < 1e-10
+
+
+@pytest.mark.parametrize("which", ["pauli", "ansatz", "qaoa"])
+@pytest.mark.parametrize("runs", [True, False])
+def test_plan_scaled_matches_unscaled_and_oracle(api, which, runs):
+    rng = np.random.default_rng(21)
+    if which == "pauli":
+        n = 9
+        circ = _pauli_circuit(n, rng, 60)
+        obs = synth.ansatz_observable(n)
+    elif which == "ansatz":
+        n = 10
+        circ = synth.ansatz(n=n, layers=3, seed=5)
+        obs = synth.ansatz_observable(n)
+    else:
+        n = 10
+        circ, obs = synth.qaoa_instance(n, rng, p=3)
+    e1, g1, st1 = _plan(api, circ, obs, n, torch.complex128, True, runs)
+    e0, g0, st0 = _plan(api, circ, obs, n, torch.complex128, False, runs)
+    assert st1 == (True, True) and st0 == (False, False)
+    assert abs(e1 - e0) < 1e-12 and np.max(np.abs(g1 - g0)) < 1e-12
+    _check_vs_oracle(circ, obs, n, e1, g1)
+
+
+def test_plan_scaled_special_angles(api):
+    """Angles where cos(a/2) or sin(a/2) is 0, where |cos| = |sin|, and just
+    either side of it: both forms of the scaled rotation and their switch."""
+    rng = np.random.default_rng(8)
+    n = 8
+    q = math.pi / 2
+    special = np.array([0.0, math.pi, 2 * math.pi, q, 3 * q, -q, q + 1e-9, q - 1e-9, math.pi - 1e-12, 1e-12])
+    circ = _pauli_circuit(n, rng, 50, theta=lambda p: np.resize(special, p))
+    obs = synth.ansatz_observable(n)
+    e1, g1, st = _plan(api, circ, obs, n, torch.complex128, True)
+    e0, g0, _ = _plan(api, circ, obs, n, torch.complex128, False)
+    assert st == (True, True)
+    assert abs(e1 - e0) < 1e-12 and np.max(np.abs(g1 - g0)) < 1e-12
+    _check_vs_oracle(circ, obs, n, e1, g1)
+
+
+def test_plan_scaled_not_used_for_complex64_or_past_the_bound(api):
+    rng = np.random.default_rng(2)
+    n = 6
+    circ = synth.ansatz(n=n, layers=2, seed=3)
+    obs = synth.ansatz_observable(n)
+    _, _, st = _plan(api, circ, obs, n, torch.complex64, True)
+    assert st == (True, False)
+    # 500 non-diagonal rotations: 1000 forward and reverse applications > 960
+    g = [synth.Gate((q,), synth.H) for q in range(4)]
+    g += [synth.Gate((i % 4,), None, param=i, gen="XY"[i % 2]) for i in range(500)]
+    big = synth.Circuit(4, g, theta=rng.uniform(0, 2 * math.pi, size=500))
+    obs4 = synth.ansatz_observable(4)
+    e, gr, st = _plan(api, big, obs4, 4, torch.complex128, True)
+    assert st == (True, False)
+    _check_vs_oracle(big, obs4, 4, e, gr)
+
+
+def test_batch_scaled_matches_unscaled_and_oracle(api):
+    inst = synth.qaoa_batch(10, seed=6, sizes=(8, 10, 12))
+    desc = [(c.n, c.gates, c.n_params, (o.xmask, o.zmask, o.coeff)) for c, o in inst]
+    theta = np.concatenate([c.theta for c, _ in inst])
+    res = {}
+    for on in (True, False):
+        b = api.Batch(desc, dtype=torch.complex128)
+        b.set_scaled(on)
+        b.set_launch(2, 128)
+        assert b.scaled() == (on, on)
+        res[on] = b.run(theta)
+        b.close()
+    (E1, G1), (E0, G0) = res[True], res[False]
+    assert np.max(np.abs(E1 - E0)) < 1e-12
+    assert max(float(np.max(np.abs(a - b))) for a, b in zip(G1, G0)) < 1e-12
+    for i in (0, 3, 7):
+        c, o = inst[i]
+        p0 = synth.basis_state(c.n, 0)
+        assert abs(E1[i] - oracle.energy(c, o, p0)) < 1e-11
+        assert np.max(np.abs(G1[i] - oracle.param_shift_grad(c, o, p0))) < 1e-10
+    # complex64 batches keep the unscaled form
+    b = api.Batch(desc, dtype=torch.complex64)
+    assert b.scaled() == (True, False)
+    b.close()
