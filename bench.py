@@ -650,11 +650,12 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
     # the same plan, complex128: gate by gate (diagonal runs off), and with
     # the rotations unscaled
-    def timed_plan(runs, scaled):
+    def timed_plan(runs, scaled, pairs=True):
         plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n,
                                dtype=torch.complex128)
         plan.set_runs(runs)
         plan.set_scaled(scaled)
+        plan.set_pairs(pairs)
         info = plan.runs(), plan.scaled()
         for _ in range(2):
             plan.run(circ.theta)
@@ -669,6 +670,9 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     out["adjoint_gate_by_gate_graph_c128"] = {"ms_per_gradient": el_off * 1e3, "grads_per_s": 1.0 / el_off}
     el_us, ((on, n_runs, steps), _) = timed_plan(True, False)
     out["adjoint_unscaled_graph_c128"] = {"ms_per_gradient": el_us * 1e3, "grads_per_s": 1.0 / el_us}
+    el_np, _ = timed_plan(True, True, pairs=False)
+    out["adjoint_unpaired_graph_c128"] = {"ms_per_gradient": el_np * 1e3, "grads_per_s": 1.0 / el_np,
+                                          "note": "one launch per rotation (fused rotation pairs off)"}
     # FP64 floor of a complex128 gradient (FP64-bound: the 16 MiB states stay in L2)
     N = 1 << n
     chunks = (n + 7) // 8
@@ -1180,6 +1184,12 @@ def main():
     ap.add_argument("--tfim-qubits", type=int, default=28)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-only", action="store_true", help="profiling entry: one batch run, fixed shape")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="profiling entry: replays of the ansatz-20 adjoint plan at a fixed sweep")
+    ap.add_argument("--adjoint-dtype", default="c128", choices=["c64", "c128"])
+    ap.add_argument("--adjoint-window", type=int, default=0)
+    ap.add_argument("--adjoint-lanes", type=int, default=1)
+    ap.add_argument("--adjoint-reps", type=int, default=3)
     ap.add_argument("--batch-cluster", type=int, default=8)
     ap.add_argument("--batch-threads", type=int, default=256)
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
@@ -1215,6 +1225,31 @@ def main():
                                      shape=(args.batch_cluster, args.batch_threads, args.batch_window,
                                             args.batch_lanes),
                                      dtypes=(args.batch_dtype,))), flush=True)
+        return
+    if args.adjoint_only:
+        # profiling entry: the plan at a fixed sweep, 2 warm-up replays and
+        # adjoint_reps timed ones (host clock), no autotuning
+        import torch
+        import synth
+        from paper_2405_01250_gb300 import build as B
+        B.build()
+        from paper_2405_01250_gb300 import api
+        circ = synth.ansatz(n=20, layers=8, seed=0)
+        obs = synth.ansatz_observable(20)
+        dt = torch.complex128 if args.adjoint_dtype == "c128" else torch.complex64
+        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), 20, dtype=dt)
+        plan.set_sweep(args.adjoint_window, args.adjoint_lanes)
+        for _ in range(2):
+            plan.run(circ.theta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.adjoint_reps):
+            e, _ = plan.run(circ.theta)
+        el = (time.perf_counter() - t0) / max(1, args.adjoint_reps)
+        print(json.dumps({"workload": "ansatz-20 adjoint plan", "dtype": args.adjoint_dtype, "sweep": plan.sweep(),
+                          "runs": plan.runs(), "scaled": plan.scaled(), "pairs": plan.pairs(),
+                          "ms_per_gradient": el * 1e3, "energy": e}), flush=True)
+        plan.close()
         return
     rank, world = _dist()
     out = run_ours(args, rank, world)

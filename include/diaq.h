@@ -506,6 +506,15 @@ diaq_status diaq_adjoint_plan_get_sweep(diaq_adjoint_plan_t p, int32_t* window, 
 diaq_status diaq_adjoint_plan_set_scaled(diaq_adjoint_plan_t p, int32_t on);
 diaq_status diaq_adjoint_plan_get_scaled(diaq_adjoint_plan_t p, int32_t* on, int32_t* active);
 
+/* Fused rotation pairs of the per-gate sweep (window 0; on by default): two
+ * consecutive one-qubit rotations with X or Y generators on different
+ * qubits run in one launch, on groups of 4 amplitudes in registers, so the
+ * states are read and written once per pair; the reverse sweep takes both
+ * gradient terms in it, each at its own gate's position. Re-records the
+ * graph. */
+diaq_status diaq_adjoint_plan_set_pairs(diaq_adjoint_plan_t p, int32_t on);
+diaq_status diaq_adjoint_plan_get_pairs(diaq_adjoint_plan_t p, int32_t* on);
+
 /* Diagonal runs of the per-gate sweep (window 0; on by default). Runs of
  * Z-type rotations (generators of I and Z letters), fixed single-qubit
  * diagonal gates and CZs - after moving the other gates that act on none of

@@ -186,6 +186,8 @@ SIGNATURES.update({
     "diaq_adjoint_plan_set_runs": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_adjoint_plan_get_runs": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "diaq_adjoint_plan_set_scaled": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_set_pairs": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_get_pairs": (ctypes.c_int, [_vp, _i32p]),
     "diaq_adjoint_plan_get_scaled": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "diaq_batch_set_scaled": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_batch_get_scaled": (ctypes.c_int, [_vp, _i32p, _i32p]),

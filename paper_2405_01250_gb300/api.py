@@ -541,6 +541,15 @@ class AdjointPlan:
         """Scaled rotations of the per-gate complex128 sweep on or off (diaq_adjoint_plan_set_scaled)."""
         check(lib().diaq_adjoint_plan_set_scaled(self.handle, int(bool(on))))
 
+    def set_pairs(self, on: bool) -> None:
+        """Fused one-qubit rotation pairs of the per-gate sweep on or off (diaq_adjoint_plan_set_pairs)."""
+        check(lib().diaq_adjoint_plan_set_pairs(self.handle, int(bool(on))))
+
+    def pairs(self) -> bool:
+        a = ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_pairs(self.handle, ctypes.byref(a)))
+        return bool(a.value)
+
     def scaled(self) -> tuple:
         """(requested, active) for the scaled rotations (diaq_adjoint_plan_get_scaled)."""
         a, b = ctypes.c_int32(0), ctypes.c_int32(0)

@@ -54,6 +54,17 @@ struct BGate {
     double re[16], im[16];  // fixed gate matrix (row-major, 2^k x 2^k)
 };
 
+// Gates that the fused pair kernels (rot2_groups) take: parametric, one
+// qubit, an X or Y generator.
+__host__ __device__ __forceinline__ bool pair_gate(const BGate& g) {
+    return g.param >= 0 && g.k == 1 && g.xl == 1 && (g.pauli[0] == 1 || g.pauli[0] == 2);
+}
+
+// Two consecutive entries of an execution list that run as one pair.
+__host__ __device__ __forceinline__ bool pair_entries(const BGate* gates, int32_t e1, int32_t e2) {
+    return e1 >= 0 && e2 >= 0 && pair_gate(gates[e1]) && pair_gate(gates[e2]) && gates[e1].t[0] != gates[e2].t[0];
+}
+
 struct BInst {
     int32_t n;
     int32_t gate_begin, gate_end;
@@ -353,6 +364,56 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
     return o;
 }
 
+// The pair of one-qubit X/Y rotations (a then b) for the team kernel:
+// dispatch on the generators and the form, one group per iteration.
+template <typename R, bool SC>
+__device__ __forceinline__ void team_rot2(amp_t<R>* psi, amp_t<R>* lam, int n, const BGate& ga, const BGate& gb,
+                                          const double* ca, const double* cb, int64_t tid, int64_t nth, double* pa,
+                                          double* pb) {
+    // ca, cb: (c0, c1, m1) of Rot1 for the direction
+    const int qa = ga.t[0], qb = gb.t[0];
+    if (ga.pauli[0] == 1) {
+        const Rot1<R, 1, SC> A{R(ca[0]), R(ca[1]), ca[2] != 0.0};
+        if (gb.pauli[0] == 1) {
+            const Rot1<R, 1, SC> B{R(cb[0]), R(cb[1]), cb[2] != 0.0};
+            rot2_groups<R, 1, 1, SC, 1>(psi, lam, n, qa, qb, A, B, tid, nth, pa, pb);
+        } else {
+            const Rot1<R, 2, SC> B{R(cb[0]), R(cb[1]), cb[2] != 0.0};
+            rot2_groups<R, 1, 2, SC, 1>(psi, lam, n, qa, qb, A, B, tid, nth, pa, pb);
+        }
+    } else {
+        const Rot1<R, 2, SC> A{R(ca[0]), R(ca[1]), ca[2] != 0.0};
+        if (gb.pauli[0] == 1) {
+            const Rot1<R, 1, SC> B{R(cb[0]), R(cb[1]), cb[2] != 0.0};
+            rot2_groups<R, 2, 1, SC, 1>(psi, lam, n, qa, qb, A, B, tid, nth, pa, pb);
+        } else {
+            const Rot1<R, 2, SC> B{R(cb[0]), R(cb[1]), cb[2] != 0.0};
+            rot2_groups<R, 2, 2, SC, 1>(psi, lam, n, qa, qb, A, B, tid, nth, pa, pb);
+        }
+    }
+}
+
+// Thread 0 of each team block: Rot1 coefficients (c0, c1, m1) of a pair
+// member for one direction; in the scaled form also multiplies inv_s by its
+// sigma.
+__device__ __forceinline__ void team_rot1_coefs(const BGate& g, const double* th, bool dagger, bool scaled,
+                                                double* c, double* inv_s) {
+    double cs, kr, ki;
+    rot_angle(g, th, dagger, &cs, &kr, &ki);
+    if (scaled) {
+        int m1;
+        double sg;
+        rot_scaled_coefs(cs, kr, ki, g.rot.ny, &m1, &c[0], &sg);
+        c[1] = 0.0;
+        c[2] = m1;
+        *inv_s *= sg;
+    } else {
+        c[0] = cs;
+        c[1] = g.pauli[0] == 1 ? ki : kr;  // kappa's non-zero part
+        c[2] = 0.0;
+    }
+}
+
 // Phase tables of every diagonal run, both directions, once per replay:
 // block (run, direction) writes its table at out + (2 run + dir) stride.
 __global__ void __launch_bounds__(256) k_phase_tables(const PhaseRun* __restrict__ runs, const double* __restrict__ theta,
@@ -372,6 +433,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     __shared__ double warps[32];
     __shared__ double ang[3];
     __shared__ double sang[2];  // scaled form: m1, V's coefficient
+    __shared__ double pang[6];  // a fused pair: Rot1 coefficients of both members
     const int C = a.C;
     const bool scaled = sizeof(R) == 8 && a.scaled != 0;
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
@@ -407,6 +469,25 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
                 double acc[1];
                 phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
                 team_sync(C);
+                continue;
+            }
+            if (x + 1 < I.exec_end && pair_entries(a.gates, gi, a.exec[x + 1])) {  // a fused pair
+                const BGate& ga = a.gates[gi];
+                const BGate& gb = a.gates[a.exec[x + 1]];
+                if (threadIdx.x == 0) {
+                    team_rot1_coefs(ga, th, false, scaled, &pang[0], &inv_s);
+                    team_rot1_coefs(gb, th, false, scaled, &pang[3], &inv_s);
+                }
+                __syncthreads();
+                double pa, pb;
+                if constexpr (sizeof(R) == 8) {
+                    if (scaled) team_rot2<R, true>(psi, nullptr, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                    else team_rot2<R, false>(psi, nullptr, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                } else {
+                    team_rot2<R, false>(psi, nullptr, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                }
+                team_sync(C);
+                ++x;
                 continue;
             }
             const BGate& g = a.gates[gi];
@@ -469,6 +550,31 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
                     for (int g2 = 1; g2 < run.n_rot; ++g2) part[int64_t(run.rot_slot[g2]) * C + rank] = 0.0;
                 }
                 team_sync(C);
+                continue;
+            }
+            if (x - 1 >= I.exec_rev_begin && pair_entries(a.gates, a.exec[x - 1], gi)) {  // a fused pair (a, b)
+                const BGate& ga = a.gates[a.exec[x - 1]];
+                const BGate& gb = a.gates[gi];
+                const double ps_b = inv_s * inv_s;  // b's partial is taken first, before b is undone
+                if (threadIdx.x == 0) team_rot1_coefs(gb, th, true, scaled, &pang[3], &inv_s);
+                const double ps_a = inv_s * inv_s;  // a's partial after b is undone
+                if (threadIdx.x == 0) team_rot1_coefs(ga, th, true, scaled, &pang[0], &inv_s);
+                __syncthreads();
+                double pa, pb;
+                if constexpr (sizeof(R) == 8) {
+                    if (scaled) team_rot2<R, true>(psi, lam, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                    else team_rot2<R, false>(psi, lam, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                } else {
+                    team_rot2<R, false>(psi, lam, I.n, ga, gb, &pang[0], &pang[3], tid, nthreads, &pa, &pb);
+                }
+                const double sa = block_sum(pa, warps);
+                const double sb = block_sum(pb, warps);
+                if (threadIdx.x == 0) {
+                    part[int64_t(ga.slot) * C + rank] = scaled ? sa * ps_a : sa;
+                    part[int64_t(gb.slot) * C + rank] = scaled ? sb * ps_b : sb;
+                }
+                team_sync(C);
+                --x;
                 continue;
             }
             const BGate& g = a.gates[gi];
@@ -2116,6 +2222,75 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
     }
 }
 
+// Two consecutive one-qubit X/Y rotations (rot2_groups) in one launch:
+// forward A then B, or reverse with both partials.
+template <typename R, int GA, int GB, int SC>
+__global__ void __launch_bounds__(256) k_plan_rot2(amp_t<R>* psi, amp_t<R>* lam, const BGate* ga, const BGate* gb,
+                                                   const RotAngles* aa, const RotAngles* ab, int n, double* part_a,
+                                                   double* part_b) {
+    __shared__ double warps[32];
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
+    const bool adj = lam != nullptr;
+    const RotAngles x = *aa, y = *ab;
+    Rot1<R, GA, SC != 0> A;
+    Rot1<R, GB, SC != 0> B;
+    if (SC) {
+        A.c0 = R(adj ? x.cfr : x.cff);
+        A.c1 = R(0);
+        A.m1 = x.m1 != 0;
+        B.c0 = R(adj ? y.cfr : y.cff);
+        B.c1 = R(0);
+        B.m1 = y.m1 != 0;
+    } else {  // kappa's non-zero part: imaginary for X, real for Y
+        A.c0 = R(x.cs);
+        A.c1 = R(GA == 1 ? (adj ? x.kai : x.kfi) : (adj ? x.kar : x.kfr));
+        A.m1 = false;
+        B.c0 = R(y.cs);
+        B.c1 = R(GB == 1 ? (adj ? y.kai : y.kfi) : (adj ? y.kar : y.kfr));
+        B.m1 = false;
+    }
+    double pa = 0.0, pb = 0.0;
+    const int qa = ga->t[0], qb = gb->t[0];
+    if (adj)
+        rot2_groups<R, GA, GB, SC != 0, (sizeof(R) == 4 ? 2 : 1)>(psi, lam, n, qa, qb, A, B, tid, nth, &pa, &pb);
+    else
+        rot2_groups<R, GA, GB, SC != 0, (sizeof(R) == 4 ? 4 : 2)>(psi, nullptr, n, qa, qb, A, B, tid, nth, &pa, &pb);
+    if (part_a) {
+        const double sa = block_sum(pa, warps);
+        const double sb = block_sum(pb, warps);
+        if (threadIdx.x == 0) {
+            part_a[blockIdx.x] = sa;
+            part_b[blockIdx.x] = sb;
+        }
+    }
+}
+
+
+template <typename R, int SC>
+static void launch_plan_rot2_sc(const BGate& a, const BGate& b, amp_t<R>* psi, amp_t<R>* lam, const BGate* da,
+                                const BGate* db, const RotAngles* aa, const RotAngles* ab, int n, double* pa,
+                                double* pb, int P, cudaStream_t s) {
+    const int ga = a.pauli[0], gb = b.pauli[0];  // 1 X, 2 Y
+    if (ga == 1 && gb == 1) k_plan_rot2<R, 1, 1, SC><<<P, 256, 0, s>>>(psi, lam, da, db, aa, ab, n, pa, pb);
+    else if (ga == 1) k_plan_rot2<R, 1, 2, SC><<<P, 256, 0, s>>>(psi, lam, da, db, aa, ab, n, pa, pb);
+    else if (gb == 1) k_plan_rot2<R, 2, 1, SC><<<P, 256, 0, s>>>(psi, lam, da, db, aa, ab, n, pa, pb);
+    else k_plan_rot2<R, 2, 2, SC><<<P, 256, 0, s>>>(psi, lam, da, db, aa, ab, n, pa, pb);
+}
+
+template <typename R>
+static void launch_plan_rot2(const BGate& a, const BGate& b, amp_t<R>* psi, amp_t<R>* lam, const BGate* da,
+                             const BGate* db, const RotAngles* aa, const RotAngles* ab, int n, double* pa, double* pb,
+                             int P, bool scaled, cudaStream_t s) {
+    if constexpr (sizeof(R) == 8) {
+        if (scaled) {
+            launch_plan_rot2_sc<R, 1>(a, b, psi, lam, da, db, aa, ab, n, pa, pb, P, s);
+            return;
+        }
+    }
+    launch_plan_rot2_sc<R, 0>(a, b, psi, lam, da, db, aa, ab, n, pa, pb, P, s);
+}
+
 // kappa's form follows from the generator: imaginary for an even Y count
 // (KT = 1), real for an odd one (KT = 2)
 template <typename R, int KT, int SC>
@@ -2399,6 +2574,7 @@ struct diaq_adjoint_plan_s {
     // scaled rotations of the per-gate complex128 sweep (rot_groups_s):
     // requested (default on); active when n_events > 0
     bool scaled = true;
+    bool pairs = true;               // fuse consecutive one-qubit X/Y rotations (k_plan_rot2)
     FinTerm* d_fin = nullptr;        // gradient terms per parameter, in gate order
     int32_t* d_fin_first = nullptr;  // n_params + 1 offsets into d_fin
     ScaleEvent* d_events = nullptr;
@@ -2537,11 +2713,24 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
         if (p->runs_on && !p->runs.empty())
             k_phase_tables<<<dim3(unsigned(p->runs.size()), 2), 256, 0, s>>>(p->d_runs, p->d_theta, p->n, PR_TAB_ALL,
                                                                               p->d_ptabs);
-        for (int32_t g : order) {
+        auto pairable = [&](int32_t g1, int32_t g2) {
+            return p->pairs && g1 >= 0 && g2 >= 0 && pair_gate(p->gates[size_t(g1)]) &&
+                   pair_gate(p->gates[size_t(g2)]) && p->gates[size_t(g1)].t[0] != p->gates[size_t(g2)].t[0];
+        };
+        for (size_t oi = 0; oi < order.size(); ++oi) {
+            const int32_t g = order[oi];
             if (g < 0) {
                 k_plan_phase<R, false><<<p->P, 256, 0, s>>>(psi, nullptr, p->d_runs + (-1 - g),
                                                             p->d_ptabs + int64_t(-1 - g) * 2 * PR_TAB_ALL, p->n,
                                                             nullptr, p->P);
+                continue;
+            }
+            if (oi + 1 < order.size() && pairable(g, order[oi + 1])) {
+                const int32_t g2 = order[oi + 1];
+                launch_plan_rot2<R>(p->gates[size_t(g)], p->gates[size_t(g2)], psi, nullptr, p->d_gates + g,
+                                    p->d_gates + g2, p->d_angles + g, p->d_angles + g2, p->n, nullptr, nullptr, p->P,
+                                    scaled, s);
+                ++oi;
                 continue;
             }
             const BGate& G = p->gates[size_t(g)];
@@ -2562,6 +2751,16 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
                 else
                     k_plan_phase<R, true><<<p->P, 256, 0, s>>>(psi, lam, p->d_runs + (-1 - g), tab, p->n, p->d_part,
                                                                p->P);
+                continue;
+            }
+            if (oi > stop && pairable(order[oi - 1], g)) {  // the pair (order[oi - 1], g), undone as one
+                const int32_t g1 = order[oi - 1];
+                const BGate& G1 = p->gates[size_t(g1)];
+                const BGate& G2 = p->gates[size_t(g)];
+                launch_plan_rot2<R>(G1, G2, psi, lam, p->d_gates + g1, p->d_gates + g, p->d_angles + g1,
+                                    p->d_angles + g, p->n, p->d_part + int64_t(G1.slot) * p->P,
+                                    p->d_part + int64_t(G2.slot) * p->P, p->P, scaled, s);
+                --oi;
                 continue;
             }
             const BGate& G = p->gates[size_t(g)];
@@ -2905,6 +3104,25 @@ diaq_status diaq_adjoint_plan_set_scaled(diaq_adjoint_plan_t p, int32_t on) {
     DIAQ_CUDA(cudaStreamSynchronize(p->stream));
     p->scaled = on != 0;
     return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_set_pairs(diaq_adjoint_plan_t p, int32_t on) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    int dev = -1;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
+    DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    p->pairs = on != 0;
+    return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_pairs(diaq_adjoint_plan_t p, int32_t* on) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (on) *on = p->pairs ? 1 : 0;
+    return DIAQ_OK;
 }
 
 diaq_status diaq_adjoint_plan_get_scaled(diaq_adjoint_plan_t p, int32_t* on, int32_t* active) {

@@ -260,6 +260,123 @@ __device__ __forceinline__ double rot_groups_sc(amp_t<R>* psi, amp_t<R>* lam, in
     return rot_groups_s<R, K, XL, U, KT, 0>(psi, lam, n, sh, cf, tid, nthreads);
 }
 
+// One-qubit rotation about X (G = 1) or Y (G = 2) on a pair of amplitudes
+// (x0: target bit 0, x1: target bit 1), for the fused pair kernels. With
+// sc = false, (c0, c1) = (cos(a/2), kappa's non-zero part): X rows are
+// cos x_r + kappa_i i x_{1-r} (kappa imaginary), Y rows cos x_r + s_r kappa
+// x_{1-r} with s_0 = -1, s_1 = +1 (kappa real). With sc = true the scaled
+// form of rot_groups_s, c0 = V's coefficient and m1 its form: m1 = 0 gives
+// x_r + c0 s_r (i)x_{1-r}, m1 = 1 gives c0 x_r + s_r (i)x_{1-r}. Either way
+// each real component costs one fused multiply-add (scaled) or a multiply
+// and a fused multiply-add (unscaled); in the scaled form the operands are
+// selected on the uniform m1 and a unit coefficient's sign is an integer
+// flip, so no FP64 instruction is issued twice.
+template <typename R, int G, bool SC>
+struct Rot1 {
+    R c0, c1;
+    bool m1;
+
+    __device__ __forceinline__ amp_t<R> row(amp_t<R> x, amp_t<R> y, int r) const {
+        amp_t<R> w;
+        // partner component feeding each output component and its sign s
+        // (X: w.x gets -y.y, w.y gets +y.x; Y: both get s_r y, s_0 = -1)
+        const R px = G == 1 ? y.y : y.x, py = G == 1 ? y.x : y.y;
+        const bool nx = G == 1 ? true : (r == 0), ny_ = G == 1 ? false : (r == 0);
+        if (!SC) {
+            w.x = fma(c0, x.x, (nx ? -c1 : c1) * px);
+            w.y = fma(c0, x.y, (ny_ ? -c1 : c1) * py);
+        } else {
+            const R tx = nx ? -c0 : c0, ty = ny_ ? -c0 : c0;
+            const R fx = flip_sign(px, nx ? 0x80000000u : 0u), fy = flip_sign(py, ny_ ? 0x80000000u : 0u);
+            w.x = fma(m1 ? c0 : tx, m1 ? x.x : px, m1 ? fx : x.x);
+            w.y = fma(m1 ? c0 : ty, m1 ? x.y : py, m1 ? fy : x.y);
+        }
+        return w;
+    }
+    __device__ __forceinline__ void apply(amp_t<R>& x0, amp_t<R>& x1) const {
+        const amp_t<R> w0 = row(x0, x1, 0), w1 = row(x1, x0, 1);
+        x0 = w0;
+        x1 = w1;
+    }
+    // Im <l|P|p> over the pair, into the positive and negative sums: X gives
+    // Im conj(l_r) p_{1-r}; Y gives s_r Re conj(l_r) p_{1-r}
+    __device__ __forceinline__ void partial(const amp_t<R>& l0, const amp_t<R>& l1, const amp_t<R>& p0,
+                                            const amp_t<R>& p1, Acc<R>& pos, Acc<R>& neg) const {
+        if (G == 1) {
+            pos.add_cross(l0.x, p1.y, l0.y, p1.x);
+            pos.add_cross(l1.x, p0.y, l1.y, p0.x);
+        } else {
+            neg.add_dot(l0.x, p1.x, l0.y, p1.y);
+            pos.add_dot(l1.x, p0.x, l1.y, p0.y);
+        }
+    }
+};
+
+// Two one-qubit X/Y rotations A (on qubit qa) then B (on qb != qa), fused:
+// each thread takes groups of the 4 amplitudes that share every other bit
+// and applies A along qa and B along qb in registers (forward), or - with
+// lam - takes B's partial, undoes B on psi and lam, takes A's partial and
+// undoes A (reverse), so a pair costs one read and one write of the states
+// instead of two. Partials go to pa and pb (this thread's shares).
+template <typename R, int GA, int GB, bool SC, int U>
+__device__ __noinline__ void rot2_groups(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n, int qa,
+                                         int qb, const Rot1<R, GA, SC> A, const Rot1<R, GB, SC> B, int64_t tid,
+                                         int64_t nthreads, double* pa, double* pb) {
+    using Am = amp_t<R>;
+    int st[2] = {qa < qb ? qa : qb, qa < qb ? qb : qa};
+    const int64_t oa = int64_t(1) << qa, ob = int64_t(1) << qb;
+    const int64_t off[4] = {0, oa, ob, oa + ob};  // bit 0 of the index: qa, bit 1: qb
+    Acc<R> a_pos, a_neg, b_pos, b_neg;
+    const int64_t G = int64_t(1) << (n - 2);
+    for (int64_t g0 = tid; g0 < G; g0 += int64_t(U) * nthreads) {
+        int64_t b[U];
+        Am p[U][4], l[U][4];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t gi = g0 + int64_t(u) * nthreads;
+            b[u] = gi < G ? insert_zeros<2>(gi, st) : int64_t(-1);
+            if (b[u] >= 0 && !DIAQ_BOUNDS_OK(b[u] + off[3], int64_t(1) << n, BS_ROTATION)) b[u] = -1;
+            if (b[u] >= 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) p[u][c] = psi[b[u] + off[c]];
+                if (lam) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) l[u][c] = lam[b[u] + off[c]];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (b[u] < 0) continue;
+            if (!lam) {
+                A.apply(p[u][0], p[u][1]);
+                A.apply(p[u][2], p[u][3]);
+                B.apply(p[u][0], p[u][2]);
+                B.apply(p[u][1], p[u][3]);
+            } else {
+                B.partial(l[u][0], l[u][2], p[u][0], p[u][2], b_pos, b_neg);
+                B.partial(l[u][1], l[u][3], p[u][1], p[u][3], b_pos, b_neg);
+                B.apply(p[u][0], p[u][2]);
+                B.apply(p[u][1], p[u][3]);
+                B.apply(l[u][0], l[u][2]);
+                B.apply(l[u][1], l[u][3]);
+                A.partial(l[u][0], l[u][1], p[u][0], p[u][1], a_pos, a_neg);
+                A.partial(l[u][2], l[u][3], p[u][2], p[u][3], a_pos, a_neg);
+                A.apply(p[u][0], p[u][1]);
+                A.apply(p[u][2], p[u][3]);
+                A.apply(l[u][0], l[u][1]);
+                A.apply(l[u][2], l[u][3]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) lam[b[u] + off[c]] = l[u][c];
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) psi[b[u] + off[c]] = p[u][c];
+        }
+    }
+    *pa = a_pos.value() - a_neg.value();
+    *pb = b_pos.value() - b_neg.value();
+}
+
 // The scaled form's coefficients from (cos, kappa) of one direction: the
 // form (m1), V's coefficient cf and sigma (U = sigma V).
 __host__ __device__ __forceinline__ void rot_scaled_coefs(double cs, double kr, double ki, int ny, int* m1, double* cf,

@@ -147,3 +147,46 @@ def test_batch_scaled_matches_unscaled_and_oracle(api):
     b = api.Batch(desc, dtype=torch.complex64)
     assert b.scaled() == (True, False)
     b.close()
+
+
+def _xy_circuit(n, rng, layers):
+    """Layers of one-qubit X and Y rotations (runs of them pair up in the
+    sweep), some on the same qubit back to back, with CZs and a dense fixed
+    gate between layers."""
+    g = [synth.Gate((q,), synth.H) for q in range(n)]
+    p = 0
+    for _ in range(layers):
+        qs = list(rng.permutation(n)) + [int(rng.integers(n))]
+        for q in qs:
+            g.append(synth.Gate((int(q),), None, param=p, gen="XY"[int(rng.integers(2))],
+                                scale=float(rng.choice([1.0, -0.5]))))
+            p += 1
+        g.append(synth.Gate((0, n - 1), synth.CZ))
+        g.append(synth.Gate((int(rng.integers(n)),), synth.random_gate(1, rng, "dense")))
+    return synth.Circuit(n, g, theta=rng.uniform(0, 2 * math.pi, size=p))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("scaled", [True, False])
+def test_plan_rotation_pairs_match_single_launches_and_oracle(api, dtype, scaled):
+    rng = np.random.default_rng(31)
+    n = 9
+    circ = _xy_circuit(n, rng, 4)
+    obs = synth.ansatz_observable(n)
+    res = {}
+    for pairs in (True, False):
+        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+        plan.set_scaled(scaled)
+        plan.set_pairs(pairs)
+        assert plan.pairs() == pairs
+        res[pairs] = plan.run(circ.theta)
+        plan.close()
+    (e1, g1), (e0, g0) = res[True], res[False]
+    psi0 = synth.basis_state(n, 0)
+    e_ref = oracle.energy(circ, obs, psi0)
+    g_ref = oracle.param_shift_grad(circ, obs, psi0)
+    if dtype == torch.complex128:
+        assert abs(e1 - e0) < 1e-12 and np.max(np.abs(g1 - g0)) < 1e-12
+        assert abs(e1 - e_ref) < 1e-11 and np.max(np.abs(g1 - g_ref)) < 1e-10
+    else:
+        assert abs(e1 - e_ref) < 2e-5 and np.max(np.abs(g1 - g_ref)) < 5e-5
