@@ -885,7 +885,29 @@ def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7, ref=None, ref_mag=None
         mags[name] = api.expect(x, obs.xmask, obs.zmask, obs.coeff).real
         out[name] = {"ms_per_circuit": ms, "gates_per_s": len(ops) / (ms / 1e3), "gbs": nbytes / (ms / 1e3) / 1e9,
                      "magnetisation": mags[name], "norm": api.norm(x)}
-        del ops, x
+        del ops
+        # the same circuit as a user runs it: each run of bond rotations fused
+        # into diagonal ops of up to 6 qubits (plan_fusion_diagonal), field
+        # rotations single, all through diaq_simulate in place on the device
+        # state (complex128 field rotations take its scaled form)
+        fops = api.build_fused(circ.gates, n, 6, 64, dtype=dt_, theta=circ.theta, diagonal=True)
+        fbytes = sum(op.apply_bytes(in_place=True) for op in fops)
+        for rep in range(2):
+            x.zero_()
+            x[0] = 1
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            f0.record(stream)
+            api.simulate(fops, x, x, x)
+            f1.record(stream)
+            torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1)
+        fmag = api.expect(x, obs.xmask, obs.zmask, obs.coeff).real
+        out[name + "_fused"] = {"ops": len(fops), "ms_per_circuit": fms, "gates_per_s": len(circ.gates) / (fms / 1e3),
+                                "moved_gbs": fbytes / (fms / 1e3) / 1e9, "speedup_vs_unfused": ms / fms,
+                                "magnetisation_abs_diff_vs_unfused": abs(fmag - mags[name])}
+        del fops, x
     out["c64_vs_c128_magnetisation_diff"] = abs(mags["c64"] - mags["c128"])
     if ref is not None:
         # the same Trotter circuit at REF_TFIM qubits against the FP64 oracle

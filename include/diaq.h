@@ -242,8 +242,16 @@ diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
  * data are copied in and out on `stream` inside the call. work0 and work1
  * are caller-owned device state buffers (work1 may be NULL when every op is
  * on-the-fly). On-the-fly ops run in place in work0 (with the identity-row
- * skip of diaq_apply). Host copies overlap the first and last ops as in
- * diaq_simulate_timed. Synchronises `stream` before returning. */
+ * skip of diaq_apply); psi_in may be work0 itself, and psi_out the buffer
+ * that ends up holding the state (work0 when every op is on-the-fly), and
+ * then no copy is made. Host copies overlap the first and last ops as in
+ * diaq_simulate_timed. In complex128, one-qubit on-the-fly ops whose rows
+ * each hold an entry of the largest magnitude sigma (RX, RY, H and the
+ * like: real diagonal, off-diagonal both real or both imaginary) run as
+ * U / sigma, one fused multiply-add per real component, and the last such
+ * op of the list runs as U times the product of the dropped sigmas, so the
+ * result equals the op-by-op one up to rounding. Synchronises `stream`
+ * before returning. */
 diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
                           void* work0, void* work1, diaq_stream_t stream);
 

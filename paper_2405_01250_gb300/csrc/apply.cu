@@ -61,7 +61,26 @@ struct SmallGateArgs {
     // non-zero diagonal with imaginary non-zero off-diagonal (RX),
     // 3 diagonal, every diagonal entry general complex (RZ; RZZ for k = 2).
     int pattern;
+    // k = 1 only, scaled form (launch_gate_scaled1): each output component
+    // is one fused multiply-add, fma(sc_a, in[sc_mul], +-in[sc_add]), with
+    // in = (own.re, own.im, partner.re, partner.im) of the row and the sign
+    // an integer flip (sc_neg); the caller tracks the dropped factor.
+    int scaled1;
+    R sc_a[2][2];
+    uint8_t sc_mul[2][2], sc_add[2][2];
+    uint32_t sc_neg[2][2];
 };
+
+// v with its sign bit XORed with m (0 or 0x80000000): an integer operation
+__device__ __forceinline__ double flip_mask(double v, uint32_t m) {
+    return __hiloint2double(__double2hiint(v) ^ int(m), __double2loint(v));
+}
+__device__ __forceinline__ float flip_mask(float v, uint32_t m) { return __int_as_float(__float_as_int(v) ^ int(m)); }
+
+template <typename R>
+__device__ __forceinline__ R pick4(int code, const amp_t<R>& own, const amp_t<R>& par) {
+    return code == 0 ? own.x : (code == 1 ? own.y : (code == 2 ? par.x : par.y));
+}
 
 template <typename R, int K, int G>
 __global__ void __launch_bounds__(256)
@@ -82,6 +101,23 @@ k_apply_small(const amp_t<R>* x, amp_t<R>* y, const __grid_constant__ SmallGateA
 #pragma unroll
             for (int c = 0; c < D; ++c) v[j][c] = ld_stream(x + b[j] + a.off[c]);
         }
+    }
+    if (K == 1 && a.scaled1) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (b[j] < 0) continue;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const A own = v[j][r], par = v[j][1 - r];
+                A w;
+                w.x = fma(a.sc_a[r][0], pick4<R>(a.sc_mul[r][0], own, par),
+                          flip_mask(pick4<R>(a.sc_add[r][0], own, par), a.sc_neg[r][0]));
+                w.y = fma(a.sc_a[r][1], pick4<R>(a.sc_mul[r][1], own, par),
+                          flip_mask(pick4<R>(a.sc_add[r][1], own, par), a.sc_neg[r][1]));
+                st_stream(y + b[j] + a.off[r], w);
+            }
+        }
+        return;
     }
     if (K == 1 && a.dense1) {
         // y_r = m_r0 x0 + m_r1 x1, each complex product as in mac_typed:
@@ -364,6 +400,102 @@ static diaq_status launch_small_G(int n, const GateDesc& g, const void* x, void*
         reinterpret_cast<const amp_t<R>*>(x), reinterpret_cast<amp_t<R>*>(y), a);
     DIAQ_CUDA(cudaGetLastError());
     return DIAQ_OK;
+}
+
+// The scaled form of a one-qubit gate whose diagonal entries are real and
+// non-zero and whose off-diagonal entries are both real or both imaginary
+// and non-zero (RX, RY, H and the like), with |m00| = |m11|: U = sigma V,
+// sigma = max(|m_rr|, |m_r,1-r|), the same for both rows. Every row of V has
+// one entry of magnitude 1 (+-1 or +-i), so each output component is one
+// fused multiply-add: fma(m / sigma, term, +-unit term). Writes sigma; false
+// when the gate has no such form.
+static bool scaled1_form(const GateDesc& g, double* sigma, double sc_a[2][2], uint8_t mul[2][2], uint8_t add[2][2],
+                         uint32_t neg[2][2]) {
+    if (g.k != 1 || g.m.size() != 4) return false;
+    const cplx m00 = g.m[0], m01 = g.m[1], m10 = g.m[2], m11 = g.m[3];
+    if (m00.imag() != 0.0 || m11.imag() != 0.0 || m00.real() == 0.0 || m11.real() == 0.0) return false;
+    int P;  // 1: real off-diagonal, 2: imaginary off-diagonal
+    if (m01.imag() == 0.0 && m10.imag() == 0.0 && m01.real() != 0.0 && m10.real() != 0.0) P = 1;
+    else if (m01.real() == 0.0 && m10.real() == 0.0 && m01.imag() != 0.0 && m10.imag() != 0.0) P = 2;
+    else return false;
+    const double d[2] = {m00.real(), m11.real()};
+    const double o[2] = {P == 1 ? m01.real() : m01.imag(), P == 1 ? m10.real() : m10.imag()};
+    const double s0 = std::max(std::fabs(d[0]), std::fabs(o[0])), s1 = std::max(std::fabs(d[1]), std::fabs(o[1]));
+    if (s0 != s1 || !(s0 > 0.0)) return false;
+    const double sg = s0;
+    constexpr uint32_t NEG = 0x80000000u;
+    for (int r = 0; r < 2; ++r) {
+        // input codes: 0 own.re, 1 own.im, 2 partner.re, 3 partner.im
+        if (std::fabs(d[r]) == sg) {  // own term +-1: fma(o/sigma, partner part, +-own)
+            const double A = o[r] / sg;
+            const uint32_t on = d[r] < 0.0 ? NEG : 0u;
+            if (P == 1) {
+                sc_a[r][0] = A; mul[r][0] = 2; add[r][0] = 0; neg[r][0] = on;
+                sc_a[r][1] = A; mul[r][1] = 3; add[r][1] = 1; neg[r][1] = on;
+            } else {  // (i A) partner = (-A p.im, A p.re)
+                sc_a[r][0] = -A; mul[r][0] = 3; add[r][0] = 0; neg[r][0] = on;
+                sc_a[r][1] = A; mul[r][1] = 2; add[r][1] = 1; neg[r][1] = on;
+            }
+        } else {  // partner term +-1 or +-i: fma(d/sigma, own part, +-partner part)
+            const double A = d[r] / sg;
+            const bool un = o[r] < 0.0;
+            if (P == 1) {
+                sc_a[r][0] = A; mul[r][0] = 0; add[r][0] = 2; neg[r][0] = un ? NEG : 0u;
+                sc_a[r][1] = A; mul[r][1] = 1; add[r][1] = 3; neg[r][1] = un ? NEG : 0u;
+            } else {  // (+-i) partner = (-+p.im, +-p.re)
+                sc_a[r][0] = A; mul[r][0] = 0; add[r][0] = 3; neg[r][0] = un ? 0u : NEG;
+                sc_a[r][1] = A; mul[r][1] = 1; add[r][1] = 2; neg[r][1] = un ? NEG : 0u;
+            }
+        }
+    }
+    *sigma = sg;
+    return true;
+}
+
+bool gate_scaled1_sigma(const GateDesc& g, double* sigma) {
+    double a[2][2];
+    uint8_t mul[2][2], add[2][2];
+    uint32_t neg[2][2];
+    return scaled1_form(g, sigma, a, mul, add, neg);
+}
+
+template <int G>
+static diaq_status launch_scaled1_G(int n, const GateDesc& g, const void* x, void* y, int threads, int64_t g_begin,
+                                    int64_t g_end, double* sigma, cudaStream_t s) {
+    SmallGateArgs<double, 1> a;
+    std::memset(&a, 0, sizeof(a));
+    double ca[2][2];
+    if (!scaled1_form(g, sigma, ca, a.sc_mul, a.sc_add, a.sc_neg))
+        return fail(DIAQ_ERR_UNSUPPORTED, "gate has no scaled one-qubit form");
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) a.sc_a[r][c] = ca[r][c];
+    a.scaled1 = 1;
+    a.g_base = g_begin;
+    a.n_groups = g_end;
+    a.N = int64_t(1) << n;
+    sorted_targets(g, a.st);
+    local_offsets(g, a.off);
+    const int64_t per_block = int64_t(threads) * G;
+    const int64_t blocks = (g_end - g_begin + per_block - 1) / per_block;
+    if (blocks <= 0) return DIAQ_OK;
+    DIAQ_PRELAUNCH("k_apply_small");
+    k_apply_small<double, 1, G><<<dim3((unsigned)blocks), threads, 0, s>>>(
+        reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), a);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
+
+// Groups [g_begin, g_end) of a complex128 one-qubit gate in the scaled form
+// (V = U / sigma, *sigma written); DIAQ_ERR_UNSUPPORTED without one.
+diaq_status launch_gate_scaled1_range(int n, const GateDesc& g, const void* x, void* y, int64_t g_begin,
+                                      int64_t g_end, double* sigma, cudaStream_t s) {
+    const LaunchCfg& cfg = launch_cfg(DIAQ_C128, 1);
+    const int G = cfg.groups > 0 ? cfg.groups : default_groups(DIAQ_C128, 1);
+    switch (G) {
+        case 1: return launch_scaled1_G<1>(n, g, x, y, cfg.threads, g_begin, g_end, sigma, s);
+        case 2: return launch_scaled1_G<2>(n, g, x, y, cfg.threads, g_begin, g_end, sigma, s);
+        default: return launch_scaled1_G<4>(n, g, x, y, cfg.threads, g_begin, g_end, sigma, s);
+    }
 }
 
 template <typename R, int K>

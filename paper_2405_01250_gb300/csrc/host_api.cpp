@@ -1061,6 +1061,61 @@ diaq_status run_inplace(const diaq_op_s* op, void* x, int64_t g0, int64_t g1, cu
     return launch_onthefly(op, x, x, s);
 }
 
+// Deferred scalars of a complex128 simulation. A one-qubit gate whose rows
+// each have an entry of the largest magnitude sigma (RX, RY, H and the
+// like: gate_scaled1_sigma) runs as V = U / sigma, one fused multiply-add
+// per real component instead of two or three FP64 instructions; the stored
+// state is then the true one divided by F, the product of the sigmas so far.
+// The last such gate of the circuit (or one where F has fallen below 2^-400,
+// so that the stored amplitudes stay far from overflow) runs as F U
+// instead, which makes the stored state the true one again; every other gate
+// is linear and leaves F alone.
+enum SimAction { SIM_PLAIN = 0, SIM_SCALED = 1, SIM_FOLD = 2 };
+
+struct SimStep {
+    int action = SIM_PLAIN;
+    GateDesc folded;  // SIM_FOLD: F U
+};
+
+static std::vector<SimStep> plan_sim_scaling(const diaq_op_t* ops, int count) {
+    std::vector<SimStep> st(static_cast<size_t>(count));
+    std::vector<double> sig(static_cast<size_t>(count), 0.0);
+    int last = -1;
+    for (int i = 0; i < count; ++i) {
+        const diaq_op_s* op = ops[i];
+        if (op->dtype == DIAQ_C128 && op->variant == DIAQ_ONTHEFLY && op->gate.k == 1 &&
+            gate_scaled1_sigma(op->gate, &sig[size_t(i)]))
+            last = i;
+        else
+            sig[size_t(i)] = 0.0;
+    }
+    double F = 1.0;
+    for (int i = 0; i <= last; ++i) {
+        if (sig[size_t(i)] == 0.0) continue;
+        if (i == last || F < 0x1p-400) {
+            SimStep& x = st[size_t(i)];
+            x.action = SIM_FOLD;
+            x.folded = ops[i]->gate;
+            for (cplx& v : x.folded.m) v *= F;
+            F = 1.0;
+        } else {
+            st[size_t(i)].action = SIM_SCALED;
+            F *= sig[size_t(i)];
+        }
+    }
+    return st;
+}
+
+static diaq_status run_inplace_step(const diaq_op_s* op, const SimStep& st, void* x, int64_t g0, int64_t g1,
+                                    cudaStream_t s) {
+    if (st.action == SIM_SCALED) {
+        double sigma = 0.0;
+        return launch_gate_scaled1_range(op->n, op->gate, x, x, g0, g1, &sigma, s);
+    }
+    if (st.action == SIM_FOLD) return launch_gate_local_range(op->n, op->dtype, st.folded, x, x, g0, g1, s);
+    return run_inplace(op, x, g0, g1, s);
+}
+
 // Streams and events of one diaq_simulate call, released on every path.
 struct SimResources {
     cudaStream_t cin = nullptr, cout = nullptr;
@@ -1096,6 +1151,7 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         any_stored |= ops[i]->variant == DIAQ_STORED;
     }
     if (any_stored && !work1) return fail(DIAQ_ERR_ARG, "stored ops need a second work buffer");
+    const std::vector<SimStep> steps = plan_sim_scaling(ops, count);
     if (mem_kind(work0) != 1 || (work1 && mem_kind(work1) != 1)) return fail(DIAQ_ERR_ARG, "work buffers must be device memory");
     const size_t s_amp = amp_bytes(dt);
     const size_t bytes = (size_t(1) << n) * s_amp;
@@ -1147,7 +1203,7 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         const size_t out_run_bytes = size_t(pout.run_len) * s_amp;
         for (size_t j = 0; j < pin.slices.size(); ++j) {
             DIAQ_CUDA(cudaStreamWaitEvent(s, got[j], 0));
-            DIAQ_TRY(run_inplace(ops[0], work0, pin.slices[j].g_begin, pin.slices[j].g_end, s));
+            DIAQ_TRY(run_inplace_step(ops[0], steps[0], work0, pin.slices[j].g_begin, pin.slices[j].g_end, s));
             if (also_out) {  // one op: each slice leaves as soon as it is done
                 cudaEvent_t done = R.make(false);
                 if (!done) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
@@ -1163,7 +1219,7 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         out_sent = also_out;
     } else {
         const cudaMemcpyKind kin = in_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-        DIAQ_CUDA(cudaMemcpyAsync(work0, psi_in, bytes, kin, s));
+        if (psi_in != work0) DIAQ_CUDA(cudaMemcpyAsync(work0, psi_in, bytes, kin, s));
         if (timing) DIAQ_CUDA(cudaEventRecord(t_in, s));
     }
     if (pipe_out && !out_sent) last = count - 1;
@@ -1171,7 +1227,8 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
     void* other = work1;
     for (int i = first; i < last; ++i) {
         if (ops[i]->variant == DIAQ_ONTHEFLY) {
-            DIAQ_TRY(run_inplace(ops[i], cur, 0, ops[i]->gate.k <= 3 ? int64_t(1) << (n - ops[i]->gate.k) : 0, s));
+            DIAQ_TRY(run_inplace_step(ops[i], steps[size_t(i)], cur, 0,
+                                      ops[i]->gate.k <= 3 ? int64_t(1) << (n - ops[i]->gate.k) : 0, s));
         } else {
             DIAQ_TRY(launch_stored(ops[i], cur, other, s));
             std::swap(cur, other);
@@ -1182,7 +1239,8 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         // slice by slice, and each slice goes out as soon as it is done
         const size_t run_bytes = size_t(pout.run_len) * s_amp;
         for (size_t j = 0; j < pout.slices.size(); ++j) {
-            DIAQ_TRY(run_inplace(ops[count - 1], cur, pout.slices[j].g_begin, pout.slices[j].g_end, s));
+            DIAQ_TRY(run_inplace_step(ops[count - 1], steps[size_t(count - 1)], cur, pout.slices[j].g_begin,
+                                      pout.slices[j].g_end, s));
             cudaEvent_t done = R.make(false);
             if (!done) return fail(DIAQ_ERR_CUDA, "cudaEventCreate failed");
             DIAQ_CUDA(cudaEventRecord(done, s));
@@ -1201,7 +1259,7 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         DIAQ_CUDA(cudaStreamWaitEvent(s, copied, 0));
     } else {
         const cudaMemcpyKind kout = out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-        DIAQ_CUDA(cudaMemcpyAsync(psi_out, cur, bytes, kout, s));
+        if (psi_out != cur) DIAQ_CUDA(cudaMemcpyAsync(psi_out, cur, bytes, kout, s));
     }
     if (R.cin) {  // nothing on `stream` may outlive this call's input copies
         cudaEvent_t in_done = R.make(false);

@@ -164,6 +164,12 @@ int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
 // Diagonal ops of 4..6 qubits (diag.cu): one table lookup and one complex
 // multiply per row; in place (x == y) rows whose entry is exactly 1 are
 // skipped.
+// Scaled form of a complex128 one-qubit gate (RX, RY, H and the like): the
+// launch applies U / sigma; gate_scaled1_sigma tells whether the gate has
+// the form and its sigma.
+bool gate_scaled1_sigma(const GateDesc& g, double* sigma);
+diaq_status launch_gate_scaled1_range(int n, const GateDesc& g, const void* x, void* y, int64_t g_begin,
+                                      int64_t g_end, double* sigma, cudaStream_t s);
 bool is_diagonal(const GateDesc& g);
 diaq_status launch_diag(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y, cudaStream_t s);
 int64_t diag_inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
