@@ -325,7 +325,7 @@ def run_ours(args, rank, world):
             # correctness: sampled amplitudes of the result against the closed form
             amp_err = float(np.max(np.abs(hout.numpy()[ks] - from_closed)))
             tl = [statistics.median(v[i] for v in legs) for i in range(3)]
-            moved = sum(op.apply_bytes(in_place=True) for op in sim_ops)
+            moved = api.simulate_bytes(sim_ops)  # merged diagonal runs and pairs counted as they run
             return {"value": world * len(ops) * bytes_op / e_s / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": N * 16, "d2h_bytes_per_step": N * 16, "ms_per_step": e_s * 1e3,
                     "gates_per_s": world * len(ops) / e_s, "ops": len(sim_ops),
@@ -540,14 +540,16 @@ def bench_sample(api, psi, n, j, stream, shots=1024, reps=10):
 # 4 (c - 1) + 2 + r + 8 reverse. The Pauli-sum lambda: 2 per term (the
 # signed weights) and 4 per X-mask group, plus 2 for the energy. The reverse
 # sweep stops at the earliest gate with a gradient term.
-def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False):
+def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False, product_layer_n=None):
     """(forward, reverse, lambda) FP64 instructions per amplitude of one
     energy + gradient of `gates`; with runs=True the diagonal runs are
     counted as the library forms them (chunks_run: (rotations, byte tables)
     of each chunk-form run in place of its member gates, or the weight form
     for runs of one-parameter rotations); with scaled=True rotations take
     the scaled form (one fused multiply-add per real component: 2 forward,
-    2 + 2 + 2 reverse)."""
+    2 + 2 + 2 reverse); with product_layer_n = n the leading fixed one-qubit
+    gates on distinct qubits are written directly as a product state from
+    per-byte tables (4 per further chunk of 8 qubits)."""
     def kind(g):
         if g.param >= 0:
             return "zrot" if set(g.gen) <= {"Z", "I"} else "rot"
@@ -558,7 +560,18 @@ def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False):
     ks = [kind(g) for g in gates]
     first = next((i for i, k in enumerate(ks) if k in ("rot", "zrot")), len(ks))
     fwd = rev = 0
+    layer = 0
+    if product_layer_n:
+        seen = set()
+        while layer < len(gates) and not gates[layer].parametric and len(gates[layer].targets) == 1 \
+                and gates[layer].targets[0] not in seen:
+            seen.add(gates[layer].targets[0])
+            layer += 1
+        if layer:
+            fwd += 4 * ((product_layer_n + 7) // 8 - 1)
     for i, k in enumerate(ks):
+        if i < layer:
+            continue
         if runs and k in ("zrot", "sign"):
             continue  # counted with the runs below
         rot_f, rot_r = (2, 6) if scaled else (4, 10)
@@ -570,9 +583,9 @@ def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False):
             if c == 0:  # weight form
                 fwd += 4
                 rev += 11
-            else:
+            else:  # r_rot: rotations whose gradient term takes a signed addition per amplitude
                 fwd += 4 * (c - 1) + 4
-                rev += 4 * (c - 1) + 2 + r_rot + 8
+                rev += 4 * (c - 1) + 2 + 1 + r_rot + 8
     # lambda = H psi: per group of equal X masks the weight comes from a
     # table (no FP64 work when the coefficients are equal, else one complex
     # addition per further chunk of 8 terms), then 2 (real weight) or 4
@@ -676,11 +689,19 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     # FP64 floor of a complex128 gradient (FP64-bound: the 16 MiB states stay in L2)
     N = 1 << n
     chunks = (n + 7) // 8
+    # the reverse chunk-form kernel takes a per-amplitude term only for
+    # rotations on bits at or above the trailing zeros of its thread count
+    # (blocks = min(N / 512, 2 SMs), 256 threads each)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nth = min(N // 512, 2 * sms) * 256
+    fixed_bits = (nth & -nth).bit_length() - 1
+    varying = max(0, n - fixed_bits)
     best = out["adjoint_autotuned_c128"]["ms_per_gradient"]
     scaled_best = out["adjoint_autotuned_c128"]["window"] == 0
     f0, r0, l0 = fp64_per_amp(circ.gates, obs, runs=False)
-    fu, ru, lu = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers)
-    f1, r1, l1 = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(n, chunks)] * layers, scaled=scaled_best)
+    fu, ru, lu = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(varying, chunks)] * layers)
+    f1, r1, l1 = fp64_per_amp(circ.gates, obs, runs=True, chunks_run=[(varying, chunks)] * layers,
+                              scaled=scaled_best)
     out["roofline_c128"] = {
         "bound": "fp64", "unit": "FP64 instructions", "peak_instr_per_s": FP64_INSTR_PER_S,
         "peak_source": "measured FP64 probe (independent DFMA chains), not MEASURED_PEAKS.json",
@@ -695,7 +716,8 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
         "frac_of_gate_by_gate_floor": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3 / best,
         "bytes_per_gradient": N * 16 * (2 * steps + 4 * steps + 2),
         "note": "per amplitude: rotation 2 forward / 6 reverse scaled (4 / 10 unscaled); chunk-form diagonal run "
-                "(RZ layer + CZ ladder) 4 (c - 1) + 4 forward, 4 (c - 1) + 10 + r reverse; lambda 2 per real term "
+                "(RZ layer + CZ ladder) 4 (c - 1) + 4 forward, 4 (c - 1) + 11 + v reverse (v rotations on bits above the "
+                "thread count's trailing zeros); lambda 2 per real term "
                 "group (weights from tables) + 2 for the energy"}
     for name in ("c128", "c64"):
         # what the graph plan and the window-fused sweep add over the
@@ -830,7 +852,8 @@ def bench_batch(api, count=256, reps=3, plain=True, shape=None, dtypes=("c64", "
         for c, o in inst:
             f0, r0, l0 = fp64_per_amp(c.gates, o, runs=False)
             fu, ru, lu = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4)
-            f1, r1, l1 = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4, scaled=scaled_best)
+            f1, r1, l1 = fp64_per_amp(c.gates, o, runs=True, chunks_run=[(0, 0)] * 4, scaled=scaled_best,
+                                      product_layer_n=c.n)
             fl0 += (1 << c.n) * (f0 + r0 + l0)
             flu += (1 << c.n) * (fu + ru + lu)
             fl1 += (1 << c.n) * (f1 + r1 + l1)
@@ -891,7 +914,7 @@ def bench_tfim(api, n=28, steps=10, dt=0.1, J=1.0, h=0.7, ref=None, ref_mag=None
         # rotations single, all through diaq_simulate in place on the device
         # state (complex128 field rotations take its scaled form)
         fops = api.build_fused(circ.gates, n, 6, 64, dtype=dt_, theta=circ.theta, diagonal=True)
-        fbytes = sum(op.apply_bytes(in_place=True) for op in fops)
+        fbytes = api.simulate_bytes(fops)
         for rep in range(2):
             x.zero_()
             x[0] = 1

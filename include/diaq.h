@@ -249,9 +249,14 @@ diaq_status diaq_op_apply_bytes(diaq_op_t op, int32_t in_place, int64_t* bytes);
  * each hold an entry of the largest magnitude sigma (RX, RY, H and the
  * like: real diagonal, off-diagonal both real or both imaginary) run as
  * U / sigma, one fused multiply-add per real component, and the last such
- * op of the list runs as U times the product of the dropped sigmas, so the
- * result equals the op-by-op one up to rounding. Synchronises `stream`
- * before returning. */
+ * op of the list runs as U times the product of the dropped sigmas. Two
+ * consecutive one-qubit on-the-fly ops with no zero entry, on different
+ * qubits, run in one pass over the state. A run
+ * of consecutive diagonal on-the-fly ops whose targets span at most 11
+ * qubits runs as one pass with the product of their diagonals (a table of
+ * up to 2048 entries, copied to the device inside the call; rows whose
+ * product is exactly 1 are not touched). The result equals the op-by-op one
+ * up to rounding. Synchronises `stream` before returning. */
 diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
                           void* work0, void* work1, diaq_stream_t stream);
 
@@ -269,6 +274,14 @@ diaq_status diaq_simulate(const diaq_op_t* ops, int32_t count, const void* psi_i
  * call; synchronises `stream`. */
 diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void* psi_in, void* psi_out,
                                 void* work0, void* work1, diaq_stream_t stream, float* timeline_ms);
+
+/* The HBM bytes diaq_simulate moves for ops on a device state (psi_in and
+ * psi_out the work buffer): each merged diagonal run reads and writes the
+ * rows whose product is not exactly 1 once, each one-qubit pair the state
+ * once, every other op its diaq_op_apply_bytes (in place on the fly,
+ * out of place stored). With host buffers the first and last ops may run
+ * slice by slice outside any pair or run. Host only. */
+diaq_status diaq_simulate_bytes(const diaq_op_t* ops, int32_t count, int64_t* bytes);
 
 /* ------------------------------------------------------------------------
  * Unitary simulation - Section II-A (a circuit's unitary as the product of

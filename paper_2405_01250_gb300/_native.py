@@ -91,6 +91,7 @@ SIGNATURES = {
     "diaq_unitary_chain": (ctypes.c_int, [_gp, ctypes.c_int32, _dp, ctypes.c_int32, ctypes.c_int, ctypes.c_int32,
                                           _i64p, _i64p, _vp, ctypes.POINTER(_op)]),
     "diaq_simulate": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "diaq_simulate_bytes": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _i64p]),
     "diaq_simulate_timed": (ctypes.c_int, [ctypes.POINTER(_op), ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
                                            ctypes.POINTER(ctypes.c_float)]),
     "diaq_norm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int, _dp, _vp]),

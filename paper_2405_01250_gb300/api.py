@@ -254,6 +254,14 @@ def simulate(ops, psi_in, psi_out, work0: torch.Tensor, work1: torch.Tensor | No
     return (psi_out, [tl[0], tl[1], tl[2]]) if timeline else psi_out
 
 
+def simulate_bytes(ops) -> int:
+    """HBM bytes that simulate moves for ops on a device state (diaq_simulate_bytes)."""
+    arr = (ctypes.c_void_p * len(ops))(*[o.handle.value for o in ops])
+    b = ctypes.c_int64(0)
+    check(lib().diaq_simulate_bytes(arr, len(ops), ctypes.byref(b)))
+    return int(b.value)
+
+
 def norm(psi: torch.Tensor, stream=None) -> float:
     _check_state(psi, "psi")
     out = ctypes.c_double(0)

@@ -69,6 +69,8 @@ struct BInst {
     int32_t n;
     int32_t gate_begin, gate_end;
     int32_t exec_begin, exec_end;    // execution list of the per-gate kernel (gates and diagonal runs)
+    int32_t exec_fwd_begin;          // the forward sweep starts here: past the leading product layer
+    int32_t init_tab;                // that layer's chunk tables (product_layer), or -1: start from |0...0>
     int32_t exec_rev_begin;          // the reverse sweep stops here: the earliest entry with a gradient term
     int32_t block_begin, block_end;  // window blocks of the instance (window-fused kernel)
     int32_t param_begin, n_params;
@@ -101,8 +103,10 @@ struct BatchArgs {
     const int32_t* exec;       // gate index, or -1 - run index
     const PhaseRun* runs;      // diagonal runs (weight form)
     const double2* ptabs;      // their phase tables: (run, direction) at (2 run + dir) PR_TAB_WEIGHT
+    const double2* init;       // product-layer tables of the instances (BInst::init_tab)
     const BTerm* terms;
     const double2* ltab;       // weight tables of the observables' term groups (lambda_tables)
+    int lflags;                // LAM_* flags that hold for every instance
     const int32_t* sched;      // instance ids, team-major: sched[team_first[c] .. team_first[c+1])
     const int32_t* team_first;
     const double* theta;
@@ -314,7 +318,14 @@ __device__ __forceinline__ void rot_angle(const BGate& g, const double* theta, b
 // bits, the chunks' values summed. A real W (real coefficients, even Y
 // counts) then costs two fused multiply-adds. Arithmetic in the state's
 // precision.
-template <typename R>
+// FL: LAM_REAL when every group's weight is real, LAM_COUNT when every group
+// is looked up by its count of odd parities; with both the loop issues no
+// FP64 instruction that a group does not need (branches whose FP64 work the
+// compiler would predicate off, but still issue, are compiled out).
+constexpr int LAM_REAL = 1;
+constexpr int LAM_COUNT = 2;
+
+template <typename R, int FL = 0>
 __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, const double2* tab,
                                                       int t0, int t1, int64_t i) {
     using A = amp_t<R>;
@@ -325,7 +336,7 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
         const uint64_t j = uint64_t(i) ^ h.x;
         const int gn = h.gn;
         R wr, wi;
-        if (h.gmode == 0) {
+        if ((FL & LAM_COUNT) || h.gmode == 0) {
             int m = 0;
             for (int u = t; u < t + gn; ++u) m += __popcll(j & terms[u].z) & 1;
             const double2 w = tab[h.gtab + m];
@@ -349,7 +360,7 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
             }
         }
         const A pj = psi[j];
-        if (h.greal) {
+        if ((FL & LAM_REAL) || h.greal) {
             lr = fma(wr, pj.x, lr);
             li = fma(wr, pj.y, li);
         } else {
@@ -362,6 +373,54 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
     o.x = lr;
     o.y = li;
     return o;
+}
+
+// lam = H psi over a grid-stride share, returning this thread's share of
+// Re <psi|lam>; fl (LAM_*) selects the instantiation outside the loop.
+template <typename R, int FL>
+__device__ __noinline__ double lambda_share(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
+                                            const double2* tab, int t0, int t1, int64_t N, int64_t tid,
+                                            int64_t nth) {
+    using A = amp_t<R>;
+    Acc<R> e;
+    for (int64_t i = tid; i < N; i += nth) {
+        const A o = pauli_lambda_elem<R, FL>(psi, terms, tab, t0, t1, i);
+        lam[i] = o;
+        const A pi = psi[i];
+        e.add_dot(pi.x, o.x, pi.y, o.y);
+    }
+    return e.value();
+}
+
+template <typename R>
+__device__ __forceinline__ double lambda_share_any(int fl, const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
+                                                   const double2* tab, int t0, int t1, int64_t N, int64_t tid,
+                                                   int64_t nth) {
+    switch (fl & 3) {
+        case 3: return lambda_share<R, 3>(psi, lam, terms, tab, t0, t1, N, tid, nth);
+        case 1: return lambda_share<R, 1>(psi, lam, terms, tab, t0, t1, N, tid, nth);
+        case 2: return lambda_share<R, 2>(psi, lam, terms, tab, t0, t1, N, tid, nth);
+        default: return lambda_share<R, 0>(psi, lam, terms, tab, t0, t1, N, tid, nth);
+    }
+}
+
+// Amplitude i of a product state from its chunk tables: tab[c 256 + v] is
+// the factor of the qubits 8c .. 8c+7 for their bit values v, the product
+// taken over the chunks in order (product_layer).
+template <typename R>
+__device__ __forceinline__ amp_t<R> product_amp(const double2* __restrict__ tab, int n, int64_t i) {
+    const double2 t0 = tab[i & 255];
+    amp_t<R> p;
+    p.x = R(t0.x);
+    p.y = R(t0.y);
+    for (int c = 1; 8 * c < n; ++c) {
+        const double2 t = tab[c * 256 + int((i >> (8 * c)) & 255)];
+        const R qr = R(t.x), qi = R(t.y);
+        const R tr = fma(p.x, qr, -p.y * qi);
+        p.y = fma(p.x, qi, p.y * qr);
+        p.x = tr;
+    }
+    return p;
 }
 
 // The pair of one-qubit X/Y rotations (a then b) for the team kernel:
@@ -451,23 +510,27 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
         // scaled form: the stored states are the true ones / inv_s (thread 0
         // tracks it; the energy and every partial are multiplied by inv_s^2)
         double inv_s = 1.0;
-        // |0...0>
+        // |0...0>, or the state after the leading product layer directly
         for (int64_t i = tid; i < N; i += nthreads) {
             A v;
-            v.x = R(i == 0 ? 1 : 0);
-            v.y = R(0);
+            if (I.init_tab >= 0) {
+                v = product_amp<R>(a.init + I.init_tab, I.n, i);
+            } else {
+                v.x = R(i == 0 ? 1 : 0);
+                v.y = R(0);
+            }
             psi[i] = v;
         }
         team_sync(C);
         // forward sweep
-        for (int x = I.exec_begin; x < I.exec_end; ++x) {
+        for (int x = I.exec_fwd_begin; x < I.exec_end; ++x) {
             const int gi = a.exec[x];
             if (gi < 0) {  // a diagonal run: one pass with its phase table
                 const PhaseRun& run = a.runs[-1 - gi];
                 phase_tables_load<PR_TAB_WEIGHT>(a.ptabs + int64_t(-1 - gi) * 2 * PR_TAB_WEIGHT, 2 * run.n_rot + 1,
                                                  &ptab);
                 double acc[1];
-                phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
+                phase_run_sweep<R, PR_WEIGHT, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
                 team_sync(C);
                 continue;
             }
@@ -525,14 +588,9 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
             team_sync(C);
         }
         // lambda = H psi and the energy Re <psi|lambda>
-        Acc<R> e;
-        for (int64_t i = tid; i < N; i += nthreads) {
-            const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
-            lam[i] = o;
-            const A pi = psi[i];
-            e.add_dot(pi.x, o.x, pi.y, o.y);
-        }
-        const double es = block_sum(e.value(), warps);
+        const double es = block_sum(lambda_share_any<R>(a.lflags, psi, lam, a.terms, a.ltab, I.term_begin, I.term_end,
+                                                        N, tid, nthreads),
+                                    warps);
         if (threadIdx.x == 0) part[0 * C + rank] = scaled ? es * (inv_s * inv_s) : es;
         team_sync(C);
         // reverse sweep: partial Im <lam|P|psi>, then U^dag on psi and lam
@@ -543,7 +601,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
                 phase_tables_load<PR_TAB_WEIGHT>(a.ptabs + (int64_t(-1 - gi) * 2 + 1) * PR_TAB_WEIGHT,
                                                  2 * run.n_rot + 1, &ptab);
                 double acc[1];
-                phase_run_sweep<R, false, PR_TAB_WEIGHT>(psi, lam, I.n, run, ptab, tid, nthreads, acc);
+                phase_run_sweep<R, PR_WEIGHT, PR_TAB_WEIGHT>(psi, lam, I.n, run, ptab, tid, nthreads, acc);
                 const double sum = block_sum(acc[0], warps);
                 if (threadIdx.x == 0) {
                     part[int64_t(run.rot_slot[0]) * C + rank] = scaled ? sum * (inv_s * inv_s) : sum;
@@ -929,6 +987,7 @@ struct diaq_batch_s {
     BTerm* d_terms = nullptr;
     std::vector<double2> ltab;   // lambda weight tables (lambda_tables)
     double2* d_ltab = nullptr;
+    int lflags = LAM_REAL | LAM_COUNT;  // what holds for every instance
     void* d_arena = nullptr;
     double* d_theta = nullptr;
     double* d_partials = nullptr;
@@ -955,6 +1014,8 @@ struct diaq_batch_s {
     int32_t* d_exec = nullptr;
     PhaseRun* d_runs = nullptr;
     double2* d_ptabs = nullptr;  // phase tables of the runs (k_phase_tables)
+    std::vector<double2> init_tabs;  // product-layer tables of the instances (product_layer)
+    double2* d_init = nullptr;
     // scaled rotations of the per-gate complex128 kernel: requested (default
     // on) and possible (every instance within the rotation bound)
     bool scaled = true;
@@ -1173,6 +1234,7 @@ static void batch_free(diaq_batch_s* b) {
     if (b->d_exec) cudaFree(b->d_exec);
     if (b->d_runs) cudaFree(b->d_runs);
     if (b->d_ptabs) cudaFree(b->d_ptabs);
+    if (b->d_init) cudaFree(b->d_init);
     for (void* p : {static_cast<void*>(b->d_inst), static_cast<void*>(b->d_gates), static_cast<void*>(b->d_terms),
                     static_cast<void*>(b->d_ltab),
                     b->d_arena, static_cast<void*>(b->d_theta), static_cast<void*>(b->d_partials),
@@ -1191,9 +1253,51 @@ static diaq_status upload(T** d, const std::vector<T>& h) {
     return DIAQ_OK;
 }
 
+// The leading product layer of an execution list: the longest prefix of
+// fixed one-qubit gates on distinct qubits. Applied to |0...0> they give a
+// product state, amplitude i = prod_q u_q[bit q of i][0] (1 or 0 for the
+// qubits outside the layer), which the kernels write directly from one
+// table of 256 entries per chunk of 8 qubits (the product of that chunk's
+// factors for each byte value) instead of running the layer gate by gate.
+// Appends the tables to *tab and returns the layer's length (0: none).
+static int product_layer(const BGate* gates, const int32_t* exec, int count, int n, std::vector<double2>* tab) {
+    std::vector<int> gate_of(size_t(n), -1);
+    int len = 0;
+    for (; len < count; ++len) {
+        const int32_t e = exec[len];
+        if (e < 0) break;
+        const BGate& g = gates[e];
+        if (g.param >= 0 || g.k != 1 || gate_of[size_t(g.t[0])] >= 0) break;
+        gate_of[size_t(g.t[0])] = e;
+    }
+    if (len == 0) return 0;
+    const int chunks = (n + 7) / 8;
+    for (int c = 0; c < chunks; ++c)
+        for (int v = 0; v < 256; ++v) {
+            cplx f(1.0, 0.0);
+            for (int b = 0; b < 8; ++b) {
+                const int q = 8 * c + b;
+                const int bit = (v >> b) & 1;
+                if (q >= n) {
+                    if (bit) f = cplx(0.0, 0.0);
+                    continue;
+                }
+                if (gate_of[size_t(q)] < 0) {
+                    if (bit) f = cplx(0.0, 0.0);
+                } else {
+                    const BGate& g = gates[gate_of[size_t(q)]];
+                    f *= cplx(g.re[2 * bit], g.im[2 * bit]);  // u[bit][0]: column 0, the image of |0>
+                }
+            }
+            tab->push_back(make_double2(f.real(), f.imag()));
+        }
+    return len;
+}
+
 // Group headers and weight tables for the terms [t0, t1) of one observable
 // (sorted by X mask; see pauli_lambda_elem), tables appended to *tab.
-static void lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector<double2>* tab) {
+static int lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector<double2>* tab) {
+    int fl = LAM_REAL | LAM_COUNT;
     for (int t = t0; t < t1;) {
         int u = t;
         while (u < t1 && terms[size_t(u)].x == terms[size_t(t)].x) ++u;
@@ -1207,6 +1311,8 @@ static void lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector
         h.gn = gn;
         h.gtab = int32_t(tab->size());
         h.greal = real ? 1 : 0;
+        if (!real) fl &= ~LAM_REAL;
+        if (!equal) fl &= ~LAM_COUNT;
         if (equal) {  // W = (gn - 2 m) kappa, m terms of odd parity
             h.gmode = 0;
             for (int m = 0; m <= gn; ++m) tab->push_back(make_double2(double(gn - 2 * m) * h.kr, double(gn - 2 * m) * h.ki));
@@ -1229,6 +1335,7 @@ static void lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector
         }
         t = u;
     }
+    return fl;
 }
 
 // The per-gate kernel's execution list of every instance (gates, or weight
@@ -1237,6 +1344,7 @@ static void lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector
 static diaq_status batch_exec(diaq_batch_s* b) {
     b->exec_list.clear();
     b->runs.clear();
+    b->init_tabs.clear();
     int first_run = 0;
     for (BInst& I : b->inst) {
         I.exec_begin = int32_t(b->exec_list.size());
@@ -1249,6 +1357,13 @@ static diaq_status batch_exec(diaq_batch_s* b) {
         for (size_t r = size_t(first_run); r < b->runs.size(); ++r) b->runs[r].param_base = I.param_begin;
         first_run = int(b->runs.size());
         I.exec_end = int32_t(b->exec_list.size());
+        {
+            const int off = int(b->init_tabs.size());
+            const int len = product_layer(b->gates.data(), b->exec_list.data() + I.exec_begin,
+                                          I.exec_end - I.exec_begin, I.n, &b->init_tabs);
+            I.init_tab = len > 0 ? off : -1;
+            I.exec_fwd_begin = I.exec_begin + len;
+        }
         // nothing below the earliest parametric entry feeds a gradient term
         I.exec_rev_begin = I.exec_end;
         for (int x = I.exec_begin; x < I.exec_end; ++x) {
@@ -1261,14 +1376,16 @@ static diaq_status batch_exec(diaq_batch_s* b) {
     }
     b->n_runs = int(b->runs.size());
     for (void* q : {static_cast<void*>(b->d_exec), static_cast<void*>(b->d_runs), static_cast<void*>(b->d_inst),
-                    static_cast<void*>(b->d_ptabs)})
+                    static_cast<void*>(b->d_ptabs), static_cast<void*>(b->d_init)})
         if (q) cudaFree(q);
     b->d_exec = nullptr;
     b->d_runs = nullptr;
     b->d_inst = nullptr;
     b->d_ptabs = nullptr;
+    b->d_init = nullptr;
     if (b->exec_list.empty()) b->exec_list.push_back(0);
     DIAQ_TRY(upload(&b->d_exec, b->exec_list));
+    DIAQ_TRY(upload(&b->d_init, b->init_tabs));
     if (!b->runs.empty()) {
         DIAQ_TRY(upload(&b->d_runs, b->runs));
         const size_t bytes = b->runs.size() * 2 * PR_TAB_WEIGHT * sizeof(double2);
@@ -1358,8 +1475,10 @@ static diaq_status launch_batch(diaq_batch_s* b, cudaStream_t s) {
     a.exec = b->d_exec;
     a.runs = b->d_runs;
     a.ptabs = b->d_ptabs;
+    a.init = b->d_init;
     a.terms = b->d_terms;
     a.ltab = b->d_ltab;
+    a.lflags = b->lflags;
     a.sched = b->d_sched;
     a.team_first = b->d_team_first;
     a.theta = b->d_theta;
@@ -1624,7 +1743,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
         std::stable_sort(b->terms.begin() + I.term_begin, b->terms.end(),
                          [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
         I.term_end = int32_t(b->terms.size());
-        lambda_tables(b->terms, I.term_begin, I.term_end, &b->ltab);
+        b->lflags &= lambda_tables(b->terms, I.term_begin, I.term_end, &b->ltab);
         I.n_slots = slots;
         I.psi_off = arena;
         arena += ((int64_t(1) << n) + align - 1) / align * align;
@@ -2007,26 +2126,24 @@ __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, 
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                                     const double2* ltab, int n_terms, int64_t N, double* part) {
-    using A = amp_t<R>;
+                                                     const double2* ltab, int n_terms, int64_t N, double* part,
+                                                     int lflags) {
     __shared__ double warps[32];
-    Acc<R> e;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
-        const A o = pauli_lambda_elem<R>(psi, terms, ltab, 0, n_terms, i);
-        lam[i] = o;
-        const A pi = psi[i];
-        e.add_dot(pi.x, o.x, pi.y, o.y);
-    }
-    const double es = block_sum(e.value(), warps);
+    const double v = lambda_share_any<R>(lflags, psi, lam, terms, ltab, 0, n_terms, N,
+                                         int64_t(blockIdx.x) * blockDim.x + threadIdx.x,
+                                         int64_t(gridDim.x) * blockDim.x);
+    const double es = block_sum(v, warps);
     if (threadIdx.x == 0) part[blockIdx.x] = es;
 }
 
 template <typename R>
-__global__ void k_plan_init(const amp_t<R>* psi0, amp_t<R>* psi, int64_t N) {
+__global__ void k_plan_init(const amp_t<R>* psi0, amp_t<R>* psi, int64_t N, const double2* init, int n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
         amp_t<R> v;
         if (psi0) {
             v = psi0[i];
+        } else if (init) {  // the state after the leading product layer
+            v = product_amp<R>(init, n, i);
         } else {
             v.x = R(i == 0 ? 1 : 0);
             v.y = R(0);
@@ -2088,7 +2205,10 @@ __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam
     double acc[PR_MAX_CROT];
     const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t nth = int64_t(gridDim.x) * blockDim.x;
-    phase_run_sweep<R, true, PR_TAB_ALL>(psi, REV ? lam : nullptr, n, rs, tb, tid, nth, acc);
+    if (rs.kind == PR_WEIGHT)
+        phase_run_sweep<R, PR_WEIGHT, PR_TAB_ALL>(psi, REV ? lam : nullptr, n, rs, tb, tid, nth, acc);
+    else
+        phase_run_sweep<R, PR_CHUNKS, PR_TAB_ALL>(psi, REV ? lam : nullptr, n, rs, tb, tid, nth, acc);
     if (!REV) return;
     if (rs.kind == PR_WEIGHT) {
         // the run's sum in the first member's row, zeros in the others' (same
@@ -2168,9 +2288,10 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
         }
         int neg = 0;  // CZs across chunks (the others are in the tables)
         for (int k = rs.n_cz_in; k < rs.n_cz; ++k) neg ^= __popcll(uint64_t(i) & rs.cz[k]) == 2;
+        const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
         A ph;
-        ph.x = neg ? -pr : pr;
-        ph.y = neg ? -pi : pi;
+        ph.x = flip_sign(pr, m);
+        ph.y = flip_sign(pi, m);
         const A p = psi[i];
         const A l = lam[i];
         const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
@@ -2549,6 +2670,7 @@ struct diaq_adjoint_plan_s {
     BGate* d_gates = nullptr;
     BTerm* d_terms = nullptr;
     double2* d_ltab = nullptr;   // lambda weight tables (lambda_tables)
+    int lflags = 0;              // LAM_* flags of the observable
     RotAngles* d_angles = nullptr;
     void* d_psi = nullptr;
     void* d_lam = nullptr;
@@ -2575,6 +2697,8 @@ struct diaq_adjoint_plan_s {
     // requested (default on); active when n_events > 0
     bool scaled = true;
     bool pairs = true;               // fuse consecutive one-qubit X/Y rotations (k_plan_rot2)
+    int layer_len = 0;               // leading product layer of the per-gate sweep (from |0...0>)
+    double2* d_init = nullptr;       // its chunk tables (product_layer)
     FinTerm* d_fin = nullptr;        // gradient terms per parameter, in gate order
     int32_t* d_fin_first = nullptr;  // n_params + 1 offsets into d_fin
     ScaleEvent* d_events = nullptr;
@@ -2584,6 +2708,8 @@ struct diaq_adjoint_plan_s {
 
 
 static void plan_free(diaq_adjoint_plan_s* p) {
+    if (p->d_init) cudaFree(p->d_init);
+    p->d_init = nullptr;
     if (p->d_ptabs) cudaFree(p->d_ptabs);
     p->d_ptabs = nullptr;
     if (p->d_fin) cudaFree(p->d_fin);
@@ -2677,6 +2803,24 @@ static diaq_status plan_scale_events(diaq_adjoint_plan_s* p) {
     return DIAQ_OK;
 }
 
+// The leading product layer of the per-gate sweep when it starts from
+// |0...0> (uploaded before the graph is recorded).
+static diaq_status plan_product_layer(diaq_adjoint_plan_s* p) {
+    if (p->d_init) cudaFree(p->d_init);
+    p->d_init = nullptr;
+    p->layer_len = 0;
+    if (p->window > 0 || p->psi0) return DIAQ_OK;
+    std::vector<int32_t> order;
+    size_t stop = 0;
+    plan_order(p, &order, &stop);
+    std::vector<double2> tab;
+    const int len = product_layer(p->gates.data(), order.data(), int(order.size()), p->n, &tab);
+    if (len == 0) return DIAQ_OK;
+    DIAQ_TRY(upload(&p->d_init, tab));
+    p->layer_len = len;
+    return DIAQ_OK;
+}
+
 template <typename R>
 static diaq_status plan_record(diaq_adjoint_plan_s* p) {
     using A = amp_t<R>;
@@ -2687,7 +2831,8 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
     DIAQ_CUDA(cudaMemcpyAsync(p->d_theta, p->h_theta, sizeof(double) * size_t(std::max(p->n_params, 1)),
                               cudaMemcpyHostToDevice, s));
     if (p->n_gates) k_plan_angles<<<(p->n_gates + 127) / 128, 128, 0, s>>>(p->d_gates, p->n_gates, p->d_theta, p->d_angles);
-    k_plan_init<R><<<p->P, 256, 0, s>>>(static_cast<const A*>(p->psi0), psi, N);
+    k_plan_init<R><<<p->P, 256, 0, s>>>(static_cast<const A*>(p->psi0), psi, N,
+                                        p->layer_len > 0 ? p->d_init : nullptr, p->n);
     DIAQ_CUDA(cudaGetLastError());
     if (p->window > 0) {
         auto block = [&](const WinBlock& w, A* l) {
@@ -2699,7 +2844,8 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
                     psi, l, p->d_gates, p->d_angles, p->d_wg, w, p->n, p->d_part, p->P);
         };
         for (const WinBlock& w : p->blocks) block(w, nullptr);
-        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part);
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part,
+                                             p->lflags);
         for (size_t b = p->blocks.size(); b-- > 0;) block(p->blocks[b], lam);
         DIAQ_CUDA(cudaGetLastError());
     } else {
@@ -2717,7 +2863,7 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
             return p->pairs && g1 >= 0 && g2 >= 0 && pair_gate(p->gates[size_t(g1)]) &&
                    pair_gate(p->gates[size_t(g2)]) && p->gates[size_t(g1)].t[0] != p->gates[size_t(g2)].t[0];
         };
-        for (size_t oi = 0; oi < order.size(); ++oi) {
+        for (size_t oi = size_t(p->layer_len); oi < order.size(); ++oi) {  // the product layer is in psi already
             const int32_t g = order[oi];
             if (g < 0) {
                 k_plan_phase<R, false><<<p->P, 256, 0, s>>>(psi, nullptr, p->d_runs + (-1 - g),
@@ -2739,7 +2885,8 @@ static diaq_status plan_record(diaq_adjoint_plan_s* p) {
             else
                 DIAQ_TRY(launch_gate_local(p->n, p->dtype, p->fwd[size_t(g)], nullptr, psi, psi, s));
         }
-        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part);
+        k_plan_lambda<R><<<p->P, 256, 0, s>>>(psi, lam, p->d_terms, p->d_ltab, p->n_terms, N, p->d_part,
+                                             p->lflags);
         // nothing below the earliest parametric entry feeds a gradient term
         for (size_t oi = order.size(); oi-- > stop;) {
             const int32_t g = order[oi];
@@ -2833,6 +2980,7 @@ static diaq_status plan_capture(diaq_adjoint_plan_s* p) {
     }
     cudaGraph_t graph = nullptr;
     DIAQ_TRY(plan_scale_events(p));
+    DIAQ_TRY(plan_product_layer(p));
     DIAQ_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
     diaq_status st = p->dtype == DIAQ_C128 ? plan_record<double>(p) : plan_record<float>(p);
     cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
@@ -2937,7 +3085,7 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
     std::stable_sort(terms.begin(), terms.end(), [](const BTerm& u, const BTerm& v) { return u.x < v.x; });
     p->n_terms = n_terms;
     std::vector<double2> ltab;
-    if (st == DIAQ_OK) lambda_tables(terms, 0, int(terms.size()), &ltab);
+    if (st == DIAQ_OK) p->lflags = lambda_tables(terms, 0, int(terms.size()), &ltab);
     cudaError_t e = cudaSuccess;
     if (st == DIAQ_OK && (e = cudaGetDevice(&p->device)) != cudaSuccess) st = cuda_fail(e, "cudaGetDevice");
     if (st == DIAQ_OK) {

@@ -117,7 +117,79 @@ diaq_status launch_diag_t(int n, const GateDesc& g, const void* x, void* y, cuda
     return DIAQ_OK;
 }
 
+// A diagonal over up to DIAG_BIG_K qubits from a table in device memory:
+// diaq_simulate merges runs of consecutive diagonal ops (a QFT's controlled
+// phases, a TFIM layer's ZZ rotations) into one such pass when their union
+// of targets is small enough, so each amplitude takes one complex multiply
+// for the whole run instead of one per op. Row i's entry is table[c],
+// c = sum_q (bit t[q] of i) << q; rows whose entry is exactly 1 (bit set in
+// skip) are neither read nor written. In place.
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_bigdiag(amp_t<R>* x, int64_t N, const __grid_constant__ BigDiagArgs a,
+                                                       const double2* __restrict__ table,
+                                                       const uint32_t* __restrict__ skip) {
+    using A = amp_t<R>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int E = 1 << a.k;
+    A* tab = reinterpret_cast<A*>(smem);
+    uint32_t* sk = reinterpret_cast<uint32_t*>(smem + sizeof(A) * size_t(E));
+    for (int c = threadIdx.x; c < E; c += blockDim.x) {
+        const double2 v = table[c];
+        A e;
+        e.x = R(v.x);
+        e.y = R(v.y);
+        tab[c] = e;
+    }
+    for (int w = threadIdx.x; w < (E + 31) / 32; w += blockDim.x) sk[w] = skip[w];
+    __syncthreads();
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += T * kDiagUnroll) {
+        int c[kDiagUnroll];
+        A v[kDiagUnroll];
+#pragma unroll
+        for (int u = 0; u < kDiagUnroll; ++u) {
+            const int64_t i = i0 + u * T;
+            int cc = -1;
+            if (i < N && DIAQ_BOUNDS_OK(i, N, BS_APPLY_DIAG)) {
+                cc = 0;
+                for (int q = 0; q < a.k; ++q) cc |= int((i >> a.t[q]) & 1) << q;
+                if ((sk[cc >> 5] >> (cc & 31)) & 1) cc = -1;  // entry exactly 1: untouched
+            }
+            c[u] = cc;
+            if (cc >= 0) v[u] = ld_stream(x + i);
+        }
+#pragma unroll
+        for (int u = 0; u < kDiagUnroll; ++u) {
+            if (c[u] < 0) continue;
+            const A m = tab[c[u]];
+            A o;
+            o.x = m.x * v[u].x;
+            o.x = fma(-m.y, v[u].y, o.x);
+            o.y = m.x * v[u].y;
+            o.y = fma(m.y, v[u].x, o.y);
+            st_stream(x + i0 + u * T, o);
+        }
+    }
+}
+
 }  // namespace
+
+diaq_status launch_bigdiag_inplace(int n, diaq_dtype dt, const BigDiagArgs& a, const double2* table,
+                                   const uint32_t* skip, void* x, cudaStream_t s) {
+    if (a.k < 1 || a.k > DIAG_BIG_K) return fail(DIAQ_ERR_ARG, "merged diagonal over %d qubits", a.k);
+    const int64_t N = int64_t(1) << n;
+    const size_t E = size_t(1) << a.k;
+    const size_t smem = (dt == DIAQ_C128 ? 16 : 8) * E + 4 * ((E + 31) / 32);
+    const int64_t want = (N + 256 * kDiagUnroll - 1) / (256 * kDiagUnroll);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, int64_t(device_sm_count()) * 6));
+    DIAQ_PRELAUNCH("k_apply_bigdiag");
+    if (dt == DIAQ_C128)
+        k_apply_bigdiag<double><<<blocks, 256, smem, s>>>(reinterpret_cast<double2*>(x), N, a, table, skip);
+    else
+        k_apply_bigdiag<float><<<blocks, 256, smem, s>>>(reinterpret_cast<float2*>(x), N, a, table, skip);
+    DIAQ_CUDA(cudaGetLastError());
+    return DIAQ_OK;
+}
 
 bool is_diagonal(const GateDesc& g) {
     const int D = 1 << g.k;

@@ -1106,6 +1106,89 @@ static std::vector<SimStep> plan_sim_scaling(const diaq_op_t* ops, int count) {
     return st;
 }
 
+// Runs of consecutive diagonal on-the-fly ops (plain steps) whose union of
+// targets has at most DIAG_BIG_K qubits, merged by diaq_simulate into one
+// pass each (k_apply_bigdiag): the table holds, for every value of the
+// union's bits, the product of the ops' diagonal entries, so every changed
+// amplitude takes one complex multiply for the whole run.
+struct SimMerge {
+    int first = 0, last = 0;  // ops [first, last]
+    BigDiagArgs args{};
+    size_t tab_off = 0, skip_off = 0;
+};
+
+static std::vector<SimMerge> plan_diag_merges(const diaq_op_t* ops, int lo, int hi, const std::vector<SimStep>& steps,
+                                              diaq_dtype dt, std::vector<double2>* tab, std::vector<uint32_t>* skip) {
+    std::vector<SimMerge> out;
+    auto eligible = [&](int i) {
+        return ops[i]->variant == DIAQ_ONTHEFLY && steps[size_t(i)].action == SIM_PLAIN && is_diagonal(ops[i]->gate);
+    };
+    for (int i = lo; i < hi;) {
+        if (!eligible(i)) {
+            ++i;
+            continue;
+        }
+        uint64_t qs = 0;
+        for (int a = 0; a < ops[i]->gate.k; ++a) qs |= uint64_t(1) << ops[i]->gate.targets[a];
+        int j = i;
+        while (j + 1 < hi && eligible(j + 1)) {
+            uint64_t q2 = qs;
+            for (int a = 0; a < ops[j + 1]->gate.k; ++a) q2 |= uint64_t(1) << ops[j + 1]->gate.targets[a];
+            if (__builtin_popcountll(q2) > DIAG_BIG_K) break;
+            qs = q2;
+            ++j;
+        }
+        if (j == i) {
+            ++i;
+            continue;
+        }
+        SimMerge m;
+        m.first = i;
+        m.last = j;
+        m.args.k = __builtin_popcountll(qs);
+        int pos[64];
+        for (int b = 0, q = 0; b < 64; ++b)
+            if ((qs >> b) & 1) {
+                m.args.t[q] = b;
+                pos[b] = q++;
+            }
+        const size_t E = size_t(1) << m.args.k;
+        m.tab_off = tab->size();
+        m.skip_off = skip->size();
+        skip->resize(skip->size() + (E + 31) / 32, 0u);
+        for (size_t c = 0; c < E; ++c) {
+            cplx v(1.0, 0.0);
+            for (int o = i; o <= j; ++o) {
+                const GateDesc& g = ops[o]->gate;
+                const int D = 1 << g.k;
+                int l = 0;
+                for (int a = 0; a < g.k; ++a) l |= int((c >> pos[g.targets[a]]) & 1) << (g.k - 1 - a);
+                v *= g.m[size_t(l) * D + l];
+            }
+            tab->push_back(make_double2(v.real(), v.imag()));
+            const bool one = dt == DIAQ_C128 ? (v.real() == 1.0 && v.imag() == 0.0)
+                                             : (float(v.real()) == 1.0f && float(v.imag()) == 0.0f);
+            if (one) (*skip)[m.skip_off + c / 32] |= 1u << (c % 32);
+        }
+        out.push_back(m);
+        i = j + 1;
+    }
+    return out;
+}
+
+// Two ops that diaq_simulate runs in one pass: on-the-fly, one qubit each,
+// different qubits, every entry non-zero (so neither has identity rows to
+// skip or structural zeros to exploit).
+static bool sim_pairable(const diaq_op_s* a, const diaq_op_s* b) {
+    auto dense1 = [](const diaq_op_s* o) {
+        if (o->variant != DIAQ_ONTHEFLY || o->gate.k != 1 || o->gate.m.size() != 4) return false;
+        for (const cplx& v : o->gate.m)
+            if (v == cplx(0.0, 0.0)) return false;
+        return true;
+    };
+    return dense1(a) && dense1(b) && a->gate.targets[0] != b->gate.targets[0];
+}
+
 static diaq_status run_inplace_step(const diaq_op_s* op, const SimStep& st, void* x, int64_t g0, int64_t g1,
                                     cudaStream_t s) {
     if (st.action == SIM_SCALED) {
@@ -1116,10 +1199,12 @@ static diaq_status run_inplace_step(const diaq_op_s* op, const SimStep& st, void
     return run_inplace(op, x, g0, g1, s);
 }
 
-// Streams and events of one diaq_simulate call, released on every path.
+// Streams, events and device buffers of one diaq_simulate call, released on
+// every path.
 struct SimResources {
     cudaStream_t cin = nullptr, cout = nullptr;
     std::vector<cudaEvent_t> events;
+    std::vector<std::pair<void*, cudaStream_t>> dev;  // stream-ordered allocations
     cudaEvent_t make(bool timing) {
         cudaEvent_t e = nullptr;
         if (cudaEventCreateWithFlags(&e, timing ? cudaEventDefault : cudaEventDisableTiming) != cudaSuccess) return nullptr;
@@ -1127,6 +1212,8 @@ struct SimResources {
         return e;
     }
     ~SimResources() {
+        for (auto& d : dev) cudaFreeAsync(d.first, d.second);
+        for (auto& d : dev) cudaStreamSynchronize(d.second);
         if (cin) cudaStreamSynchronize(cin);
         if (cout) cudaStreamSynchronize(cout);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -1223,9 +1310,43 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         if (timing) DIAQ_CUDA(cudaEventRecord(t_in, s));
     }
     if (pipe_out && !out_sent) last = count - 1;
+    // merged diagonal runs: their tables go to the device once, on `stream`
+    std::vector<double2> mtab;
+    std::vector<uint32_t> mskip;
+    const std::vector<SimMerge> merges = plan_diag_merges(ops, first, last, steps, dt, &mtab, &mskip);
+    double2* d_mtab = nullptr;
+    if (!merges.empty()) {
+        const size_t tb = mtab.size() * sizeof(double2), sb = mskip.size() * sizeof(uint32_t);
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_mtab), tb + sb, s);
+        if (e != cudaSuccess) return fail(DIAQ_ERR_ALLOC, "cudaMallocAsync(merged diagonal tables): %s", cudaGetErrorString(e));
+        R.dev.push_back({d_mtab, s});
+        DIAQ_CUDA(cudaMemcpyAsync(d_mtab, mtab.data(), tb, cudaMemcpyHostToDevice, s));
+        DIAQ_CUDA(cudaMemcpyAsync(reinterpret_cast<char*>(d_mtab) + tb, mskip.data(), sb, cudaMemcpyHostToDevice, s));
+    }
+    const uint32_t* d_mskip =
+        d_mtab ? reinterpret_cast<const uint32_t*>(reinterpret_cast<const char*>(d_mtab) + mtab.size() * sizeof(double2))
+               : nullptr;
+    size_t next_merge = 0;
     void* cur = work0;
     void* other = work1;
     for (int i = first; i < last; ++i) {
+        if (next_merge < merges.size() && merges[next_merge].first == i) {
+            const SimMerge& m = merges[next_merge++];
+            DIAQ_TRY(launch_bigdiag_inplace(n, dt, m.args, d_mtab + m.tab_off, d_mskip + m.skip_off, cur, s));
+            i = m.last;
+            continue;
+        }
+        // two consecutive one-qubit ops with no zero entry on different
+        // qubits run in one pass (k_apply_pair1), each in its own form
+        if (i + 1 < last && sim_pairable(ops[i], ops[i + 1])) {
+            const SimStep& sa = steps[size_t(i)];
+            const SimStep& sb = steps[size_t(i + 1)];
+            DIAQ_TRY(launch_pair1_inplace(n, dt, sa.action == SIM_FOLD ? sa.folded : ops[i]->gate,
+                                          sa.action == SIM_SCALED, sb.action == SIM_FOLD ? sb.folded : ops[i + 1]->gate,
+                                          sb.action == SIM_SCALED, cur, s));
+            ++i;
+            continue;
+        }
         if (ops[i]->variant == DIAQ_ONTHEFLY) {
             DIAQ_TRY(run_inplace_step(ops[i], steps[size_t(i)], cur, 0,
                                       ops[i]->gate.k <= 3 ? int64_t(1) << (n - ops[i]->gate.k) : 0, s));
@@ -1274,6 +1395,49 @@ diaq_status diaq_simulate_timed(const diaq_op_t* ops, int32_t count, const void*
         DIAQ_CUDA(cudaEventElapsedTime(&timeline_ms[1], t_start, t_compute));
         DIAQ_CUDA(cudaEventElapsedTime(&timeline_ms[2], t_start, t_end));
     }
+    return DIAQ_OK;
+}
+
+diaq_status diaq_simulate_bytes(const diaq_op_t* ops, int32_t count, int64_t* bytes) {
+    clear_error();
+    if (count < 0 || (count && !ops) || !bytes) return fail(DIAQ_ERR_ARG, "bad op list or NULL bytes");
+    *bytes = 0;
+    if (count == 0) return DIAQ_OK;
+    const int n = ops[0]->n;
+    const diaq_dtype dt = ops[0]->dtype;
+    for (int i = 0; i < count; ++i) {
+        if (!ops[i]) return fail(DIAQ_ERR_ARG, "op %d is NULL", i);
+        if (ops[i]->n != n || ops[i]->dtype != dt) return fail(DIAQ_ERR_SHAPE, "op %d has another size or dtype", i);
+    }
+    const int64_t N = int64_t(1) << n;
+    const int64_t s = int64_t(amp_bytes(dt));
+    const std::vector<SimStep> steps = plan_sim_scaling(ops, count);
+    std::vector<double2> tab;
+    std::vector<uint32_t> skip;
+    const std::vector<SimMerge> merges = plan_diag_merges(ops, 0, count, steps, dt, &tab, &skip);
+    size_t next_merge = 0;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (next_merge < merges.size() && merges[next_merge].first == i) {
+            const SimMerge& m = merges[next_merge++];
+            const int64_t E = int64_t(1) << m.args.k;
+            int64_t changed = 0;
+            for (int64_t c = 0; c < E; ++c)
+                if (!((skip[m.skip_off + size_t(c / 32)] >> (c % 32)) & 1)) ++changed;
+            total += 2 * (N / E) * changed * s;
+            i = m.last;
+            continue;
+        }
+        if (i + 1 < count && sim_pairable(ops[i], ops[i + 1])) {
+            total += 2 * N * s;
+            ++i;
+            continue;
+        }
+        int64_t b = 0;
+        DIAQ_TRY(diaq_op_apply_bytes(ops[i], ops[i]->variant == DIAQ_ONTHEFLY ? 1 : 0, &b));
+        total += b;
+    }
+    *bytes = total;
     return DIAQ_OK;
 }
 

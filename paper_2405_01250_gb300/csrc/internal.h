@@ -170,6 +170,19 @@ int64_t inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);
 bool gate_scaled1_sigma(const GateDesc& g, double* sigma);
 diaq_status launch_gate_scaled1_range(int n, const GateDesc& g, const void* x, void* y, int64_t g_begin,
                                       int64_t g_end, double* sigma, cudaStream_t s);
+// One in-place pass of two one-qubit gates on different qubits (a then b),
+// each in the scaled form (complex128) or general.
+diaq_status launch_pair1_inplace(int n, diaq_dtype dt, const GateDesc& ga, bool sa, const GateDesc& gb, bool sb,
+                                 void* x, cudaStream_t s);
+// A merged run of diagonal ops (diaq_simulate): up to DIAG_BIG_K targets,
+// the table index takes bit t[q] of the row as its bit q.
+constexpr int DIAG_BIG_K = 11;
+struct BigDiagArgs {
+    int k;
+    int t[DIAG_BIG_K];
+};
+diaq_status launch_bigdiag_inplace(int n, diaq_dtype dt, const BigDiagArgs& a, const double2* table,
+                                   const uint32_t* skip, void* x, cudaStream_t s);
 bool is_diagonal(const GateDesc& g);
 diaq_status launch_diag(int n, diaq_dtype dt, const GateDesc& g, const void* x, void* y, cudaStream_t s);
 int64_t diag_inplace_bytes(int n, diaq_dtype dt, const GateDesc& g);

@@ -132,21 +132,24 @@ __device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
 // One run over a grid-stride share [tid, N) of the state. Forward
 // (lam == nullptr): psi <- D psi. Reverse: the gradient terms first, then
 // psi <- D^dag psi, lam <- D^dag lam (tables built for the direction).
-// Gradient terms go to acc[]: weight form acc[0] (the run's sum
-// sum_i W(i) t_i); chunk form (CHUNKS only) one per rotation.
-template <typename R, bool CHUNKS, int E>
+// FORM (PR_WEIGHT or PR_CHUNKS) is the run's form, fixed at compile time so
+// that no FP64 work of the other form is issued predicated off. Gradient
+// terms go to acc[]: weight form acc[0] (the run's sum sum_i W(i) t_i);
+// chunk form one per rotation.
+template <typename R, int FORM, int E>
 __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
                                              const PhaseRun& r, const PhaseTables<E>& tb, int64_t tid, int64_t nth,
                                              double* acc) {
     using A = amp_t<R>;
+    constexpr bool CH = FORM == PR_CHUNKS;
     const int64_t N = int64_t(1) << n;
     const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
     Acc<R> a_w;
-    Acc<R> a_c[CHUNKS ? PR_MAX_CROT : 1];
+    Acc<R> a_c[CH ? PR_MAX_CROT : 1];
     for (int64_t i = tid; i < N; i += nth) {
         A ph;
         int w = 0;
-        if (!CHUNKS || r.kind == PR_WEIGHT) {
+        if (!CH) {
             for (int g = 0; g < r.n_rot; ++g) w += (__popcll(uint64_t(i) & r.rot_z[g]) & 1) ? -1 : 1;
             ph.x = R(tb.re[w + r.n_rot]);
             ph.y = R(tb.im[w + r.n_rot]);
@@ -161,14 +164,15 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
             }
             int neg = 0;  // CZs across chunks (the others are in the tables)
             for (int k = r.n_cz_in; k < r.n_cz; ++k) neg ^= __popcll(uint64_t(i) & r.cz[k]) == 2;
-            ph.x = neg ? -pr : pr;
-            ph.y = neg ? -pi : pi;
+            const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
+            ph.x = flip_sign(pr, m);
+            ph.y = flip_sign(pi, m);
         }
         const A p = psi[i];
         if (lam) {
             const A l = lam[i];
             const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
-            if (!CHUNKS || r.kind == PR_WEIGHT) {
+            if (!CH) {
                 if constexpr (sizeof(R) == 8) {
                     a_w.s = fma(double(w), t, a_w.s);
                 } else {
@@ -176,7 +180,7 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
                 }
             } else {
 #pragma unroll
-                for (int g = 0; g < (CHUNKS ? PR_MAX_CROT : 1); ++g) {
+                for (int g = 0; g < (CH ? PR_MAX_CROT : 1); ++g) {
                     if (g >= r.n_rot) break;
                     a_c[g].add(flip_sign(t, (uint64_t(i) & r.rot_z[g]) ? 0x80000000u : 0u));
                 }
@@ -185,10 +189,10 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
         }
         psi[i] = cmul<R>(ph, p);
     }
-    if (!CHUNKS || r.kind == PR_WEIGHT) {
+    if (!CH) {
         acc[0] = a_w.value();
     } else {
-        for (int g = 0; g < r.n_rot && g < (CHUNKS ? PR_MAX_CROT : 1); ++g) acc[g] = a_c[g].value();
+        for (int g = 0; g < r.n_rot && g < (CH ? PR_MAX_CROT : 1); ++g) acc[g] = a_c[g].value();
     }
 }
 

@@ -190,3 +190,43 @@ def test_plan_rotation_pairs_match_single_launches_and_oracle(api, dtype, scaled
         assert abs(e1 - e_ref) < 1e-11 and np.max(np.abs(g1 - g_ref)) < 1e-10
     else:
         assert abs(e1 - e_ref) < 2e-5 and np.max(np.abs(g1 - g_ref)) < 5e-5
+
+
+def _layer_circuit(n, rng):
+    """A leading layer of dense one-qubit gates on all qubits but the last
+    (written directly as a product state), a second gate on qubit 3 (which
+    ends the layer), then rotations and CZs."""
+    g = [synth.Gate((q,), synth.random_gate(1, rng, "dense")) for q in range(n - 1)]
+    g.append(synth.Gate((3,), synth.H))
+    p = 0
+    for i in range(3 * n):
+        g.append(synth.Gate((int(rng.integers(n)),), None, param=p, gen="XYZ"[i % 3]))
+        p += 1
+        if i % 5 == 4:
+            a, b = rng.choice(n, size=2, replace=False)
+            g.append(synth.Gate((int(a), int(b)), synth.CZ))
+    return synth.Circuit(n, g, theta=rng.uniform(0, 2 * math.pi, size=p))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_leading_product_layer_plan_and_batch(api, dtype):
+    rng = np.random.default_rng(12)
+    n = 10
+    circs = [_layer_circuit(n, rng) for _ in range(3)]
+    obs = synth.ansatz_observable(n)
+    psi0 = synth.basis_state(n, 0)
+    tol_e, tol_g = (1e-11, 1e-10) if dtype == torch.complex128 else (2e-5, 5e-5)
+    for c in circs[:1]:
+        plan = api.AdjointPlan(c.gates, c.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+        e, g = plan.run(c.theta)
+        plan.close()
+        assert abs(e - oracle.energy(c, obs, psi0)) < tol_e
+        assert np.max(np.abs(g - oracle.param_shift_grad(c, obs, psi0))) < tol_g
+    desc = [(c.n, c.gates, c.n_params, (obs.xmask, obs.zmask, obs.coeff)) for c in circs]
+    b = api.Batch(desc, dtype=dtype)
+    b.set_launch(2, 128)
+    E, G = b.run(np.concatenate([c.theta for c in circs]))
+    b.close()
+    for i, c in enumerate(circs):
+        assert abs(E[i] - oracle.energy(c, obs, psi0)) < tol_e
+        assert np.max(np.abs(G[i] - oracle.param_shift_grad(c, obs, psi0))) < tol_g
