@@ -291,10 +291,24 @@ def run_ours(args, rank, world):
         f1.record(stream)
         torch.cuda.synchronize()
         fms = f0.elapsed_time(f1) / args.steps
+        # the same ops through diaq_simulate in place on the device state
+        # (consecutive fused ops merge into passes of up to 11 qubits; H in
+        # the scaled form)
+        sbytes = api.simulate_bytes(fops)
+        api.simulate(fops, c, c, c)
+        torch.cuda.synchronize()
+        f0.record(stream)
+        for _ in range(args.steps):
+            api.simulate(fops, c, c, c)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        sms = f0.elapsed_time(f1) / args.steps
         fused = {"workload": f"qft-{n} complex128, runs of controlled phases fused into diagonal ops, in place",
                  "ops": len(fops), "gates": len(ops), "ms_per_step": fms, "gates_per_s": len(ops) / (fms / 1e3),
                  "moved_bytes_per_step": fbytes, "moved_gbs": fbytes / (fms / 1e3) / 1e9,
                  "speedup_vs_unfused_in_place": (inplace["ms_per_step"] / fms) if inplace else None,
+                 "simulate": {"ms_per_step": sms, "gates_per_s": len(ops) / (sms / 1e3),
+                              "moved_bytes_per_step": sbytes, "moved_gbs": sbytes / (sms / 1e3) / 1e9},
                  "norm": api.norm(c)}
         del c, fops
 
@@ -1003,8 +1017,8 @@ def bench_random(api, n=24, depth=40, ref=None):
     out = {"workload": f"random-{n} depth {depth}: {len(circ.gates)} gates, in place",
            "reference": "FP64 oracle (cpu_baseline leg)" if ref is not None else None}
     for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
-        for fused in (False, True):
-            if fused:
+        for mode in ("plain", "fused", "simulate"):
+            if mode == "fused":
                 ops = api.build_fused(circ.gates, n, 3, 6, dtype=dt, commuting=True)
                 ks = [op.info()["k"] for op in ops]
             else:
@@ -1016,11 +1030,14 @@ def bench_random(api, n=24, depth=40, ref=None):
                 x[0] = 1
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                for op in ops:
-                    api.apply(op, x, x)
+                if mode == "simulate":  # the user-level call: pairs and merged CZ runs
+                    api.simulate(ops, x, x, x)
+                else:
+                    for op in ops:
+                        api.apply(op, x, x)
                 torch.cuda.synchronize()
                 el = time.perf_counter() - t0
-            key = name + ("_fused" if fused else "")
+            key = name + ("" if mode == "plain" else "_" + mode)
             rec = {"ops": len(ops), "s_per_circuit": el, "gates_per_s": len(circ.gates) / el, "norm": api.norm(x)}
             if ref is not None:
                 rec.update(state_errors(x.cpu().numpy(), ref))
