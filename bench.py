@@ -657,9 +657,9 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
         el = (time.perf_counter() - t0) / r
         out[f"adjoint_graph_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3,
                                         "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(g - grads[name])))}
-        # window-fused sweeps: blocks of <= w qubits, one launch per block
         # window-fused sweeps: blocks of <= w qubits, one launch per block, with
-        # 1 or 4 threads per group; the autotuner keeps the fastest sweep
+        # 1 or 4 threads per group, and the per-gate sweep at 2, 4 and 8
+        # blocks per SM; the autotuner keeps the fastest
         tune = plan.autotune(circ.theta, reps=5)
         for _ in range(2):
             e, gw = plan.run(circ.theta)
@@ -670,9 +670,10 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
         w, ln, nb = plan.sweep()
         energies_grads[f"adjoint_autotuned_{name}"] = (e, gw)
         out[f"adjoint_autotuned_{name}"] = {
-            "window": w, "lanes": ln, "launches_per_sweep": nb, "grads_per_s": 1.0 / elw,
+            "window": w, "lanes": ln, "blocks": plan.blocks(), "launches_per_sweep": nb, "grads_per_s": 1.0 / elw,
             "ms_per_gradient": elw * 1e3, "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(gw - grads[name]))),
-            "device_ms_by_sweep": {f"w{tw}_l{tl}": m for tw, tl, m in tune["tried"]}}
+            "device_ms_by_sweep": {f"w{tw}_l{tl}" + (f"_b{tb}" if tw == 0 else ""): m
+                                   for tw, tl, tb, m in tune["tried"]}}
         plan.close()
     out["c64_vs_c128_max_abs_grad_diff"] = float(np.max(np.abs(grads["c64"] - grads["c128"])))
     # the same plan, complex128: gate by gate (diagonal runs off), and with
@@ -1252,6 +1253,7 @@ def main():
     ap.add_argument("--adjoint-window", type=int, default=0)
     ap.add_argument("--adjoint-lanes", type=int, default=1)
     ap.add_argument("--adjoint-reps", type=int, default=3)
+    ap.add_argument("--adjoint-blocks", type=int, default=0, help="per-gate sweep blocks (0: two per SM)")
     ap.add_argument("--batch-cluster", type=int, default=8)
     ap.add_argument("--batch-threads", type=int, default=256)
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
@@ -1301,6 +1303,7 @@ def main():
         dt = torch.complex128 if args.adjoint_dtype == "c128" else torch.complex64
         plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), 20, dtype=dt)
         plan.set_sweep(args.adjoint_window, args.adjoint_lanes)
+        plan.set_blocks(args.adjoint_blocks)
         for _ in range(2):
             plan.run(circ.theta)
         torch.cuda.synchronize()
@@ -1310,7 +1313,7 @@ def main():
         el = (time.perf_counter() - t0) / max(1, args.adjoint_reps)
         print(json.dumps({"workload": "ansatz-20 adjoint plan", "dtype": args.adjoint_dtype, "sweep": plan.sweep(),
                           "runs": plan.runs(), "scaled": plan.scaled(), "pairs": plan.pairs(),
-                          "ms_per_gradient": el * 1e3, "energy": e}), flush=True)
+                          "blocks": plan.blocks(), "ms_per_gradient": el * 1e3, "energy": e}), flush=True)
         plan.close()
         return
     rank, world = _dist()

@@ -140,11 +140,13 @@ class diaq_apply_tuning(ctypes.Structure):
 class diaq_plan_tuning(ctypes.Structure):
     _fields_ = [
         ("n_tried", ctypes.c_int32),
-        ("window", ctypes.c_int32 * 8),
-        ("lanes", ctypes.c_int32 * 8),
-        ("ms", ctypes.c_float * 8),
+        ("window", ctypes.c_int32 * 12),
+        ("lanes", ctypes.c_int32 * 12),
+        ("blocks", ctypes.c_int32 * 12),
+        ("ms", ctypes.c_float * 12),
         ("best_window", ctypes.c_int32),
         ("best_lanes", ctypes.c_int32),
+        ("best_blocks", ctypes.c_int32),
         ("best_ms", ctypes.c_float),
     ]
 
@@ -177,6 +179,8 @@ SIGNATURES.update({
     "diaq_adjoint_plan_set_sweep": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),
     "diaq_adjoint_plan_get_sweep": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
     "diaq_adjoint_plan_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int32, ctypes.POINTER(diaq_plan_tuning)]),
+    "diaq_adjoint_plan_set_blocks": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "diaq_adjoint_plan_get_blocks": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32)]),
     "diaq_batch_set_window": (ctypes.c_int, [_vp, ctypes.c_int32]),
     "diaq_batch_get_window": (ctypes.c_int, [_vp, _i32p]),
     "diaq_batch_set_sweep": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32]),

@@ -534,8 +534,18 @@ class AdjointPlan:
         rep = N.diaq_plan_tuning()
         check(lib().diaq_adjoint_plan_autotune(self.handle, _dptr(th) if len(th) else None, int(reps),
                                                ctypes.byref(rep)))
-        return {"tried": [(rep.window[i], rep.lanes[i], rep.ms[i]) for i in range(rep.n_tried)],
-                "best_window": rep.best_window, "best_lanes": rep.best_lanes, "best_ms": rep.best_ms}
+        return {"tried": [(rep.window[i], rep.lanes[i], rep.blocks[i], rep.ms[i]) for i in range(rep.n_tried)],
+                "best_window": rep.best_window, "best_lanes": rep.best_lanes, "best_blocks": rep.best_blocks,
+                "best_ms": rep.best_ms}
+
+    def set_blocks(self, blocks: int) -> None:
+        """Blocks of the per-gate sweep's kernels; 0 = two per SM (diaq_adjoint_plan_set_blocks)."""
+        check(lib().diaq_adjoint_plan_set_blocks(self.handle, int(blocks)))
+
+    def blocks(self) -> int:
+        a = ctypes.c_int32(0)
+        check(lib().diaq_adjoint_plan_get_blocks(self.handle, ctypes.byref(a)))
+        return int(a.value)
 
     def set_sweep(self, window: int, lanes: int) -> None:
         """window 0 (per gate) or 2..5, with 1 or 4 threads per group (diaq_adjoint_plan_set_sweep)."""

@@ -103,9 +103,9 @@ struct BatchArgs {
     const int32_t* exec;       // gate index, or -1 - run index
     const PhaseRun* runs;      // diagonal runs (weight form)
     const double2* ptabs;      // their phase tables: (run, direction) at (2 run + dir) PR_TAB_WEIGHT
-    const double2* init;       // product-layer tables of the instances (BInst::init_tab)
+    const void* init;          // product-layer tables of the instances (BInst::init_tab), state precision
     const BTerm* terms;
-    const double2* ltab;       // weight tables of the observables' term groups (lambda_tables)
+    const void* ltab;          // weight tables of the observables' term groups (lambda_tables), state precision
     int lflags;                // LAM_* flags that hold for every instance
     const int32_t* sched;      // instance ids, team-major: sched[team_first[c] .. team_first[c+1])
     const int32_t* team_first;
@@ -326,7 +326,7 @@ constexpr int LAM_REAL = 1;
 constexpr int LAM_COUNT = 2;
 
 template <typename R, int FL = 0>
-__device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, const double2* tab,
+__device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const BTerm* terms, const amp_t<R>* tab,
                                                       int t0, int t1, int64_t i) {
     using A = amp_t<R>;
     R lr = R(0), li = R(0);
@@ -339,9 +339,9 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
         if ((FL & LAM_COUNT) || h.gmode == 0) {
             int m = 0;
             for (int u = t; u < t + gn; ++u) m += __popcll(j & terms[u].z) & 1;
-            const double2 w = tab[h.gtab + m];
-            wr = R(w.x);
-            wi = R(w.y);
+            const A w = tab[h.gtab + m];
+            wr = w.x;
+            wi = w.y;
         } else {
             wr = R(0);
             wi = R(0);
@@ -349,13 +349,13 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
                 int bits = 0;
                 const int u1 = min(t + 8 * c + 8, t + gn);
                 for (int u = t + 8 * c; u < u1; ++u) bits |= (__popcll(j & terms[u].z) & 1) << (u - t - 8 * c);
-                const double2 w = tab[h.gtab + 256 * c + bits];
+                const A w = tab[h.gtab + 256 * c + bits];
                 if (c == 0) {
-                    wr = R(w.x);
-                    wi = R(w.y);
+                    wr = w.x;
+                    wi = w.y;
                 } else {
-                    wr += R(w.x);
-                    wi += R(w.y);
+                    wr += w.x;
+                    wi += w.y;
                 }
             }
         }
@@ -379,7 +379,7 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
 // Re <psi|lam>; fl (LAM_*) selects the instantiation outside the loop.
 template <typename R, int FL>
 __device__ __noinline__ double lambda_share(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                            const double2* tab, int t0, int t1, int64_t N, int64_t tid,
+                                            const amp_t<R>* tab, int t0, int t1, int64_t N, int64_t tid,
                                             int64_t nth) {
     using A = amp_t<R>;
     Acc<R> e;
@@ -394,7 +394,7 @@ __device__ __noinline__ double lambda_share(const amp_t<R>* psi, amp_t<R>* lam, 
 
 template <typename R>
 __device__ __forceinline__ double lambda_share_any(int fl, const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                                   const double2* tab, int t0, int t1, int64_t N, int64_t tid,
+                                                   const amp_t<R>* tab, int t0, int t1, int64_t N, int64_t tid,
                                                    int64_t nth) {
     switch (fl & 3) {
         case 3: return lambda_share<R, 3>(psi, lam, terms, tab, t0, t1, N, tid, nth);
@@ -408,14 +408,11 @@ __device__ __forceinline__ double lambda_share_any(int fl, const amp_t<R>* psi, 
 // the factor of the qubits 8c .. 8c+7 for their bit values v, the product
 // taken over the chunks in order (product_layer).
 template <typename R>
-__device__ __forceinline__ amp_t<R> product_amp(const double2* __restrict__ tab, int n, int64_t i) {
-    const double2 t0 = tab[i & 255];
-    amp_t<R> p;
-    p.x = R(t0.x);
-    p.y = R(t0.y);
+__device__ __forceinline__ amp_t<R> product_amp(const amp_t<R>* __restrict__ tab, int n, int64_t i) {
+    amp_t<R> p = tab[i & 255];
     for (int c = 1; 8 * c < n; ++c) {
-        const double2 t = tab[c * 256 + int((i >> (8 * c)) & 255)];
-        const R qr = R(t.x), qi = R(t.y);
+        const amp_t<R> t = tab[c * 256 + int((i >> (8 * c)) & 255)];
+        const R qr = t.x, qi = t.y;
         const R tr = fma(p.x, qr, -p.y * qi);
         p.y = fma(p.x, qi, p.y * qr);
         p.x = tr;
@@ -473,6 +470,60 @@ __device__ __forceinline__ void team_rot1_coefs(const BGate& g, const double* th
     }
 }
 
+// complex64 teams take up to three consecutive one-qubit X/Y rotations on
+// distinct qubits per pass (rotq_groups): one cluster barrier per tile. (The
+// adjoint plan keeps pairs in complex64 too: there one launch per tile ran
+// slower than one per pair.)
+constexpr int kTeamTile = 3;
+
+// The tile of the execution list at position x (dir +1 forward, -1 backward,
+// not past lim): its length and gate indices in execution order.
+__device__ __forceinline__ int team_tile(const BatchArgs& a, int x, int dir, int lim, int* g) {
+    int nq = 0;
+    uint64_t used = 0;
+    int gs[kTeamTile];
+    for (int y = x; nq < kTeamTile; y += dir) {
+        if (dir > 0 ? y >= lim : y < lim) break;
+        const int e = a.exec[y];
+        if (e < 0 || !pair_gate(a.gates[e])) break;
+        const uint64_t bit = uint64_t(1) << a.gates[e].t[0];
+        if (used & bit) break;
+        used |= bit;
+        gs[nq++] = e;
+    }
+    for (int j = 0; j < nq; ++j) g[j] = dir > 0 ? gs[j] : gs[nq - 1 - j];
+    return nq;
+}
+
+// RotG of a tile member for one direction (thread 0 writes it to shared).
+template <typename R>
+__device__ __forceinline__ void team_rotg(const BGate& G, const double* th, bool dagger, RotG<R>* out, int* q) {
+    double cs, kr, ki;
+    rot_angle(G, th, dagger, &cs, &kr, &ki);
+    const bool neg0 = (G.rot.zl & 1) != 0;
+    out->a = R(cs);
+    out->br[0] = R(neg0 ? -kr : kr);
+    out->bi[0] = R(neg0 ? -ki : ki);
+    out->br[1] = R(kr);
+    out->bi[1] = R(ki);
+    const double2 p0 = mul_ipow(make_double2(neg0 ? -1.0 : 1.0, 0.0), G.rot.ny);
+    const double2 p1 = mul_ipow(make_double2(1.0, 0.0), G.rot.ny);
+    out->pr[0] = R(p0.x);
+    out->pi[0] = R(p0.y);
+    out->pr[1] = R(p1.x);
+    out->pi[1] = R(p1.y);
+    *q = G.t[0];
+}
+
+template <typename R, int NQ>
+__device__ __noinline__ void team_rotq(amp_t<R>* psi, amp_t<R>* lam, int n, const int* q, const RotG<R>* rot,
+                                       int64_t tid, int64_t nth, double* part) {
+    int qq[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) qq[j] = q[j];
+    rotq_groups<R, NQ>(psi, lam, n, qq, rot, tid, nth, part);  // coefficients read from shared memory
+}
+
 // Phase tables of every diagonal run, both directions, once per replay:
 // block (run, direction) writes its table at out + (2 run + dir) stride.
 __global__ void __launch_bounds__(256) k_phase_tables(const PhaseRun* __restrict__ runs, const double* __restrict__ theta,
@@ -488,11 +539,13 @@ template <typename R>
 __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
     using A = amp_t<R>;
     __shared__ StepMats<R> mats;
-    __shared__ PhaseTables<PR_TAB_WEIGHT> ptab;
+    __shared__ PhaseTables<PR_TAB_WEIGHT, R> ptab;
     __shared__ double warps[32];
     __shared__ double ang[3];
     __shared__ double sang[2];  // scaled form: m1, V's coefficient
     __shared__ double pang[6];  // a fused pair: Rot1 coefficients of both members
+    __shared__ RotG<R> tg[kTeamTile];  // a complex64 tile's rotations
+    __shared__ int tq[kTeamTile];
     const int C = a.C;
     const bool scaled = sizeof(R) == 8 && a.scaled != 0;
     const int rank = C == 1 ? 0 : (int)cg::this_cluster().block_rank();
@@ -514,7 +567,7 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
         for (int64_t i = tid; i < N; i += nthreads) {
             A v;
             if (I.init_tab >= 0) {
-                v = product_amp<R>(a.init + I.init_tab, I.n, i);
+                v = product_amp<R>(reinterpret_cast<const A*>(a.init) + I.init_tab, I.n, i);
             } else {
                 v.x = R(i == 0 ? 1 : 0);
                 v.y = R(0);
@@ -533,6 +586,21 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
                 phase_run_sweep<R, PR_WEIGHT, PR_TAB_WEIGHT>(psi, nullptr, I.n, run, ptab, tid, nthreads, acc);
                 team_sync(C);
                 continue;
+            }
+            if constexpr (sizeof(R) == 4) {  // complex64: a tile of up to three rotations
+                int tgs[kTeamTile];
+                const int nq = team_tile(a, x, +1, I.exec_end, tgs);
+                if (nq >= 2) {
+                    if (threadIdx.x == 0)
+                        for (int j = 0; j < nq; ++j) team_rotg<R>(a.gates[tgs[j]], th, false, &tg[j], &tq[j]);
+                    __syncthreads();
+                    double pv[kTeamTile];
+                    if (nq == 3) team_rotq<R, 3>(psi, nullptr, I.n, tq, tg, tid, nthreads, pv);
+                    else team_rotq<R, 2>(psi, nullptr, I.n, tq, tg, tid, nthreads, pv);
+                    team_sync(C);
+                    x += nq - 1;
+                    continue;
+                }
             }
             if (x + 1 < I.exec_end && pair_entries(a.gates, gi, a.exec[x + 1])) {  // a fused pair
                 const BGate& ga = a.gates[gi];
@@ -588,7 +656,8 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
             team_sync(C);
         }
         // lambda = H psi and the energy Re <psi|lambda>
-        const double es = block_sum(lambda_share_any<R>(a.lflags, psi, lam, a.terms, a.ltab, I.term_begin, I.term_end,
+        const double es = block_sum(lambda_share_any<R>(a.lflags, psi, lam, a.terms, reinterpret_cast<const A*>(a.ltab),
+                                                        I.term_begin, I.term_end,
                                                         N, tid, nthreads),
                                     warps);
         if (threadIdx.x == 0) part[0 * C + rank] = scaled ? es * (inv_s * inv_s) : es;
@@ -609,6 +678,25 @@ __global__ void __launch_bounds__(256, 2) k_batch(const BatchArgs a) {
                 }
                 team_sync(C);
                 continue;
+            }
+            if constexpr (sizeof(R) == 4) {
+                int tgs[kTeamTile];
+                const int nq = team_tile(a, x, -1, I.exec_rev_begin, tgs);
+                if (nq >= 2) {
+                    if (threadIdx.x == 0)
+                        for (int j = 0; j < nq; ++j) team_rotg<R>(a.gates[tgs[j]], th, true, &tg[j], &tq[j]);
+                    __syncthreads();
+                    double pv[kTeamTile];
+                    if (nq == 3) team_rotq<R, 3>(psi, lam, I.n, tq, tg, tid, nthreads, pv);
+                    else team_rotq<R, 2>(psi, lam, I.n, tq, tg, tid, nthreads, pv);
+                    for (int j = 0; j < nq; ++j) {
+                        const double sj = block_sum(pv[j], warps);
+                        if (threadIdx.x == 0) part[int64_t(a.gates[tgs[j]].slot) * C + rank] = sj;
+                    }
+                    team_sync(C);
+                    x -= nq - 1;
+                    continue;
+                }
             }
             if (x - 1 >= I.exec_rev_begin && pair_entries(a.gates, a.exec[x - 1], gi)) {  // a fused pair (a, b)
                 const BGate& ga = a.gates[a.exec[x - 1]];
@@ -786,7 +874,7 @@ __global__ void __launch_bounds__(WIN_THREADS) k_batch_win(const BatchArgs a, co
         // lambda = H psi and the energy Re <psi|lambda>
         Acc<R> e;
         for (int64_t i = tid; i < N; i += nthreads) {
-            const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
+            const A o = pauli_lambda_elem<R>(psi, a.terms, reinterpret_cast<const A*>(a.ltab), I.term_begin, I.term_end, i);
             lam[i] = o;
             const A pi = psi[i];
             e.add_dot(pi.x, o.x, pi.y, o.y);
@@ -877,7 +965,7 @@ __global__ void __launch_bounds__(WIN_THREADS, 4) k_batch_win_l(const BatchArgs 
                 // lambda = H psi and the energy Re <psi|lambda>
                 Acc<R> e;
                 for (int64_t i = tid; i < N; i += nthreads) {
-                    const A o = pauli_lambda_elem<R>(psi, a.terms, a.ltab, I.term_begin, I.term_end, i);
+                    const A o = pauli_lambda_elem<R>(psi, a.terms, reinterpret_cast<const A*>(a.ltab), I.term_begin, I.term_end, i);
                     lam[i] = o;
                     const A pi = psi[i];
                     e.add_dot(pi.x, o.x, pi.y, o.y);
@@ -986,7 +1074,7 @@ struct diaq_batch_s {
     BGate* d_gates = nullptr;
     BTerm* d_terms = nullptr;
     std::vector<double2> ltab;   // lambda weight tables (lambda_tables)
-    double2* d_ltab = nullptr;
+    void* d_ltab = nullptr;      // in the batch's precision
     int lflags = LAM_REAL | LAM_COUNT;  // what holds for every instance
     void* d_arena = nullptr;
     double* d_theta = nullptr;
@@ -1015,7 +1103,7 @@ struct diaq_batch_s {
     PhaseRun* d_runs = nullptr;
     double2* d_ptabs = nullptr;  // phase tables of the runs (k_phase_tables)
     std::vector<double2> init_tabs;  // product-layer tables of the instances (product_layer)
-    double2* d_init = nullptr;
+    void* d_init = nullptr;      // in the batch's precision
     // scaled rotations of the per-gate complex128 kernel: requested (default
     // on) and possible (every instance within the rotation bound)
     bool scaled = true;
@@ -1253,6 +1341,15 @@ static diaq_status upload(T** d, const std::vector<T>& h) {
     return DIAQ_OK;
 }
 
+// A table of complex values uploaded in the state's precision (float2 for
+// complex64), so kernels read it without a conversion per amplitude.
+static diaq_status upload_amps(diaq_dtype dt, const std::vector<double2>& h, void** d) {
+    if (dt == DIAQ_C128) return upload(reinterpret_cast<double2**>(d), h);
+    std::vector<float2> f(h.size());
+    for (size_t i = 0; i < h.size(); ++i) f[i] = make_float2(float(h[i].x), float(h[i].y));
+    return upload(reinterpret_cast<float2**>(d), f);
+}
+
 // The leading product layer of an execution list: the longest prefix of
 // fixed one-qubit gates on distinct qubits. Applied to |0...0> they give a
 // product state, amplitude i = prod_q u_q[bit q of i][0] (1 or 0 for the
@@ -1385,7 +1482,7 @@ static diaq_status batch_exec(diaq_batch_s* b) {
     b->d_init = nullptr;
     if (b->exec_list.empty()) b->exec_list.push_back(0);
     DIAQ_TRY(upload(&b->d_exec, b->exec_list));
-    DIAQ_TRY(upload(&b->d_init, b->init_tabs));
+    DIAQ_TRY(upload_amps(b->dtype, b->init_tabs, &b->d_init));
     if (!b->runs.empty()) {
         DIAQ_TRY(upload(&b->d_runs, b->runs));
         const size_t bytes = b->runs.size() * 2 * PR_TAB_WEIGHT * sizeof(double2);
@@ -1764,7 +1861,7 @@ diaq_status diaq_batch_create(int32_t n_inst, const int32_t* n_qubits, const int
     if (st == DIAQ_OK) st = batch_exec(b);
     if (st == DIAQ_OK) st = upload(&b->d_gates, b->gates);
     if (st == DIAQ_OK) st = upload(&b->d_terms, b->terms);
-    if (st == DIAQ_OK) st = upload(&b->d_ltab, b->ltab);
+    if (st == DIAQ_OK) st = upload_amps(b->dtype, b->ltab, &b->d_ltab);
     if (st == DIAQ_OK) {
         const size_t bytes = size_t(std::max<int64_t>(arena, 1)) * amp_bytes(dtype);
         if ((e = cudaMalloc(&b->d_arena, bytes)) != cudaSuccess)
@@ -2126,10 +2223,10 @@ __global__ void __launch_bounds__(256) k_plan_rot(amp_t<R>* psi, amp_t<R>* lam, 
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                                     const double2* ltab, int n_terms, int64_t N, double* part,
+                                                     const void* ltab, int n_terms, int64_t N, double* part,
                                                      int lflags) {
     __shared__ double warps[32];
-    const double v = lambda_share_any<R>(lflags, psi, lam, terms, ltab, 0, n_terms, N,
+    const double v = lambda_share_any<R>(lflags, psi, lam, terms, reinterpret_cast<const amp_t<R>*>(ltab), 0, n_terms, N,
                                          int64_t(blockIdx.x) * blockDim.x + threadIdx.x,
                                          int64_t(gridDim.x) * blockDim.x);
     const double es = block_sum(v, warps);
@@ -2137,13 +2234,13 @@ __global__ void __launch_bounds__(256) k_plan_lambda(const amp_t<R>* psi, amp_t<
 }
 
 template <typename R>
-__global__ void k_plan_init(const amp_t<R>* psi0, amp_t<R>* psi, int64_t N, const double2* init, int n) {
+__global__ void k_plan_init(const amp_t<R>* psi0, amp_t<R>* psi, int64_t N, const void* init, int n) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
         amp_t<R> v;
         if (psi0) {
             v = psi0[i];
         } else if (init) {  // the state after the leading product layer
-            v = product_amp<R>(init, n, i);
+            v = product_amp<R>(reinterpret_cast<const amp_t<R>*>(init), n, i);
         } else {
             v.x = R(i == 0 ? 1 : 0);
             v.y = R(0);
@@ -2192,7 +2289,7 @@ __global__ void __launch_bounds__(256) k_plan_finish(const FinTerm* __restrict__
 template <typename R, bool REV>
 __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam, const PhaseRun* __restrict__ run,
                                                     const double2* __restrict__ table, int n, double* part, int P) {
-    __shared__ PhaseTables<PR_TAB_ALL> tb;
+    __shared__ PhaseTables<PR_TAB_ALL, R> tb;
     __shared__ PhaseRun rs;
     __shared__ double warps[32];
     {
@@ -2243,7 +2340,7 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
                                                                const double2* __restrict__ table, int n, double* part,
                                                                int P) {
     using A = amp_t<R>;
-    __shared__ PhaseTables<PR_TAB_ALL> tb;
+    __shared__ PhaseTables<PR_TAB_ALL, R> tb;
     __shared__ PhaseRun rs;
     __shared__ double wt[8][6];               // per warp: sum T, then the lane-bit sums S_0 .. S_4
     __shared__ double wv[8][PR_MAX_CROT];     // per warp: the varying-bit sums
@@ -2278,10 +2375,10 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
     Acc<R> tot;
     Acc<R> av[PR_MAX_CROT];
     for (int64_t i = tid; i < N; i += nth) {
-        R pr = R(tb.re[i & 255]), pi = R(tb.im[i & 255]);
+        R pr = tb.re[i & 255], pi = tb.im[i & 255];
         for (int c = 1; c < chunks; ++c) {
             const int e = (c << 8) | int((i >> (8 * c)) & 255);
-            const R qr = R(tb.re[e]), qi = R(tb.im[e]);
+            const R qr = tb.re[e], qi = tb.im[e];
             const R tr = fma(pr, qr, -pi * qi);
             pi = fma(pr, qi, pi * qr);
             pr = tr;
@@ -2669,7 +2766,7 @@ struct diaq_adjoint_plan_s {
     std::vector<GateDesc> fwd, bwd;  // fixed gates: U and U^dag
     BGate* d_gates = nullptr;
     BTerm* d_terms = nullptr;
-    double2* d_ltab = nullptr;   // lambda weight tables (lambda_tables)
+    void* d_ltab = nullptr;      // lambda weight tables (lambda_tables), plan precision
     int lflags = 0;              // LAM_* flags of the observable
     RotAngles* d_angles = nullptr;
     void* d_psi = nullptr;
@@ -2698,7 +2795,7 @@ struct diaq_adjoint_plan_s {
     bool scaled = true;
     bool pairs = true;               // fuse consecutive one-qubit X/Y rotations (k_plan_rot2)
     int layer_len = 0;               // leading product layer of the per-gate sweep (from |0...0>)
-    double2* d_init = nullptr;       // its chunk tables (product_layer)
+    void* d_init = nullptr;          // its chunk tables (product_layer), plan precision
     FinTerm* d_fin = nullptr;        // gradient terms per parameter, in gate order
     int32_t* d_fin_first = nullptr;  // n_params + 1 offsets into d_fin
     ScaleEvent* d_events = nullptr;
@@ -2816,7 +2913,7 @@ static diaq_status plan_product_layer(diaq_adjoint_plan_s* p) {
     std::vector<double2> tab;
     const int len = product_layer(p->gates.data(), order.data(), int(order.size()), p->n, &tab);
     if (len == 0) return DIAQ_OK;
-    DIAQ_TRY(upload(&p->d_init, tab));
+    DIAQ_TRY(upload_amps(p->dtype, tab, &p->d_init));
     p->layer_len = len;
     return DIAQ_OK;
 }
@@ -3125,7 +3222,7 @@ diaq_status diaq_adjoint_plan_create(const diaq_gate* gates, int32_t n_gates, in
         }
     }
     if (st == DIAQ_OK) st = upload(&p->d_terms, terms);
-    if (st == DIAQ_OK) st = upload(&p->d_ltab, ltab);
+    if (st == DIAQ_OK) st = upload_amps(dtype, ltab, &p->d_ltab);
     if (st == DIAQ_OK &&
         ((e = cudaMalloc(reinterpret_cast<void**>(&p->d_angles), sizeof(RotAngles) * size_t(std::max(n_gates, 1)))) != cudaSuccess ||
          (e = cudaMalloc(&p->d_psi, N * ab)) != cudaSuccess || (e = cudaMalloc(&p->d_lam, N * ab)) != cudaSuccess ||
@@ -3281,6 +3378,40 @@ diaq_status diaq_adjoint_plan_get_scaled(diaq_adjoint_plan_t p, int32_t* on, int
     return DIAQ_OK;
 }
 
+diaq_status diaq_adjoint_plan_set_blocks(diaq_adjoint_plan_t p, int32_t blocks) {
+    clear_error();
+    cudaGetLastError();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (blocks < 0) return fail(DIAQ_ERR_ARG, "blocks = %d: use 0 (two per SM) or a positive count", blocks);
+    int dev = -1;
+    DIAQ_CUDA(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(DIAQ_ERR_ARG, "plan was created on device %d but device %d is current", p->device, dev);
+    int sms = 1;
+    DIAQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    const int64_t want = ((int64_t(1) << p->n) / 2 + 255) / 256;  // one group of 2 amplitudes per thread
+    const int64_t b = blocks == 0 ? int64_t(sms) * 2 : std::min<int64_t>(blocks, int64_t(sms) * 64);
+    DIAQ_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->exec) {  // it uses the partials replaced below
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    p->P_gate = int(std::max<int64_t>(1, std::min<int64_t>(want, b)));
+    diaq_status st = plan_windows(p, p->window, p->lanes);
+    if (st != DIAQ_OK) {
+        plan_windows(p, 0, 1);
+        plan_capture(p);
+        return st;
+    }
+    return plan_capture(p);
+}
+
+diaq_status diaq_adjoint_plan_get_blocks(diaq_adjoint_plan_t p, int32_t* blocks) {
+    clear_error();
+    if (!p) return fail(DIAQ_ERR_ARG, "plan is NULL");
+    if (blocks) *blocks = p->P_gate;
+    return DIAQ_OK;
+}
+
 diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
                                        diaq_plan_tuning* report) {
     clear_error();
@@ -3290,20 +3421,15 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
     if (reps < 1) reps = 1;
     const int wins[] = {0, 3, 4, 5, 3, 4, 5};
     const int lns[] = {1, 1, 1, 1, WIN_LANES, WIN_LANES, WIN_LANES};
-    int best_w = 0, best_l = 1, tried = 0;
+    int best_w = 0, best_l = 1, best_b = p->P_gate, tried = 0;
     float best = 1e30f;
     cudaEvent_t e0, e1;
     DIAQ_CUDA(cudaEventCreate(&e0));
     DIAQ_CUDA(cudaEventCreate(&e1));
     if (p->n_params) std::memcpy(p->h_theta, theta, sizeof(double) * size_t(p->n_params));
-    for (int c = 0; c < 7; ++c) {
-        const int w = wins[c], ln = lns[c];
-        if (diaq_adjoint_plan_set_sweep(p, w, ln) != DIAQ_OK) {
-            clear_error();
-            cudaGetLastError();
-            continue;  // this window does not fit the circuit
-        }
-        DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));  // warm
+    // one warm replay, then `reps` timed; recorded in the report, kept if fastest
+    auto measure = [&](int w, int ln, int blocks) -> diaq_status {
+        DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));
         DIAQ_CUDA(cudaEventRecord(e0, p->stream));
         for (int r = 0; r < reps; ++r) DIAQ_CUDA(cudaGraphLaunch(p->exec, p->stream));
         DIAQ_CUDA(cudaEventRecord(e1, p->stream));
@@ -3314,6 +3440,7 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
         if (report && tried < DIAQ_PLAN_TUNE_MAX) {
             report->window[tried] = w;
             report->lanes[tried] = ln;
+            report->blocks[tried] = blocks;
             report->ms[tried] = ms;
         }
         ++tried;
@@ -3321,16 +3448,48 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
             best = ms;
             best_w = w;
             best_l = ln;
+            if (w == 0) best_b = blocks;
+        }
+        return DIAQ_OK;
+    };
+    diaq_status st = DIAQ_OK;
+    for (int c = 0; c < 7 && st == DIAQ_OK; ++c) {
+        const int w = wins[c], ln = lns[c];
+        if (diaq_adjoint_plan_set_sweep(p, w, ln) != DIAQ_OK) {
+            clear_error();
+            cudaGetLastError();
+            continue;  // this window does not fit the circuit
+        }
+        st = measure(w, ln, w == 0 ? p->P_gate : 0);
+    }
+    if (st == DIAQ_OK && tried && best_w == 0) {  // the per-gate sweep at more blocks per SM
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+        if ((st = diaq_adjoint_plan_set_sweep(p, 0, 1)) == DIAQ_OK) {
+            int last = p->P_gate;
+            for (int m : {4, 8}) {
+                if ((st = diaq_adjoint_plan_set_blocks(p, sms * m)) != DIAQ_OK) break;
+                if (p->P_gate == last) continue;  // clamped to the blocks already timed
+                last = p->P_gate;
+                if ((st = measure(0, 1, p->P_gate)) != DIAQ_OK) break;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != DIAQ_OK) return st;
     if (!tried) return fail(DIAQ_ERR_UNSUPPORTED, "no sweep fits");
-    DIAQ_TRY(diaq_adjoint_plan_set_sweep(p, best_w, best_l));
+    if (best_w == 0) {
+        DIAQ_TRY(diaq_adjoint_plan_set_sweep(p, 0, 1));
+        DIAQ_TRY(diaq_adjoint_plan_set_blocks(p, best_b));
+    } else {
+        DIAQ_TRY(diaq_adjoint_plan_set_sweep(p, best_w, best_l));
+    }
     if (report) {
         report->n_tried = std::min(tried, DIAQ_PLAN_TUNE_MAX);
         report->best_window = best_w;
         report->best_lanes = best_l;
+        report->best_blocks = best_w == 0 ? best_b : 0;
         report->best_ms = best;
     }
     return DIAQ_OK;

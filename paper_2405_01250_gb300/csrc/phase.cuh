@@ -60,10 +60,12 @@ struct PhaseRun {
 constexpr int PR_TAB_WEIGHT = 2 * PR_MAX_ROT + 1;
 constexpr int PR_TAB_ALL = PR_MAX_CHUNKS * 256;
 
-template <int E>
+// Stored in the state's precision: a complex64 sweep then converts no table
+// entry per amplitude (a double-to-float conversion takes an FP64 pipe slot).
+template <int E, typename T = double>
 struct PhaseTables {
-    double re[E];
-    double im[E];
+    T re[E];
+    T im[E];
 };
 
 // Entry e of a run's table for one direction (rev: U^dag), from the
@@ -111,12 +113,13 @@ __host__ __device__ __forceinline__ int phase_entries(const PhaseRun& r, int n) 
 
 // Copy a run's table, built once per replay in global memory, into the
 // block's shared tables (all threads take part; synchronises).
-template <int E>
-__device__ __forceinline__ void phase_tables_load(const double2* __restrict__ src, int entries, PhaseTables<E>* tb) {
+template <int E, typename T>
+__device__ __forceinline__ void phase_tables_load(const double2* __restrict__ src, int entries,
+                                                  PhaseTables<E, T>* tb) {
     for (int e = threadIdx.x; e < entries && e < E; e += blockDim.x) {
         const double2 v = src[e];
-        tb->re[e] = v.x;
-        tb->im[e] = v.y;
+        tb->re[e] = T(v.x);
+        tb->im[e] = T(v.y);
     }
     __syncthreads();
 }
@@ -138,7 +141,7 @@ __device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
 // chunk form one per rotation.
 template <typename R, int FORM, int E>
 __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
-                                             const PhaseRun& r, const PhaseTables<E>& tb, int64_t tid, int64_t nth,
+                                             const PhaseRun& r, const PhaseTables<E, R>& tb, int64_t tid, int64_t nth,
                                              double* acc) {
     using A = amp_t<R>;
     constexpr bool CH = FORM == PR_CHUNKS;
@@ -151,13 +154,13 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
         int w = 0;
         if (!CH) {
             for (int g = 0; g < r.n_rot; ++g) w += (__popcll(uint64_t(i) & r.rot_z[g]) & 1) ? -1 : 1;
-            ph.x = R(tb.re[w + r.n_rot]);
-            ph.y = R(tb.im[w + r.n_rot]);
+            ph.x = tb.re[w + r.n_rot];
+            ph.y = tb.im[w + r.n_rot];
         } else {
-            R pr = R(tb.re[i & 255]), pi = R(tb.im[i & 255]);
+            R pr = tb.re[i & 255], pi = tb.im[i & 255];
             for (int c = 1; c < chunks; ++c) {
                 const int e = (c << 8) | int((i >> (8 * c)) & 255);
-                const R qr = R(tb.re[e]), qi = R(tb.im[e]);
+                const R qr = tb.re[e], qi = tb.im[e];
                 const R tr = fma(pr, qr, -pi * qi);
                 pi = fma(pr, qi, pi * qr);
                 pr = tr;

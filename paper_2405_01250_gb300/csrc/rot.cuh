@@ -377,6 +377,116 @@ __device__ __noinline__ void rot2_groups(amp_t<R>* __restrict__ psi, amp_t<R>* _
     *pb = b_pos.value() - b_neg.value();
 }
 
+// One-qubit rotation about X or Y with the generator's structure taken at
+// run time, for the complex64 rotation tiles (FP32 work is cheap there, the
+// passes over the states are not): rows w_r = a x_r + b_r x_{1-r} with
+// a = cos(a/2) and b_r = kappa s_r, and the gradient term
+// sum_r Im conj(l_r) pi_r p_{1-r}, pi_r = i^ny s_r (+-1 for X, +-i for Y).
+template <typename R>
+struct RotG {
+    R a;
+    R br[2], bi[2];
+    R pr[2], pi[2];
+
+    __device__ __forceinline__ void apply(amp_t<R>& x0, amp_t<R>& x1) const {
+        amp_t<R> w0, w1;
+        w0.x = fma(a, x0.x, fma(br[0], x1.x, -bi[0] * x1.y));
+        w0.y = fma(a, x0.y, fma(br[0], x1.y, bi[0] * x1.x));
+        w1.x = fma(a, x1.x, fma(br[1], x0.x, -bi[1] * x0.y));
+        w1.y = fma(a, x1.y, fma(br[1], x0.y, bi[1] * x0.x));
+        x0 = w0;
+        x1 = w1;
+    }
+    __device__ __forceinline__ void partial(const amp_t<R>& l0, const amp_t<R>& l1, const amp_t<R>& p0,
+                                            const amp_t<R>& p1, Acc<R>& acc) const {
+        // t_r = pi_r p_{1-r}; Im conj(l_r) t_r = l.x t.y - l.y t.x
+        const R t0x = pr[0] * p1.x - pi[0] * p1.y, t0y = pr[0] * p1.y + pi[0] * p1.x;
+        const R t1x = pr[1] * p0.x - pi[1] * p0.y, t1y = pr[1] * p0.y + pi[1] * p0.x;
+        acc.add_cross(l0.x, t0y, l0.y, t0x);
+        acc.add_cross(l1.x, t1y, l1.y, t1x);
+    }
+};
+
+// A tile of NQ one-qubit X/Y rotations on distinct qubits q[0..NQ-1],
+// applied in that order (forward) or undone in reverse order with each
+// rotation's partial taken before it is undone (reverse, lam != NULL), on
+// groups of 2^NQ amplitudes held in registers: the states are read and
+// written once per tile. Bit j of a group's local index is qubit q[j].
+template <typename R, int NQ>
+__device__ __forceinline__ void rotq_groups(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
+                                         const int* q, const RotG<R>* rot, int64_t tid, int64_t nthreads,
+                                         double* part) {
+    constexpr int D = 1 << NQ;
+    using Am = amp_t<R>;
+    int st[NQ];
+    int64_t o[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        st[j] = q[j];
+        o[j] = int64_t(1) << q[j];
+    }
+    // ascending targets for insert_zeros (a few swaps of a tiny array)
+#pragma unroll
+    for (int x = 0; x < NQ; ++x)
+#pragma unroll
+        for (int y = 0; y + 1 < NQ - x; ++y)
+            if (st[y] > st[y + 1]) {
+                const int t = st[y];
+                st[y] = st[y + 1];
+                st[y + 1] = t;
+            }
+    Acc<R> acc[NQ];
+    const int64_t G = int64_t(1) << (n - NQ);
+    for (int64_t g = tid; g < G; g += nthreads) {
+        const int64_t b = insert_zeros<NQ>(g, st);
+        int64_t last = b;
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) last += o[j];
+        if (!DIAQ_BOUNDS_OK(last, int64_t(1) << n, BS_ROTATION)) continue;
+        Am p[D], l[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            int64_t off = 0;
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+                if ((c >> j) & 1) off += o[j];
+            p[c] = psi[b + off];
+            if (lam) l[c] = lam[b + off];
+        }
+        if (!lam) {
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (!((c >> j) & 1)) rot[j].apply(p[c], p[c | (1 << j)]);
+        } else {
+#pragma unroll
+            for (int j = NQ - 1; j >= 0; --j) {
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (!((c >> j) & 1)) rot[j].partial(l[c], l[c | (1 << j)], p[c], p[c | (1 << j)], acc[j]);
+#pragma unroll
+                for (int c = 0; c < D; ++c)
+                    if (!((c >> j) & 1)) {
+                        rot[j].apply(p[c], p[c | (1 << j)]);
+                        rot[j].apply(l[c], l[c | (1 << j)]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            int64_t off = 0;
+#pragma unroll
+            for (int j = 0; j < NQ; ++j)
+                if ((c >> j) & 1) off += o[j];
+            psi[b + off] = p[c];
+            if (lam) lam[b + off] = l[c];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) part[j] = acc[j].value();
+}
+
 // The scaled form's coefficients from (cos, kappa) of one direction: the
 // form (m1), V's coefficient cf and sigma (U = sigma V).
 __host__ __device__ __forceinline__ void rot_scaled_coefs(double cs, double kr, double ki, int ny, int* m1, double* cf,

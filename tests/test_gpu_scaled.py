@@ -230,3 +230,63 @@ def test_leading_product_layer_plan_and_batch(api, dtype):
     for i, c in enumerate(circs):
         assert abs(E[i] - oracle.energy(c, obs, psi0)) < tol_e
         assert np.max(np.abs(G[i] - oracle.param_shift_grad(c, obs, psi0))) < tol_g
+
+
+@pytest.mark.parametrize("launch", [(2, 128), (4, 256), (1, 64)])
+def test_complex64_batch_rotation_tiles_match_complex128_and_oracle(api, launch):
+    """complex64 teams take up to three consecutive one-qubit X/Y rotations on
+    distinct qubits per pass (tiles of 2 and 3, lone rotations where a qubit
+    repeats, both sweeps); against the complex128 batch (pairs) and the
+    oracle."""
+    rng = np.random.default_rng(41)
+    n = 9
+    circs = [_xy_circuit(n, rng, 3 + i) for i in range(3)]
+    obs = synth.ansatz_observable(n)
+    desc = [(c.n, c.gates, c.n_params, (obs.xmask, obs.zmask, obs.coeff)) for c in circs]
+    theta = np.concatenate([c.theta for c in circs])
+    out = {}
+    for dt in (torch.complex64, torch.complex128):
+        b = api.Batch(desc, dtype=dt)
+        b.set_launch(*launch)
+        out[dt] = b.run(theta)
+        b.close()
+    (E1, G1), (E2, G2) = out[torch.complex64], out[torch.complex128]
+    psi0 = synth.basis_state(n, 0)
+    for i, c in enumerate(circs):
+        assert abs(E2[i] - oracle.energy(c, obs, psi0)) < 1e-11
+        assert abs(E1[i] - E2[i]) < 2e-5
+        g_ref = oracle.param_shift_grad(c, obs, psi0)
+        assert np.max(np.abs(G2[i] - g_ref)) < 1e-10
+        assert np.max(np.abs(G1[i] - g_ref)) < 5e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_plan_blocks_keep_parity(api, dtype):
+    """The per-gate sweep at other block counts (more partial columns per
+    gradient term, fewer groups per thread, clamped at one group per thread)
+    gives the same energy and gradient; 0 restores two blocks per SM."""
+    rng = np.random.default_rng(7)
+    n = 11
+    circ = _xy_circuit(n, rng, 3)
+    obs = synth.ansatz_observable(n)
+    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    want = (2 ** n // 2 + 255) // 256
+    assert plan.blocks() == min(want, 2 * sms)
+    e0, g0 = plan.run(circ.theta)
+    psi0 = synth.basis_state(n, 0)
+    tol_e, tol_g = (1e-11, 1e-10) if dtype == torch.complex128 else (2e-5, 5e-5)
+    assert abs(e0 - oracle.energy(circ, obs, psi0)) < tol_e
+    g_ref = oracle.param_shift_grad(circ, obs, psi0)
+    assert np.max(np.abs(g0 - g_ref)) < tol_g
+    for b in (1, 3, 1000000):
+        plan.set_blocks(b)
+        assert plan.blocks() == max(1, min(b, want, 64 * sms))
+        e, g = plan.run(circ.theta)
+        if dtype == torch.complex128:
+            assert abs(e - e0) < 1e-12 and np.max(np.abs(g - g0)) < 1e-12, b
+        assert abs(e - oracle.energy(circ, obs, psi0)) < tol_e
+        assert np.max(np.abs(g - g_ref)) < tol_g
+    plan.set_blocks(0)
+    assert plan.blocks() == min(want, 2 * sms)
+    plan.close()

@@ -137,8 +137,12 @@ def test_plan_autotune_keeps_parity(api, dtype):
     n = circ.n
     plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
     rep = plan.autotune(circ.theta, reps=2)
-    assert {(w, ln) for w, ln, _ in rep["tried"]} == {(0, 1), (3, 1), (4, 1), (5, 1), (3, 4), (4, 4), (5, 4)}
+    assert {(w, ln) for w, ln, _, _ in rep["tried"]} == {(0, 1), (3, 1), (4, 1), (5, 1), (3, 4), (4, 4), (5, 4)}
+    assert all(b == 0 for w, _, b, _ in rep["tried"] if w > 0)
+    assert all(b > 0 for w, _, b, _ in rep["tried"] if w == 0)
     assert plan.sweep()[:2] == (rep["best_window"], rep["best_lanes"])
+    if rep["best_window"] == 0:
+        assert plan.blocks() == rep["best_blocks"] > 0
     e, g = plan.run(circ.theta)
     psi0 = synth.basis_state(n, 0)
     tol_e, tol_g = _tols(dtype, circ, obs)
