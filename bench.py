@@ -658,7 +658,7 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
         out[f"adjoint_graph_{name}"] = {"grads_per_s": 1.0 / el, "ms_per_gradient": el * 1e3,
                                         "max_abs_grad_diff_vs_launch_path": float(np.max(np.abs(g - grads[name])))}
         # window-fused sweeps: blocks of <= w qubits, one launch per block, with
-        # 1 or 4 threads per group, and the per-gate sweep at 2, 4 and 8
+        # 1 or 4 threads per group, and the per-gate sweep at 1, 2 and 4
         # blocks per SM; the autotuner keeps the fastest
         tune = plan.autotune(circ.theta, reps=5)
         for _ in range(2):
@@ -1254,6 +1254,7 @@ def main():
     ap.add_argument("--adjoint-lanes", type=int, default=1)
     ap.add_argument("--adjoint-reps", type=int, default=3)
     ap.add_argument("--adjoint-blocks", type=int, default=0, help="per-gate sweep blocks (0: two per SM)")
+    ap.add_argument("--adjoint-qubits", type=int, default=20)
     ap.add_argument("--batch-cluster", type=int, default=8)
     ap.add_argument("--batch-threads", type=int, default=256)
     ap.add_argument("--batch-dtype", default="c64", choices=["c64", "c128"])
@@ -1298,10 +1299,11 @@ def main():
         from paper_2405_01250_gb300 import build as B
         B.build()
         from paper_2405_01250_gb300 import api
-        circ = synth.ansatz(n=20, layers=8, seed=0)
-        obs = synth.ansatz_observable(20)
+        nq = args.adjoint_qubits
+        circ = synth.ansatz(n=nq, layers=8, seed=0)
+        obs = synth.ansatz_observable(nq)
         dt = torch.complex128 if args.adjoint_dtype == "c128" else torch.complex64
-        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), 20, dtype=dt)
+        plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), nq, dtype=dt)
         plan.set_sweep(args.adjoint_window, args.adjoint_lanes)
         plan.set_blocks(args.adjoint_blocks)
         for _ in range(2):
@@ -1311,7 +1313,7 @@ def main():
         for _ in range(args.adjoint_reps):
             e, _ = plan.run(circ.theta)
         el = (time.perf_counter() - t0) / max(1, args.adjoint_reps)
-        print(json.dumps({"workload": "ansatz-20 adjoint plan", "dtype": args.adjoint_dtype, "sweep": plan.sweep(),
+        print(json.dumps({"workload": f"ansatz-{nq} adjoint plan", "dtype": args.adjoint_dtype, "sweep": plan.sweep(),
                           "runs": plan.runs(), "scaled": plan.scaled(), "pairs": plan.pairs(),
                           "blocks": plan.blocks(), "ms_per_gradient": el * 1e3, "energy": e}), flush=True)
         plan.close()

@@ -557,10 +557,10 @@ diaq_status diaq_adjoint_plan_get_runs(diaq_adjoint_plan_t p, int32_t* on, int32
  * `blocks` blocks of 256 threads over the state, grid-stride, and every
  * gradient term is summed over that many partial columns. 0 restores the
  * default, two per SM (one resident wave at the rotation kernels' register
- * counts), at most one group per thread. A state that stays in L2 between
- * launches (a complex64 sweep at 20 qubits) can gain from more blocks in
- * flight. Values above 64 per SM, or above one group of 2 amplitudes per
- * thread, are clamped. Re-records the graph. get_blocks: the blocks in use. */
+ * counts), at most one group per thread. More blocks cost more per launch
+ * (each block stages its phase tables and writes its partials). Values above
+ * 64 per SM, or above one group of 2 amplitudes per thread, are clamped.
+ * Re-records the graph. get_blocks: the blocks in use. */
 diaq_status diaq_adjoint_plan_set_blocks(diaq_adjoint_plan_t p, int32_t blocks);
 diaq_status diaq_adjoint_plan_get_blocks(diaq_adjoint_plan_t p, int32_t* blocks);
 
@@ -580,8 +580,8 @@ typedef struct {
 
 /* Time the sweep per gate and window-fused with windows 3, 4 and 5 at 1 and
  * 4 lanes (`reps` graph replays each, with theta, host array of n_params)
- * and keep the fastest; when the per-gate sweep wins, also time it at 4
- * and 8 blocks per SM (diaq_adjoint_plan_set_blocks) and keep the fastest
+ * and keep the fastest; when the per-gate sweep wins, also time it at 1
+ * and 4 blocks per SM (diaq_adjoint_plan_set_blocks) and keep the fastest
  * of those. report may be NULL. Synchronises. */
 diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* theta, int32_t reps,
                                        diaq_plan_tuning* report);

@@ -3467,7 +3467,7 @@ diaq_status diaq_adjoint_plan_autotune(diaq_adjoint_plan_t p, const double* thet
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
         if ((st = diaq_adjoint_plan_set_sweep(p, 0, 1)) == DIAQ_OK) {
             int last = p->P_gate;
-            for (int m : {4, 8}) {
+            for (int m : {1, 4}) {
                 if ((st = diaq_adjoint_plan_set_blocks(p, sms * m)) != DIAQ_OK) break;
                 if (p->P_gate == last) continue;  // clamped to the blocks already timed
                 last = p->P_gate;
