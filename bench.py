@@ -597,9 +597,12 @@ def fp64_per_amp(gates, obs, runs, chunks_run=None, scaled=False, product_layer_
             if c == 0:  # weight form
                 fwd += 4
                 rev += 11
-            else:  # r_rot: rotations whose gradient term takes a signed addition per amplitude
-                fwd += 4 * (c - 1) + 4
-                rev += 4 * (c - 1) + 2 + 1 + r_rot + 8
+            else:  # amplitudes by blocks of 256: the higher chunks' product once per block and lane
+                ph = (4 if c > 1 else 0) + 4 * max(0, c - 2) / 8
+                fwd += ph + 4
+                # the term, its per-j and block sums, D^dag on psi and lambda; r_rot rotations on
+                # bits fixed within a block but not for the thread take one signed addition per block
+                rev += ph + 2 + 1 + 1 + 8 + r_rot / 8
     # lambda = H psi: per group of equal X masks the weight comes from a
     # table (no FP64 work when the coefficients are equal, else one complex
     # addition per further chunk of 8 terms), then 2 (real weight) or 4
@@ -704,12 +707,12 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
     # FP64 floor of a complex128 gradient (FP64-bound: the 16 MiB states stay in L2)
     N = 1 << n
     chunks = (n + 7) // 8
-    # the reverse chunk-form kernel takes a per-amplitude term only for
-    # rotations on bits at or above the trailing zeros of its thread count
+    # the reverse chunk-form kernel takes a per-block term only for rotations
+    # on bits at or above 11 + the trailing zeros of its block count
     # (blocks = min(N / 512, 2 SMs), 256 threads each)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    nth = min(N // 512, 2 * sms) * 256
-    fixed_bits = (nth & -nth).bit_length() - 1
+    blocks = min(N // 512, 2 * sms)
+    fixed_bits = 11 + (blocks & -blocks).bit_length() - 1
     varying = max(0, n - fixed_bits)
     best = out["adjoint_autotuned_c128"]["ms_per_gradient"]
     scaled_best = out["adjoint_autotuned_c128"]["window"] == 0
@@ -731,9 +734,10 @@ def bench_adjoint(api, n=20, layers=8, reps=3, refs=None):
         "frac_of_gate_by_gate_floor": (f0 + r0 + l0) * N / FP64_INSTR_PER_S * 1e3 / best,
         "bytes_per_gradient": N * 16 * (2 * steps + 4 * steps + 2),
         "note": "per amplitude: rotation 2 forward / 6 reverse scaled (4 / 10 unscaled); chunk-form diagonal run "
-                "(RZ layer + CZ ladder) 4 (c - 1) + 4 forward, 4 (c - 1) + 11 + v reverse (v rotations on bits above the "
-                "thread count's trailing zeros); lambda 2 per real term "
-                "group (weights from tables) + 2 for the energy"}
+                "(RZ layer + CZ ladder) p + 4 forward, p + 12 + v / 8 reverse, p = 4 + 4 (c - 2) / 8 for the phase "
+                "(amplitudes by blocks of 256, the higher chunks once per block; v rotations on bits at or above 11 + "
+                "the block count's trailing zeros); lambda 2 per real term group (weights from tables) + 2 for the "
+                "energy"}
     for name in ("c128", "c64"):
         # what the graph plan and the window-fused sweep add over the
         # one-launch-per-gate adjoint sweep (the same algorithm)

@@ -1226,6 +1226,7 @@ static void plan_phase_runs(const BGate* gates, int n_gates, int gate_base, bool
                 const int lo = __builtin_ctzll(r.cz[k]), hi = 63 - __builtin_clzll(r.cz[k]);
                 if (lo / PR_CHUNK_BITS == hi / PR_CHUNK_BITS) ++r.n_cz_in;
             }
+            if (weight) phase_run_classes(&r);
             exec->push_back(-1 - int32_t(runs->size()));
             runs->push_back(r);
         } else {
@@ -2325,24 +2326,30 @@ __global__ void __launch_bounds__(256) k_plan_phase(amp_t<R>* psi, amp_t<R>* lam
 
 // Reverse step of a chunk-form run (an ansatz layer's RZs and CZ ladder)
 // with cheaper gradient terms. The term of a rotation on qubit q is
-// sum_i (-1)^(bit q of i) t_i, t_i = Im(conj(lambda_i) psi_i). In the
-// grid-stride loop i = tid + k nth, and nth = blocks x 256 is a multiple of
-// 2^f (f = trailing zero bits of nth), so bits 0 .. f-1 of i are those of
-// tid: fixed for the thread. The thread therefore sums t_i once (T) and
-// keeps a signed sum per amplitude only for rotations on bits >= f. At the
-// end, the fixed-bit terms come out of T: a Walsh-Hadamard butterfly over
-// the lanes gives sum (-1)^(lane bit q) T for q < 5, the warps' totals
-// signed by their warp bit give q = 5..7, and the block's total signed by
-// its block-index bit gives q = 8 .. f-1. Requires 256 threads per block.
+// sum_i (-1)^(bit q of i) t_i, t_i = Im(conj(lambda_i) psi_i). The loop
+// order is phase_run_sweep's chunk form: warp v of the grid (W = 8 P warps)
+// takes the aligned blocks of 256 amplitudes v, v + W, ..., its lane l the
+// amplitudes 32 j + l of each. So bits 0..4 of i are the lane's, bits 5..7
+// are j, and, W being a multiple of 2^(3 + z) (z = trailing zero bits of P),
+// bits 8..10 are those of the warp within its block and bits 11..10+z those
+// of the block index: all fixed for the thread or known per j. The thread
+// therefore sums t_i per j (T_j), and for rotations on bits >= f = 11 + z
+// (bits of base, fixed within a block of 256) adds its block share, signed
+// by that bit, once per block. At the end, a Walsh-Hadamard
+// butterfly over the lanes of T = sum_j T_j gives the terms for q < 5,
+// signed sums of the T_j those for q = 5..7, the warps' totals signed by
+// their warp bit those for q = 8..10, and the block's total signed by its
+// block-index bit those for q = 11..f-1. Requires 256 threads per block.
 template <typename R>
-__global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, amp_t<R>* lam,
+__global__ void __launch_bounds__(256, 2) k_plan_phase_rev_chunks(amp_t<R>* __restrict__ psi,
+                                                               amp_t<R>* __restrict__ lam,
                                                                const PhaseRun* __restrict__ run,
                                                                const double2* __restrict__ table, int n, double* part,
                                                                int P) {
     using A = amp_t<R>;
     __shared__ PhaseTables<PR_TAB_ALL, R> tb;
     __shared__ PhaseRun rs;
-    __shared__ double wt[8][6];               // per warp: sum T, then the lane-bit sums S_0 .. S_4
+    __shared__ double wt[8][9];               // per warp: sum T, lane-bit sums S_0 .. S_4, j-bit sums J_5 .. J_7
     __shared__ double wv[8][PR_MAX_CROT];     // per warp: the varying-bit sums
     __shared__ int vq[PR_MAX_CROT];           // varying-bit rotations: their qubit
     __shared__ int vg[PR_MAX_CROT];           // ... and their index in the run
@@ -2353,9 +2360,8 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
         for (int i = threadIdx.x; i < int(sizeof(PhaseRun) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
     }
     const int64_t N = int64_t(1) << n;
-    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int64_t nth = int64_t(gridDim.x) * blockDim.x;
-    const int f = __ffsll((long long)nth) - 1;  // bits 0 .. f-1 of i are those of tid
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int f = 11 + __ffs(int(gridDim.x)) - 1;  // bits 0 .. f-1 of i are fixed or known per j
     __syncthreads();
     if (threadIdx.x == 0) {
         int c = 0;
@@ -2372,38 +2378,64 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
     phase_tables_load<PR_TAB_ALL>(table, phase_entries(rs, n), &tb);  // synchronises
     const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
     const int n_var = nv;
-    Acc<R> tot;
+    const int64_t nblk = (N + 255) >> 8;
+    const int64_t W = int64_t(gridDim.x) * 8;
+    Acc<R> tj[8];
     Acc<R> av[PR_MAX_CROT];
-    for (int64_t i = tid; i < N; i += nth) {
-        R pr = tb.re[i & 255], pi = tb.im[i & 255];
+    for (int64_t blk = int64_t(blockIdx.x) * 8 + warp; blk < nblk; blk += W) {
+        const int64_t base = blk << 8;
+        R hr = R(1), hi = R(0);  // the higher chunks' product
         for (int c = 1; c < chunks; ++c) {
-            const int e = (c << 8) | int((i >> (8 * c)) & 255);
+            const int e = (c << 8) | int((base >> (8 * c)) & 255);
             const R qr = tb.re[e], qi = tb.im[e];
-            const R tr = fma(pr, qr, -pi * qi);
-            pi = fma(pr, qi, pi * qr);
-            pr = tr;
+            if (c == 1) {
+                hr = qr;
+                hi = qi;
+            } else {
+                const R tr = fma(hr, qr, -hi * qi);
+                hi = fma(hr, qi, hi * qr);
+                hr = tr;
+            }
         }
-        int neg = 0;  // CZs across chunks (the others are in the tables)
-        for (int k = rs.n_cz_in; k < rs.n_cz; ++k) neg ^= __popcll(uint64_t(i) & rs.cz[k]) == 2;
-        const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
-        A ph;
-        ph.x = flip_sign(pr, m);
-        ph.y = flip_sign(pi, m);
-        const A p = psi[i];
-        const A l = lam[i];
-        const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
-        tot.add(t);
+        int bneg;
+        unsigned lmask;
+        phase_cz_block(rs, uint64_t(base), &bneg, &lmask);
+        R sb = R(0);  // this lane's share of the block: bits >= 8 of i are those of base
 #pragma unroll
-        for (int j = 0; j < PR_MAX_CROT; ++j) {
-            if (j >= n_var) break;
-            av[j].add(flip_sign(t, ((uint64_t(i) >> vq[j]) & 1) ? 0x80000000u : 0u));
+        for (int j = 0; j < 8; ++j) {
+            const int lo = lane + 32 * j;
+            const int64_t i = base + lo;
+            if (i >= N) break;  // n < 8 only
+            R pr = tb.re[lo], pi = tb.im[lo];
+            if (chunks > 1) {
+                const R tr = fma(pr, hr, -pi * hi);
+                pi = fma(pr, hi, pi * hr);
+                pr = tr;
+            }
+            const int neg = bneg ^ (__popc(unsigned(lo) & lmask) & 1);
+            const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
+            A ph;
+            ph.x = flip_sign(pr, m);
+            ph.y = flip_sign(pi, m);
+            const A p = psi[i];
+            const A l = lam[i];
+            const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
+            tj[j].add(t);
+            sb += t;
+            lam[i] = cmul<R>(ph, l);
+            psi[i] = cmul<R>(ph, p);
         }
-        lam[i] = cmul<R>(ph, l);
-        psi[i] = cmul<R>(ph, p);
+#pragma unroll
+        for (int u = 0; u < PR_MAX_CROT; ++u) {
+            if (u >= n_var) break;
+            av[u].add(flip_sign(sb, ((uint64_t(base) >> vq[u]) & 1) ? 0x80000000u : 0u));
+        }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double tv[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tv[j] = tj[j].value();
     // lane butterfly: lane m ends with sum_l (-1)^popc(l & m) T_l
-    double w = tot.value();
+    double w = ((tv[0] + tv[1]) + (tv[2] + tv[3])) + ((tv[4] + tv[5]) + (tv[6] + tv[7]));
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const double v = __shfl_xor_sync(0xffffffffu, w, o);
@@ -2413,11 +2445,20 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
 #pragma unroll
     for (int q = 0; q < 5; ++q)
         if (lane == (1 << q)) wt[warp][1 + q] = w;
-    for (int j = 0; j < n_var; ++j) {
-        double v = av[j].value();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {  // q = 5 + b: sum_j (-1)^(bit b of j) T_j over the warp
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v += ((j >> b) & 1) ? -tv[j] : tv[j];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) wv[warp][j] = v;
+        if (lane == 0) wt[warp][6 + b] = v;
+    }
+    for (int u = 0; u < n_var; ++u) {
+        double v = av[u].value();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) wv[warp][u] = v;
     }
     __syncthreads();
     if (threadIdx.x < rs.n_rot && threadIdx.x < PR_MAX_CROT) {
@@ -2425,16 +2466,18 @@ __global__ void __launch_bounds__(256) k_plan_phase_rev_chunks(amp_t<R>* psi, am
         const int q = __ffsll((long long)rs.rot_z[g]) - 1;
         double v = 0.0;
         if (q >= f) {
-            int j = 0;
-            while (vg[j] != g) ++j;
-            for (int x = 0; x < 8; ++x) v += wv[x][j];
+            int u = 0;
+            while (vg[u] != g) ++u;
+            for (int x = 0; x < 8; ++x) v += wv[x][u];
         } else if (q < 5) {
             for (int x = 0; x < 8; ++x) v += wt[x][1 + q];
         } else if (q < 8) {
-            for (int x = 0; x < 8; ++x) v += ((x >> (q - 5)) & 1) ? -wt[x][0] : wt[x][0];
+            for (int x = 0; x < 8; ++x) v += wt[x][6 + q - 5];
+        } else if (q < 11) {
+            for (int x = 0; x < 8; ++x) v += ((x >> (q - 8)) & 1) ? -wt[x][0] : wt[x][0];
         } else {
             for (int x = 0; x < 8; ++x) v += wt[x][0];
-            if ((blockIdx.x >> (q - 8)) & 1) v = -v;
+            if ((blockIdx.x >> (q - 11)) & 1) v = -v;
         }
         part[int64_t(rs.rot_slot[g]) * P + blockIdx.x] = v;
     }

@@ -52,7 +52,22 @@ struct PhaseRun {
     int32_t n_fix1;
     int32_t fix1_q[PR_MAX_FIX1];    // qubit of a fixed single-qubit diagonal gate
     double fix1_re[2 * PR_MAX_FIX1], fix1_im[2 * PR_MAX_FIX1];  // its entries for bit 0 and bit 1
+    // weight form: the Z masks with bits 5..7 cleared, grouped by those three
+    // bits (class k = bits 5..7 of the mask): class k at wz[wcls[k] .. wcls[k + 1])
+    uint64_t wz[PR_MAX_ROT];
+    int32_t wcls[9];
 };
+
+// Weight-form class table of a run (host): rot_z grouped by bits 5..7.
+inline void phase_run_classes(PhaseRun* r) {
+    int at = 0;
+    for (int k = 0; k < 8; ++k) {
+        r->wcls[k] = at;
+        for (int g = 0; g < r->n_rot && g < PR_MAX_ROT; ++g)
+            if (int((r->rot_z[g] >> 5) & 7) == k) r->wz[at++] = r->rot_z[g] & ~uint64_t(0xE0);
+    }
+    r->wcls[8] = at;
+}
 
 // Shared-memory tables of one run and direction: weight form entry W + T;
 // chunk form entry c * 256 + v. E entries: PR_TAB_WEIGHT holds the weight
@@ -124,6 +139,25 @@ __device__ __forceinline__ void phase_tables_load(const double2* __restrict__ sr
     __syncthreads();
 }
 
+// The sign of the CZs across chunks (those inside one chunk are in its
+// table) for the aligned block of 256 amplitudes at base: a CZ on two bits
+// at or above bit 8 gives the same sign to the whole block (*bneg); one with
+// its low bit a below 8 flips the sign of the amplitudes with bit a set when
+// its high bit is set in base, so the sign of amplitude base + lo is
+// *bneg ^ parity(lo & *lmask).
+__device__ __forceinline__ void phase_cz_block(const PhaseRun& r, uint64_t base, int* bneg, unsigned* lmask) {
+    int b = 0;
+    unsigned m = 0;
+    for (int k = r.n_cz_in; k < r.n_cz; ++k) {
+        const uint64_t cz = r.cz[k];
+        const unsigned low = unsigned(cz & 255u);
+        if (low == 0) b ^= __popcll(base & cz) == 2;
+        else if (base & cz) m ^= low;
+    }
+    *bneg = b;
+    *lmask = m;
+}
+
 template <typename R>
 __device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
     amp_t<R> o;
@@ -132,13 +166,19 @@ __device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
     return o;
 }
 
-// One run over a grid-stride share [tid, N) of the state. Forward
+// One run over a grid-stride share of the state. Forward
 // (lam == nullptr): psi <- D psi. Reverse: the gradient terms first, then
 // psi <- D^dag psi, lam <- D^dag lam (tables built for the direction).
 // FORM (PR_WEIGHT or PR_CHUNKS) is the run's form, fixed at compile time so
 // that no FP64 work of the other form is issued predicated off. Gradient
 // terms go to acc[]: weight form acc[0] (the run's sum sum_i W(i) t_i);
 // chunk form one per rotation.
+// Both forms take aligned blocks of 256 amplitudes: warp w of the grid
+// (nth / 32 warps; nth must be a multiple of 32) takes blocks w,
+// w + nth / 32, ..., its lane l the amplitudes l + 32 j (j = 0..7) of each.
+// The chunk form then forms the product of the higher chunks' table entries
+// (shared by the block) once per block and lane instead of once per
+// amplitude; the weight form its eight weights W as below.
 template <typename R, int FORM, int E>
 __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
                                              const PhaseRun& r, const PhaseTables<E, R>& tb, int64_t tid, int64_t nth,
@@ -146,31 +186,10 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
     using A = amp_t<R>;
     constexpr bool CH = FORM == PR_CHUNKS;
     const int64_t N = int64_t(1) << n;
-    const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
     Acc<R> a_w;
     Acc<R> a_c[CH ? PR_MAX_CROT : 1];
-    for (int64_t i = tid; i < N; i += nth) {
-        A ph;
-        int w = 0;
-        if (!CH) {
-            for (int g = 0; g < r.n_rot; ++g) w += (__popcll(uint64_t(i) & r.rot_z[g]) & 1) ? -1 : 1;
-            ph.x = tb.re[w + r.n_rot];
-            ph.y = tb.im[w + r.n_rot];
-        } else {
-            R pr = tb.re[i & 255], pi = tb.im[i & 255];
-            for (int c = 1; c < chunks; ++c) {
-                const int e = (c << 8) | int((i >> (8 * c)) & 255);
-                const R qr = tb.re[e], qi = tb.im[e];
-                const R tr = fma(pr, qr, -pi * qi);
-                pi = fma(pr, qi, pi * qr);
-                pr = tr;
-            }
-            int neg = 0;  // CZs across chunks (the others are in the tables)
-            for (int k = r.n_cz_in; k < r.n_cz; ++k) neg ^= __popcll(uint64_t(i) & r.cz[k]) == 2;
-            const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
-            ph.x = flip_sign(pr, m);
-            ph.y = flip_sign(pi, m);
-        }
+    // amplitude i with its phase ph (w: the weight-form W(i))
+    auto step = [&](int64_t i, A ph, int w) {
         const A p = psi[i];
         if (lam) {
             const A l = lam[i];
@@ -191,11 +210,87 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
             lam[i] = cmul<R>(ph, l);
         }
         psi[i] = cmul<R>(ph, p);
-    }
-    if (!CH) {
+    };
+    const int lane = int(tid & 31);
+    const int64_t nblk = (N + 255) >> 8;
+    if constexpr (!CH) {
+        // W(i) = sum_g (-1)^popc(i & z_g). With i = x + 32 j (x = base | lane,
+        // bits 5..7 clear) the sign of rotation g is (-1)^popc(x & z'_g) times
+        // (-1)^popc(j & k_g), k_g = bits 5..7 of z_g, z'_g = z_g without them.
+        // So the eight W of a block and lane are the Walsh-Hadamard transform
+        // over j of C_k = sum over class k of (-1)^popc(x & z'_g): one pass
+        // over the rotations per 8 amplitudes instead of one per amplitude.
+        for (int64_t blk = tid >> 5; blk < nblk; blk += nth >> 5) {
+            const int64_t base = blk << 8;
+            const uint64_t x = uint64_t(base) | uint64_t(lane);
+            int C[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int odd = 0;
+                const int g0 = r.wcls[k], g1 = r.wcls[k + 1];
+                for (int g = g0; g < g1; ++g) odd += __popcll(x & r.wz[g]) & 1;
+                C[k] = (g1 - g0) - 2 * odd;
+            }
+#pragma unroll
+            for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (!(k & h)) {
+                        const int a = C[k], b = C[k + h];
+                        C[k] = a + b;
+                        C[k + h] = a - b;
+                    }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int64_t i = base + lane + 32 * j;
+                if (i >= N) break;  // n < 8 only
+                A ph;
+                ph.x = tb.re[C[j] + r.n_rot];
+                ph.y = tb.im[C[j] + r.n_rot];
+                step(i, ph, C[j]);
+            }
+        }
         acc[0] = a_w.value();
     } else {
-        for (int g = 0; g < r.n_rot && g < (CH ? PR_MAX_CROT : 1); ++g) acc[g] = a_c[g].value();
+        const int chunks = (n + PR_CHUNK_BITS - 1) / PR_CHUNK_BITS;
+        for (int64_t blk = tid >> 5; blk < nblk; blk += nth >> 5) {
+            const int64_t base = blk << 8;
+            R hr = R(1), hi = R(0);  // the higher chunks' product
+            for (int c = 1; c < chunks; ++c) {
+                const int e = (c << 8) | int((base >> (8 * c)) & 255);
+                const R qr = tb.re[e], qi = tb.im[e];
+                if (c == 1) {
+                    hr = qr;
+                    hi = qi;
+                } else {
+                    const R tr = fma(hr, qr, -hi * qi);
+                    hi = fma(hr, qi, hi * qr);
+                    hr = tr;
+                }
+            }
+            int bneg;
+            unsigned lmask;
+            phase_cz_block(r, uint64_t(base), &bneg, &lmask);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int lo = lane + 32 * j;
+                const int64_t i = base + lo;
+                if (i >= N) break;  // n < 8 only
+                R pr = tb.re[lo], pi = tb.im[lo];
+                if (chunks > 1) {
+                    const R tr = fma(pr, hr, -pi * hi);
+                    pi = fma(pr, hi, pi * hr);
+                    pr = tr;
+                }
+                const int neg = bneg ^ (__popc(unsigned(lo) & lmask) & 1);
+                const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
+                A ph;
+                ph.x = flip_sign(pr, m);
+                ph.y = flip_sign(pi, m);
+                step(i, ph, 0);
+            }
+        }
+        for (int g = 0; g < r.n_rot && g < PR_MAX_CROT; ++g) acc[g] = a_c[g].value();
     }
 }
 

@@ -261,13 +261,22 @@ def test_complex64_batch_rotation_tiles_match_complex128_and_oracle(api, launch)
 
 
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
-def test_plan_blocks_keep_parity(api, dtype):
+@pytest.mark.parametrize("kind", ["xy", "ansatz"])
+def test_plan_blocks_keep_parity(api, dtype, kind):
     """The per-gate sweep at other block counts (more partial columns per
     gradient term, fewer groups per thread, clamped at one group per thread)
-    gives the same energy and gradient; 0 restores two blocks per SM."""
+    gives the same energy and gradient; 0 restores two blocks per SM. The
+    ansatz's RZ layers run as chunk-form diagonal runs, whose reverse step
+    takes the terms of rotations on low bits from per-thread totals: with 1,
+    3, 2, 8 and 16 blocks the split between those bits and the per-amplitude
+    ones moves (it depends on the trailing zero bits of the block count)."""
     rng = np.random.default_rng(7)
-    n = 11
-    circ = _xy_circuit(n, rng, 3)
+    if kind == "xy":
+        n = 11
+        circ = _xy_circuit(n, rng, 3)
+    else:
+        n = 13
+        circ = synth.ansatz(n=n, layers=3, seed=4)
     obs = synth.ansatz_observable(n)
     plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
@@ -279,7 +288,7 @@ def test_plan_blocks_keep_parity(api, dtype):
     assert abs(e0 - oracle.energy(circ, obs, psi0)) < tol_e
     g_ref = oracle.param_shift_grad(circ, obs, psi0)
     assert np.max(np.abs(g0 - g_ref)) < tol_g
-    for b in (1, 3, 1000000):
+    for b in (1, 3, 2, 8, 16, 1000000):
         plan.set_blocks(b)
         assert plan.blocks() == max(1, min(b, want, 64 * sms))
         e, g = plan.run(circ.theta)
