@@ -179,7 +179,9 @@ __device__ __forceinline__ amp_t<R> cmul(amp_t<R> a, amp_t<R> b) {
 // The chunk form then forms the product of the higher chunks' table entries
 // (shared by the block) once per block and lane instead of once per
 // amplitude; the weight form its eight weights W as below.
-template <typename R, int FORM, int E>
+// V: amplitudes whose loads are in flight together (fewer where the caller
+// has fewer registers to spare).
+template <typename R, int FORM, int E, int V = (sizeof(R) == 4 ? 8 : 4)>
 __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam, int n,
                                              const PhaseRun& r, const PhaseTables<E, R>& tb, int64_t tid, int64_t nth,
                                              double* acc) {
@@ -188,11 +190,9 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
     const int64_t N = int64_t(1) << n;
     Acc<R> a_w;
     Acc<R> a_c[CH ? PR_MAX_CROT : 1];
-    // amplitude i with its phase ph (w: the weight-form W(i))
-    auto step = [&](int64_t i, A ph, int w) {
-        const A p = psi[i];
+    // amplitude i (values p, l) with its phase ph (w: the weight-form W(i))
+    auto finish = [&](int64_t i, A ph, int w, const A& p, const A& l) {
         if (lam) {
-            const A l = lam[i];
             const R t = fma(l.x, p.y, -l.y * p.x);  // Im(conj(l) p)
             if (!CH) {
                 if constexpr (sizeof(R) == 8) {
@@ -211,7 +211,42 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
         }
         psi[i] = cmul<R>(ph, p);
     };
+    // the eight amplitudes l + 32 j of a block; phase(j, &ph, &w) gives each
+    // one's phase. In a whole block (n >= 8) the loads of V amplitudes are
+    // issued before any of them is used, so their latencies overlap.
     const int lane = int(tid & 31);
+    auto block8 = [&](int64_t base, auto&& phase) {
+        if (base + 256 <= N) {
+#pragma unroll
+            for (int j0 = 0; j0 < 8; j0 += V) {
+                A p[V], l[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int64_t i = base + lane + 32 * (j0 + v);
+                    p[v] = psi[i];
+                    if (lam) l[v] = lam[i];
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    A ph;
+                    int w;
+                    phase(j0 + v, &ph, &w);
+                    finish(base + lane + 32 * (j0 + v), ph, w, p[v], l[v]);
+                }
+            }
+        } else {
+            for (int j = 0; j < 8; ++j) {
+                const int64_t i = base + lane + 32 * j;
+                if (i >= N) break;  // n < 8 only
+                A ph;
+                int w;
+                phase(j, &ph, &w);
+                A l = {};
+                if (lam) l = lam[i];
+                finish(i, ph, w, psi[i], l);
+            }
+        }
+    };
     const int64_t nblk = (N + 255) >> 8;
     if constexpr (!CH) {
         // W(i) = sum_g (-1)^popc(i & z_g). With i = x + 32 j (x = base | lane,
@@ -240,15 +275,11 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
                         C[k] = a + b;
                         C[k + h] = a - b;
                     }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int64_t i = base + lane + 32 * j;
-                if (i >= N) break;  // n < 8 only
-                A ph;
-                ph.x = tb.re[C[j] + r.n_rot];
-                ph.y = tb.im[C[j] + r.n_rot];
-                step(i, ph, C[j]);
-            }
+            block8(base, [&](int j, A* ph, int* w) {
+                *w = C[j];
+                ph->x = tb.re[C[j] + r.n_rot];
+                ph->y = tb.im[C[j] + r.n_rot];
+            });
         }
         acc[0] = a_w.value();
     } else {
@@ -271,11 +302,8 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
             int bneg;
             unsigned lmask;
             phase_cz_block(r, uint64_t(base), &bneg, &lmask);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            block8(base, [&](int j, A* ph, int* w) {
                 const int lo = lane + 32 * j;
-                const int64_t i = base + lo;
-                if (i >= N) break;  // n < 8 only
                 R pr = tb.re[lo], pi = tb.im[lo];
                 if (chunks > 1) {
                     const R tr = fma(pr, hr, -pi * hi);
@@ -284,11 +312,10 @@ __device__ __noinline__ void phase_run_sweep(amp_t<R>* __restrict__ psi, amp_t<R
                 }
                 const int neg = bneg ^ (__popc(unsigned(lo) & lmask) & 1);
                 const unsigned m = neg ? 0x80000000u : 0u;  // the sign by an integer flip
-                A ph;
-                ph.x = flip_sign(pr, m);
-                ph.y = flip_sign(pi, m);
-                step(i, ph, 0);
-            }
+                ph->x = flip_sign(pr, m);
+                ph->y = flip_sign(pi, m);
+                *w = 0;
+            });
         }
         for (int g = 0; g < r.n_rot && g < PR_MAX_CROT; ++g) acc[g] = a_c[g].value();
     }
