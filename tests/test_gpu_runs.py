@@ -91,6 +91,27 @@ def test_plan_runs_match_gate_by_gate_and_oracle(api, dtype, which):
         assert abs(e_on - e_ref) < 2e-5 and np.max(np.abs(g_on - g_ref)) < 5e-5
 
 
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("which", ["ansatz-5", "ansatz-7", "qaoa-6"])
+def test_plan_runs_on_states_below_one_block(api, dtype, which):
+    """States of fewer than 256 amplitudes: the run kernels' blocks of 256
+    are partial (lanes and rows past the state's end take no part)."""
+    rng = np.random.default_rng(11)
+    if which.startswith("ansatz"):
+        n = int(which.split("-")[1])
+        circ = synth.ansatz(n=n, layers=2, seed=3)
+        obs = synth.ansatz_observable(n)
+    else:
+        n = 6
+        circ, obs = synth.qaoa_instance(n, rng, p=2)
+    e_on, g_on, info = _plan_grad(api, circ, obs, n, dtype, True)
+    assert info[0] and info[1] >= 1
+    psi0 = synth.basis_state(n, 0)
+    tol_e, tol_g = (1e-11, 1e-10) if dtype == torch.complex128 else (2e-5, 5e-5)
+    assert abs(e_on - oracle.energy(circ, obs, psi0)) < tol_e
+    assert np.max(np.abs(g_on - oracle.param_shift_grad(circ, obs, psi0))) < tol_g
+
+
 def test_plan_runs_beyond_form_limits_fall_back(api):
     """A run of 60 one-parameter ZZ rotations (over the weight form's 48) and
     a run of 28 single-qubit rotations (over the chunk form's 24) are applied
