@@ -161,3 +161,36 @@ def test_precision_fields_helpers():
     e = bench.state_errors(b, a)
     assert e["fidelity_vs_oracle"] == pytest.approx(oracle.fidelity(a, b), rel=1e-14)
     assert e["max_abs_err_vs_oracle"] == oracle.max_abs_err(a, b)
+
+
+def test_fp64_floor_model_counts():
+    """The FP64-instruction model behind the adjoint and batch floors, on a
+    hand-countable circuit: a fixed gate before the first rotation counts
+    forward only; rotations take 2 forward / 6 reverse scaled (4 / 10
+    unscaled); a fixed gate after it 4 / 8; chunk-form runs (blocks of 256,
+    the higher chunks' product once per block) p + 4 forward and p + 12 + v/8
+    reverse with p = 4 + 4 (c - 2) / 8; weight-form runs 4 / 11; lambda 2
+    per real group with equal weights, 2 more per further chunk of 8 terms
+    when they differ, plus 2 for the energy."""
+    import numpy as np
+    import synth
+    g = [synth.Gate((0,), synth.H),                                   # before the first rotation
+         synth.Gate((1,), None, param=0, gen="X"),
+         synth.Gate((0, 1), synth.CZ),                                # a sign gate: no FP64 work
+         synth.Gate((1,), synth.random_gate(1, np.random.default_rng(0), "dense")),
+         synth.Gate((0, 1), None, param=1, gen="ZZ")]                 # a Z-type rotation
+    obs = synth.Observable(np.array([0, 0, 1], dtype=np.uint64), np.array([3, 1, 0], dtype=np.uint64),
+                           np.array([1.0, 1.0, 0.5]))
+    # lambda: group x=0 (two terms, equal) 2, group x=1 (one term) 2, energy 2
+    assert bench.fp64_per_amp(g, obs, runs=False) == (4 + 4 + 4 + 4, 10 + 8 + 10, 6)
+    assert bench.fp64_per_amp(g, obs, runs=False, scaled=True) == (4 + 2 + 4 + 2, 6 + 8 + 6, 6)
+    # with runs the Z-type rotation and the sign gate move into the runs given
+    f, r, lam = bench.fp64_per_amp(g, obs, runs=True, chunks_run=[(0, 0)], scaled=True)
+    assert (f, r, lam) == (4 + 2 + 4 + 4, 6 + 8 + 11, 6)
+    f, r, _ = bench.fp64_per_amp(g, obs, runs=True, chunks_run=[(8, 3)], scaled=True)
+    p = 4 + 4 * 1 / 8
+    assert (f, r) == (4 + 2 + 4 + p + 4, 6 + 8 + p + 12 + 8 / 8)
+    # unequal weights in one group of 9 terms: two chunks of 8
+    obs9 = synth.Observable(np.zeros(9, dtype=np.uint64), np.arange(1, 10, dtype=np.uint64),
+                            np.linspace(0.1, 0.9, 9))
+    assert bench.fp64_per_amp(g, obs9, runs=False)[2] == 2 + 2 + 2
