@@ -95,7 +95,13 @@ struct BTerm {
     // 1: per chunk of 8 terms by their parity bits, chunk values summed),
     // its first table entry, and whether every weight is real
     int32_t gn, gmode, gtab, greal;
+    // count-form groups of at least kLamClassMin terms: the terms sorted by
+    // their Z mask's bits 5..7 (class k), gk[k] of class k, and gcls = 1
+    int32_t gcls;
+    int16_t gk[8];
 };
+
+constexpr int kLamClassMin = 4;
 
 struct BatchArgs {
     const BInst* inst;
@@ -375,19 +381,121 @@ __device__ __forceinline__ amp_t<R> pauli_lambda_elem(const amp_t<R>* psi, const
     return o;
 }
 
-// lam = H psi over a grid-stride share, returning this thread's share of
-// Re <psi|lam>; fl (LAM_*) selects the instantiation outside the loop.
+// lam = H psi, returning this thread's share of Re <psi|lam>; FL (LAM_*)
+// selects the instantiation outside the loop. Amplitudes by aligned blocks
+// of 256 as in the diagonal runs: warp w of the grid (nth / 32 warps; nth a
+// multiple of 32) takes blocks w, w + nth / 32, ..., its lane l the
+// amplitudes l + 32 j (j = 0..7). A count-form group of at least
+// kLamClassMin terms then counts its odd parities for all eight at once:
+// with y = (base | l) ^ x, the parity of term u at amplitude j is
+// a_u ^ parity(s & k_u) (a_u = parity(y & z_u) outside bits 5..7, k_u = bits
+// 5..7 of z_u, s = j ^ bits 5..7 of x), so with D_k = n_k - 2 sum_{u in k} a_u
+// the count is sum_u a_u + (sum_k D_k - WHT(D)[s]) / 2: one pass over the
+// group's terms per 8 amplitudes. Other groups take one pass per amplitude.
 template <typename R, int FL>
-__device__ __noinline__ double lambda_share(const amp_t<R>* psi, amp_t<R>* lam, const BTerm* terms,
-                                            const amp_t<R>* tab, int t0, int t1, int64_t N, int64_t tid,
-                                            int64_t nth) {
+__device__ __noinline__ double lambda_share(const amp_t<R>* __restrict__ psi, amp_t<R>* __restrict__ lam,
+                                            const BTerm* terms, const amp_t<R>* tab, int t0, int t1, int64_t N,
+                                            int64_t tid, int64_t nth) {
     using A = amp_t<R>;
     Acc<R> e;
-    for (int64_t i = tid; i < N; i += nth) {
-        const A o = pauli_lambda_elem<R, FL>(psi, terms, tab, t0, t1, i);
-        lam[i] = o;
-        const A pi = psi[i];
-        e.add_dot(pi.x, o.x, pi.y, o.y);
+    const int lane = int(tid & 31);
+    const int64_t nblk = (N + 255) >> 8;
+    for (int64_t blk = tid >> 5; blk < nblk; blk += nth >> 5) {
+        const int64_t base = blk << 8;
+        R lr[8], li[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            lr[j] = R(0);
+            li[j] = R(0);
+        }
+        for (int t = t0; t < t1;) {
+            const BTerm& h = terms[t];
+            const int gn = h.gn;
+            const bool real = (FL & LAM_REAL) || h.greal;
+            int m8[8];
+            if (((FL & LAM_COUNT) || h.gmode == 0) && h.gcls) {
+                const uint64_t ym = ((uint64_t(base) | uint64_t(lane)) ^ h.x) & ~uint64_t(0xE0);
+                int D[8];
+                int odd_tot = 0;
+                int u = t;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    int odd = 0;
+                    const int end = u + h.gk[k];
+                    for (; u < end; ++u) odd += __popcll(ym & terms[u].z) & 1;
+                    D[k] = h.gk[k] - 2 * odd;
+                    odd_tot += odd;
+                }
+                const int dtot = gn - 2 * odd_tot;
+#pragma unroll
+                for (int hh = 1; hh < 8; hh <<= 1)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        if (!(k & hh)) {
+                            const int a = D[k], b = D[k + hh];
+                            D[k] = a + b;
+                            D[k + hh] = a - b;
+                        }
+                const int xj = int((h.x >> 5) & 7);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m8[j] = odd_tot + ((dtot - D[j ^ xj]) >> 1);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int64_t i = base + lane + 32 * j;
+                if (i >= N) break;  // n < 8 only
+                const uint64_t jx = uint64_t(i) ^ h.x;
+                R wr, wi;
+                if (((FL & LAM_COUNT) || h.gmode == 0) && h.gcls) {
+                    const A w = tab[h.gtab + m8[j]];
+                    wr = w.x;
+                    wi = w.y;
+                } else if ((FL & LAM_COUNT) || h.gmode == 0) {
+                    int m = 0;
+                    for (int v = t; v < t + gn; ++v) m += __popcll(jx & terms[v].z) & 1;
+                    const A w = tab[h.gtab + m];
+                    wr = w.x;
+                    wi = w.y;
+                } else {
+                    wr = R(0);
+                    wi = R(0);
+                    for (int c = 0; 8 * c < gn; ++c) {
+                        int bits = 0;
+                        const int v1 = min(t + 8 * c + 8, t + gn);
+                        for (int v = t + 8 * c; v < v1; ++v)
+                            bits |= (__popcll(jx & terms[v].z) & 1) << (v - t - 8 * c);
+                        const A w = tab[h.gtab + 256 * c + bits];
+                        if (c == 0) {
+                            wr = w.x;
+                            wi = w.y;
+                        } else {
+                            wr += w.x;
+                            wi += w.y;
+                        }
+                    }
+                }
+                const A pj = psi[jx];
+                if (real) {
+                    lr[j] = fma(wr, pj.x, lr[j]);
+                    li[j] = fma(wr, pj.y, li[j]);
+                } else {
+                    lr[j] = fma(wr, pj.x, fma(-wi, pj.y, lr[j]));
+                    li[j] = fma(wr, pj.y, fma(wi, pj.x, li[j]));
+                }
+            }
+            t += gn;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int64_t i = base + lane + 32 * j;
+            if (i >= N) break;
+            A o;
+            o.x = lr[j];
+            o.y = li[j];
+            lam[i] = o;
+            const A pi = psi[i];
+            e.add_dot(pi.x, o.x, pi.y, o.y);
+        }
     }
     return e.value();
 }
@@ -1412,10 +1520,19 @@ static int lambda_tables(std::vector<BTerm>& terms, int t0, int t1, std::vector<
             equal &= terms[size_t(v)].kr == terms[size_t(t)].kr && terms[size_t(v)].ki == terms[size_t(t)].ki;
             real &= terms[size_t(v)].ki == 0.0;
         }
+        int16_t gk[8] = {};
+        const bool cls = equal && gn >= kLamClassMin;
+        if (cls) {  // count form: the order within the group is free, so group the terms by class
+            std::stable_sort(terms.begin() + t, terms.begin() + u,
+                             [](const BTerm& a, const BTerm& b) { return ((a.z >> 5) & 7) < ((b.z >> 5) & 7); });
+            for (int v = t; v < u; ++v) ++gk[(terms[size_t(v)].z >> 5) & 7];
+        }
         BTerm& h = terms[size_t(t)];
         h.gn = gn;
         h.gtab = int32_t(tab->size());
         h.greal = real ? 1 : 0;
+        h.gcls = cls ? 1 : 0;
+        for (int k = 0; k < 8; ++k) h.gk[k] = gk[k];
         if (!real) fl &= ~LAM_REAL;
         if (!equal) fl &= ~LAM_COUNT;
         if (equal) {  // W = (gn - 2 m) kappa, m terms of odd parity

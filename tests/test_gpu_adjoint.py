@@ -150,3 +150,40 @@ def test_autograd_with_plan(api):
     E.backward()
     g_ps = oracle.param_shift_grad(circ, obs, synth.basis_state(n, 0))
     assert np.max(np.abs(theta.grad.numpy() - g_ps)) <= 1e-10
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_plan_and_batch_lambda_groups_sharing_an_x_mask(api, dtype):
+    """lambda = H psi for an observable whose term groups share X masks with
+    bits among 5..7 and many equal-weight terms (counted for eight amplitudes
+    at once), beside a group of unequal weights, single terms and Y letters;
+    the plan and the batch against the oracle."""
+    rng = np.random.default_rng(21)
+    n = 10
+    circ = synth.ansatz(n=n, layers=2, seed=6)
+    xs, zs, cs = [], [], []
+    for x in (0, (1 << 6) | (1 << 2), (1 << 7) | (1 << 5) | 1):
+        for _ in range(7):  # equal weights: the count form
+            xs.append(x)
+            zs.append(int(rng.integers(0, 1 << n)))
+            cs.append(0.3)
+    for _ in range(5):  # one X mask, unequal weights
+        xs.append(1 << 9)
+        zs.append(int(rng.integers(0, 1 << n)))
+        cs.append(float(rng.uniform(-1, 1)))
+    xs.append(1 << 3)
+    zs.append(1 << 3)  # a Y letter
+    cs.append(0.7)
+    obs = synth.Observable(np.array(xs, dtype=np.uint64), np.array(zs, dtype=np.uint64), np.array(cs))
+    psi0 = synth.basis_state(n, 0)
+    e_ref = oracle.energy(circ, obs, psi0)
+    g_ref = oracle.param_shift_grad(circ, obs, psi0)
+    tol_e, tol_g = (1e-11, 1e-10) if dtype == torch.complex128 else (2e-5, 5e-5)
+    plan = api.AdjointPlan(circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff), n, dtype=dtype)
+    e, g = plan.run(circ.theta)
+    plan.close()
+    assert abs(e - e_ref) < tol_e and np.max(np.abs(g - g_ref)) < tol_g
+    b = api.Batch([(n, circ.gates, circ.n_params, (obs.xmask, obs.zmask, obs.coeff))], dtype=dtype)
+    E, G = b.run(circ.theta)
+    b.close()
+    assert abs(E[0] - e_ref) < tol_e and np.max(np.abs(G[0] - g_ref)) < tol_g
